@@ -1,0 +1,222 @@
+/*
+ * tnc.h -- C ABI of libtnc: exact model counting by tensor-network contraction
+ * on one GB300 GPU (sm_103a).
+ *
+ * Method: Kourtis, Chamon, Mucciolo, Ruckenstein, "Fast counting with tensor
+ * networks".  A #CSP formula becomes a network with one COPY tensor per
+ * variable (Eq. var) and one clause tensor per clause (Eq. or, Eq. 1in3, ...),
+ * every occurrence of a variable in a clause being one bond of dimension 2
+ * (Sec. 2.1).  Its full contraction (Eq. z at beta -> infinity) is the number
+ * of satisfying assignments.  The contraction is a sequence of pairwise steps,
+ * each merging two tensors over all the bonds they share (edge contraction of
+ * Sec. 2.2), along an order from the paper's graph heuristics (tensor-greedy,
+ * tensor-METIS-style recursive bisection, tensor-GN; Sec. 3.1.1).
+ *
+ * Exactness: counts exceed 2^64, so every tensor entry is kept as residues
+ * modulo R primes below 2^31 and the final count is rebuilt as a big integer
+ * by the Chinese remainder theorem (Garner's mixed radix).  The paper counts
+ * in floating point and notes its rounding errors from about 100 vertices
+ * (Sec. 3.2); this library is exact whenever the count is below the product
+ * of the primes, and flags results for which it cannot certify that.
+ *
+ * Conventions for every entry point:
+ *   - return 0 (TNC_OK) on success, a negative TNC_ERR_* code otherwise;
+ *     tnc_last_error() then describes the failure (thread-local string);
+ *   - no C++ exception crosses this boundary;
+ *   - pointers documented "host" must be host memory, "device" device memory
+ *     of the current CUDA device; sizes are in bytes unless stated;
+ *   - objects returned through `T** out` are owned by the library and freed
+ *     with the matching tnc_free_* call; all caller buffers stay owned by the
+ *     caller and are not retained after the call returns (except where a
+ *     batch documents otherwise);
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it.
+ */
+#ifndef TNC_H
+#define TNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define TNC_OK 0
+#define TNC_ERR_INVALID (-1)   /* malformed argument or formula */
+#define TNC_ERR_TOO_LARGE (-2) /* rank cap or memory bound exceeded (found at plan time) */
+#define TNC_ERR_CUDA (-3)      /* a CUDA call failed; see tnc_last_error() */
+#define TNC_ERR_BUFFER (-4)    /* caller buffer too small; needed size reported */
+#define TNC_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define TNC_ERR_NOMEM (-6)     /* host allocation failed */
+
+/* ---- clause kinds (clause tensor definitions, Sec. 2.1 and Sec. 3.2) ----- */
+#define TNC_1IN3 0  /* 1 iff exactly one index is 1 (Eq. 1in3; any arity)       */
+#define TNC_OR 1    /* 0 iff all indices are 0 (Eq. or)                          */
+#define TNC_NAND 2  /* 0 iff all indices are 1 (independent-set edge)           */
+#define TNC_TABLE 3 /* explicit 2^arity non-negative weights, index bit j =
+                       value of the clause's j-th variable                       */
+
+/* ---- planners (Sec. 3.1.1) ----------------------------------------------- */
+#define TNC_PLAN_GREEDY 0   /* tensor-greedy: smallest result rank first          */
+#define TNC_PLAN_BISECT 1   /* tensor-METIS reading: recursive min-cut bisection,
+                               best of `tries` per split                          */
+#define TNC_PLAN_GN 2       /* tensor-GN: Girvan-Newman community dendrogram      */
+#define TNC_PLAN_EXPLICIT 3 /* caller-given pairwise order                        */
+#define TNC_PLAN_BEST 4     /* run GREEDY, BISECT and GN; keep the cheapest       */
+
+/* ---- arithmetic paths ---------------------------------------------------- */
+#define TNC_PATH_INT64 0 /* CUDA cores: u32 residues, 64-bit multiply-accumulate */
+
+/* ---- result flags -------------------------------------------------------- */
+#define TNC_MAYBE_WRAPPED 1u /* the certified bound on the count is not below the
+                                product of the primes: the CRT value may be the
+                                count reduced modulo that product               */
+
+typedef struct tnc_network_s tnc_network_t;
+typedef struct tnc_plan_s tnc_plan_t;
+typedef struct tnc_batch_s tnc_batch_t;
+
+/* A formula.  All arrays are host memory owned by the caller and copied in.
+ *   var_of   : concatenation of each clause's variable list (sum of arity);
+ *              variables within one clause must be distinct;
+ *   kind     : one TNC_* clause kind per clause;
+ *   table    : for TABLE clauses only, 2^arity weights each, concatenated in
+ *              clause order (may be NULL when no clause is TABLE);
+ *   open_vars: variables whose COPY tensor keeps one extra, uncontracted bond;
+ *              the result is then a tensor of 2^n_open counts, entry index bit
+ *              i = value of open_vars[i] (the open network of the worked
+ *              example, Sec. 2.1).  n_open <= 20. */
+typedef struct {
+  int32_t n_vars;
+  int32_t n_cons;
+  const int32_t* arity;
+  const int32_t* var_of;
+  const uint8_t* kind;
+  const uint32_t* table;
+  int32_t n_open;
+  const int32_t* open_vars;
+} tnc_formula;
+
+typedef struct {
+  int32_t heuristic;     /* TNC_PLAN_*                                              */
+  int32_t rank_cap;      /* refuse plans whose largest tensor has a higher rank
+                            (<= 0: default 32)                                      */
+  int32_t tries;         /* bisections per split, best kept (<= 0: 2, Sec. 3.1.1)   */
+  uint64_t seed;         /* seed of the randomised planners                         */
+  const int32_t* order;  /* EXPLICIT: n_order pairs (a, b) of live tensor ids; ids:
+                            clause c -> c, variable v -> n_cons + v, result of the
+                            i-th pair -> n_cons + n_vars + i.  Tensors left over
+                            are finished by tensor-greedy.                          */
+  int32_t n_order;
+} tnc_plan_opts;
+
+/* Exact cost of a plan, predicted before any tensor is touched (the "lazy"
+ * evaluation of Sec. 4).  MACs count one multiply-accumulate per residue-free
+ * scalar: sum over steps of 2^(a+b-k) for ranks a, b sharing k bonds. */
+typedef struct {
+  int32_t max_rank;       /* largest tensor rank along the plan                   */
+  int32_t n_steps;        /* pairwise contractions                                */
+  int32_t n_leaves;       /* tensors of the network                               */
+  int32_t depth;          /* longest root-to-leaf path of the contraction tree    */
+  double total_macs;      /* sum of 2^(a+b-k)                                     */
+  double total_entries;   /* sum of 2^a + 2^b + 2^(a+b-2k): entries moved          */
+  double log2_bound;      /* log2 of the certified upper bound on every count      */
+} tnc_plan_stats;
+
+typedef struct {
+  int32_t path;          /* TNC_PATH_*                                           */
+  int32_t n_residues;    /* R, 1..16                                             */
+  const uint32_t* primes;/* host, R distinct primes in (2^30, 2^31); NULL = the R
+                            largest primes below 2^31                            */
+} tnc_contract_opts;
+
+/* One formula's result.  Caller-allocated host buffers.
+ *   residues : [n_out][R]   count mod primes[r];
+ *   limbs    : [n_out][cap_limbs] little-endian u32 limbs of the CRT value;
+ *   n_out    : out, 2^n_open;
+ *   n_limbs  : out, limbs needed per entry (if > cap_limbs: TNC_ERR_BUFFER and
+ *              nothing written to limbs);
+ *   flags    : out, TNC_MAYBE_WRAPPED or 0. */
+typedef struct {
+  uint32_t* residues;
+  uint32_t* limbs;
+  int32_t cap_out;
+  int32_t cap_limbs;
+  int32_t n_out;
+  int32_t n_limbs;
+  uint32_t flags;
+} tnc_count;
+
+/* ---- library ------------------------------------------------------------- */
+const char* tnc_version(void);
+/* Last error message of the calling thread ("" if none). */
+const char* tnc_last_error(void);
+/* The n largest primes below 2^31, descending (deterministic Miller-Rabin). */
+int tnc_default_primes(int32_t n, uint32_t* out /* host, n */);
+
+/* ---- network (Sec. 2.1): formula -> COPY + clause tensors, bonds --------- */
+int tnc_build_network(const tnc_formula* f, tnc_network_t** out);
+/* Counts of the network: tensors, bonds (incl. open), connected components. */
+int tnc_network_info(const tnc_network_t* net, int32_t* n_tensors, int32_t* n_bonds,
+                     int32_t* n_components);
+void tnc_free_network(tnc_network_t* net);
+
+/* ---- planning (Sec. 2.2, Sec. 3.1.1, Sec. 4) ----------------------------- */
+/* Builds the contraction tree and lowers it (layouts, arena offsets).
+ * stats may be NULL.  TNC_ERR_TOO_LARGE if max_rank > rank_cap. */
+int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** out,
+             tnc_plan_stats* stats);
+/* Plans n networks in parallel on the host cores (OpenMP).  out[i] and, if
+ * stats is not NULL, stats[i] receive formula i's plan.  All or nothing: on
+ * any failure every out[i] is NULL and the first failing formula is named in
+ * tnc_last_error(). */
+int tnc_plan_many(const tnc_network_t* const* nets, int32_t n, const tnc_plan_opts* opts,
+                  tnc_plan_t** out, tnc_plan_stats* stats);
+/* Contraction tree as pairs: for step i, the tensor ids it merges (ids as in
+ * tnc_plan_opts.order).  left/right: host arrays of n_steps entries. */
+int tnc_plan_steps(const tnc_plan_t* plan, int32_t* left, int32_t* right, int32_t cap);
+void tnc_free_plan(tnc_plan_t* plan);
+
+/* ---- single formula (Sec. 2.1 contraction; one launch per step) --------- */
+/* Device workspace needed by tnc_contract for R residues. */
+size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues);
+/* Contracts the plan on the GPU and returns the count(s) in `out` (host).
+ * dev_ws: device buffer of at least tnc_workspace_bytes(plan, R) bytes, 256-byte
+ * aligned, owned by the caller, free for the library's use during the call.
+ * Synchronises `cuda_stream` before returning. */
+int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws,
+                 size_t ws_bytes, void* cuda_stream, tnc_count* out);
+
+/* ---- batches: many formulas in one persistent launch -------------------- */
+/* Packs the plans (host work only).  The plans must outlive the batch. */
+int tnc_batch_create(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                     tnc_batch_t** out);
+size_t tnc_batch_workspace_bytes(const tnc_batch_t* b);
+/* Sizes of a batch: bytes uploaded by tnc_batch_upload (h2d), bytes read back
+ * by tnc_batch_download (d2h), result entries, device kernels per launch.
+ * Any pointer may be NULL. */
+int tnc_batch_info(const tnc_batch_t* b, size_t* h2d_bytes, size_t* d2h_bytes, uint64_t* n_entries,
+                   int32_t* kernels_per_launch);
+/* Host -> device copy of the packed descriptors into dev_ws (async on stream). */
+int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, void* cuda_stream);
+/* Device-only work: all contractions + CRT of the batch, results left in dev_ws.
+ * Requires a prior tnc_batch_upload to the same dev_ws.  The launch sequence is
+ * captured once into a CUDA graph per (dev_ws, stream) and replayed. */
+int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream);
+/* Device -> host copy of the results; synchronises the stream.  outs: n counts. */
+int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs);
+/* Status word of the last launch (0, or TNC_ERR_TIMEOUT if a bounded device
+ * wait gave up); synchronises the stream. */
+int tnc_batch_status(tnc_batch_t* b, const void* dev_ws, void* cuda_stream);
+void tnc_free_batch(tnc_batch_t* b);
+
+/* Upload + launch + download in one call. */
+int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                       void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* outs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNC_H */

@@ -1,0 +1,622 @@
+// C ABI, device half: single-formula contraction (one launch per step) and the
+// persistent, graph-captured batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tnc_internal.h"
+
+using namespace tnc;
+using tnc_dev::BatchArgs;
+using tnc_dev::CrtConsts;
+using tnc_dev::FormDesc;
+using tnc_dev::ModGroup;
+using tnc_dev::RootMap;
+
+namespace {
+
+#define CUDA_TRY(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return set_error(TNC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  return n;
+}
+
+uint32_t powmod(uint64_t a, uint64_t e, uint32_t p) {
+  uint64_t r = 1;
+  a %= p;
+  while (e) {
+    if (e & 1) r = r * a % p;
+    a = a * a % p;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+// Residues are processed in groups of 4, 2 or 1 primes (one pass each).
+struct Groups {
+  std::vector<int> rg, col;
+};
+
+Groups split_groups(int R) {
+  Groups g;
+  int c = 0;
+  for (int s : {4, 2, 1})
+    while (R - c >= s) {
+      g.rg.push_back(s);
+      g.col.push_back(c);
+      c += s;
+    }
+  return g;
+}
+
+struct Arith {
+  int R = 0;
+  std::vector<uint32_t> primes;
+  CrtConsts crt{};
+  double log2_prod = 0;
+  Groups groups;
+  ModGroup group(int gi) const {
+    ModGroup m{};
+    for (int r = 0; r < 4; r++) {
+      uint32_t p = r < groups.rg[gi] ? primes[groups.col[gi] + r] : primes[groups.col[gi]];
+      m.p[r] = p;
+      m.mu[r] = ~0ull / p;
+    }
+    return m;
+  }
+};
+
+int make_arith(const tnc_contract_opts* o, Arith& a) {
+  if (!o) return set_error(TNC_ERR_INVALID, "contract opts NULL");
+  if (o->path != TNC_PATH_INT64) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
+  if (o->n_residues < 1 || o->n_residues > 16) return set_error(TNC_ERR_INVALID, "n_residues must be in [1, 16]");
+  a.R = o->n_residues;
+  if (o->primes) {
+    a.primes.assign(o->primes, o->primes + a.R);
+    for (int i = 0; i < a.R; i++) {
+      uint32_t p = a.primes[i];
+      if (p <= (1u << 30) || p >= (1u << 31) || !is_prime_u32(p))
+        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^30, 2^31)");
+      for (int j = 0; j < i; j++)
+        if (a.primes[j] == p) return set_error(TNC_ERR_INVALID, "primes must be distinct");
+    }
+  } else {
+    a.primes = largest_primes_below_2_31(a.R);
+  }
+  a.crt = CrtConsts{};
+  a.crt.R = a.R;
+  a.log2_prod = 0;
+  for (int i = 0; i < a.R; i++) {
+    const uint32_t p = a.primes[i];
+    a.crt.p[i] = p;
+    a.crt.mu[i] = ~0ull / p;
+    uint64_t prod = 1;
+    for (int j = 0; j < i; j++) prod = prod * (a.primes[j] % p) % p;
+    a.crt.inv[i] = i == 0 ? 1u : powmod(prod, p - 2, p);
+    a.log2_prod += std::log2((double)p);
+  }
+  a.crt.n_limbs = (31 * a.R + 31) / 32;
+  a.groups = split_groups(a.R);
+  return TNC_OK;
+}
+
+uint32_t result_flags(const tnc_plan_t* p, const Arith& a) {
+  return p->net.log2_bound >= a.log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u;
+}
+
+template <typename F>
+int dispatch_rg(int rg, F&& f) {
+  switch (rg) {
+    case 4: return f(std::integral_constant<int, 4>());
+    case 2: return f(std::integral_constant<int, 2>());
+    default: return f(std::integral_constant<int, 1>());
+  }
+}
+
+// ---------------------------------------------------------------- single formula
+
+struct SeqLayout {
+  size_t off_leaves, off_tables, off_steps, off_results, off_limbs, off_arena, total;
+  uint64_t n_out;
+};
+
+using tnc_dev::GridStep;
+
+// Launch shape of a grid-wide step: S = threads * blocks = 2^s <= 2^c.
+void grid_shape(int c, int* threads, int* blocks, int* s) {
+  const int t = c >= 8 ? 8 : c;
+  const int b = c >= 8 ? std::min(c - 8, 10) : 0;
+  *threads = 1 << t;
+  *blocks = 1 << b;
+  *s = t + b;
+}
+
+GridStep make_grid_step(const StepDesc& d) {
+  GridStep g;
+  std::memset(&g, 0, sizeof(g));
+  g.d = d;
+  int op[64] = {0}, dst[64] = {0};
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++)
+      for (int q = 0; q < d.map.runs.ra[i].len; q++) {
+        op[d.map.runs.ra[i].src + q] = 0;
+        dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
+      }
+    for (int i = 0; i < d.nrb; i++)
+      for (int q = 0; q < d.map.runs.rb[i].len; q++) {
+        op[d.map.runs.rb[i].src + q] = 1;
+        dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
+      }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      op[j] = d.map.bit[j] >> 7;
+      dst[j] = d.map.bit[j] & 63;
+    }
+  }
+  for (int j = 0; j < d.c; j++) {
+    g.wA[j] = op[j] == 0 ? 1ull << dst[j] : 0ull;
+    g.wB[j] = op[j] == 1 ? 1ull << dst[j] : 0ull;
+  }
+  int threads, blocks, sh;
+  grid_shape(d.c, &threads, &blocks, &sh);
+  g.s = (uint32_t)sh;
+  for (int t = sh; t < d.c; t++) {
+    uint64_t sa = 0, sb = 0;
+    for (int j = sh; j < t; j++) {
+      sa += g.wA[j];
+      sb += g.wB[j];
+    }
+    g.dA[t] = g.wA[t] - sa;
+    g.dB[t] = g.wB[t] - sb;
+  }
+  return g;
+}
+
+SeqLayout seq_layout(const tnc_plan_t* p, int R) {
+  SeqLayout s{};
+  const int rg_max = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+  s.n_out = 1ull << p->net.open_vars.size();
+  size_t o = 0;
+  s.off_leaves = o;
+  o = align_up(o + p->low.leaves.size() * sizeof(LeafDesc));
+  s.off_tables = o;
+  o = align_up(o + p->low.leaf_tables.size() * sizeof(uint32_t));
+  s.off_steps = o;
+  o = align_up(o + p->low.seq_steps.size() * sizeof(GridStep));
+  s.off_results = o;
+  o = align_up(o + s.n_out * R * sizeof(uint32_t));
+  s.off_limbs = o;
+  o = align_up(o + s.n_out * ((31 * R + 31) / 32) * sizeof(uint32_t));
+  s.off_arena = o;
+  o = align_up(o + p->low.seq_arena_entries * rg_max * sizeof(uint32_t));
+  s.total = o;
+  return s;
+}
+
+int fill_count(tnc_count* out, uint64_t n_out, const Arith& a, const uint32_t* res, const uint32_t* limbs,
+               uint32_t flags) {
+  out->n_out = (int32_t)n_out;
+  out->n_limbs = a.crt.n_limbs;
+  out->flags = flags;
+  if (out->cap_out < (int32_t)n_out) return set_error(TNC_ERR_BUFFER, "count buffer holds fewer entries than 2^n_open");
+  if (out->residues) std::memcpy(out->residues, res, n_out * a.R * sizeof(uint32_t));
+  if (out->limbs) {
+    if (out->cap_limbs < a.crt.n_limbs) return set_error(TNC_ERR_BUFFER, "need " + std::to_string(a.crt.n_limbs) + " limbs");
+    for (uint64_t e = 0; e < n_out; e++) {
+      std::memset(out->limbs + e * out->cap_limbs, 0, out->cap_limbs * sizeof(uint32_t));
+      std::memcpy(out->limbs + e * out->cap_limbs, limbs + e * a.crt.n_limbs, a.crt.n_limbs * sizeof(uint32_t));
+    }
+  }
+  return TNC_OK;
+}
+
+}  // namespace
+
+extern "C" size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues) {
+  if (!plan || n_residues < 1 || n_residues > 16) return 0;
+  return seq_layout(plan, n_residues).total;
+}
+
+extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
+                            void* cuda_stream, tnc_count* out) {
+  clear_error();
+  if (!plan || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
+  Arith a;
+  int rc = make_arith(opts, a);
+  if (rc) return rc;
+  const SeqLayout L = seq_layout(plan, a.R);
+  const uint32_t flags = result_flags(plan, a);
+  if (plan->tree.nodes.empty()) {  // empty network: the empty product, 1
+    std::vector<uint32_t> res(a.R, 1u), limbs(a.crt.n_limbs, 0u);
+    limbs[0] = 1;
+    return fill_count(out, 1, a, res.data(), limbs.data(), 0);
+  }
+  if (!dev_ws || ws_bytes < L.total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_workspace_bytes");
+  if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* ws = (char*)dev_ws;
+  // leaves (offsets of the sequential schedule) and tables
+  std::vector<LeafDesc> leaves = plan->low.leaves;
+  for (size_t i = 0; i < leaves.size(); i++) leaves[i].off = plan->low.seq_leaf_off[i];
+  CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice, st));
+  if (!plan->low.leaf_tables.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, plan->low.leaf_tables.data(),
+                             plan->low.leaf_tables.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  std::vector<GridStep> gsteps;
+  gsteps.reserve(plan->low.seq_steps.size());
+  for (const StepDesc& d : plan->low.seq_steps) gsteps.push_back(make_grid_step(d));
+  if (!gsteps.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_steps, gsteps.data(), gsteps.size() * sizeof(GridStep), cudaMemcpyHostToDevice,
+                             st));
+  const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
+  uint32_t* arena = (uint32_t*)(ws + L.off_arena);
+  uint32_t* results = (uint32_t*)(ws + L.off_results);
+  RootMap rm{};
+  rm.n_open = (int)plan->net.open_vars.size();
+  for (int j = 0; j < rm.n_open; j++) rm.perm[j] = plan->low.root_perm[j];
+  const int sms = sm_count();
+  for (size_t gi = 0; gi < a.groups.rg.size(); gi++) {
+    const ModGroup mg = a.group((int)gi);
+    rc = dispatch_rg(a.groups.rg[gi], [&](auto rgc) -> int {
+      constexpr int RG = decltype(rgc)::value;
+      const int nl = (int)leaves.size();
+      tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
+          (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
+      for (size_t i = 0; i < gsteps.size(); i++) {
+        int threads, blocks, sh;
+        grid_shape(gsteps[i].d.c, &threads, &blocks, &sh);
+        tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
+      }
+      tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
+          arena, plan->low.seq_steps.empty() ? plan->low.seq_leaf_off[plan->tree.root] : plan->low.seq_root_off, rm,
+          results, a.R, a.groups.col[gi]);
+      CUDA_TRY(cudaGetLastError());
+      return TNC_OK;
+    });
+    if (rc) return rc;
+  }
+  uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
+  tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((L.n_out + 127) / 128, 1024), 128, 0, st>>>(results, L.n_out, a.crt,
+                                                                                                  limbs);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<uint32_t> h_res(L.n_out * a.R), h_limbs(L.n_out * a.crt.n_limbs);
+  CUDA_TRY(cudaMemcpyAsync(h_res.data(), results, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return fill_count(out, L.n_out, a, h_res.data(), h_limbs.data(), flags);
+}
+
+// ======================================================================= batch
+
+struct tnc_batch_s {
+  std::vector<const tnc_plan_t*> plans;
+  Arith a;
+  // packed descriptors (host staging, same layout as the workspace prefix)
+  std::vector<char> staging;
+  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_lvl = 0, off_leaves = 0, off_tables = 0, off_perms = 0,
+         off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0, total = 0;
+  size_t desc_bytes = 0;  // bytes uploaded from staging (from off_forms)
+  uint32_t n_forms = 0;
+  uint64_t total_out = 0;
+  std::vector<uint64_t> res_off;  // per formula
+  uint64_t max_arena = 0;         // entries
+  int threads = 256;
+  std::vector<int> grid, smem_mode;
+  std::vector<size_t> smem_bytes;
+  uint64_t arena_stride = 0;
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  void* g_ws = nullptr;
+  cudaStream_t g_stream = nullptr;
+  ~tnc_batch_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+  }
+};
+
+namespace {
+
+constexpr size_t kSmemArenaMax = 100 * 1024;
+
+template <int RG>
+int occupancy(int threads, size_t smem, int* blocks) {
+  if (smem > 48 * 1024)
+    CUDA_TRY(cudaFuncSetAttribute(tnc_dev::batch_kernel<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tnc_dev::batch_kernel<RG>, threads, smem));
+  return TNC_OK;
+}
+
+int batch_pack(tnc_batch_t* b) {
+  const uint32_t n = b->n_forms;
+  std::vector<FormDesc> forms(n);
+  std::vector<StepDesc> steps;
+  std::vector<uint32_t> lvl;
+  std::vector<LeafDesc> leaves;
+  std::vector<uint32_t> tables;
+  std::vector<uint8_t> perms;
+  b->res_off.assign(n, 0);
+  uint64_t out = 0;
+  b->max_arena = 8;
+  for (uint32_t i = 0; i < n; i++) {
+    const tnc_plan_t* p = b->plans[i];
+    if (p->tree.nodes.empty()) return set_error(TNC_ERR_INVALID, "batch formula with an empty network");
+    if (p->cost.max_rank > 24 || !p->low.lvl_fits)
+      return set_error(TNC_ERR_TOO_LARGE, "batch formulas must have plan rank <= 24");
+    const Lowered& lw = p->low;
+    FormDesc& f = forms[i];
+    std::memset(&f, 0, sizeof(f));
+    f.step0 = (uint32_t)steps.size();
+    f.lvl0 = (uint32_t)lvl.size();
+    f.nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
+    f.leaf0 = (uint32_t)leaves.size();
+    f.nleaf = (uint32_t)lw.leaves.size();
+    f.res_off = (uint32_t)out;
+    f.n_open = (uint32_t)p->net.open_vars.size();
+    f.n_out = 1u << f.n_open;
+    f.perm_off = (uint32_t)perms.size();
+    f.root_off = lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off;
+    b->res_off[i] = out;
+    out += f.n_out;
+    steps.insert(steps.end(), lw.lvl_steps.begin(), lw.lvl_steps.end());
+    lvl.insert(lvl.end(), lw.lvl_start.begin(), lw.lvl_start.end());
+    if (lw.lvl_start.empty()) lvl.push_back(0);
+    const uint32_t toff = (uint32_t)tables.size();
+    for (size_t l = 0; l < lw.leaves.size(); l++) {
+      LeafDesc d = lw.leaves[l];
+      d.off = lw.lvl_leaf_off[l];
+      d.table_off += toff;
+      leaves.push_back(d);
+    }
+    tables.insert(tables.end(), lw.leaf_tables.begin(), lw.leaf_tables.end());
+    perms.insert(perms.end(), lw.root_perm.begin(), lw.root_perm.end());
+    b->max_arena = std::max<uint64_t>(b->max_arena, lw.lvl_arena_entries);
+  }
+  b->total_out = out;
+  // largest formulas first (longest-processing-time order)
+  std::vector<uint32_t> order(n);
+  for (uint32_t i = 0; i < n; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    return b->plans[x]->cost.macs + b->plans[x]->cost.entries > b->plans[y]->cost.macs + b->plans[y]->cost.entries;
+  });
+  // launch shapes per residue group
+  const int sms = sm_count();
+  b->grid.clear();
+  b->smem_mode.clear();
+  b->smem_bytes.clear();
+  b->arena_stride = (b->max_arena + 7) / 8 * 8;
+  int max_grid_global = 0;
+  for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
+    const int rg = b->a.groups.rg[gi];
+    const size_t bytes = b->max_arena * rg * sizeof(uint32_t);
+    const int smem = bytes <= kSmemArenaMax;
+    int occ = 0;
+    int rc = dispatch_rg(rg, [&](auto rgc) -> int {
+      return occupancy<decltype(rgc)::value>(b->threads, smem ? bytes : 0, &occ);
+    });
+    if (rc) return rc;
+    if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
+    int g = std::min<int>(sms * occ, (int)n);
+    b->grid.push_back(std::max(g, 1));
+    b->smem_mode.push_back(smem);
+    b->smem_bytes.push_back(smem ? bytes : 0);
+    if (!smem) max_grid_global = std::max(max_grid_global, g * rg);
+  }
+  // workspace layout
+  size_t o = 0;
+  b->off_queue = o;
+  o = align_up(o + 64 * sizeof(uint32_t));
+  b->off_forms = o;
+  o = align_up(o + forms.size() * sizeof(FormDesc));
+  b->off_steps = o;
+  o = align_up(o + steps.size() * sizeof(StepDesc));
+  b->off_lvl = o;
+  o = align_up(o + lvl.size() * sizeof(uint32_t));
+  b->off_leaves = o;
+  o = align_up(o + leaves.size() * sizeof(LeafDesc));
+  b->off_tables = o;
+  o = align_up(o + tables.size() * sizeof(uint32_t));
+  b->off_perms = o;
+  o = align_up(o + perms.size());
+  b->off_order = o;
+  o = align_up(o + order.size() * sizeof(uint32_t));
+  b->desc_bytes = o - b->off_forms;
+  b->off_results = o;
+  o = align_up(o + out * b->a.R * sizeof(uint32_t));
+  b->off_limbs = o;
+  o = align_up(o + out * b->a.crt.n_limbs * sizeof(uint32_t));
+  b->off_arena = o;
+  o = align_up(o + (size_t)max_grid_global * b->arena_stride * sizeof(uint32_t));
+  b->total = o;
+  b->staging.assign(b->desc_bytes, 0);
+  char* s = b->staging.data() - b->off_forms;
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(s + off, src, bytes);
+  };
+  put(b->off_forms, forms.data(), forms.size() * sizeof(FormDesc));
+  put(b->off_steps, steps.data(), steps.size() * sizeof(StepDesc));
+  put(b->off_lvl, lvl.data(), lvl.size() * sizeof(uint32_t));
+  put(b->off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc));
+  put(b->off_tables, tables.data(), tables.size() * sizeof(uint32_t));
+  put(b->off_perms, perms.data(), perms.size());
+  put(b->off_order, order.data(), order.size() * sizeof(uint32_t));
+  return TNC_OK;
+}
+
+int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
+  char* ws = (char*)dev_ws;
+  CUDA_TRY(cudaMemsetAsync(ws + b->off_queue, 0, 64 * sizeof(uint32_t), st));
+  for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
+    BatchArgs args{};
+    args.forms = (const FormDesc*)(ws + b->off_forms);
+    args.steps = (const StepDesc*)(ws + b->off_steps);
+    args.lvl_start = (const uint32_t*)(ws + b->off_lvl);
+    args.leaves = (const LeafDesc*)(ws + b->off_leaves);
+    args.tables = (const uint32_t*)(ws + b->off_tables);
+    args.perms = (const uint8_t*)(ws + b->off_perms);
+    args.order = (const uint32_t*)(ws + b->off_order);
+    args.n_forms = b->n_forms;
+    args.queue = (uint32_t*)(ws + b->off_queue) + gi;
+    args.results = (uint32_t*)(ws + b->off_results);
+    args.arena = (uint32_t*)(ws + b->off_arena);
+    args.arena_stride = b->arena_stride;
+    args.R = b->a.R;
+    args.col = b->a.groups.col[gi];
+    args.smem_arena = b->smem_mode[gi];
+    const ModGroup mg = b->a.group((int)gi);
+    const int grid = b->grid[gi];
+    const size_t smem = b->smem_bytes[gi];
+    int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
+      constexpr int RG = decltype(rgc)::value;
+      tnc_dev::batch_kernel<RG><<<grid, b->threads, smem, st>>>(args, mg);
+      CUDA_TRY(cudaGetLastError());
+      return TNC_OK;
+    });
+    if (rc) return rc;
+  }
+  tnc_dev::crt_kernel<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>((b->total_out + 127) / 128, 4096)), 128, 0,
+                        st>>>((const uint32_t*)(ws + b->off_results), b->total_out, b->a.crt,
+                              (uint32_t*)(ws + b->off_limbs));
+  CUDA_TRY(cudaGetLastError());
+  return TNC_OK;
+}
+
+}  // namespace
+
+extern "C" int tnc_batch_create(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                                tnc_batch_t** out) {
+  clear_error();
+  if (!plans || n <= 0 || !out) return set_error(TNC_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  try {
+    auto* b = new tnc_batch_t();
+    int rc = make_arith(opts, b->a);
+    if (!rc) {
+      for (int i = 0; i < n; i++) {
+        if (!plans[i]) rc = set_error(TNC_ERR_INVALID, "NULL plan in batch");
+        b->plans.push_back(plans[i]);
+      }
+    }
+    b->n_forms = (uint32_t)n;
+    if (!rc) rc = batch_pack(b);
+    if (rc) {
+      delete b;
+      return rc;
+    }
+    *out = b;
+    return TNC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_error(TNC_ERR_NOMEM, "out of host memory");
+  }
+}
+
+extern "C" size_t tnc_batch_workspace_bytes(const tnc_batch_t* b) { return b ? b->total : 0; }
+
+extern "C" int tnc_batch_info(const tnc_batch_t* b, size_t* h2d_bytes, size_t* d2h_bytes, uint64_t* n_entries,
+                              int32_t* kernels_per_launch) {
+  clear_error();
+  if (!b) return set_error(TNC_ERR_INVALID, "batch is NULL");
+  if (h2d_bytes) *h2d_bytes = b->desc_bytes;
+  if (d2h_bytes) *d2h_bytes = b->total_out * (size_t)(b->a.R + b->a.crt.n_limbs) * sizeof(uint32_t);
+  if (n_entries) *n_entries = b->total_out;
+  if (kernels_per_launch) *kernels_per_launch = (int32_t)b->a.groups.rg.size() + 1;
+  return TNC_OK;
+}
+
+extern "C" int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, void* cuda_stream) {
+  clear_error();
+  if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  if (ws_bytes < b->total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_batch_workspace_bytes");
+  if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
+  CUDA_TRY(cudaMemcpyAsync((char*)dev_ws + b->off_forms, b->staging.data(), b->desc_bytes, cudaMemcpyHostToDevice,
+                           (cudaStream_t)cuda_stream));
+  return TNC_OK;
+}
+
+extern "C" int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream) {
+  clear_error();
+  if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (st == nullptr) return batch_enqueue(b, dev_ws, st);  // legacy stream: cannot capture
+  if (b->gexec && (b->g_ws != dev_ws || b->g_stream != st)) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  if (!b->gexec) {
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_enqueue(b, dev_ws, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->gexec = nullptr;
+      return set_error(TNC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->g_ws = dev_ws;
+    b->g_stream = st;
+  }
+  CUDA_TRY(cudaGraphLaunch(b->gexec, st));
+  return TNC_OK;
+}
+
+extern "C" int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs) {
+  clear_error();
+  if (!b || !dev_ws || !outs) return set_error(TNC_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<uint32_t> res(b->total_out * b->a.R), limbs(b->total_out * b->a.crt.n_limbs);
+  CUDA_TRY(cudaMemcpyAsync(res.data(), (const char*)dev_ws + b->off_results, res.size() * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(limbs.data(), (const char*)dev_ws + b->off_limbs, limbs.size() * 4, cudaMemcpyDeviceToHost,
+                           st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (uint32_t i = 0; i < b->n_forms; i++) {
+    const tnc_plan_t* p = b->plans[i];
+    const uint64_t n_out = 1ull << p->net.open_vars.size();
+    int rc = fill_count(&outs[i], n_out, b->a, res.data() + b->res_off[i] * b->a.R,
+                        limbs.data() + b->res_off[i] * b->a.crt.n_limbs, result_flags(p, b->a));
+    if (rc) return rc;
+  }
+  return TNC_OK;
+}
+
+extern "C" int tnc_batch_status(tnc_batch_t* b, const void* dev_ws, void* cuda_stream) {
+  clear_error();
+  if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  return TNC_OK;
+}
+
+extern "C" void tnc_free_batch(tnc_batch_t* b) { delete b; }
+
+extern "C" int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts, void* dev_ws,
+                                  size_t ws_bytes, void* cuda_stream, tnc_count* outs) {
+  tnc_batch_t* b = nullptr;
+  int rc = tnc_batch_create(plans, n, opts, &b);
+  if (rc) return rc;
+  rc = tnc_batch_upload(b, dev_ws, ws_bytes, cuda_stream);
+  if (!rc) rc = batch_enqueue(b, dev_ws, (cudaStream_t)cuda_stream);
+  if (!rc) rc = tnc_batch_download(b, dev_ws, cuda_stream, outs);
+  tnc_free_batch(b);
+  return rc;
+}

@@ -1,0 +1,348 @@
+// Device code of libtnc: modular arithmetic, leaf tensors, the fused
+// permute-and-multiply step, the persistent batch kernel and the CRT.
+#pragma once
+
+#include <cstdint>
+
+#include "step_desc.h"
+
+namespace tnc_dev {
+
+// One residue group: RG <= 4 primes processed together; an entry of a tensor
+// holds RG u32 residues side by side (16 bytes for RG = 4).
+struct ModGroup {
+  uint32_t p[4];
+  uint64_t mu[4];  // floor(2^64 / p), Barrett constant
+};
+
+// x mod p for any 64-bit x (Barrett reduction with mu = floor(2^64/p):
+// the quotient estimate is at most one short, so one correction suffices;
+// a second one is kept as a margin).
+__device__ __forceinline__ uint32_t mod_reduce(uint64_t x, uint32_t p, uint64_t mu) {
+  const uint64_t q = __umul64hi(x, mu);
+  uint64_t r = x - q * (uint64_t)p;
+  if (r >= p) r -= p;
+  if (r >= p) r -= p;
+  return (uint32_t)r;
+}
+
+template <int RG>
+__device__ __forceinline__ void load_entry(const uint32_t* src, uint32_t (&v)[RG]) {
+  if constexpr (RG == 4) {
+    const uint4 t = *reinterpret_cast<const uint4*>(src);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (RG == 2) {
+    const uint2 t = *reinterpret_cast<const uint2*>(src);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    v[0] = *src;
+  }
+}
+
+template <int RG>
+__device__ __forceinline__ void store_entry(uint32_t* dst, const uint32_t (&v)[RG]) {
+  if constexpr (RG == 4) {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (RG == 2) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1]);
+  } else {
+    dst[0] = v[0];
+  }
+}
+
+// Operand addresses of output entry o (descriptor in global or shared memory).
+__device__ __forceinline__ void map_addr(const StepDesc& d, uint64_t o, uint64_t& ia, uint64_t& ib) {
+  ia = 0;
+  ib = 0;
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++) {
+      const TncRun r = d.map.runs.ra[i];
+      ia |= ((o >> r.src) & ((1ull << r.len) - 1ull)) << r.dst;
+    }
+    for (int i = 0; i < d.nrb; i++) {
+      const TncRun r = d.map.runs.rb[i];
+      ib |= ((o >> r.src) & ((1ull << r.len) - 1ull)) << r.dst;
+    }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      const uint32_t m = d.map.bit[j];
+      const uint64_t bit = ((o >> j) & 1ull) << (m & 63u);
+      if (m & 0x80u) ib |= bit;
+      else ia |= bit;
+    }
+  }
+}
+
+// Leaf tensor entry (Sec. 2.1, Sec. 3.2): COPY (Eq. var; rank 0 is the sum
+// over the variable's two values, 2), exactly-one (Eq. 1in3), OR (Eq. or),
+// NAND, or an explicit table already permuted to the leaf's layout.
+__device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uint32_t idx,
+                                               const uint32_t* tables, uint32_t toff, uint32_t p) {
+  const uint32_t all = (uint32_t)((1ull << rank) - 1ull);
+  switch (kind) {
+    case 0: return __popc(idx) == 1 ? 1u : 0u;
+    case 1: return idx != 0u ? 1u : 0u;
+    case 2: return idx != all ? 1u : 0u;
+    case 3: return tables[toff + idx] % p;
+    default: return rank == 0 ? 2u : ((idx == 0u || idx == all) ? 1u : 0u);
+  }
+}
+
+// One output entry of a pairwise step: the sum over the 2^k shared-bond
+// values of A*B, for every residue of the group.  Products of residues below
+// 2^31 are below 2^62, so four of them plus a reduced partial sum fit in 64
+// bits: reduce after every fourth product.
+template <int RG>
+__device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
+                                              uint64_t ib, const uint32_t* A0, const uint32_t* B0, uint32_t* C0,
+                                              const ModGroup& mg) {
+  const uint32_t* A = A0 + ia * RG;
+  const uint32_t* B = B0 + ib * RG;
+  const uint64_t sa = (uint64_t)RG << ka, sb = (uint64_t)RG << kb;
+  const uint32_t K = 1u << k;
+  uint64_t acc[RG];
+#pragma unroll
+  for (int r = 0; r < RG; r++) acc[r] = 0;
+  uint32_t q = 0;
+  for (; q + 4 <= K; q += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      uint32_t va[RG], vb[RG];
+      load_entry<RG>(A + (uint64_t)(q + u) * sa, va);
+      load_entry<RG>(B + (uint64_t)(q + u) * sb, vb);
+#pragma unroll
+      for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  }
+  for (; q < K; q++) {
+    uint32_t va[RG], vb[RG];
+    load_entry<RG>(A + (uint64_t)q * sa, va);
+    load_entry<RG>(B + (uint64_t)q * sb, vb);
+#pragma unroll
+    for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+  }
+  uint32_t out[RG];
+#pragma unroll
+  for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  store_entry<RG>(C0 + o * RG, out);
+}
+
+template <int RG>
+__device__ __forceinline__ void step_entry(const StepDesc& d, uint64_t o, const uint32_t* A0, const uint32_t* B0,
+                                           uint32_t* C0, const ModGroup& mg) {
+  uint64_t ia, ib;
+  map_addr(d, o, ia, ib);
+  step_entry_at<RG>(d.k, d.ka, d.kb, o, ia, ib, A0, B0, C0, mg);
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <int RG>
+__global__ void __launch_bounds__(256) leaf_fill_kernel(const LeafDesc* __restrict__ leaves, int n_leaves,
+                                                        const uint32_t* __restrict__ tables,
+                                                        uint32_t* __restrict__ arena, ModGroup mg) {
+  for (int l = blockIdx.x; l < n_leaves; l += gridDim.x) {
+    const LeafDesc ld = leaves[l];
+    const uint64_t n = 1ull << ld.rank;
+    uint32_t* dst = arena + ld.off * RG;
+    for (uint64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      uint32_t v[RG];
+#pragma unroll
+      for (int r = 0; r < RG; r++) v[r] = leaf_value(ld.kind, ld.rank, (uint32_t)idx, tables, ld.table_off, mg.p[r]);
+      store_entry<RG>(dst + idx * RG, v);
+    }
+  }
+}
+
+// A step launched over the whole GPU.  With S = 2^s threads in the grid, a
+// thread visits o, o + S, o + 2S, ...: from one to the next the counter o >> s
+// gains one, which clears its trailing ones and sets bit t, so each operand
+// address changes by the precomputed delta[t] = w[t] - sum_{s <= j < t} w[j]
+// (w[j] = operand weight of output bit j).  Any bit permutation costs the
+// same two adds per entry.
+struct GridStep {
+  StepDesc d;
+  uint64_t wA[32], wB[32];  // operand address weight of output bit j
+  uint64_t dA[32], dB[32];  // address delta when the counter sets bit t
+  uint32_t s;               // log2(total threads)
+  uint32_t pad[3];
+};
+
+template <int RG>
+__global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ g, uint32_t* __restrict__ arena,
+                                                   ModGroup mg) {
+  const uint32_t c = g->d.c, k = g->d.k, ka = g->d.ka, kb = g->d.kb, s = g->s;
+  const uint64_t n = 1ull << c;
+  const uint32_t* A0 = arena + g->d.a_off * RG;
+  const uint32_t* B0 = arena + g->d.b_off * RG;
+  uint32_t* C0 = arena + g->d.c_off * RG;
+  uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  uint64_t ia = 0, ib = 0;
+  for (uint32_t j = 0; j < c; j++)
+    if ((o >> j) & 1ull) {
+      ia += g->wA[j];
+      ib += g->wB[j];
+    }
+  for (;;) {
+    step_entry_at<RG>(k, ka, kb, o, ia, ib, A0, B0, C0, mg);
+    const uint64_t u = o >> s;
+    o += 1ull << s;
+    if (o >= n) break;
+    const uint32_t t = s + (uint32_t)(__ffsll((long long)~u) - 1);
+    ia += g->dA[t];
+    ib += g->dB[t];
+  }
+}
+
+struct RootMap {
+  uint8_t perm[24];  // root bit j -> open variable index
+  int n_open;
+};
+
+// Root tensor -> result residues [entry][R], entry index bit i = open var i.
+template <int RG>
+__global__ void extract_kernel(const uint32_t* __restrict__ arena, uint64_t root_off, RootMap rm,
+                               uint32_t* __restrict__ results, int R, int col) {
+  const uint32_t n_out = 1u << rm.n_open;
+  for (uint32_t J = blockIdx.x * blockDim.x + threadIdx.x; J < n_out; J += gridDim.x * blockDim.x) {
+    uint64_t a = 0;
+#pragma unroll
+    for (int j = 0; j < 24; j++)
+      if (j < rm.n_open) a |= (uint64_t)((J >> rm.perm[j]) & 1u) << j;
+#pragma unroll
+    for (int r = 0; r < RG; r++) results[(uint64_t)J * R + col + r] = arena[(root_off + a) * RG + r];
+  }
+}
+
+// Chinese remaindering by Garner's mixed radix:
+//   v0 = r0,  v_i = (r_i - (v0 + v1 p0 + ... + v_{i-1} p0..p_{i-2})) * inv_i  mod p_i,
+//   X = v0 + p0 (v1 + p1 (v2 + ...)),  0 <= X < p0 p1 ... p_{R-1}.
+struct CrtConsts {
+  uint32_t p[16];
+  uint64_t mu[16];
+  uint32_t inv[16];  // (p0 ... p_{i-1})^{-1} mod p_i
+  int R;
+  int n_limbs;
+};
+
+__global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_entries, CrtConsts cc,
+                           uint32_t* __restrict__ limbs) {
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_entries;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v[16];
+    const uint32_t* r = residues + e * cc.R;
+    for (int i = 0; i < cc.R; i++) {
+      const uint32_t p = cc.p[i];
+      const uint64_t mu = cc.mu[i];
+      uint32_t ri = r[i] % p;
+      if (i == 0) {
+        v[0] = ri;
+        continue;
+      }
+      uint32_t t = mod_reduce(v[i - 1], p, mu);
+      for (int j = i - 2; j >= 0; j--) t = mod_reduce((uint64_t)t * cc.p[j] + v[j], p, mu);
+      const uint32_t diff = ri >= t ? ri - t : ri + (p - t);
+      v[i] = mod_reduce((uint64_t)diff * cc.inv[i], p, mu);
+    }
+    uint32_t x[17];
+    for (int l = 0; l < 17; l++) x[l] = 0;
+    x[0] = v[cc.R - 1];
+    for (int i = cc.R - 2; i >= 0; i--) {
+      uint64_t carry = v[i];
+      for (int l = 0; l < cc.n_limbs; l++) {
+        const uint64_t t = (uint64_t)x[l] * cc.p[i] + carry;
+        x[l] = (uint32_t)t;
+        carry = t >> 32;
+      }
+    }
+    for (int l = 0; l < cc.n_limbs; l++) limbs[e * cc.n_limbs + l] = x[l];
+  }
+}
+
+// ------------------------------------------------------- persistent batch
+
+struct FormDesc {
+  uint32_t step0, lvl0, nlev, leaf0;
+  uint32_t nleaf, res_off, n_out, perm_off;
+  uint64_t root_off;
+  uint32_t n_open, pad;
+};
+
+struct BatchArgs {
+  const FormDesc* forms;
+  const StepDesc* steps;
+  const uint32_t* lvl_start;
+  const LeafDesc* leaves;
+  const uint32_t* tables;
+  const uint8_t* perms;
+  const uint32_t* order;  // queue slot -> formula (largest first)
+  uint32_t n_forms;
+  uint32_t* queue;        // work counter, zeroed before the launch
+  uint32_t* results;      // [entry][R]
+  uint32_t* arena;        // global arenas (when not in shared memory)
+  uint64_t arena_stride;  // entries per CTA
+  int R;
+  int col;                // first residue column of this group
+  int smem_arena;         // 1: arena in dynamic shared memory
+};
+
+// Each CTA repeatedly takes the next formula from the queue and contracts it
+// alone, level by level: all steps of one tree level are independent, so the
+// CTA's threads share the level's output entries (found by binary search over
+// the per-step work offsets) and synchronise once per level.
+template <int RG>
+__global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
+  extern __shared__ uint4 smem_raw[];
+  __shared__ uint32_t task;
+  uint32_t* arena = a.smem_arena ? reinterpret_cast<uint32_t*>(smem_raw)
+                                 : a.arena + (uint64_t)blockIdx.x * a.arena_stride * RG;
+  for (;;) {
+    if (threadIdx.x == 0) task = atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const uint32_t t = task;
+    __syncthreads();
+    if (t >= a.n_forms) break;
+    const FormDesc f = a.forms[a.order[t]];
+    for (uint32_t l = threadIdx.x; l < f.nleaf; l += blockDim.x) {
+      const LeafDesc ld = a.leaves[f.leaf0 + l];
+      uint32_t* dst = arena + ld.off * RG;
+      const uint32_t n = 1u << ld.rank;
+      for (uint32_t idx = 0; idx < n; idx++) {
+        uint32_t v[RG];
+#pragma unroll
+        for (int r = 0; r < RG; r++) v[r] = leaf_value(ld.kind, ld.rank, idx, a.tables, ld.table_off, mg.p[r]);
+        store_entry<RG>(dst + (uint64_t)idx * RG, v);
+      }
+    }
+    __syncthreads();
+    for (uint32_t l = 0; l < f.nlev; l++) {
+      const uint32_t s0 = f.step0 + a.lvl_start[f.lvl0 + l];
+      const uint32_t s1 = f.step0 + a.lvl_start[f.lvl0 + l + 1];
+      const uint32_t total = a.steps[s1 - 1].work_lo + (1u << a.steps[s1 - 1].c);
+      for (uint32_t w = threadIdx.x; w < total; w += blockDim.x) {
+        uint32_t lo = s0, hi = s1 - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (a.steps[mid].work_lo <= w) lo = mid;
+          else hi = mid - 1;
+        }
+        const StepDesc& d = a.steps[lo];
+        step_entry<RG>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
+      }
+      __syncthreads();
+    }
+    for (uint32_t J = threadIdx.x; J < f.n_out; J += blockDim.x) {
+      uint64_t ad = 0;
+      for (uint32_t j = 0; j < f.n_open; j++) ad |= (uint64_t)((J >> a.perms[f.perm_off + j]) & 1u) << j;
+#pragma unroll
+      for (int r = 0; r < RG; r++)
+        a.results[((uint64_t)f.res_off + J) * a.R + a.col + r] = arena[(f.root_off + ad) * RG + r];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tnc_dev

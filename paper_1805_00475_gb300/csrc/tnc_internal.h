@@ -1,0 +1,121 @@
+// Internal host-side structures of libtnc (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tnc.h"
+#include "step_desc.h"
+
+namespace tnc {
+
+// Leaf tensor kinds: the four clause kinds of tnc.h plus the variable COPY.
+enum LeafKind : uint8_t { LK_1IN3 = 0, LK_OR = 1, LK_NAND = 2, LK_TABLE = 3, LK_COPY = 4 };
+
+struct Leaf {
+  uint8_t kind = LK_COPY;
+  std::vector<int> bonds;       // bond ids; bit j of an entry index = value on bonds[j]
+  std::vector<uint32_t> table;  // TABLE only: 2^rank weights in `bonds` order
+  int rank() const { return (int)bonds.size(); }
+};
+
+// A formula's tensor network (Sec. 2.1): clause c -> leaf c, variable v ->
+// leaf n_cons + v.  Bond b joins leaves bond_end[b][0] and bond_end[b][1]
+// (-1 for the free end of an open bond).
+struct Network {
+  int n_vars = 0, n_cons = 0;
+  std::vector<int> open_vars;
+  std::vector<Leaf> leaves;
+  int n_bonds = 0;
+  std::vector<int> bond_end0, bond_end1;
+  int first_open_bond = 0;  // open bond of open_vars[i] = first_open_bond + i
+  int n_components = 0;
+  double log2_bound = 0.0;  // certified log2 upper bound on any count entry
+  int n_leaves() const { return (int)leaves.size(); }
+};
+
+// Binary contraction tree.  Leaves 0..L-1, internal nodes L..2L-2 created in
+// an order where children precede parents (so ascending id = a valid
+// execution order).
+struct Node {
+  int left = -1, right = -1;
+  std::vector<int> bonds;  // sorted bond ids of this tensor
+};
+
+struct Tree {
+  std::vector<Node> nodes;
+  int n_leaves = 0;
+  int root = -1;
+};
+
+struct TreeCost {
+  int max_rank = 0;
+  int depth = 0;
+  double macs = 0.0;
+  double entries = 0.0;
+};
+
+// A lowered plan.
+struct Lowered {
+  std::vector<std::vector<int>> layout;  // node -> bond ids in bit order
+  // sequential (one launch per step) schedule
+  std::vector<StepDesc> seq_steps;  // internal nodes ascending
+  std::vector<uint64_t> seq_leaf_off;
+  uint64_t seq_arena_entries = 0;
+  uint64_t seq_root_off = 0;
+  // level-synchronous schedule (persistent batch kernel)
+  std::vector<StepDesc> lvl_steps;  // sorted by level, work_lo filled
+  std::vector<uint32_t> lvl_start;  // n_levels + 1
+  std::vector<uint64_t> lvl_leaf_off;
+  uint64_t lvl_arena_entries = 0;
+  uint64_t lvl_root_off = 0;
+  // leaves
+  std::vector<LeafDesc> leaves;          // offsets filled per schedule at pack time
+  std::vector<uint32_t> leaf_tables;     // TABLE entries permuted to leaf layouts
+  std::vector<uint8_t> root_perm;        // root bit j -> open variable index
+  int max_runs = 0;
+  int n_bitmap_steps = 0;
+  bool lvl_fits = false;  // level schedule validated (work offsets fit 32 bits)
+};
+
+}  // namespace tnc
+
+struct tnc_network_s {
+  tnc::Network net;
+};
+
+struct tnc_plan_s {
+  tnc::Network net;  // own copy: a plan outlives its network handle
+  tnc::Tree tree;
+  tnc::TreeCost cost;
+  tnc::Lowered low;
+  tnc_plan_stats stats{};
+};
+
+namespace tnc {
+
+// thread-local error reporting
+int set_error(int code, const std::string& msg);
+void clear_error();
+
+// network.cpp
+int build_network(const tnc_formula* f, Network& out);
+
+// planner.cpp
+int plan_tree(const Network& net, const tnc_plan_opts& opts, Tree& out);
+TreeCost tree_cost(const Tree& t);
+void tree_from_merges(const Network& net, const std::vector<std::pair<int, int>>& merges, Tree& t);
+int plan_greedy(const Network& net, Tree& t);
+int plan_bisect(const Network& net, int tries, uint64_t seed, Tree& t);
+int plan_gn(const Network& net, Tree& t);
+
+// lower.cpp
+int lower_plan(const Network& net, const Tree& tree, Lowered& low);
+int validate_lowered(const Network& net, const Tree& tree, Lowered& low);
+
+// primes.cpp
+std::vector<uint32_t> largest_primes_below_2_31(int n);
+bool is_prime_u32(uint32_t n);
+
+}  // namespace tnc

@@ -1,0 +1,388 @@
+"""Thin Python binding of libtnc (include/tnc.h): argument marshalling only.
+
+Every step of the counting path -- leaf tensors, pairwise contractions, residue
+extraction, CRT -- runs in libtnc's CUDA kernels; planning runs in libtnc's C++
+host code.  PyTorch is used for device memory (the workspace) and streams only.
+The binding raises if the library is missing: there is no fallback path.
+
+Names follow the C ABI: build_network, plan, workspace_bytes, contract,
+Batch.{create, upload, launch, download}, contract_batch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtnc.so")
+
+TNC_OK = 0
+ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4: "TNC_ERR_BUFFER",
+          -5: "TNC_ERR_TIMEOUT", -6: "TNC_ERR_NOMEM"}
+HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4}
+PATHS = {"int64": 0}
+TNC_MAYBE_WRAPPED = 1
+
+# every symbol include/tnc.h declares
+EXPORTS = [
+    "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_build_network", "tnc_network_info",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes",
+    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload",
+    "tnc_batch_launch", "tnc_batch_download", "tnc_batch_status", "tnc_free_batch",
+    "tnc_contract_batch",
+]
+
+
+class TncError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Formula(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_int32), ("n_cons", ctypes.c_int32),
+                ("arity", ctypes.POINTER(ctypes.c_int32)), ("var_of", ctypes.POINTER(ctypes.c_int32)),
+                ("kind", ctypes.POINTER(ctypes.c_uint8)), ("table", ctypes.POINTER(ctypes.c_uint32)),
+                ("n_open", ctypes.c_int32), ("open_vars", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _PlanOpts(ctypes.Structure):
+    _fields_ = [("heuristic", ctypes.c_int32), ("rank_cap", ctypes.c_int32), ("tries", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("order", ctypes.POINTER(ctypes.c_int32)),
+                ("n_order", ctypes.c_int32)]
+
+
+class _PlanStats(ctypes.Structure):
+    _fields_ = [("max_rank", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("total_macs", ctypes.c_double),
+                ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double)]
+
+
+class _ContractOpts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("n_residues", ctypes.c_int32),
+                ("primes", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class _Count(ctypes.Structure):
+    _fields_ = [("residues", ctypes.POINTER(ctypes.c_uint32)), ("limbs", ctypes.POINTER(ctypes.c_uint32)),
+                ("cap_out", ctypes.c_int32), ("cap_limbs", ctypes.c_int32), ("n_out", ctypes.c_int32),
+                ("n_limbs", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib():
+    """Load libtnc.so (built by paper_1805_00475_gb300.build); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtnc.so not built ({LIB_PATH}); run python -m paper_1805_00475_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz = ctypes.c_void_p, ctypes.c_size_t
+        i32, u32p, i32p = ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32)
+        sig = {
+            "tnc_version": ([], ctypes.c_char_p),
+            "tnc_last_error": ([], ctypes.c_char_p),
+            "tnc_default_primes": ([i32, u32p], ctypes.c_int),
+            "tnc_build_network": ([ctypes.POINTER(_Formula), ctypes.POINTER(vp)], ctypes.c_int),
+            "tnc_network_info": ([vp, i32p, i32p, i32p], ctypes.c_int),
+            "tnc_free_network": ([vp], None),
+            "tnc_plan": ([vp, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp), ctypes.POINTER(_PlanStats)],
+                         ctypes.c_int),
+            "tnc_plan_many": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp),
+                               ctypes.POINTER(_PlanStats)], ctypes.c_int),
+            "tnc_plan_steps": ([vp, i32p, i32p, i32], ctypes.c_int),
+            "tnc_free_plan": ([vp], None),
+            "tnc_workspace_bytes": ([vp, i32], sz),
+            "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
+                             ctypes.c_int),
+            "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
+                                 ctypes.c_int),
+            "tnc_batch_workspace_bytes": ([vp], sz),
+            "tnc_batch_info": ([vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_uint64),
+                                i32p], ctypes.c_int),
+            "tnc_batch_upload": ([vp, vp, sz, vp], ctypes.c_int),
+            "tnc_batch_launch": ([vp, vp, vp], ctypes.c_int),
+            "tnc_batch_download": ([vp, vp, vp, ctypes.POINTER(_Count)], ctypes.c_int),
+            "tnc_batch_status": ([vp, vp, vp], ctypes.c_int),
+            "tnc_free_batch": ([vp], None),
+            "tnc_contract_batch": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), vp, sz, vp,
+                                    ctypes.POINTER(_Count)], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != TNC_OK:
+        raise TncError(rc, lib().tnc_last_error().decode())
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def version() -> str:
+    return lib().tnc_version().decode()
+
+
+def default_primes(n: int) -> List[int]:
+    out = np.zeros(max(n, 1), dtype=np.uint32)
+    _check(lib().tnc_default_primes(n, _p(out, ctypes.c_uint32)))
+    return [int(x) for x in out[:n]]
+
+
+# ------------------------------------------------------------------ network
+
+class Network:
+    """tnc_network_t: the COPY + clause tensor network of a formula (Sec. 2.1)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tnc_free_network(self.h)
+            self.h = None
+
+    def info(self) -> Tuple[int, int, int]:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tnc_network_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+
+def build_network(formula) -> Network:
+    """formula: any object with n_vars, clauses, kinds, tables, open_vars."""
+    arity = np.array([len(c) for c in formula.clauses] or [0], dtype=np.int32)
+    var_of = np.array([v for c in formula.clauses for v in c] or [0], dtype=np.int32)
+    kind = np.array(list(formula.kinds) or [0], dtype=np.uint8)
+    tab = []
+    for k, t in zip(formula.kinds, getattr(formula, "tables", None) or [None] * len(formula.kinds)):
+        if k == 3:
+            tab.extend(int(x) for x in t)
+    table = np.array(tab or [0], dtype=np.uint32)
+    opens = np.array(list(formula.open_vars) or [0], dtype=np.int32)
+    f = _Formula(formula.n_vars, len(formula.clauses), _p(arity, ctypes.c_int32), _p(var_of, ctypes.c_int32),
+                 _p(kind, ctypes.c_uint8), _p(table, ctypes.c_uint32), len(formula.open_vars),
+                 _p(opens, ctypes.c_int32))
+    h = ctypes.c_void_p()
+    _check(lib().tnc_build_network(ctypes.byref(f), ctypes.byref(h)))
+    return Network(h)
+
+
+# ------------------------------------------------------------------ plan
+
+@dataclass
+class PlanStats:
+    max_rank: int
+    n_steps: int
+    n_leaves: int
+    depth: int
+    total_macs: float
+    total_entries: float
+    log2_bound: float
+
+
+class Plan:
+    """tnc_plan_t: contraction tree + lowered descriptors."""
+
+    def __init__(self, handle, stats: PlanStats, n_open: int):
+        self.h = handle
+        self.stats = stats
+        self.n_open = n_open
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tnc_free_plan(self.h)
+            self.h = None
+
+    def steps(self) -> List[Tuple[int, int]]:
+        n = self.stats.n_steps
+        l = np.zeros(max(n, 1), dtype=np.int32)
+        r = np.zeros(max(n, 1), dtype=np.int32)
+        _check(lib().tnc_plan_steps(self.h, _p(l, ctypes.c_int32), _p(r, ctypes.c_int32), n))
+        return [(int(a), int(b)) for a, b in zip(l[:n], r[:n])]
+
+
+def plan(network: Network, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0,
+         order: Optional[Sequence[Tuple[int, int]]] = None, n_open: int = 0) -> Plan:
+    ordr = np.array([x for p in (order or []) for x in p] or [0], dtype=np.int32)
+    o = _PlanOpts(HEURISTICS[heuristic] if order is None else HEURISTICS["explicit"], rank_cap, tries, seed,
+                  _p(ordr, ctypes.c_int32), len(order or []))
+    st = _PlanStats()
+    h = ctypes.c_void_p()
+    _check(lib().tnc_plan(network.h, ctypes.byref(o), ctypes.byref(h), ctypes.byref(st)))
+    return Plan(h, _stats(st), n_open)
+
+
+def _stats(st: _PlanStats) -> PlanStats:
+    return PlanStats(st.max_rank, st.n_steps, st.n_leaves, st.depth, st.total_macs, st.total_entries,
+                     st.log2_bound)
+
+
+def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0
+              ) -> List[Plan]:
+    """Build and plan many formulas; planning runs in parallel on the host
+    cores inside libtnc (tnc_plan_many)."""
+    nets = [build_network(f) for f in formulas]
+    n = len(nets)
+    arr = (ctypes.c_void_p * n)(*[x.h.value for x in nets])
+    outs = (ctypes.c_void_p * n)()
+    sts = (_PlanStats * n)()
+    ordr = np.zeros(1, dtype=np.int32)
+    o = _PlanOpts(HEURISTICS[heuristic], rank_cap, tries, seed, _p(ordr, ctypes.c_int32), 0)
+    _check(lib().tnc_plan_many(arr, n, ctypes.byref(o), outs, sts))
+    return [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), len(formulas[i].open_vars)) for i in range(n)]
+
+
+def plan_formula(formula, **kw) -> Plan:
+    net = build_network(formula)
+    return plan(net, n_open=len(formula.open_vars), **kw)
+
+
+# ------------------------------------------------------------------ contraction
+
+@dataclass
+class Count:
+    counts: List[int]          # exact CRT values, one per open index
+    residues: np.ndarray       # [n_out, R]
+    primes: List[int]
+    flags: int
+
+    @property
+    def value(self) -> int:
+        return self.counts[0]
+
+
+def _opts(n_residues: int, primes: Optional[Sequence[int]], path: str = "int64"):
+    pr = np.array(list(primes) if primes is not None else default_primes(n_residues), dtype=np.uint32)
+    o = _ContractOpts(PATHS[path], n_residues, _p(pr, ctypes.c_uint32))
+    return o, pr
+
+
+def _count_buffers(n_out: int, R: int):
+    res = np.zeros((n_out, R), dtype=np.uint32)
+    cap_limbs = (31 * R + 31) // 32
+    limbs = np.zeros((n_out, cap_limbs), dtype=np.uint32)
+    c = _Count(_p(res, ctypes.c_uint32), _p(limbs, ctypes.c_uint32), n_out, cap_limbs, 0, 0, 0)
+    return c, res, limbs
+
+
+def _to_count(c: _Count, res: np.ndarray, limbs: np.ndarray, primes) -> Count:
+    counts = []
+    for row in limbs[: c.n_out]:
+        v = 0
+        for x in row[::-1]:
+            v = (v << 32) | int(x)
+        counts.append(v)
+    return Count(counts, res[: c.n_out].copy(), [int(p) for p in primes], int(c.flags))
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int, ws=None):
+    import torch
+    if ws is not None:
+        if ws.numel() * ws.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return ws
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+
+
+def workspace_bytes(p: Plan, n_residues: int) -> int:
+    return int(lib().tnc_workspace_bytes(p.h, n_residues))
+
+
+def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=None, path: str = "int64") -> Count:
+    """Contract one plan on the GPU (tnc_contract); returns exact counts."""
+    o, pr = _opts(n_residues, primes, path)
+    nb = workspace_bytes(p, n_residues)
+    ws = _workspace(nb, workspace)
+    c, res, limbs = _count_buffers(1 << p.n_open, n_residues)
+    _check(lib().tnc_contract(p.h, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream),
+                              ctypes.byref(c)))
+    return _to_count(c, res, limbs, pr)
+
+
+class Batch:
+    """tnc_batch_t: many plans in one persistent, graph-captured launch."""
+
+    def __init__(self, plans: Sequence[Plan], n_residues: int = 2, primes=None, path: str = "int64"):
+        self.plans = list(plans)
+        self.R = n_residues
+        self._o, self._pr = _opts(n_residues, primes, path)
+        arr = (ctypes.c_void_p * len(self.plans))(*[pp.h.value for pp in self.plans])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        _check(lib().tnc_batch_create(arr, len(self.plans), ctypes.byref(self._o), ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tnc_free_batch(self.h)
+            self.h = None
+
+    def workspace_bytes(self) -> int:
+        return int(lib().tnc_batch_workspace_bytes(self.h))
+
+    def info(self):
+        """(h2d bytes per upload, d2h bytes per download, result entries, kernels per launch)."""
+        a, b, c, d = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_uint64(), ctypes.c_int32()
+        _check(lib().tnc_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return a.value, b.value, c.value, d.value
+
+    def upload(self, ws, stream=None):
+        _check(lib().tnc_batch_upload(self.h, ctypes.c_void_p(ws.data_ptr()), self.workspace_bytes(),
+                                      _stream_ptr(stream)))
+
+    def launch(self, ws, stream=None):
+        _check(lib().tnc_batch_launch(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+
+    def download(self, ws, stream=None) -> List[Count]:
+        n = len(self.plans)
+        bufs = [_count_buffers(1 << pp.n_open, self.R) for pp in self.plans]
+        arr = (_Count * n)(*[b[0] for b in bufs])
+        _check(lib().tnc_batch_download(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream), arr))
+        return [_to_count(arr[i], bufs[i][1], bufs[i][2], self._pr) for i in range(n)]
+
+    def status(self, ws, stream=None) -> int:
+        return int(lib().tnc_batch_status(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+
+
+def contract_batch(plans: Sequence[Plan], n_residues: int = 2, primes=None, workspace=None, stream=None,
+                   path: str = "int64") -> List[Count]:
+    """Upload + persistent launch + download (tnc_contract_batch)."""
+    b = Batch(plans, n_residues, primes, path)
+    ws = _workspace(b.workspace_bytes(), workspace)
+    n = len(b.plans)
+    bufs = [_count_buffers(1 << pp.n_open, n_residues) for pp in b.plans]
+    arr = (_Count * n)(*[x[0] for x in bufs])
+    _check(lib().tnc_contract_batch(b._arr, n, ctypes.byref(b._o), ctypes.c_void_p(ws.data_ptr()),
+                                    b.workspace_bytes(), _stream_ptr(stream), arr))
+    return [_to_count(arr[i], bufs[i][1], bufs[i][2], b._pr) for i in range(n)]
+
+
+def count(formula, n_residues: int = 4, heuristic: str = "bisect", **kw) -> Count:
+    """Convenience: build, plan and contract one formula."""
+    return contract(plan_formula(formula, heuristic=heuristic), n_residues, **kw)

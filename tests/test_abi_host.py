@@ -1,0 +1,148 @@
+"""Host-side checks of libtnc (no GPU): exports, networks, planners, lowering."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1805_00475_gb300 import build as tnc_build
+from paper_1805_00475_gb300 import instances as I
+from paper_1805_00475_gb300 import tnc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tnc_build.build()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tnc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[\w\s\*]+?\b(tnc_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", tnc.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tnc_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(tnc.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n)
+    assert sorted(tnc.EXPORTS) == names
+
+
+def test_version_and_primes():
+    assert "sm_103a" in tnc.version()
+    p = tnc.default_primes(8)
+    assert p[0] == 2 ** 31 - 1 and p == sorted(p, reverse=True) and len(set(p)) == 8
+
+    def isprime(n):
+        if n < 2:
+            return False
+        i = 2
+        while i * i <= n:
+            if n % i == 0:
+                return False
+            i += 1
+        return True
+    # every odd number between consecutive returned primes is composite
+    for a, b in zip(p, p[1:]):
+        assert isprime(a) and isprime(b)
+        for x in range(b + 2, a, 2):
+            assert not isprime(x)
+
+
+def test_network_info_and_components():
+    f = I.cubic_vertex_cover(20, 0)
+    n, bonds, comps = tnc.build_network(f).info()
+    assert (n, bonds, comps) == (20 + 30, 60, 1)
+    g = I.Formula(7, [(0, 1), (2, 3)], [I.KIND_OR, I.KIND_OR])
+    n, bonds, comps = tnc.build_network(g).info()
+    assert (n, bonds) == (2 + 7, 4) and comps == 2 + 3  # two clause components + 3 lone vars
+
+
+def test_invalid_formulas_are_rejected():
+    with pytest.raises(tnc.TncError) as e:
+        tnc.build_network(type("F", (), dict(n_vars=2, clauses=[(0, 5)], kinds=[1], tables=[None],
+                                             open_vars=[]))())
+    assert e.value.code == -1
+    with pytest.raises(tnc.TncError):
+        tnc.build_network(type("F", (), dict(n_vars=2, clauses=[(0, 1)], kinds=[9], tables=[None],
+                                             open_vars=[]))())
+    with pytest.raises(tnc.TncError):
+        tnc.build_network(type("F", (), dict(n_vars=2, clauses=[(0, 1)], kinds=[1], tables=[None],
+                                             open_vars=[0, 0]))())
+
+
+@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best"])
+def test_planners_build_full_trees(h):
+    f = I.cubic_vertex_cover(60, 3)
+    p = tnc.plan(tnc.build_network(f), heuristic=h)
+    steps = p.steps()
+    L = f.n_vars + f.n_cons
+    assert len(steps) == L - 1 == p.stats.n_steps
+    used = set()
+    for i, (a, b) in enumerate(steps):
+        assert a < L + i and b < L + i and a != b
+        assert a not in used and b not in used
+        used |= {a, b}
+    assert len(used) == 2 * (L - 1)
+    assert 3 <= p.stats.max_rank <= 16
+
+
+def test_explicit_order_is_kept():
+    f = I.worked_example()
+    order = [(0, 2), (1, 3), (6, 7), (4, 8), (5, 9)]  # ids as the oracle numbers them
+    p = tnc.plan(tnc.build_network(f), order=order, n_open=2)
+    assert p.steps() == order
+    with pytest.raises(tnc.TncError):
+        tnc.plan(tnc.build_network(f), order=[(0, 0)], n_open=2)
+
+
+def test_rank_cap_reports_too_large():
+    f = I.cubic_vertex_cover(60, 0)
+    with pytest.raises(tnc.TncError) as e:
+        tnc.plan(tnc.build_network(f), heuristic="greedy", rank_cap=6)
+    assert e.value.code == -2
+
+
+def test_lazy_cost_matches_definition():
+    """Plan stats are the exact sum over steps of 2^(a+b-k) (Corollary 2 cost),
+    recomputed here from the exported tree and the bond structure."""
+    f = I.one_in_three(30, 18, 2)
+    p = tnc.plan(tnc.build_network(f), heuristic="bisect")
+    bonds = {}
+    b = 0
+    for c, vs in enumerate(f.clauses):
+        for v in vs:
+            bonds.setdefault(c, set()).add(b)
+            bonds.setdefault(f.n_cons + v, set()).add(b)
+            b += 1
+    for t in range(f.n_cons + f.n_vars):
+        bonds.setdefault(t, set())
+    macs, mx = 0, max(len(s) for s in bonds.values())
+    nxt = f.n_cons + f.n_vars
+    for a, c in p.steps():
+        A, B = bonds.pop(a), bonds.pop(c)
+        k = len(A & B)
+        macs += 2 ** (len(A) + len(B) - k)
+        bonds[nxt] = A ^ B
+        mx = max(mx, len(A ^ B))
+        nxt += 1
+    assert math.isclose(p.stats.total_macs, macs) and p.stats.max_rank == mx
+
+
+def test_bound_certifies_small_counts():
+    import oracle
+    for s in range(5):
+        f = I.one_in_three(40, 25, s)
+        p = tnc.plan(tnc.build_network(f), heuristic="greedy")
+        z = oracle.count(f)[0]
+        assert z <= 2 ** p.stats.log2_bound + 1e-6

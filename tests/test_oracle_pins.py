@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle.pyoracle import py_bruteforce, py_contract
 from paper_1805_00475_gb300 import instances as I
+from _util import random_order
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -223,33 +224,6 @@ def test_contract_equals_bruteforce_random(seed):
         assert py_contract(f) == bf
 
 
-def _random_order(rng, f):
-    """A random full contraction order over connected pairs (ids as the oracle)."""
-    n_leaf = f.n_cons + f.n_vars
-    bonds = {}
-    for c, vs in enumerate(f.clauses):
-        for v in vs:
-            bonds.setdefault(c, set()).add(f.n_cons + v)
-            bonds.setdefault(f.n_cons + v, set()).add(c)
-    live = set(range(n_leaf))
-    for t in live:
-        bonds.setdefault(t, set())
-    nxt, order = n_leaf, []
-    while len(live) > 1:
-        pairs = sorted((a, b) for a in live for b in bonds[a] if b in live and a < b)
-        a, b = rng.choice(pairs) if pairs else tuple(sorted(rng.sample(sorted(live), 2)))
-        order.append((a, b))
-        nb = (bonds[a] | bonds[b]) - {a, b}
-        for x in nb:
-            bonds[x] -= {a, b}
-            bonds[x].add(nxt)
-        bonds[nxt] = nb
-        live -= {a, b}
-        live.add(nxt)
-        nxt += 1
-    return order
-
-
 @pytest.mark.parametrize("seed", range(10))
 def test_order_independence(seed):
     """The full trace does not depend on the contraction order (Sec. 2.1)."""
@@ -257,7 +231,7 @@ def test_order_independence(seed):
     f = I.one_in_three(24, 16, seed) if seed % 2 else I.cubic_vertex_cover(20, seed)
     ref = oracle.count(f)
     for _ in range(3):
-        assert oracle.count(f, order=_random_order(rng, f), max_rank=26) == ref
+        assert oracle.count(f, order=random_order(rng, f), max_rank=26) == ref
     if f.n_vars <= 24:
         assert oracle.bruteforce(f) == ref
 
