@@ -303,6 +303,8 @@ static int check_step(const StepDesc& d, uint64_t arena) {
 
 int validate_lowered(const Network& net, const Tree& tree, Lowered& low) {
   const int L = tree.n_leaves;
+  if (tree.nodes.empty()) return TNC_OK;  // empty network: nothing is launched
+  if (tree.root < 0 || tree.root >= (int)tree.nodes.size()) return set_error(TNC_ERR_INVALID, "internal: root");
   if ((int)low.leaves.size() != L) return set_error(TNC_ERR_INVALID, "internal: leaf count");
   for (int sched = 0; sched < 2; sched++) {
     const uint64_t arena = sched ? low.lvl_arena_entries : low.seq_arena_entries;

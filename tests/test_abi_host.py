@@ -146,3 +146,23 @@ def test_bound_certifies_small_counts():
         p = tnc.plan(tnc.build_network(f), heuristic="greedy")
         z = oracle.count(f)[0]
         assert z <= 2 ** p.stats.log2_bound + 1e-6
+
+
+DEGENERATE = [
+    I.Formula(1, [], []),
+    I.Formula(0, [], []),
+    I.Formula(3, [(0, 1, 2), ()], [I.KIND_1IN3, I.KIND_OR]),
+    I.Formula(5, [(0, 1, 2)], [I.KIND_1IN3]),
+    I.Formula(4, [(0, 1)], [I.KIND_OR], open_vars=[3, 0]),
+    I.Formula(6, [(0, 1), (2, 3), (4, 5)], [I.KIND_NAND] * 3),
+    I.Formula(2, [()], [I.KIND_TABLE], tables=[[7]]),
+    I.Formula(3, [(0,), (1,), (2,)], [I.KIND_OR] * 3, open_vars=[0, 1, 2]),
+]
+
+
+@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best"])
+def test_degenerate_formulas_plan(h):
+    for f in DEGENERATE:
+        p = tnc.plan_formula(f, heuristic=h)
+        assert p.stats.n_steps == max(f.n_vars + f.n_cons - 1, 0)
+    tnc.plan_many(DEGENERATE, heuristic=h)
