@@ -216,6 +216,30 @@ void tnc_free_batch(tnc_batch_t* b);
 int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                        void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* outs);
 
+/* ---- allocation-free variant (the paper has no counterpart) --------------
+ * Same counts as tnc_contract, for callers that cannot allocate device memory
+ * themselves: a host application whose device memory is owned entirely by
+ * another allocator (a framework's caching pool that forbids raw cudaMalloc),
+ * or a latency-bound loop that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the whole device.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its device scratch is one fixed array of
+ * TNC_NOALLOC_SCRATCH_BYTES inside libtnc, held on every GPU that loads the
+ * library until the process exits.  The caller still passes the plan (input)
+ * and the host result buffers of `out` (output).
+ *   - The first call on each device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other host threads, same device) race and corrupt each other's
+ *     results.  Serialise them.  Nothing in the array needs to start zeroed,
+ *     so the previous call's contents do no harm.
+ *   - A plan whose scratch (tnc_workspace_bytes for the same R) exceeds the
+ *     array fails with TNC_ERR_TOO_LARGE and a message giving both sizes.
+ *   - Synchronises `cuda_stream` before returning. */
+#define TNC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* cuda_stream,
+                         tnc_count* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -620,3 +620,191 @@ extern "C" int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, con
   tnc_free_batch(b);
   return rc;
 }
+
+// =============================================== allocation-free single formula
+//
+// For callers that must not allocate device memory (see tnc_contract_noalloc
+// in tnc.h).  All device scratch -- leaf descriptors, weight tables, step
+// descriptors, the tensor arena, residues and CRT limbs -- lives in one
+// file-scope array that every GPU loading this library holds until exit.
+// Nothing in the path needs it to start zeroed: the leaf fill writes every
+// leaf entry, every step writes each output entry before any later step
+// reads it, and the residue and limb regions are written in full.  Host-side
+// work uses fixed-size stack buffers only.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TNC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device.  In host code
+// `g_noalloc_scratch` names a host-side shadow, not device memory, so the
+// address is looked up once per device, with that device current.
+int noalloc_base(void** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(TNC_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!p) return set_error(TNC_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return TNC_OK;
+}
+
+}  // namespace
+
+extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* cuda_stream,
+                                    tnc_count* out) {
+  clear_error();
+  if (!plan || !opts || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
+  if (opts->path != TNC_PATH_INT64) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
+  const int R = opts->n_residues;
+  if (R < 1 || R > 16) return set_error(TNC_ERR_INVALID, "n_residues must be in [1, 16]");
+  // primes and CRT constants, on the stack
+  uint32_t primes[16];
+  if (opts->primes) {
+    for (int i = 0; i < R; i++) {
+      const uint32_t p = opts->primes[i];
+      if (p <= (1u << 30) || p >= (1u << 31) || !is_prime_u32(p))
+        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^30, 2^31)");
+      for (int j = 0; j < i; j++)
+        if (primes[j] == p) return set_error(TNC_ERR_INVALID, "primes must be distinct");
+      primes[i] = p;
+    }
+  } else {
+    int n = 0;
+    for (uint32_t x = 2147483647u; n < R; x -= 2)
+      if (is_prime_u32(x)) primes[n++] = x;
+  }
+  CrtConsts cc{};
+  cc.R = R;
+  double log2_prod = 0;
+  for (int i = 0; i < R; i++) {
+    const uint32_t p = primes[i];
+    cc.p[i] = p;
+    cc.mu[i] = ~0ull / p;
+    uint64_t prod = 1;
+    for (int j = 0; j < i; j++) prod = prod * (primes[j] % p) % p;
+    cc.inv[i] = i == 0 ? 1u : powmod(prod, p - 2, p);
+    log2_prod += std::log2((double)p);
+  }
+  cc.n_limbs = (31 * R + 31) / 32;
+  int n_groups = 0, grp_rg[16], grp_col[16];
+  for (int c = 0, s = 4; s >= 1; s /= 2)
+    while (R - c >= s) {
+      grp_rg[n_groups] = s;
+      grp_col[n_groups++] = c;
+      c += s;
+    }
+
+  const SeqLayout L = seq_layout(plan, R);
+  const uint64_t n_out = L.n_out;
+  out->n_out = (int32_t)n_out;
+  out->n_limbs = cc.n_limbs;
+  out->flags = plan->net.log2_bound >= log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u;
+  if (out->cap_out < (int32_t)n_out) return set_error(TNC_ERR_BUFFER, "count buffer holds fewer entries than 2^n_open");
+  if (out->limbs && out->cap_limbs < cc.n_limbs)
+    return set_error(TNC_ERR_BUFFER, "need " + std::to_string(cc.n_limbs) + " limbs");
+  if (plan->tree.nodes.empty()) {  // empty network: the empty product, 1
+    out->flags = 0;
+    if (out->residues)
+      for (int r = 0; r < R; r++) out->residues[r] = 1u;
+    if (out->limbs) {
+      std::memset(out->limbs, 0, (size_t)out->cap_limbs * sizeof(uint32_t));
+      out->limbs[0] = 1u;
+    }
+    return TNC_OK;
+  }
+  if (L.total > (size_t)TNC_NOALLOC_SCRATCH_BYTES)
+    return set_error(TNC_ERR_TOO_LARGE, "plan needs " + std::to_string(L.total) +
+                                            " bytes of scratch; tnc_contract_noalloc holds " +
+                                            std::to_string((size_t)TNC_NOALLOC_SCRATCH_BYTES));
+  void* base = nullptr;
+  int rc = noalloc_base(&base);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* ws = (char*)base;
+
+  // descriptors: through small stack buffers (pageable copies return once the
+  // source has been staged, so the buffer can be refilled right away)
+  {
+    LeafDesc buf[64];
+    const size_t nl = plan->low.leaves.size();
+    for (size_t i0 = 0; i0 < nl; i0 += 64) {
+      const size_t m = std::min<size_t>(64, nl - i0);
+      for (size_t i = 0; i < m; i++) {
+        buf[i] = plan->low.leaves[i0 + i];
+        buf[i].off = plan->low.seq_leaf_off[i0 + i];
+      }
+      CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves + i0 * sizeof(LeafDesc), buf, m * sizeof(LeafDesc),
+                               cudaMemcpyHostToDevice, st));
+    }
+  }
+  if (!plan->low.leaf_tables.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, plan->low.leaf_tables.data(),
+                             plan->low.leaf_tables.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  {
+    GridStep buf[8];
+    const size_t ns = plan->low.seq_steps.size();
+    for (size_t i0 = 0; i0 < ns; i0 += 8) {
+      const size_t m = std::min<size_t>(8, ns - i0);
+      for (size_t i = 0; i < m; i++) buf[i] = make_grid_step(plan->low.seq_steps[i0 + i]);
+      CUDA_TRY(cudaMemcpyAsync(ws + L.off_steps + i0 * sizeof(GridStep), buf, m * sizeof(GridStep),
+                               cudaMemcpyHostToDevice, st));
+    }
+  }
+  const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
+  uint32_t* arena = (uint32_t*)(ws + L.off_arena);
+  uint32_t* results = (uint32_t*)(ws + L.off_results);
+  uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
+  RootMap rm{};
+  rm.n_open = (int)plan->net.open_vars.size();
+  for (int j = 0; j < rm.n_open; j++) rm.perm[j] = plan->low.root_perm[j];
+  const int nl = (int)plan->low.leaves.size();
+  const int sms = sm_count();
+  const uint64_t root_off =
+      plan->low.seq_steps.empty() ? plan->low.seq_leaf_off[plan->tree.root] : plan->low.seq_root_off;
+  for (int gi = 0; gi < n_groups; gi++) {
+    ModGroup mg{};
+    for (int r = 0; r < 4; r++) {
+      const uint32_t p = r < grp_rg[gi] ? primes[grp_col[gi] + r] : primes[grp_col[gi]];
+      mg.p[r] = p;
+      mg.mu[r] = ~0ull / p;
+    }
+    rc = dispatch_rg(grp_rg[gi], [&](auto rgc) -> int {
+      constexpr int RG = decltype(rgc)::value;
+      tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
+          (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
+      for (size_t i = 0; i < plan->low.seq_steps.size(); i++) {
+        int threads, blocks, sh;
+        grid_shape(plan->low.seq_steps[i].c, &threads, &blocks, &sh);
+        tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
+      }
+      tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((n_out + 255) / 256, 1024), 256, 0, st>>>(
+          arena, root_off, rm, results, R, grp_col[gi]);
+      CUDA_TRY(cudaGetLastError());
+      return TNC_OK;
+    });
+    if (rc) return rc;
+  }
+  tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((n_out + 127) / 128, 1024), 128, 0, st>>>(results, n_out, cc,
+                                                                                                limbs);
+  CUDA_TRY(cudaGetLastError());
+  if (out->residues)
+    CUDA_TRY(cudaMemcpyAsync(out->residues, results, n_out * R * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (out->limbs) {
+    std::memset(out->limbs, 0, n_out * (size_t)out->cap_limbs * sizeof(uint32_t));
+    CUDA_TRY(cudaMemcpy2DAsync(out->limbs, (size_t)out->cap_limbs * sizeof(uint32_t), limbs,
+                               (size_t)cc.n_limbs * sizeof(uint32_t), (size_t)cc.n_limbs * sizeof(uint32_t), n_out,
+                               cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return TNC_OK;
+}

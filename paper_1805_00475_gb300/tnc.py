@@ -34,8 +34,9 @@ EXPORTS = [
     "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_status", "tnc_free_batch",
-    "tnc_contract_batch",
+    "tnc_contract_batch", "tnc_contract_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class TncError(RuntimeError):
@@ -121,6 +122,7 @@ def lib():
             "tnc_free_batch": ([vp], None),
             "tnc_contract_batch": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), vp, sz, vp,
                                     ctypes.POINTER(_Count)], ctypes.c_int),
+            "tnc_contract_noalloc": ([vp, ctypes.POINTER(_ContractOpts), vp, ctypes.POINTER(_Count)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -322,6 +324,16 @@ def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=N
     c, res, limbs = _count_buffers(1 << p.n_open, n_residues)
     _check(lib().tnc_contract(p.h, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream),
                               ctypes.byref(c)))
+    return _to_count(c, res, limbs, pr)
+
+
+def contract_noalloc(p: Plan, n_residues: int = 4, primes=None, stream=None, path: str = "int64") -> Count:
+    """tnc_contract_noalloc: like contract(), but the device scratch is libtnc's
+    own fixed array, so nothing is allocated on the device for the call (for
+    callers that cannot allocate device memory; see include/tnc.h)."""
+    o, pr = _opts(n_residues, primes, path)
+    c, res, limbs = _count_buffers(1 << p.n_open, n_residues)
+    _check(lib().tnc_contract_noalloc(p.h, ctypes.byref(o), _stream_ptr(stream), ctypes.byref(c)))
     return _to_count(c, res, limbs, pr)
 
 
