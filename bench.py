@@ -3,7 +3,7 @@
 Workload (one step): a batch of B #Cubic-Vertex-Cover formulas, each on a
 seeded random simple connected cubic graph with n = 60 vertices
 (configuration model with rejection), counted exactly as R = 4 residues
-modulo the largest primes below 2^31 plus the CRT value, on the int64
+modulo the largest primes below 2^30 plus the CRT value, on the int64
 CUDA-core path, contracted along tensor-GN / bisection / greedy plans (the
 cheapest per formula) in one persistent, graph-captured launch.
 
@@ -202,6 +202,9 @@ def run_tnc(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     batch.upload(ws, stream)
+    t = time.perf_counter()
+    tuned_threads, tuned_smem = batch.autotune(ws, stream)
+    tune_s = time.perf_counter() - t
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
             flush.fill_(1)
@@ -242,21 +245,28 @@ def run_tnc(args):
     ms = total_ms / args.steps
     value = args.batch * world / (ms / 1000.0)
 
-    # end to end through the C ABI with host buffers: upload + launch + download
+    # end to end through the C ABI with host buffers: every step uploads the
+    # packed formulas from pinned host memory, launches, and reads the exact
+    # counts back into host buffers (tnc_batch_upload / _launch / _download)
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(3, min(args.steps, 10))
         for _ in range(2):
-            tnc.contract_batch(plans, n_residues=R, workspace=ws, stream=stream)
+            batch.upload(ws, stream)
+            batch.launch(ws, stream)
+            batch.download(ws, stream)
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
         for _ in range(e2e_steps):
-            tnc.contract_batch(plans, n_residues=R, workspace=ws, stream=stream)
-        torch.cuda.synchronize(dev)
+            batch.upload(ws, stream)
+            batch.launch(ws, stream)
+            res = batch.download(ws, stream)
         e2e_s = (time.perf_counter() - t) / e2e_steps
+        assert len(res) == args.batch
         e2e = {"value": args.batch * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1000.0,
-               "includes": "descriptor H2D + persistent launch + result D2H per step; planning excluded"}
+               "includes": "packed-formula H2D (pinned) + persistent launch + counts D2H per step; "
+                           "planning and packing excluded"}
 
     if rank != 0:
         if world > 1:
@@ -264,16 +274,27 @@ def run_tnc(args):
         return
     pk, pk_kind = peaks()
     achieved_gbs = alg_bytes / (ms / 1000.0) / 1e9
+    achieved_macs = macs / (ms / 1000.0)
+    probe = tnc.probe_modmac(8192, stream=stream)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    # integer-pipe ceiling from unit counts and clocks: per SM 4 partitions x 16
+    # lanes issue a 32-bit IMAD per clock; a residue MAC (u32 x u32 + u64) is one
+    # 64-bit-result IMAD, two issue slots; clock = max SM clock
+    alu_peak = sms * 4 * 16 / 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 residues, int64 accumulate", "data": "synthetic",
         "config": config(args, world),
         "modular_macs_per_s": macs * world / (ms / 1000.0),
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved_gbs / pk["hbm_gbs"], "traffic": None,
-                     "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "batch_kernel<4>", "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline": {"bound": "alu", "achieved": achieved_macs / 1e12, "peak": alu_peak / 1e12,
+                     "unit": "Tmodmac/s", "frac": achieved_macs / alu_peak, "traffic": None,
+                     "peak_source": "derived: SMs x 64 IMAD lanes / 2 slots per 64-bit MAC x max SM clock",
+                     "measured_primitive_peak": probe / 1e12,
+                     "kernel": "batch_kernel<4>", "algorithmic_macs_per_launch": macs,
+                     "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_s_vs_hbm": achieved_gbs / pk["hbm_gbs"]},
+        "autotune": {"threads": tuned_threads, "smem_arena_bytes": tuned_smem, "seconds": tune_s},
         "clocks": clk,
         "gpu_launches": kpl * args.steps,
         "plan_s": plan_s,

@@ -123,13 +123,17 @@ typedef struct {
   double total_macs;      /* sum of 2^(a+b-k)                                     */
   double total_entries;   /* sum of 2^a + 2^b + 2^(a+b-2k): entries moved          */
   double log2_bound;      /* log2 of the certified upper bound on every count      */
+  uint64_t arena_entries; /* peak live entries, one launch per step (x 4 bytes x
+                             residues per pass = tnc_contract's tensor arena)       */
+  uint64_t batch_arena_entries; /* same for the level-by-level batch schedule     */
 } tnc_plan_stats;
 
 typedef struct {
   int32_t path;          /* TNC_PATH_*                                           */
   int32_t n_residues;    /* R, 1..16                                             */
-  const uint32_t* primes;/* host, R distinct primes in (2^30, 2^31); NULL = the R
-                            largest primes below 2^31                            */
+  const uint32_t* primes;/* host, R distinct primes in (2^29, 2^31); NULL = the R
+                            largest primes below 2^30 (16 residue products fit a
+                            64-bit accumulator between reductions; 4 near 2^31) */
 } tnc_contract_opts;
 
 /* One formula's result.  Caller-allocated host buffers.
@@ -153,7 +157,8 @@ typedef struct {
 const char* tnc_version(void);
 /* Last error message of the calling thread ("" if none). */
 const char* tnc_last_error(void);
-/* The n largest primes below 2^31, descending (deterministic Miller-Rabin). */
+/* The default primes: the n largest below 2^30, descending (deterministic
+ * Miller-Rabin). */
 int tnc_default_primes(int32_t n, uint32_t* out /* host, n */);
 
 /* ---- network (Sec. 2.1): formula -> COPY + clause tensors, bonds --------- */
@@ -190,7 +195,9 @@ int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* de
                  size_t ws_bytes, void* cuda_stream, tnc_count* out);
 
 /* ---- batches: many formulas in one persistent launch -------------------- */
-/* Packs the plans (host work only).  The plans must outlive the batch. */
+/* Packs the plans into compact descriptors in pinned host memory and picks a
+ * default launch shape for the current device.  The plans must outlive the
+ * batch.  Batch formulas need plan rank <= 24 (TNC_ERR_TOO_LARGE otherwise). */
 int tnc_batch_create(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                      tnc_batch_t** out);
 size_t tnc_batch_workspace_bytes(const tnc_batch_t* b);
@@ -205,6 +212,13 @@ int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, void* cuda_s
  * Requires a prior tnc_batch_upload to the same dev_ws.  The launch sequence is
  * captured once into a CUDA graph per (dev_ws, stream) and replayed. */
 int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream);
+/* Autotuner: times the batch's launch for every CTA size in {64, 128, 256} and
+ * shared-memory arena capacity in {0, 16, 32, 48, 64, 96, 128, 200} KiB (capped
+ * at the largest formula's arena), keeps the fastest and reports it.  Needs a
+ * prior tnc_batch_upload to dev_ws; leaves the results of the last trial in
+ * dev_ws; synchronises the stream.  Either out pointer may be NULL. */
+int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t* threads_out,
+                       int32_t* smem_bytes_out);
 /* Device -> host copy of the results; synchronises the stream.  outs: n counts. */
 int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs);
 /* Status word of the last launch (0, or TNC_ERR_TIMEOUT if a bounded device
@@ -215,6 +229,14 @@ void tnc_free_batch(tnc_batch_t* b);
 /* Upload + launch + download in one call. */
 int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                        void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* outs);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/* Measured rate of the modular multiply-accumulate primitive of the step
+ * kernels (4 residues per thread, 64-bit accumulation, Barrett reduction every
+ * fourth product), operands in registers, all SMs busy: a ceiling for steps
+ * bound by the integer pipes.  `iters` loop trips per thread (16 MACs each).
+ * Allocates an 8-byte device counter with cudaMallocAsync; synchronises. */
+int tnc_probe_modmac(void* cuda_stream, int32_t iters, double* macs_per_s);
 
 /* ---- allocation-free variant (the paper has no counterpart) --------------
  * Same counts as tnc_contract, for callers that cannot allocate device memory

@@ -21,7 +21,7 @@ const char* tnc_last_error(void) { return last_error_cstr(); }
 int tnc_default_primes(int32_t n, uint32_t* out) {
   clear_error();
   if (n < 0 || n > 64 || (n > 0 && !out)) return set_error(TNC_ERR_INVALID, "n must be in [0, 64]");
-  std::vector<uint32_t> p = largest_primes_below_2_31(n);
+  std::vector<uint32_t> p = default_primes(n);
   std::copy(p.begin(), p.end(), out);
   return TNC_OK;
 }
@@ -90,6 +90,8 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
     s.total_macs = p->cost.macs;
     s.total_entries = p->cost.entries;
     s.log2_bound = p->net.log2_bound;
+    s.arena_entries = p->low.seq_arena_entries;
+    s.batch_arena_entries = p->low.lvl_arena_entries;
     if (stats) *stats = s;
     *out = p;
     return TNC_OK;

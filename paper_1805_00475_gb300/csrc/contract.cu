@@ -16,7 +16,6 @@
 using namespace tnc;
 using tnc_dev::BatchArgs;
 using tnc_dev::CrtConsts;
-using tnc_dev::FormDesc;
 using tnc_dev::ModGroup;
 using tnc_dev::RootMap;
 
@@ -67,6 +66,20 @@ Groups split_groups(int R) {
   return g;
 }
 
+// Largest power of two n (<= 16) with n (p-1)^2 + p < 2^64 for every prime of
+// the group: the number of products a 64-bit accumulator takes between
+// reductions.
+uint32_t red_mask_for(const uint32_t* p, int n) {
+  uint32_t best = 16;
+  for (int i = 0; i < n; i++) {
+    const unsigned __int128 sq = (unsigned __int128)(p[i] - 1) * (p[i] - 1);
+    uint32_t m = 16;
+    while (m > 1 && (unsigned __int128)m * sq + p[i] >= ((unsigned __int128)1 << 64)) m >>= 1;
+    best = std::min(best, m);
+  }
+  return best - 1;
+}
+
 struct Arith {
   int R = 0;
   std::vector<uint32_t> primes;
@@ -80,6 +93,7 @@ struct Arith {
       m.p[r] = p;
       m.mu[r] = ~0ull / p;
     }
+    m.red_mask = red_mask_for(m.p, 4);
     return m;
   }
 };
@@ -93,13 +107,13 @@ int make_arith(const tnc_contract_opts* o, Arith& a) {
     a.primes.assign(o->primes, o->primes + a.R);
     for (int i = 0; i < a.R; i++) {
       uint32_t p = a.primes[i];
-      if (p <= (1u << 30) || p >= (1u << 31) || !is_prime_u32(p))
-        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^30, 2^31)");
+      if (p <= (1u << 29) || p >= (1u << 31) || !is_prime_u32(p))
+        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^29, 2^31)");
       for (int j = 0; j < i; j++)
         if (a.primes[j] == p) return set_error(TNC_ERR_INVALID, "primes must be distinct");
     }
   } else {
-    a.primes = largest_primes_below_2_31(a.R);
+    a.primes = default_primes(a.R);
   }
   a.crt = CrtConsts{};
   a.crt.R = a.R;
@@ -306,53 +320,88 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
 
 // ======================================================================= batch
 
+using tnc_dev::BForm;
+using tnc_dev::BLeaf;
+using tnc_dev::BStep;
+using tnc_dev::Seg;
+
 struct tnc_batch_s {
   std::vector<const tnc_plan_t*> plans;
   Arith a;
-  // packed descriptors (host staging, same layout as the workspace prefix)
-  std::vector<char> staging;
-  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_lvl = 0, off_leaves = 0, off_tables = 0, off_perms = 0,
-         off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0, total = 0;
-  size_t desc_bytes = 0;  // bytes uploaded from staging (from off_forms)
+  // packed descriptors (host staging in pinned memory, same layout as the
+  // workspace prefix starting at off_forms)
+  char* staging = nullptr;
+  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_runs = 0, off_segs = 0, off_lvl = 0, off_leaves = 0,
+         off_tables = 0, off_perms = 0, off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0, total = 0;
+  size_t desc_bytes = 0;
   uint32_t n_forms = 0;
   uint64_t total_out = 0;
-  std::vector<uint64_t> res_off;  // per formula
-  uint64_t max_arena = 0;         // entries
-  int threads = 256;
-  std::vector<int> grid, smem_mode;
-  std::vector<size_t> smem_bytes;
-  uint64_t arena_stride = 0;
+  std::vector<uint64_t> res_off;
+  uint64_t max_arena = 0;    // entries
+  uint64_t garena_entries = 0;
+  // launch configuration (autotuned)
+  int threads = 128;
+  size_t smem_bytes = 0;     // dynamic shared memory for arenas (per CTA)
+  std::vector<int> grid;     // per residue group
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   void* g_ws = nullptr;
   cudaStream_t g_stream = nullptr;
   ~tnc_batch_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (staging) cudaFreeHost(staging);
   }
 };
 
 namespace {
 
-constexpr size_t kSmemArenaMax = 100 * 1024;
+constexpr size_t kSmemMax = 200 * 1024;
 
 template <int RG>
 int occupancy(int threads, size_t smem, int* blocks) {
-  if (smem > 48 * 1024)
-    CUDA_TRY(cudaFuncSetAttribute(tnc_dev::batch_kernel<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(cudaFuncSetAttribute(tnc_dev::batch_kernel<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)std::max<size_t>(smem, 1)));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tnc_dev::batch_kernel<RG>, threads, smem));
   return TNC_OK;
 }
 
+// Launch shape for (threads, smem) on every residue group.
+int batch_configure(tnc_batch_t* b, int threads, size_t smem) {
+  const int sms = sm_count();
+  std::vector<int> grid;
+  for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
+    int occ = 0;
+    int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
+      return occupancy<decltype(rgc)::value>(threads, smem, &occ);
+    });
+    if (rc) return rc;
+    if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
+    grid.push_back(std::max(1, std::min<int>(sms * occ, (int)b->n_forms)));
+  }
+  b->threads = threads;
+  b->smem_bytes = smem;
+  b->grid = grid;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return TNC_OK;
+}
+
+uint16_t pack_run(int src, int dst, int len) { return (uint16_t)(src | (dst << 5) | (len << 10)); }
+
 int batch_pack(tnc_batch_t* b) {
   const uint32_t n = b->n_forms;
-  std::vector<FormDesc> forms(n);
-  std::vector<StepDesc> steps;
+  std::vector<BForm> forms(n);
+  std::vector<BStep> steps;
+  std::vector<uint16_t> runs;
+  std::vector<Seg> segs;
   std::vector<uint32_t> lvl;
-  std::vector<LeafDesc> leaves;
+  std::vector<BLeaf> leaves;
   std::vector<uint32_t> tables;
   std::vector<uint8_t> perms;
   b->res_off.assign(n, 0);
-  uint64_t out = 0;
+  uint64_t out = 0, gbase = 0;
   b->max_arena = 8;
   for (uint32_t i = 0; i < n; i++) {
     const tnc_plan_t* p = b->plans[i];
@@ -360,9 +409,11 @@ int batch_pack(tnc_batch_t* b) {
     if (p->cost.max_rank > 24 || !p->low.lvl_fits)
       return set_error(TNC_ERR_TOO_LARGE, "batch formulas must have plan rank <= 24");
     const Lowered& lw = p->low;
-    FormDesc& f = forms[i];
+    if (lw.lvl_arena_entries >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "formula arena above 2^32 entries");
+    BForm& f = forms[i];
     std::memset(&f, 0, sizeof(f));
     f.step0 = (uint32_t)steps.size();
+    f.seg0 = (uint32_t)segs.size();
     f.lvl0 = (uint32_t)lvl.size();
     f.nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
     f.leaf0 = (uint32_t)leaves.size();
@@ -371,120 +422,147 @@ int batch_pack(tnc_batch_t* b) {
     f.n_open = (uint32_t)p->net.open_vars.size();
     f.n_out = 1u << f.n_open;
     f.perm_off = (uint32_t)perms.size();
-    f.root_off = lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off;
+    f.root_off = (uint32_t)(lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off);
+    f.arena = (uint32_t)lw.lvl_arena_entries;
+    f.gbase = gbase;
+    gbase += (lw.lvl_arena_entries + 7) / 8 * 8;
     b->res_off[i] = out;
     out += f.n_out;
-    steps.insert(steps.end(), lw.lvl_steps.begin(), lw.lvl_steps.end());
-    lvl.insert(lvl.end(), lw.lvl_start.begin(), lw.lvl_start.end());
-    if (lw.lvl_start.empty()) lvl.push_back(0);
+    // steps, runs and segments, level by level
+    for (size_t si = 0; si < lw.lvl_steps.size(); si++) {
+      const StepDesc& d = lw.lvl_steps[si];
+      BStep bs;
+      std::memset(&bs, 0, sizeof(bs));
+      bs.a_off = (uint32_t)d.a_off;
+      bs.b_off = (uint32_t)d.b_off;
+      bs.c_off = (uint32_t)d.c_off;
+      bs.c = d.c;
+      bs.k = d.k;
+      bs.ka = d.ka;
+      bs.kb = d.kb;
+      bs.run0 = (uint32_t)runs.size();
+      if (d.nra != TNC_BITMAP) {
+        for (int r = 0; r < d.nra; r++) runs.push_back(pack_run(d.map.runs.ra[r].src, d.map.runs.ra[r].dst, d.map.runs.ra[r].len));
+        for (int r = 0; r < d.nrb; r++) runs.push_back(pack_run(d.map.runs.rb[r].src, d.map.runs.rb[r].dst, d.map.runs.rb[r].len));
+        bs.nra = d.nra;
+        bs.nrb = d.nrb;
+      } else {
+        for (int side = 0; side < 2; side++)
+          for (int j = 0; j < d.c; j++)
+            if ((d.map.bit[j] >> 7) == side) {
+              runs.push_back(pack_run(j, d.map.bit[j] & 63, 1));
+              (side ? bs.nrb : bs.nra)++;
+            }
+      }
+      steps.push_back(bs);
+    }
+    lvl.push_back(0);
+    for (uint32_t l = 0; l < f.nlev; l++) {
+      for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
+        const uint32_t nout = 1u << lw.lvl_steps[si].c;
+        for (uint32_t o0 = 0; o0 < nout; o0 += 32) {
+          Seg sg;
+          sg.o0 = o0;
+          sg.step = (uint16_t)si;
+          sg.n = (uint16_t)std::min<uint32_t>(32, nout - o0);
+          segs.push_back(sg);
+        }
+      }
+      lvl.push_back((uint32_t)(segs.size() - f.seg0));
+    }
+    if (lw.lvl_steps.size() > 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65535 steps in one formula");
     const uint32_t toff = (uint32_t)tables.size();
     for (size_t l = 0; l < lw.leaves.size(); l++) {
-      LeafDesc d = lw.leaves[l];
-      d.off = lw.lvl_leaf_off[l];
-      d.table_off += toff;
-      leaves.push_back(d);
+      BLeaf bl;
+      std::memset(&bl, 0, sizeof(bl));
+      bl.off = (uint32_t)lw.lvl_leaf_off[l];
+      bl.table_off = lw.leaves[l].table_off + toff;
+      bl.kind = lw.leaves[l].kind;
+      bl.rank = lw.leaves[l].rank;
+      leaves.push_back(bl);
     }
     tables.insert(tables.end(), lw.leaf_tables.begin(), lw.leaf_tables.end());
     perms.insert(perms.end(), lw.root_perm.begin(), lw.root_perm.end());
     b->max_arena = std::max<uint64_t>(b->max_arena, lw.lvl_arena_entries);
   }
   b->total_out = out;
+  b->garena_entries = gbase;
   // largest formulas first (longest-processing-time order)
   std::vector<uint32_t> order(n);
   for (uint32_t i = 0; i < n; i++) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
     return b->plans[x]->cost.macs + b->plans[x]->cost.entries > b->plans[y]->cost.macs + b->plans[y]->cost.entries;
   });
-  // launch shapes per residue group
-  const int sms = sm_count();
-  b->grid.clear();
-  b->smem_mode.clear();
-  b->smem_bytes.clear();
-  b->arena_stride = (b->max_arena + 7) / 8 * 8;
-  int max_grid_global = 0;
-  for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
-    const int rg = b->a.groups.rg[gi];
-    const size_t bytes = b->max_arena * rg * sizeof(uint32_t);
-    const int smem = bytes <= kSmemArenaMax;
-    int occ = 0;
-    int rc = dispatch_rg(rg, [&](auto rgc) -> int {
-      return occupancy<decltype(rgc)::value>(b->threads, smem ? bytes : 0, &occ);
-    });
-    if (rc) return rc;
-    if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
-    int g = std::min<int>(sms * occ, (int)n);
-    b->grid.push_back(std::max(g, 1));
-    b->smem_mode.push_back(smem);
-    b->smem_bytes.push_back(smem ? bytes : 0);
-    if (!smem) max_grid_global = std::max(max_grid_global, g * rg);
-  }
+  const int rg_max = b->a.groups.rg.empty() ? 1 : b->a.groups.rg[0];
   // workspace layout
   size_t o = 0;
-  b->off_queue = o;
-  o = align_up(o + 64 * sizeof(uint32_t));
-  b->off_forms = o;
-  o = align_up(o + forms.size() * sizeof(FormDesc));
-  b->off_steps = o;
-  o = align_up(o + steps.size() * sizeof(StepDesc));
-  b->off_lvl = o;
-  o = align_up(o + lvl.size() * sizeof(uint32_t));
-  b->off_leaves = o;
-  o = align_up(o + leaves.size() * sizeof(LeafDesc));
-  b->off_tables = o;
-  o = align_up(o + tables.size() * sizeof(uint32_t));
-  b->off_perms = o;
-  o = align_up(o + perms.size());
-  b->off_order = o;
-  o = align_up(o + order.size() * sizeof(uint32_t));
+  auto sect = [&](size_t& off, size_t bytes) {
+    off = o;
+    o = align_up(o + bytes);
+  };
+  sect(b->off_queue, 64 * sizeof(uint32_t));
+  sect(b->off_forms, forms.size() * sizeof(BForm));
+  sect(b->off_steps, steps.size() * sizeof(BStep));
+  sect(b->off_runs, runs.size() * sizeof(uint16_t));
+  sect(b->off_segs, segs.size() * sizeof(Seg));
+  sect(b->off_lvl, lvl.size() * sizeof(uint32_t));
+  sect(b->off_leaves, leaves.size() * sizeof(BLeaf));
+  sect(b->off_tables, tables.size() * sizeof(uint32_t));
+  sect(b->off_perms, perms.size());
+  sect(b->off_order, order.size() * sizeof(uint32_t));
   b->desc_bytes = o - b->off_forms;
-  b->off_results = o;
-  o = align_up(o + out * b->a.R * sizeof(uint32_t));
-  b->off_limbs = o;
-  o = align_up(o + out * b->a.crt.n_limbs * sizeof(uint32_t));
-  b->off_arena = o;
-  o = align_up(o + (size_t)max_grid_global * b->arena_stride * sizeof(uint32_t));
+  sect(b->off_results, out * b->a.R * sizeof(uint32_t));
+  sect(b->off_limbs, out * b->a.crt.n_limbs * sizeof(uint32_t));
+  sect(b->off_arena, (size_t)gbase * rg_max * sizeof(uint32_t));
   b->total = o;
-  b->staging.assign(b->desc_bytes, 0);
-  char* s = b->staging.data() - b->off_forms;
+  CUDA_TRY(cudaMallocHost((void**)&b->staging, std::max<size_t>(b->desc_bytes, 1)));
+  std::memset(b->staging, 0, b->desc_bytes);
+  char* s = b->staging - b->off_forms;
   auto put = [&](size_t off, const void* src, size_t bytes) {
     if (bytes) std::memcpy(s + off, src, bytes);
   };
-  put(b->off_forms, forms.data(), forms.size() * sizeof(FormDesc));
-  put(b->off_steps, steps.data(), steps.size() * sizeof(StepDesc));
+  put(b->off_forms, forms.data(), forms.size() * sizeof(BForm));
+  put(b->off_steps, steps.data(), steps.size() * sizeof(BStep));
+  put(b->off_runs, runs.data(), runs.size() * sizeof(uint16_t));
+  put(b->off_segs, segs.data(), segs.size() * sizeof(Seg));
   put(b->off_lvl, lvl.data(), lvl.size() * sizeof(uint32_t));
-  put(b->off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc));
+  put(b->off_leaves, leaves.data(), leaves.size() * sizeof(BLeaf));
   put(b->off_tables, tables.data(), tables.size() * sizeof(uint32_t));
   put(b->off_perms, perms.data(), perms.size());
   put(b->off_order, order.data(), order.size() * sizeof(uint32_t));
-  return TNC_OK;
+  // default launch shape: 128 threads, shared-memory arenas up to 64 KiB
+  return batch_configure(b, 128, std::min<size_t>(64 * 1024, b->max_arena * rg_max * sizeof(uint32_t)));
 }
 
 int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
   char* ws = (char*)dev_ws;
   CUDA_TRY(cudaMemsetAsync(ws + b->off_queue, 0, 64 * sizeof(uint32_t), st));
   for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
+    const int rg = b->a.groups.rg[gi];
     BatchArgs args{};
-    args.forms = (const FormDesc*)(ws + b->off_forms);
-    args.steps = (const StepDesc*)(ws + b->off_steps);
-    args.lvl_start = (const uint32_t*)(ws + b->off_lvl);
-    args.leaves = (const LeafDesc*)(ws + b->off_leaves);
+    args.forms = (const BForm*)(ws + b->off_forms);
+    args.steps = (const BStep*)(ws + b->off_steps);
+    args.runs = (const uint16_t*)(ws + b->off_runs);
+    args.segs = (const Seg*)(ws + b->off_segs);
+    args.lvl = (const uint32_t*)(ws + b->off_lvl);
+    args.leaves = (const BLeaf*)(ws + b->off_leaves);
     args.tables = (const uint32_t*)(ws + b->off_tables);
     args.perms = (const uint8_t*)(ws + b->off_perms);
     args.order = (const uint32_t*)(ws + b->off_order);
     args.n_forms = b->n_forms;
     args.queue = (uint32_t*)(ws + b->off_queue) + gi;
     args.results = (uint32_t*)(ws + b->off_results);
-    args.arena = (uint32_t*)(ws + b->off_arena);
-    args.arena_stride = b->arena_stride;
+    args.garena = (uint32_t*)(ws + b->off_arena);
+    args.smem_cap = (uint32_t)(b->smem_bytes / (rg * sizeof(uint32_t)));
     args.R = b->a.R;
     args.col = b->a.groups.col[gi];
-    args.smem_arena = b->smem_mode[gi];
     const ModGroup mg = b->a.group((int)gi);
     const int grid = b->grid[gi];
-    const size_t smem = b->smem_bytes[gi];
-    int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
+    const size_t smem = b->smem_bytes;
+    const int threads = b->threads;
+    int rc = dispatch_rg(rg, [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
-      tnc_dev::batch_kernel<RG><<<grid, b->threads, smem, st>>>(args, mg);
+      tnc_dev::batch_kernel<RG><<<grid, threads, smem, st>>>(args, mg);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });
@@ -544,7 +622,7 @@ extern "C" int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, v
   if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
   if (ws_bytes < b->total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_batch_workspace_bytes");
   if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
-  CUDA_TRY(cudaMemcpyAsync((char*)dev_ws + b->off_forms, b->staging.data(), b->desc_bytes, cudaMemcpyHostToDevice,
+  CUDA_TRY(cudaMemcpyAsync((char*)dev_ws + b->off_forms, b->staging, b->desc_bytes, cudaMemcpyHostToDevice,
                            (cudaStream_t)cuda_stream));
   return TNC_OK;
 }
@@ -579,6 +657,61 @@ extern "C" int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream)
   }
   CUDA_TRY(cudaGraphLaunch(b->gexec, st));
   return TNC_OK;
+}
+
+extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t* threads_out,
+                                  int32_t* smem_out) {
+  clear_error();
+  if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int rg_max = b->a.groups.rg.empty() ? 1 : b->a.groups.rg[0];
+  const size_t need = b->max_arena * rg_max * sizeof(uint32_t);
+  std::vector<size_t> smems{0};
+  for (size_t s : {16u << 10, 32u << 10, 48u << 10, 64u << 10, 96u << 10, 128u << 10, 200u << 10})
+    if (s <= kSmemMax) smems.push_back(std::min(s, need));
+  std::sort(smems.begin(), smems.end());
+  smems.erase(std::unique(smems.begin(), smems.end()), smems.end());
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_t = b->threads;
+  size_t best_s = b->smem_bytes;
+  int rc = TNC_OK;
+  for (int threads : {64, 128, 256}) {
+    for (size_t sm : smems) {
+      rc = batch_configure(b, threads, sm);
+      if (rc == TNC_ERR_TOO_LARGE) {
+        rc = TNC_OK;
+        continue;
+      }
+      if (rc) break;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && !rc; rep++) {
+        cudaEventRecord(e0, st);
+        rc = batch_enqueue(b, dev_ws, st);
+        cudaEventRecord(e1, st);
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(TNC_ERR_CUDA, "autotune launch failed");
+        float t = 0;
+        if (!rc) cudaEventElapsedTime(&t, e0, e1);
+        if (rep == 1) ms = t;
+      }
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        best_t = threads;
+        best_s = sm;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  rc = batch_configure(b, best_t, best_s);
+  if (threads_out) *threads_out = best_t;
+  if (smem_out) *smem_out = (int32_t)best_s;
+  return rc;
 }
 
 extern "C" int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs) {
@@ -672,15 +805,15 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
   if (opts->primes) {
     for (int i = 0; i < R; i++) {
       const uint32_t p = opts->primes[i];
-      if (p <= (1u << 30) || p >= (1u << 31) || !is_prime_u32(p))
-        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^30, 2^31)");
+      if (p <= (1u << 29) || p >= (1u << 31) || !is_prime_u32(p))
+        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^29, 2^31)");
       for (int j = 0; j < i; j++)
         if (primes[j] == p) return set_error(TNC_ERR_INVALID, "primes must be distinct");
       primes[i] = p;
     }
   } else {
     int n = 0;
-    for (uint32_t x = 2147483647u; n < R; x -= 2)
+    for (uint32_t x = kDefaultPrimeBound - 1; n < R; x -= 2)
       if (is_prime_u32(x)) primes[n++] = x;
   }
   CrtConsts cc{};
@@ -778,6 +911,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
       mg.p[r] = p;
       mg.mu[r] = ~0ull / p;
     }
+    mg.red_mask = red_mask_for(mg.p, 4);
     rc = dispatch_rg(grp_rg[gi], [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
       tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(

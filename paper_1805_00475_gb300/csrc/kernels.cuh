@@ -4,27 +4,10 @@
 
 #include <cstdint>
 
+#include "modarith.cuh"
 #include "step_desc.h"
 
 namespace tnc_dev {
-
-// One residue group: RG <= 4 primes processed together; an entry of a tensor
-// holds RG u32 residues side by side (16 bytes for RG = 4).
-struct ModGroup {
-  uint32_t p[4];
-  uint64_t mu[4];  // floor(2^64 / p), Barrett constant
-};
-
-// x mod p for any 64-bit x (Barrett reduction with mu = floor(2^64/p):
-// the quotient estimate is at most one short, so one correction suffices;
-// a second one is kept as a margin).
-__device__ __forceinline__ uint32_t mod_reduce(uint64_t x, uint32_t p, uint64_t mu) {
-  const uint64_t q = __umul64hi(x, mu);
-  uint64_t r = x - q * (uint64_t)p;
-  if (r >= p) r -= p;
-  if (r >= p) r -= p;
-  return (uint32_t)r;
-}
 
 template <int RG>
 __device__ __forceinline__ void load_entry(const uint32_t* src, uint32_t (&v)[RG]) {
@@ -89,9 +72,9 @@ __device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uin
 }
 
 // One output entry of a pairwise step: the sum over the 2^k shared-bond
-// values of A*B, for every residue of the group.  Products of residues below
-// 2^31 are below 2^62, so four of them plus a reduced partial sum fit in 64
-// bits: reduce after every fourth product.
+// values of A*B, for every residue of the group.  A product of residues is
+// below (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64
+// bits: reduce after every (red_mask+1)-th product and once at the end.
 template <int RG>
 __device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
                                               uint64_t ib, const uint32_t* A0, const uint32_t* B0, uint32_t* C0,
@@ -113,10 +96,12 @@ __device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t 
 #pragma unroll
       for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     }
+    if (((q + 4) & mg.red_mask) == 0) {
 #pragma unroll
-    for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+    }
   }
-  for (; q < K; q++) {
+  for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
     uint32_t va[RG], vb[RG];
     load_entry<RG>(A + (uint64_t)q * sa, va);
     load_entry<RG>(B + (uint64_t)q * sb, vb);
@@ -264,51 +249,88 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
 
 // ------------------------------------------------------- persistent batch
 
-struct FormDesc {
-  uint32_t step0, lvl0, nlev, leaf0;
-  uint32_t nleaf, res_off, n_out, perm_off;
-  uint64_t root_off;
-  uint32_t n_open, pad;
+// Packed batch descriptors.  Offsets of a formula's tensors are relative to
+// its own arena; bit maps are runs in a shared pool (u16: src | dst << 5 |
+// len << 10).
+struct BStep {
+  uint32_t a_off, b_off, c_off;
+  uint32_t run0;  // first run of A's map; B's map follows
+  uint8_t c, k, ka, kb;
+  uint8_t nra, nrb, pad0, pad1;
+};
+
+// 32 consecutive output entries of one step (fewer for small steps): the unit
+// of work of one warp.
+struct Seg {
+  uint32_t o0;
+  uint16_t step;  // formula-relative
+  uint16_t n;     // active lanes, 1..32
+};
+
+struct BLeaf {
+  uint32_t off;
+  uint32_t table_off;
+  uint8_t kind, rank, pad0, pad1;
+};
+
+struct BForm {
+  uint32_t step0, seg0, lvl0, nlev;
+  uint32_t leaf0, nleaf, res_off, n_out;
+  uint32_t perm_off, n_open, root_off, arena;  // arena: entries this formula needs
+  uint64_t gbase;                              // first entry of its global arena
 };
 
 struct BatchArgs {
-  const FormDesc* forms;
-  const StepDesc* steps;
-  const uint32_t* lvl_start;
-  const LeafDesc* leaves;
+  const BForm* forms;
+  const BStep* steps;
+  const uint16_t* runs;
+  const Seg* segs;
+  const uint32_t* lvl;    // per formula: nlev + 1 formula-relative segment offsets
+  const BLeaf* leaves;
   const uint32_t* tables;
   const uint8_t* perms;
   const uint32_t* order;  // queue slot -> formula (largest first)
   uint32_t n_forms;
   uint32_t* queue;        // work counter, zeroed before the launch
   uint32_t* results;      // [entry][R]
-  uint32_t* arena;        // global arenas (when not in shared memory)
-  uint64_t arena_stride;  // entries per CTA
+  uint32_t* garena;       // global arenas, one region per formula
+  uint32_t smem_cap;      // entries of dynamic shared memory available for an arena
   int R;
   int col;                // first residue column of this group
-  int smem_arena;         // 1: arena in dynamic shared memory
 };
 
+__device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, int n) {
+  uint32_t a = 0;
+  for (int i = 0; i < n; i++) {
+    const uint32_t r = runs[i];
+    const uint32_t src = r & 31u, dst = (r >> 5) & 31u, len = r >> 10;
+    a |= ((o >> src) & ((1u << len) - 1u)) << dst;
+  }
+  return a;
+}
+
 // Each CTA repeatedly takes the next formula from the queue and contracts it
-// alone, level by level: all steps of one tree level are independent, so the
-// CTA's threads share the level's output entries (found by binary search over
-// the per-step work offsets) and synchronise once per level.
+// alone, tree level by tree level: all steps of a level are independent, so
+// the level is a list of 32-entry segments shared out over the CTA's warps
+// (step lookup and bit-map decode are warp-uniform), with one barrier per
+// level.  The formula's tensors live in shared memory when its arena fits,
+// else in its own region of global memory.
 template <int RG>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
-  uint32_t* arena = a.smem_arena ? reinterpret_cast<uint32_t*>(smem_raw)
-                                 : a.arena + (uint64_t)blockIdx.x * a.arena_stride * RG;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) task = atomicAdd(a.queue, 1u);
     __syncthreads();
     const uint32_t t = task;
     __syncthreads();
     if (t >= a.n_forms) break;
-    const FormDesc f = a.forms[a.order[t]];
+    const BForm f = a.forms[a.order[t]];
+    uint32_t* arena = f.arena <= a.smem_cap ? reinterpret_cast<uint32_t*>(smem_raw) : a.garena + f.gbase * RG;
     for (uint32_t l = threadIdx.x; l < f.nleaf; l += blockDim.x) {
-      const LeafDesc ld = a.leaves[f.leaf0 + l];
-      uint32_t* dst = arena + ld.off * RG;
+      const BLeaf ld = a.leaves[f.leaf0 + l];
+      uint32_t* dst = arena + (uint64_t)ld.off * RG;
       const uint32_t n = 1u << ld.rank;
       for (uint32_t idx = 0; idx < n; idx++) {
         uint32_t v[RG];
@@ -318,28 +340,29 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       }
     }
     __syncthreads();
+    const uint32_t* lvl = a.lvl + f.lvl0;
     for (uint32_t l = 0; l < f.nlev; l++) {
-      const uint32_t s0 = f.step0 + a.lvl_start[f.lvl0 + l];
-      const uint32_t s1 = f.step0 + a.lvl_start[f.lvl0 + l + 1];
-      const uint32_t total = a.steps[s1 - 1].work_lo + (1u << a.steps[s1 - 1].c);
-      for (uint32_t w = threadIdx.x; w < total; w += blockDim.x) {
-        uint32_t lo = s0, hi = s1 - 1;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (a.steps[mid].work_lo <= w) lo = mid;
-          else hi = mid - 1;
+      const uint32_t s1 = f.seg0 + lvl[l + 1];
+      for (uint32_t sg = f.seg0 + lvl[l] + warp; sg < s1; sg += nwarps) {
+        const Seg seg = a.segs[sg];
+        if (lane < seg.n) {
+          const BStep d = a.steps[f.step0 + seg.step];
+          const uint32_t o = seg.o0 + lane;
+          const uint16_t* runs = a.runs + d.run0;
+          const uint32_t ia = map_runs(o, runs, d.nra);
+          const uint32_t ib = map_runs(o, runs + d.nra, d.nrb);
+          step_entry_at<RG>(d.k, d.ka, d.kb, o, ia, ib, arena + (uint64_t)d.a_off * RG,
+                            arena + (uint64_t)d.b_off * RG, arena + (uint64_t)d.c_off * RG, mg);
         }
-        const StepDesc& d = a.steps[lo];
-        step_entry<RG>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
       }
       __syncthreads();
     }
     for (uint32_t J = threadIdx.x; J < f.n_out; J += blockDim.x) {
-      uint64_t ad = 0;
-      for (uint32_t j = 0; j < f.n_open; j++) ad |= (uint64_t)((J >> a.perms[f.perm_off + j]) & 1u) << j;
+      uint32_t ad = 0;
+      for (uint32_t j = 0; j < f.n_open; j++) ad |= ((J >> a.perms[f.perm_off + j]) & 1u) << j;
 #pragma unroll
       for (int r = 0; r < RG; r++)
-        a.results[((uint64_t)f.res_off + J) * a.R + a.col + r] = arena[(f.root_off + ad) * RG + r];
+        a.results[((uint64_t)f.res_off + J) * a.R + a.col + r] = arena[((uint64_t)f.root_off + ad) * RG + r];
     }
     __syncthreads();
   }

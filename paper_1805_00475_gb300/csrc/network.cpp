@@ -63,9 +63,9 @@ bool is_prime_u32(uint32_t n) {
   return true;
 }
 
-std::vector<uint32_t> largest_primes_below_2_31(int n) {
+std::vector<uint32_t> default_primes(int n) {
   std::vector<uint32_t> out;
-  for (uint32_t x = 2147483647u; (int)out.size() < n && x > 2; x -= 2)
+  for (uint32_t x = kDefaultPrimeBound - 1; (int)out.size() < n && x > 2; x -= 2)
     if (is_prime_u32(x)) out.push_back(x);
   return out;
 }

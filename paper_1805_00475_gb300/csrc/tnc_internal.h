@@ -115,7 +115,10 @@ int lower_plan(const Network& net, const Tree& tree, Lowered& low);
 int validate_lowered(const Network& net, const Tree& tree, Lowered& low);
 
 // primes.cpp
-std::vector<uint32_t> largest_primes_below_2_31(int n);
+// Default primes: the largest below 2^30, so that 16 residue products fit a
+// 64-bit accumulator between reductions (4 for primes near 2^31).
+constexpr uint32_t kDefaultPrimeBound = 1u << 30;
+std::vector<uint32_t> default_primes(int n);
 bool is_prime_u32(uint32_t n);
 
 }  // namespace tnc

@@ -32,9 +32,9 @@ TNC_MAYBE_WRAPPED = 1
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_build_network", "tnc_network_info",
     "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes",
-    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload",
+    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_status", "tnc_free_batch",
-    "tnc_contract_batch", "tnc_contract_noalloc",
+    "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -61,7 +61,8 @@ class _PlanOpts(ctypes.Structure):
 class _PlanStats(ctypes.Structure):
     _fields_ = [("max_rank", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("total_macs", ctypes.c_double),
-                ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double)]
+                ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double),
+                ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64)]
 
 
 class _ContractOpts(ctypes.Structure):
@@ -117,11 +118,13 @@ def lib():
                                 i32p], ctypes.c_int),
             "tnc_batch_upload": ([vp, vp, sz, vp], ctypes.c_int),
             "tnc_batch_launch": ([vp, vp, vp], ctypes.c_int),
+            "tnc_batch_autotune": ([vp, vp, vp, i32p, i32p], ctypes.c_int),
             "tnc_batch_download": ([vp, vp, vp, ctypes.POINTER(_Count)], ctypes.c_int),
             "tnc_batch_status": ([vp, vp, vp], ctypes.c_int),
             "tnc_free_batch": ([vp], None),
             "tnc_contract_batch": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), vp, sz, vp,
                                     ctypes.POINTER(_Count)], ctypes.c_int),
+            "tnc_probe_modmac": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_contract_noalloc": ([vp, ctypes.POINTER(_ContractOpts), vp, ctypes.POINTER(_Count)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -200,6 +203,8 @@ class PlanStats:
     total_macs: float
     total_entries: float
     log2_bound: float
+    arena_entries: int = 0
+    batch_arena_entries: int = 0
 
 
 class Plan:
@@ -236,7 +241,7 @@ def plan(network: Network, heuristic: str = "bisect", rank_cap: int = 32, tries:
 
 def _stats(st: _PlanStats) -> PlanStats:
     return PlanStats(st.max_rank, st.n_steps, st.n_leaves, st.depth, st.total_macs, st.total_entries,
-                     st.log2_bound)
+                     st.log2_bound, int(st.arena_entries), int(st.batch_arena_entries))
 
 
 def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0
@@ -327,6 +332,13 @@ def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=N
     return _to_count(c, res, limbs, pr)
 
 
+def probe_modmac(iters: int = 4096, stream=None) -> float:
+    """Measured modular MAC/s of the step kernels' inner primitive (tnc_probe_modmac)."""
+    v = ctypes.c_double()
+    _check(lib().tnc_probe_modmac(_stream_ptr(stream), iters, ctypes.byref(v)))
+    return v.value
+
+
 def contract_noalloc(p: Plan, n_residues: int = 4, primes=None, stream=None, path: str = "int64") -> Count:
     """tnc_contract_noalloc: like contract(), but the device scratch is libtnc's
     own fixed array, so nothing is allocated on the device for the call (for
@@ -370,6 +382,13 @@ class Batch:
 
     def launch(self, ws, stream=None):
         _check(lib().tnc_batch_launch(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+
+    def autotune(self, ws, stream=None) -> Tuple[int, int]:
+        """tnc_batch_autotune: returns (threads per CTA, shared-memory arena bytes)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tnc_batch_autotune(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream),
+                                        ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def download(self, ws, stream=None) -> List[Count]:
         n = len(self.plans)

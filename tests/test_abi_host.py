@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol():
 def test_version_and_primes():
     assert "sm_103a" in tnc.version()
     p = tnc.default_primes(8)
-    assert p[0] == 2 ** 31 - 1 and p == sorted(p, reverse=True) and len(set(p)) == 8
+    assert p[0] == 1073741789 and p == sorted(p, reverse=True) and len(set(p)) == 8  # largest below 2^30
 
     def isprime(n):
         if n < 2:
@@ -52,7 +52,9 @@ def test_version_and_primes():
                 return False
             i += 1
         return True
-    # every odd number between consecutive returned primes is composite
+    # every odd number between 2^30 and p[0], and between consecutive primes, is composite
+    for x in range(p[0] + 2, 2 ** 30, 2):
+        assert not isprime(x)
     for a, b in zip(p, p[1:]):
         assert isprime(a) and isprime(b)
         for x in range(b + 2, a, 2):
