@@ -221,6 +221,12 @@ int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t*
                        int32_t* smem_bytes_out);
 /* Device -> host copy of the results; synchronises the stream.  outs: n counts. */
 int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs);
+/* Bulk form of tnc_batch_download: residues [E][R] and CRT limbs
+ * [E][ceil(31R/32)] of all E result entries (formula after formula, 2^n_open
+ * entries each, in the order the plans were given), and one TNC_* flag word
+ * per formula.  Host buffers; any may be NULL; synchronises the stream. */
+int tnc_batch_download_flat(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, uint32_t* residues,
+                            uint32_t* limbs, uint32_t* flags);
 /* Status word of the last launch (0, or TNC_ERR_TIMEOUT if a bounded device
  * wait gave up); synchronises the stream. */
 int tnc_batch_status(tnc_batch_t* b, const void* dev_ws, void* cuda_stream);

@@ -331,8 +331,9 @@ struct tnc_batch_s {
   // packed descriptors (host staging in pinned memory, same layout as the
   // workspace prefix starting at off_forms)
   char* staging = nullptr;
-  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_runs = 0, off_segs = 0, off_lvl = 0, off_leaves = 0,
-         off_tables = 0, off_perms = 0, off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0, total = 0;
+  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_runs = 0, off_segs = 0, off_lvl = 0, off_items = 0,
+         off_leaves = 0, off_tables = 0, off_perms = 0, off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0,
+         total = 0;
   size_t desc_bytes = 0;
   uint32_t n_forms = 0;
   uint64_t total_out = 0;
@@ -397,6 +398,7 @@ int batch_pack(tnc_batch_t* b) {
   std::vector<uint16_t> runs;
   std::vector<Seg> segs;
   std::vector<uint32_t> lvl;
+  std::vector<uint32_t> items;
   std::vector<BLeaf> leaves;
   std::vector<uint32_t> tables;
   std::vector<uint8_t> perms;
@@ -458,19 +460,33 @@ int batch_pack(tnc_batch_t* b) {
     }
     lvl.push_back(0);
     for (uint32_t l = 0; l < f.nlev; l++) {
+      // steps of 32+ entries: whole-warp segments; smaller ones: packed lanes
+      std::vector<uint32_t> small;
       for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
         const uint32_t nout = 1u << lw.lvl_steps[si].c;
+        if (nout < 32) {
+          for (uint32_t o = 0; o < nout; o++) small.push_back(si | (o << 16));
+          continue;
+        }
         for (uint32_t o0 = 0; o0 < nout; o0 += 32) {
           Seg sg;
           sg.o0 = o0;
           sg.step = (uint16_t)si;
-          sg.n = (uint16_t)std::min<uint32_t>(32, nout - o0);
+          sg.n = 32;
           segs.push_back(sg);
         }
       }
+      for (size_t i0 = 0; i0 < small.size(); i0 += 32) {
+        Seg sg;
+        sg.o0 = (uint32_t)items.size();
+        sg.step = tnc_dev::kPacked;
+        sg.n = (uint16_t)std::min<size_t>(32, small.size() - i0);
+        items.insert(items.end(), small.begin() + i0, small.begin() + i0 + sg.n);
+        segs.push_back(sg);
+      }
       lvl.push_back((uint32_t)(segs.size() - f.seg0));
     }
-    if (lw.lvl_steps.size() > 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65535 steps in one formula");
+    if (lw.lvl_steps.size() >= 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65534 steps in one formula");
     const uint32_t toff = (uint32_t)tables.size();
     for (size_t l = 0; l < lw.leaves.size(); l++) {
       BLeaf bl;
@@ -506,6 +522,7 @@ int batch_pack(tnc_batch_t* b) {
   sect(b->off_runs, runs.size() * sizeof(uint16_t));
   sect(b->off_segs, segs.size() * sizeof(Seg));
   sect(b->off_lvl, lvl.size() * sizeof(uint32_t));
+  sect(b->off_items, items.size() * sizeof(uint32_t));
   sect(b->off_leaves, leaves.size() * sizeof(BLeaf));
   sect(b->off_tables, tables.size() * sizeof(uint32_t));
   sect(b->off_perms, perms.size());
@@ -526,6 +543,7 @@ int batch_pack(tnc_batch_t* b) {
   put(b->off_runs, runs.data(), runs.size() * sizeof(uint16_t));
   put(b->off_segs, segs.data(), segs.size() * sizeof(Seg));
   put(b->off_lvl, lvl.data(), lvl.size() * sizeof(uint32_t));
+  put(b->off_items, items.data(), items.size() * sizeof(uint32_t));
   put(b->off_leaves, leaves.data(), leaves.size() * sizeof(BLeaf));
   put(b->off_tables, tables.data(), tables.size() * sizeof(uint32_t));
   put(b->off_perms, perms.data(), perms.size());
@@ -545,6 +563,7 @@ int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
     args.runs = (const uint16_t*)(ws + b->off_runs);
     args.segs = (const Seg*)(ws + b->off_segs);
     args.lvl = (const uint32_t*)(ws + b->off_lvl);
+    args.items = (const uint32_t*)(ws + b->off_items);
     args.leaves = (const BLeaf*)(ws + b->off_leaves);
     args.tables = (const uint32_t*)(ws + b->off_tables);
     args.perms = (const uint8_t*)(ws + b->off_perms);
@@ -730,6 +749,23 @@ extern "C" int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda
                         limbs.data() + b->res_off[i] * b->a.crt.n_limbs, result_flags(p, b->a));
     if (rc) return rc;
   }
+  return TNC_OK;
+}
+
+extern "C" int tnc_batch_download_flat(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, uint32_t* residues,
+                                       uint32_t* limbs, uint32_t* flags) {
+  clear_error();
+  if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (residues)
+    CUDA_TRY(cudaMemcpyAsync(residues, (const char*)dev_ws + b->off_results, b->total_out * b->a.R * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, st));
+  if (limbs)
+    CUDA_TRY(cudaMemcpyAsync(limbs, (const char*)dev_ws + b->off_limbs,
+                             b->total_out * b->a.crt.n_limbs * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (flags)
+    for (uint32_t i = 0; i < b->n_forms; i++) flags[i] = result_flags(b->plans[i], b->a);
+  CUDA_TRY(cudaStreamSynchronize(st));
   return TNC_OK;
 }
 

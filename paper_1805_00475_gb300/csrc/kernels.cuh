@@ -259,12 +259,16 @@ struct BStep {
   uint8_t nra, nrb, pad0, pad1;
 };
 
-// 32 consecutive output entries of one step (fewer for small steps): the unit
-// of work of one warp.
+// The unit of work of one warp.  Either 32 consecutive output entries of one
+// step (fewer at its end): step = formula-relative index, o0 = first entry;
+// or, for steps of fewer than 32 entries, up to 32 entries of several such
+// steps packed lane by lane: step = kPacked, o0 = first of n items
+// (item = step | entry << 16, formula-relative).
+constexpr uint16_t kPacked = 0xFFFF;
 struct Seg {
   uint32_t o0;
-  uint16_t step;  // formula-relative
-  uint16_t n;     // active lanes, 1..32
+  uint16_t step;
+  uint16_t n;  // active lanes, 1..32
 };
 
 struct BLeaf {
@@ -286,6 +290,7 @@ struct BatchArgs {
   const uint16_t* runs;
   const Seg* segs;
   const uint32_t* lvl;    // per formula: nlev + 1 formula-relative segment offsets
+  const uint32_t* items;  // packed lanes of small steps
   const BLeaf* leaves;
   const uint32_t* tables;
   const uint8_t* perms;
@@ -346,8 +351,13 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       for (uint32_t sg = f.seg0 + lvl[l] + warp; sg < s1; sg += nwarps) {
         const Seg seg = a.segs[sg];
         if (lane < seg.n) {
-          const BStep d = a.steps[f.step0 + seg.step];
-          const uint32_t o = seg.o0 + lane;
+          uint32_t st = seg.step, o = seg.o0 + lane;
+          if (st == kPacked) {
+            const uint32_t it = a.items[o];
+            st = it & 0xFFFFu;
+            o = it >> 16;
+          }
+          const BStep d = a.steps[f.step0 + st];
           const uint16_t* runs = a.runs + d.run0;
           const uint32_t ia = map_runs(o, runs, d.nra);
           const uint32_t ib = map_runs(o, runs + d.nra, d.nrb);

@@ -33,7 +33,7 @@ EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_build_network", "tnc_network_info",
     "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune",
-    "tnc_batch_launch", "tnc_batch_download", "tnc_batch_status", "tnc_free_batch",
+    "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -120,6 +120,7 @@ def lib():
             "tnc_batch_launch": ([vp, vp, vp], ctypes.c_int),
             "tnc_batch_autotune": ([vp, vp, vp, i32p, i32p], ctypes.c_int),
             "tnc_batch_download": ([vp, vp, vp, ctypes.POINTER(_Count)], ctypes.c_int),
+            "tnc_batch_download_flat": ([vp, vp, vp, u32p, u32p, u32p], ctypes.c_int),
             "tnc_batch_status": ([vp, vp, vp], ctypes.c_int),
             "tnc_free_batch": ([vp], None),
             "tnc_contract_batch": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), vp, sz, vp,
@@ -396,6 +397,30 @@ class Batch:
         arr = (_Count * n)(*[b[0] for b in bufs])
         _check(lib().tnc_batch_download(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream), arr))
         return [_to_count(arr[i], bufs[i][1], bufs[i][2], self._pr) for i in range(n)]
+
+    def download_flat(self, ws, stream=None, out=None):
+        """tnc_batch_download_flat into reusable numpy arrays:
+        (residues [E, R], limbs [E, L], flags [n]); entries formula after formula."""
+        _, _, n_entries, _ = self.info()
+        L = (31 * self.R + 31) // 32
+        if out is None:
+            out = (np.empty((n_entries, self.R), dtype=np.uint32), np.empty((n_entries, L), dtype=np.uint32),
+                   np.empty(len(self.plans), dtype=np.uint32))
+        res, limbs, flags = out
+        _check(lib().tnc_batch_download_flat(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream),
+                                             _p(res, ctypes.c_uint32), _p(limbs, ctypes.c_uint32),
+                                             _p(flags, ctypes.c_uint32)))
+        return out
+
+    @staticmethod
+    def counts_from_limbs(limbs: np.ndarray) -> List[int]:
+        out = []
+        for row in limbs:
+            v = 0
+            for x in row[::-1]:
+                v = (v << 32) | int(x)
+            out.append(v)
+        return out
 
     def status(self, ws, stream=None) -> int:
         return int(lib().tnc_batch_status(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))

@@ -129,6 +129,14 @@ def test_batch_matches_oracle_and_replays(R):
         out = b.download(ws, stream)
         for r, z in zip(out, exact):
             _check(r, z, R)
+    res, limbs, flags = b.download_flat(ws, stream)  # bulk form, formula after formula
+    e = 0
+    for f, r, z in zip(forms, out, exact):
+        n = 1 << len(f.open_vars)
+        assert res[e:e + n].tolist() == r.residues.tolist()
+        assert tnc.Batch.counts_from_limbs(limbs[e:e + n]) == r.counts
+        e += n
+    assert e == res.shape[0] and flags.tolist() == [r.flags for r in out]
     ws2 = torch.full_like(ws, 0x5A)  # stale garbage everywhere: results must not depend on it
     b.upload(ws2, stream)
     b.launch(ws2, stream)
