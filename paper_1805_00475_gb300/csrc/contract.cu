@@ -331,18 +331,18 @@ struct tnc_batch_s {
   // packed descriptors (host staging in pinned memory, same layout as the
   // workspace prefix starting at off_forms)
   char* staging = nullptr;
-  size_t off_queue = 0, off_forms = 0, off_steps = 0, off_runs = 0, off_segs = 0, off_lvl = 0, off_items = 0,
-         off_leaves = 0, off_tables = 0, off_perms = 0, off_order = 0, off_results = 0, off_limbs = 0, off_arena = 0,
-         total = 0;
+  size_t off_queue = 0, off_forms = 0, off_blobs = 0, off_leaves = 0, off_tables = 0, off_perms = 0, off_order = 0,
+         off_results = 0, off_limbs = 0, off_arena = 0, total = 0;
   size_t desc_bytes = 0;
   uint32_t n_forms = 0;
   uint64_t total_out = 0;
   std::vector<uint64_t> res_off;
   uint64_t max_arena = 0;    // entries
+  uint64_t max_blob = 0;     // bytes of the largest descriptor blob
   uint64_t garena_entries = 0;
   // launch configuration (autotuned)
   int threads = 128;
-  size_t smem_bytes = 0;     // dynamic shared memory for arenas (per CTA)
+  size_t smem_bytes = 0;     // dynamic shared memory for arenas (per CTA), beyond the blob
   std::vector<int> grid;     // per residue group
   // graph cache
   cudaGraphExec_t gexec = nullptr;
@@ -356,7 +356,7 @@ struct tnc_batch_s {
 
 namespace {
 
-constexpr size_t kSmemMax = 200 * 1024;
+constexpr size_t kSmemMax = 227 * 1024;
 
 template <int RG>
 int occupancy(int threads, size_t smem, int* blocks) {
@@ -373,7 +373,7 @@ int batch_configure(tnc_batch_t* b, int threads, size_t smem) {
   for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
     int occ = 0;
     int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
-      return occupancy<decltype(rgc)::value>(threads, smem, &occ);
+      return occupancy<decltype(rgc)::value>(threads, b->max_blob + smem, &occ);
     });
     if (rc) return rc;
     if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
@@ -391,20 +391,25 @@ int batch_configure(tnc_batch_t* b, int threads, size_t smem) {
 
 uint16_t pack_run(int src, int dst, int len) { return (uint16_t)(src | (dst << 5) | (len << 10)); }
 
+// Appends `bytes` at a 16-byte boundary of the blob; returns the offset.
+size_t blob_put(std::vector<char>& blob, const void* src, size_t bytes) {
+  const size_t at = (blob.size() + 15) / 16 * 16;
+  blob.resize(at + bytes);
+  if (bytes) std::memcpy(blob.data() + at, src, bytes);
+  return at;
+}
+
 int batch_pack(tnc_batch_t* b) {
   const uint32_t n = b->n_forms;
   std::vector<BForm> forms(n);
-  std::vector<BStep> steps;
-  std::vector<uint16_t> runs;
-  std::vector<Seg> segs;
-  std::vector<uint32_t> lvl;
-  std::vector<uint32_t> items;
+  std::vector<char> blobs;  // all formulas' blobs, each 16-byte aligned
   std::vector<BLeaf> leaves;
   std::vector<uint32_t> tables;
   std::vector<uint8_t> perms;
   b->res_off.assign(n, 0);
   uint64_t out = 0, gbase = 0;
   b->max_arena = 8;
+  b->max_blob = 16;
   for (uint32_t i = 0; i < n; i++) {
     const tnc_plan_t* p = b->plans[i];
     if (p->tree.nodes.empty()) return set_error(TNC_ERR_INVALID, "batch formula with an empty network");
@@ -412,27 +417,11 @@ int batch_pack(tnc_batch_t* b) {
       return set_error(TNC_ERR_TOO_LARGE, "batch formulas must have plan rank <= 24");
     const Lowered& lw = p->low;
     if (lw.lvl_arena_entries >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "formula arena above 2^32 entries");
-    BForm& f = forms[i];
-    std::memset(&f, 0, sizeof(f));
-    f.step0 = (uint32_t)steps.size();
-    f.seg0 = (uint32_t)segs.size();
-    f.lvl0 = (uint32_t)lvl.size();
-    f.nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
-    f.leaf0 = (uint32_t)leaves.size();
-    f.nleaf = (uint32_t)lw.leaves.size();
-    f.res_off = (uint32_t)out;
-    f.n_open = (uint32_t)p->net.open_vars.size();
-    f.n_out = 1u << f.n_open;
-    f.perm_off = (uint32_t)perms.size();
-    f.root_off = (uint32_t)(lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off);
-    f.arena = (uint32_t)lw.lvl_arena_entries;
-    f.gbase = gbase;
-    gbase += (lw.lvl_arena_entries + 7) / 8 * 8;
-    b->res_off[i] = out;
-    out += f.n_out;
-    // steps, runs and segments, level by level
-    for (size_t si = 0; si < lw.lvl_steps.size(); si++) {
-      const StepDesc& d = lw.lvl_steps[si];
+    if (lw.lvl_steps.size() >= 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65534 steps in one formula");
+    // steps and runs
+    std::vector<BStep> steps;
+    std::vector<uint16_t> runs;
+    for (const StepDesc& d : lw.lvl_steps) {
       BStep bs;
       std::memset(&bs, 0, sizeof(bs));
       bs.a_off = (uint32_t)d.a_off;
@@ -444,8 +433,10 @@ int batch_pack(tnc_batch_t* b) {
       bs.kb = d.kb;
       bs.run0 = (uint32_t)runs.size();
       if (d.nra != TNC_BITMAP) {
-        for (int r = 0; r < d.nra; r++) runs.push_back(pack_run(d.map.runs.ra[r].src, d.map.runs.ra[r].dst, d.map.runs.ra[r].len));
-        for (int r = 0; r < d.nrb; r++) runs.push_back(pack_run(d.map.runs.rb[r].src, d.map.runs.rb[r].dst, d.map.runs.rb[r].len));
+        for (int r = 0; r < d.nra; r++)
+          runs.push_back(pack_run(d.map.runs.ra[r].src, d.map.runs.ra[r].dst, d.map.runs.ra[r].len));
+        for (int r = 0; r < d.nrb; r++)
+          runs.push_back(pack_run(d.map.runs.rb[r].src, d.map.runs.rb[r].dst, d.map.runs.rb[r].len));
         bs.nra = d.nra;
         bs.nrb = d.nrb;
       } else {
@@ -458,9 +449,12 @@ int batch_pack(tnc_batch_t* b) {
       }
       steps.push_back(bs);
     }
-    lvl.push_back(0);
-    for (uint32_t l = 0; l < f.nlev; l++) {
-      // steps of 32+ entries: whole-warp segments; smaller ones: packed lanes
+    // segments per level: steps of 32+ entries get whole-warp segments, the
+    // smaller ones share packed segments lane by lane
+    std::vector<Seg> segs;
+    std::vector<uint32_t> items, lvl{0};
+    const uint32_t nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
+    for (uint32_t l = 0; l < nlev; l++) {
       std::vector<uint32_t> small;
       for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
         const uint32_t nout = 1u << lw.lvl_steps[si].c;
@@ -468,25 +462,42 @@ int batch_pack(tnc_batch_t* b) {
           for (uint32_t o = 0; o < nout; o++) small.push_back(si | (o << 16));
           continue;
         }
-        for (uint32_t o0 = 0; o0 < nout; o0 += 32) {
-          Seg sg;
-          sg.o0 = o0;
-          sg.step = (uint16_t)si;
-          sg.n = 32;
-          segs.push_back(sg);
-        }
+        for (uint32_t o0 = 0; o0 < nout; o0 += 32) segs.push_back(Seg{o0, (uint16_t)si, 32});
       }
       for (size_t i0 = 0; i0 < small.size(); i0 += 32) {
-        Seg sg;
-        sg.o0 = (uint32_t)items.size();
-        sg.step = tnc_dev::kPacked;
-        sg.n = (uint16_t)std::min<size_t>(32, small.size() - i0);
-        items.insert(items.end(), small.begin() + i0, small.begin() + i0 + sg.n);
-        segs.push_back(sg);
+        const uint16_t cnt = (uint16_t)std::min<size_t>(32, small.size() - i0);
+        segs.push_back(Seg{(uint32_t)items.size(), tnc_dev::kPacked, cnt});
+        items.insert(items.end(), small.begin() + i0, small.begin() + i0 + cnt);
       }
-      lvl.push_back((uint32_t)(segs.size() - f.seg0));
+      lvl.push_back((uint32_t)segs.size());
     }
-    if (lw.lvl_steps.size() >= 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65534 steps in one formula");
+    // the blob
+    std::vector<char> blob;
+    blob_put(blob, steps.data(), steps.size() * sizeof(BStep));
+    BForm& f = forms[i];
+    std::memset(&f, 0, sizeof(f));
+    f.segs_at = (uint32_t)blob_put(blob, segs.data(), segs.size() * sizeof(Seg));
+    f.items_at = (uint32_t)blob_put(blob, items.data(), items.size() * sizeof(uint32_t));
+    f.runs_at = (uint32_t)blob_put(blob, runs.data(), runs.size() * sizeof(uint16_t));
+    f.lvl_at = (uint32_t)blob_put(blob, lvl.data(), lvl.size() * sizeof(uint32_t));
+    blob.resize((blob.size() + 15) / 16 * 16);
+    f.blob = (uint32_t)(blobs.size() / 16);
+    f.blob_n = (uint32_t)(blob.size() / 16);
+    blobs.insert(blobs.end(), blob.begin(), blob.end());
+    b->max_blob = std::max<uint64_t>(b->max_blob, blob.size());
+    f.nlev = nlev;
+    f.leaf0 = (uint32_t)leaves.size();
+    f.nleaf = (uint32_t)lw.leaves.size();
+    f.res_off = (uint32_t)out;
+    f.n_open = (uint32_t)p->net.open_vars.size();
+    f.n_out = 1u << f.n_open;
+    f.perm_off = (uint32_t)perms.size();
+    f.root_off = (uint32_t)(lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off);
+    f.arena = (uint32_t)lw.lvl_arena_entries;
+    f.gbase = gbase;
+    gbase += (lw.lvl_arena_entries + 7) / 8 * 8;
+    b->res_off[i] = out;
+    out += f.n_out;
     const uint32_t toff = (uint32_t)tables.size();
     for (size_t l = 0; l < lw.leaves.size(); l++) {
       BLeaf bl;
@@ -501,6 +512,7 @@ int batch_pack(tnc_batch_t* b) {
     perms.insert(perms.end(), lw.root_perm.begin(), lw.root_perm.end());
     b->max_arena = std::max<uint64_t>(b->max_arena, lw.lvl_arena_entries);
   }
+  if (blobs.size() / 16 >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "batch descriptors above 64 GiB");
   b->total_out = out;
   b->garena_entries = gbase;
   // largest formulas first (longest-processing-time order)
@@ -518,11 +530,7 @@ int batch_pack(tnc_batch_t* b) {
   };
   sect(b->off_queue, 64 * sizeof(uint32_t));
   sect(b->off_forms, forms.size() * sizeof(BForm));
-  sect(b->off_steps, steps.size() * sizeof(BStep));
-  sect(b->off_runs, runs.size() * sizeof(uint16_t));
-  sect(b->off_segs, segs.size() * sizeof(Seg));
-  sect(b->off_lvl, lvl.size() * sizeof(uint32_t));
-  sect(b->off_items, items.size() * sizeof(uint32_t));
+  sect(b->off_blobs, blobs.size());
   sect(b->off_leaves, leaves.size() * sizeof(BLeaf));
   sect(b->off_tables, tables.size() * sizeof(uint32_t));
   sect(b->off_perms, perms.size());
@@ -539,17 +547,15 @@ int batch_pack(tnc_batch_t* b) {
     if (bytes) std::memcpy(s + off, src, bytes);
   };
   put(b->off_forms, forms.data(), forms.size() * sizeof(BForm));
-  put(b->off_steps, steps.data(), steps.size() * sizeof(BStep));
-  put(b->off_runs, runs.data(), runs.size() * sizeof(uint16_t));
-  put(b->off_segs, segs.data(), segs.size() * sizeof(Seg));
-  put(b->off_lvl, lvl.data(), lvl.size() * sizeof(uint32_t));
-  put(b->off_items, items.data(), items.size() * sizeof(uint32_t));
+  put(b->off_blobs, blobs.data(), blobs.size());
   put(b->off_leaves, leaves.data(), leaves.size() * sizeof(BLeaf));
   put(b->off_tables, tables.data(), tables.size() * sizeof(uint32_t));
   put(b->off_perms, perms.data(), perms.size());
   put(b->off_order, order.data(), order.size() * sizeof(uint32_t));
   // default launch shape: 128 threads, shared-memory arenas up to 64 KiB
-  return batch_configure(b, 128, std::min<size_t>(64 * 1024, b->max_arena * rg_max * sizeof(uint32_t)));
+  if (b->max_blob > kSmemMax) return set_error(TNC_ERR_TOO_LARGE, "a formula's descriptors exceed shared memory");
+  return batch_configure(b, 128, std::min<size_t>(std::min<size_t>(64 * 1024, kSmemMax - b->max_blob),
+                                                  b->max_arena * rg_max * sizeof(uint32_t)));
 }
 
 int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
@@ -559,11 +565,7 @@ int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
     const int rg = b->a.groups.rg[gi];
     BatchArgs args{};
     args.forms = (const BForm*)(ws + b->off_forms);
-    args.steps = (const BStep*)(ws + b->off_steps);
-    args.runs = (const uint16_t*)(ws + b->off_runs);
-    args.segs = (const Seg*)(ws + b->off_segs);
-    args.lvl = (const uint32_t*)(ws + b->off_lvl);
-    args.items = (const uint32_t*)(ws + b->off_items);
+    args.blobs = (const uint4*)(ws + b->off_blobs);
     args.leaves = (const BLeaf*)(ws + b->off_leaves);
     args.tables = (const uint32_t*)(ws + b->off_tables);
     args.perms = (const uint8_t*)(ws + b->off_perms);
@@ -572,12 +574,13 @@ int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
     args.queue = (uint32_t*)(ws + b->off_queue) + gi;
     args.results = (uint32_t*)(ws + b->off_results);
     args.garena = (uint32_t*)(ws + b->off_arena);
+    args.blob_cap = (uint32_t)b->max_blob;
     args.smem_cap = (uint32_t)(b->smem_bytes / (rg * sizeof(uint32_t)));
     args.R = b->a.R;
     args.col = b->a.groups.col[gi];
     const ModGroup mg = b->a.group((int)gi);
     const int grid = b->grid[gi];
-    const size_t smem = b->smem_bytes;
+    const size_t smem = b->max_blob + b->smem_bytes;
     const int threads = b->threads;
     int rc = dispatch_rg(rg, [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
@@ -686,8 +689,8 @@ extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_strea
   const int rg_max = b->a.groups.rg.empty() ? 1 : b->a.groups.rg[0];
   const size_t need = b->max_arena * rg_max * sizeof(uint32_t);
   std::vector<size_t> smems{0};
-  for (size_t s : {16u << 10, 32u << 10, 48u << 10, 64u << 10, 96u << 10, 128u << 10, 200u << 10})
-    if (s <= kSmemMax) smems.push_back(std::min(s, need));
+  for (size_t s : {16u << 10, 32u << 10, 48u << 10, 64u << 10, 96u << 10, 128u << 10, 192u << 10})
+    if (s + b->max_blob <= kSmemMax) smems.push_back(std::min(s, need));
   std::sort(smems.begin(), smems.end());
   smems.erase(std::unique(smems.begin(), smems.end()), smems.end());
   cudaEvent_t e0 = nullptr, e1 = nullptr;

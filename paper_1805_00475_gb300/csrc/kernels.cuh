@@ -249,21 +249,22 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
 
 // ------------------------------------------------------- persistent batch
 
-// Packed batch descriptors.  Offsets of a formula's tensors are relative to
-// its own arena; bit maps are runs in a shared pool (u16: src | dst << 5 |
-// len << 10).
+// Packed batch descriptors.  Everything one formula's contraction looks up is
+// one contiguous, 16-byte aligned blob (steps, segments, packed items, bit-map
+// runs, level table), copied to shared memory in one coalesced pass when a
+// CTA starts the formula.  Offsets are relative to the formula's own arena;
+// a run is a u16: src | dst << 5 | len << 10.
 struct BStep {
   uint32_t a_off, b_off, c_off;
-  uint32_t run0;  // first run of A's map; B's map follows
+  uint32_t run0;  // first run of A's map (blob-relative); B's map follows
   uint8_t c, k, ka, kb;
   uint8_t nra, nrb, pad0, pad1;
 };
 
 // The unit of work of one warp.  Either 32 consecutive output entries of one
-// step (fewer at its end): step = formula-relative index, o0 = first entry;
-// or, for steps of fewer than 32 entries, up to 32 entries of several such
-// steps packed lane by lane: step = kPacked, o0 = first of n items
-// (item = step | entry << 16, formula-relative).
+// step: step = step index, o0 = first entry; or, for steps of fewer than 32
+// entries, up to 32 entries of several such steps packed lane by lane:
+// step = kPacked, o0 = first of n items (item = step | entry << 16).
 constexpr uint16_t kPacked = 0xFFFF;
 struct Seg {
   uint32_t o0;
@@ -278,19 +279,17 @@ struct BLeaf {
 };
 
 struct BForm {
-  uint32_t step0, seg0, lvl0, nlev;
-  uint32_t leaf0, nleaf, res_off, n_out;
-  uint32_t perm_off, n_open, root_off, arena;  // arena: entries this formula needs
-  uint64_t gbase;                              // first entry of its global arena
+  uint32_t blob;                     // first uint4 of the formula's blob
+  uint32_t blob_n;                   // uint4 count
+  uint32_t segs_at, items_at, runs_at, lvl_at;  // byte offsets of the blob sections (steps at 0)
+  uint32_t nlev, leaf0, nleaf, res_off, n_out, perm_off;
+  uint32_t n_open, root_off, arena, pad;  // arena: entries this formula needs
+  uint64_t gbase;                          // first entry of its global arena
 };
 
 struct BatchArgs {
   const BForm* forms;
-  const BStep* steps;
-  const uint16_t* runs;
-  const Seg* segs;
-  const uint32_t* lvl;    // per formula: nlev + 1 formula-relative segment offsets
-  const uint32_t* items;  // packed lanes of small steps
+  const uint4* blobs;
   const BLeaf* leaves;
   const uint32_t* tables;
   const uint8_t* perms;
@@ -299,6 +298,7 @@ struct BatchArgs {
   uint32_t* queue;        // work counter, zeroed before the launch
   uint32_t* results;      // [entry][R]
   uint32_t* garena;       // global arenas, one region per formula
+  uint32_t blob_cap;      // bytes of dynamic shared memory reserved for a blob
   uint32_t smem_cap;      // entries of dynamic shared memory available for an arena
   int R;
   int col;                // first residue column of this group
@@ -316,23 +316,25 @@ __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, i
 
 // Each CTA repeatedly takes the next formula from the queue and contracts it
 // alone, tree level by tree level: all steps of a level are independent, so
-// the level is a list of 32-entry segments shared out over the CTA's warps
-// (step lookup and bit-map decode are warp-uniform), with one barrier per
-// level.  The formula's tensors live in shared memory when its arena fits,
-// else in its own region of global memory.
+// the level is a list of segments shared out over the CTA's warps, with one
+// barrier per level.  Descriptors are read from shared memory; the tensors
+// live in shared memory when the formula's arena fits, else in its own region
+// of global memory.
 template <int RG>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint4* blob = smem_raw;
+  uint32_t* sarena = reinterpret_cast<uint32_t*>(smem_raw + (a.blob_cap >> 4));
   for (;;) {
     if (threadIdx.x == 0) task = atomicAdd(a.queue, 1u);
     __syncthreads();
     const uint32_t t = task;
-    __syncthreads();
     if (t >= a.n_forms) break;
     const BForm f = a.forms[a.order[t]];
-    uint32_t* arena = f.arena <= a.smem_cap ? reinterpret_cast<uint32_t*>(smem_raw) : a.garena + f.gbase * RG;
+    for (uint32_t i = threadIdx.x; i < f.blob_n; i += blockDim.x) blob[i] = a.blobs[f.blob + i];
+    uint32_t* arena = f.arena <= a.smem_cap ? sarena : a.garena + f.gbase * RG;
     for (uint32_t l = threadIdx.x; l < f.nleaf; l += blockDim.x) {
       const BLeaf ld = a.leaves[f.leaf0 + l];
       uint32_t* dst = arena + (uint64_t)ld.off * RG;
@@ -345,20 +347,25 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       }
     }
     __syncthreads();
-    const uint32_t* lvl = a.lvl + f.lvl0;
+    const char* bb = reinterpret_cast<const char*>(blob);
+    const BStep* steps = reinterpret_cast<const BStep*>(bb);
+    const Seg* segs = reinterpret_cast<const Seg*>(bb + f.segs_at);
+    const uint32_t* items = reinterpret_cast<const uint32_t*>(bb + f.items_at);
+    const uint16_t* runs_all = reinterpret_cast<const uint16_t*>(bb + f.runs_at);
+    const uint32_t* lvl = reinterpret_cast<const uint32_t*>(bb + f.lvl_at);
     for (uint32_t l = 0; l < f.nlev; l++) {
-      const uint32_t s1 = f.seg0 + lvl[l + 1];
-      for (uint32_t sg = f.seg0 + lvl[l] + warp; sg < s1; sg += nwarps) {
-        const Seg seg = a.segs[sg];
+      const uint32_t s1 = lvl[l + 1];
+      for (uint32_t sg = lvl[l] + warp; sg < s1; sg += nwarps) {
+        const Seg seg = segs[sg];
         if (lane < seg.n) {
           uint32_t st = seg.step, o = seg.o0 + lane;
           if (st == kPacked) {
-            const uint32_t it = a.items[o];
+            const uint32_t it = items[o];
             st = it & 0xFFFFu;
             o = it >> 16;
           }
-          const BStep d = a.steps[f.step0 + st];
-          const uint16_t* runs = a.runs + d.run0;
+          const BStep d = steps[st];
+          const uint16_t* runs = runs_all + d.run0;
           const uint32_t ia = map_runs(o, runs, d.nra);
           const uint32_t ib = map_runs(o, runs + d.nra, d.nrb);
           step_entry_at<RG>(d.k, d.ka, d.kb, o, ia, ib, arena + (uint64_t)d.a_off * RG,
