@@ -68,6 +68,11 @@ extern "C" {
 
 /* ---- arithmetic paths ---------------------------------------------------- */
 #define TNC_PATH_INT64 0 /* CUDA cores: u32 residues, 64-bit multiply-accumulate */
+#define TNC_PATH_TC 1    /* dense steps (k >= 6 shared bonds, one side >= 2^7 and the
+                            other >= 2^5 free entries) as exact 8-bit-limb GEMMs on the
+                            tcgen05 tensor cores (bf16 limbs, fp32 accumulation below
+                            2^24, K chunks of 64); other steps as TNC_PATH_INT64; one
+                            pass per residue.  tnc_contract only. */
 
 /* ---- result flags -------------------------------------------------------- */
 #define TNC_MAYBE_WRAPPED 1u /* the certified bound on the count is not below the
@@ -126,6 +131,8 @@ typedef struct {
   uint64_t arena_entries; /* peak live entries, one launch per step (x 4 bytes x
                              residues per pass = tnc_contract's tensor arena)       */
   uint64_t batch_arena_entries; /* same for the level-by-level batch schedule     */
+  int32_t n_dense_steps;  /* steps TNC_PATH_TC runs on the tensor cores            */
+  double dense_macs;      /* their share of total_macs                             */
 } tnc_plan_stats;
 
 typedef struct {

@@ -92,6 +92,13 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
     s.log2_bound = p->net.log2_bound;
     s.arena_entries = p->low.seq_arena_entries;
     s.batch_arena_entries = p->low.lvl_arena_entries;
+    s.n_dense_steps = 0;
+    s.dense_macs = 0;
+    for (const StepDesc& d : p->low.seq_steps)
+      if (tc_eligible(d)) {
+        s.n_dense_steps++;
+        s.dense_macs += std::ldexp(1.0, d.ka + d.kb + d.k);
+      }
     if (stats) *stats = s;
     *out = p;
     return TNC_OK;

@@ -100,7 +100,7 @@ struct Arith {
 
 int make_arith(const tnc_contract_opts* o, Arith& a) {
   if (!o) return set_error(TNC_ERR_INVALID, "contract opts NULL");
-  if (o->path != TNC_PATH_INT64) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
+  if (o->path != TNC_PATH_INT64 && o->path != TNC_PATH_TC) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
   if (o->n_residues < 1 || o->n_residues > 16) return set_error(TNC_ERR_INVALID, "n_residues must be in [1, 16]");
   a.R = o->n_residues;
   if (o->primes) {
@@ -148,8 +148,9 @@ int dispatch_rg(int rg, F&& f) {
 // ---------------------------------------------------------------- single formula
 
 struct SeqLayout {
-  size_t off_leaves, off_tables, off_steps, off_results, off_limbs, off_arena, total;
+  size_t off_leaves, off_tables, off_steps, off_tc, off_err, off_results, off_limbs, off_arena, total;
   uint64_t n_out;
+  size_t n_dense;
 };
 
 using tnc_dev::GridStep;
@@ -215,6 +216,12 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
   o = align_up(o + p->low.leaf_tables.size() * sizeof(uint32_t));
   s.off_steps = o;
   o = align_up(o + p->low.seq_steps.size() * sizeof(GridStep));
+  s.n_dense = 0;
+  for (const StepDesc& d : p->low.seq_steps) s.n_dense += tc_eligible(d) ? 1 : 0;
+  s.off_tc = o;
+  o = align_up(o + s.n_dense * R * tc_step_bytes());
+  s.off_err = o;
+  o = align_up(o + 64);
   s.off_results = o;
   o = align_up(o + s.n_out * R * sizeof(uint32_t));
   s.off_limbs = o;
@@ -280,6 +287,31 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   if (!gsteps.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_steps, gsteps.data(), gsteps.size() * sizeof(GridStep), cudaMemcpyHostToDevice,
                              st));
+  // tensor-core path: one pass per residue, dense steps on tcgen05
+  const bool tc = opts->path == TNC_PATH_TC;
+  Groups groups = a.groups;
+  std::vector<int> dense_idx(plan->low.seq_steps.size(), -1);
+  std::vector<char> tcbuf;
+  if (tc) {
+    groups = Groups();
+    for (int r = 0; r < a.R; r++) {
+      groups.rg.push_back(1);
+      groups.col.push_back(r);
+    }
+    size_t nd = 0;
+    for (size_t i = 0; i < plan->low.seq_steps.size(); i++)
+      if (tc_eligible(plan->low.seq_steps[i])) dense_idx[i] = (int)nd++;
+    tcbuf.assign(nd * a.R * tc_step_bytes(), 0);
+    for (size_t i = 0; i < plan->low.seq_steps.size(); i++)
+      if (dense_idx[i] >= 0)
+        for (int r = 0; r < a.R; r++)
+          tc_make_step(plan->low.seq_steps[i], a.primes[r],
+                       tcbuf.data() + ((size_t)dense_idx[i] * a.R + r) * tc_step_bytes());
+    if (!tcbuf.empty())
+      CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
+  }
+  uint32_t* d_err = (uint32_t*)(ws + L.off_err);
+  CUDA_TRY(cudaMemsetAsync(d_err, 0, 64, st));
   const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
   uint32_t* arena = (uint32_t*)(ws + L.off_arena);
   uint32_t* results = (uint32_t*)(ws + L.off_results);
@@ -287,21 +319,33 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   rm.n_open = (int)plan->net.open_vars.size();
   for (int j = 0; j < rm.n_open; j++) rm.perm[j] = plan->low.root_perm[j];
   const int sms = sm_count();
-  for (size_t gi = 0; gi < a.groups.rg.size(); gi++) {
-    const ModGroup mg = a.group((int)gi);
-    rc = dispatch_rg(a.groups.rg[gi], [&](auto rgc) -> int {
+  for (size_t gi = 0; gi < groups.rg.size(); gi++) {
+    ModGroup mg{};
+    for (int r = 0; r < 4; r++) {
+      const uint32_t p = r < groups.rg[gi] ? a.primes[groups.col[gi] + r] : a.primes[groups.col[gi]];
+      mg.p[r] = p;
+      mg.mu[r] = ~0ull / p;
+    }
+    mg.red_mask = red_mask_for(mg.p, 4);
+    rc = dispatch_rg(groups.rg[gi], [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
       const int nl = (int)leaves.size();
       tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
       for (size_t i = 0; i < gsteps.size(); i++) {
+        if (RG == 1 && tc && dense_idx[i] >= 0) {
+          const char* dstep = ws + L.off_tc + ((size_t)dense_idx[i] * a.R + groups.col[gi]) * tc_step_bytes();
+          int rc2 = tc_launch(dstep, plan->low.seq_steps[i], arena, d_err, st);
+          if (rc2) return rc2;
+          continue;
+        }
         int threads, blocks, sh;
         grid_shape(gsteps[i].d.c, &threads, &blocks, &sh);
         tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
       }
       tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
           arena, plan->low.seq_steps.empty() ? plan->low.seq_leaf_off[plan->tree.root] : plan->low.seq_root_off, rm,
-          results, a.R, a.groups.col[gi]);
+          results, a.R, groups.col[gi]);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });
@@ -311,10 +355,13 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((L.n_out + 127) / 128, 1024), 128, 0, st>>>(results, L.n_out, a.crt,
                                                                                                   limbs);
   CUDA_TRY(cudaGetLastError());
+  uint32_t h_err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   std::vector<uint32_t> h_res(L.n_out * a.R), h_limbs(L.n_out * a.crt.n_limbs);
   CUDA_TRY(cudaMemcpyAsync(h_res.data(), results, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_err) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
   return fill_count(out, L.n_out, a, h_res.data(), h_limbs.data(), flags);
 }
 

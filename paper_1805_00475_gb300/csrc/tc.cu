@@ -1,0 +1,366 @@
+// Dense pairwise steps on the 5th-generation tensor cores (tcgen05), exact.
+//
+// A step C[m,n] = sum_q A[m,q] B[n,q] mod p (A: M x K, B: N x K, residues
+// below 2^30; the bit maps of the lowering make both operands plain
+// column-major matrices) is computed from 8-bit limbs:
+//   a = sum_i a_i 256^i,  b = sum_j b_j 256^j,  0 <= a_i, b_j <= 255,
+//   C = sum_s 256^s C_s mod p,  C_s = sum_{i+j=s} A_i B_j^T   (s = 0..6).
+// Limb values are exact in bf16 and products below 2^16, so C_s accumulates
+// exactly in the fp32 tensor-core accumulators as long as it stays below
+// 2^24: at most 4 limb pairs share an s, 4 * 255^2 * 64 < 2^24, so K is
+// processed in chunks of 64 and every chunk's C_s is folded into 64-bit
+// integer accumulators, C += C_s * (256^s mod p), reduced mod p.  No
+// precision is lost.  The tensor cores run kind::f16 (bf16 inputs, fp32
+// accumulate): on this GPU the 8-bit integer tensor rate is far below the
+// bf16 rate, and bf16 carries 8-bit limbs exactly.
+//
+// CTA tile: 128 rows of C (TMEM lanes) x 32 columns; one thread per row.  Per
+// K chunk all 128 threads stage A's and B's limbs into shared memory in the
+// canonical K-major, no-swizzle layout (8 x 16-byte core matrices), one
+// thread issues 16 pairs x 4 MMAs of 128 x 32 x 16 into 7 TMEM accumulators
+// (224 columns), commits to an mbarrier, and all threads fold the
+// accumulators into their 32 residues.  Every wait is bounded: on timeout the
+// kernel records an error word, still frees its TMEM and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "modarith.cuh"
+#include "tnc_internal.h"
+
+namespace tnc_tc {
+
+constexpr int kTileM = 128;
+constexpr int kTileN = 32;
+constexpr int kChunkK = 64;
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 256;  // 7 accumulators x 32 columns = 224
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+// Shared memory per CTA: A limbs 4 x (128 x 64 bf16) + B limbs 4 x (32 x 64 bf16).
+constexpr uint32_t kALimbBytes = kTileM * kChunkK * 2;  // 16 KiB
+constexpr uint32_t kBLimbBytes = kTileN * kChunkK * 2;  // 4 KiB
+constexpr uint32_t kSmemBytes = 4 * kALimbBytes + 4 * kBLimbBytes + 1024;
+
+struct TcStep {
+  uint64_t a_off, b_off, c_off;  // entries (one residue per entry)
+  uint32_t fa, fb, k;            // M = 2^fa, N = 2^fb, K = 2^k
+  uint32_t pad;
+  uint64_t wm[32], wn[32];       // output address weight of row bit j / column bit j
+  uint32_t p, red_pad;
+  uint64_t mu;
+  uint32_t w256[7];              // 256^s mod p
+  uint32_t pad2;
+};
+
+// ---- PTX helpers -----------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Canonical K-major, no-swizzle shared-memory matrix descriptor: core matrices
+// of 8 rows x 16 bytes, LBO = byte distance between core matrices adjacent in
+// K, SBO = between core matrices adjacent in M/N; version 1; layout 0.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// bf16 bit pattern of an integer 0..255 (exact: at most 8 significant bits).
+__device__ __forceinline__ uint32_t limb_bf16(uint32_t x) { return __float_as_uint((float)x) >> 16; }
+
+// ---- the kernel ------------------------------------------------------------
+
+// Byte offset of element (row r, k-index q) of a K-major limb tile whose core
+// matrices are 8 rows x 8 elements: core (r/8, q/8) at (r/8)*SBO + (q/8)*128,
+// element at (r%8)*16 + (q%8)*2; SBO = (kChunkK/8)*128 = 1024.
+__device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t q) {
+  return (r >> 3) * 1024u + (q >> 3) * 128u + (r & 7u) * 16u + (q & 7u) * 2u;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __restrict__ g, uint32_t* arena,
+                                                             uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t mbar_storage;
+  __shared__ uint32_t tmem_base_s;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t M = 1u << g->fa, N = 1u << g->fb, K = 1u << g->k;
+  const uint32_t tiles_m = M / kTileM;
+  const uint32_t tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const uint32_t m0 = tm * kTileM, n0 = tn * kTileN;
+  uint8_t* sA = smem;                    // 4 limb tiles of 16 KiB
+  uint8_t* sB = smem + 4 * kALimbBytes;  // 4 limb tiles of 4 KiB
+  const uint32_t mbar = smem_u32(&mbar_storage);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  const uint32_t* A = arena + g->a_off;
+  const uint32_t* B = arena + g->b_off;
+  const uint32_t p = g->p;
+  const uint64_t mu = g->mu;
+  uint64_t acc[kTileN];
+#pragma unroll
+  for (int j = 0; j < kTileN; j++) acc[j] = 0;
+  constexpr uint32_t idesc = make_idesc(kTileM, kTileN);
+  bool ok = true;
+  uint32_t phase = 0;
+
+  for (uint32_t k0 = 0; k0 < K && ok; k0 += kChunkK) {
+    // stage limbs: thread t covers rows t of A (all 64 q) and, for t < 32, row t of B
+    {
+      const uint32_t r = tid;
+      for (uint32_t q8 = 0; q8 < kChunkK; q8 += 8) {
+        uint32_t l[4][4];  // [limb][pair of bf16]
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          const uint32_t x0 = A[(uint64_t)(k0 + q8 + e) * M + m0 + r];
+          const uint32_t x1 = A[(uint64_t)(k0 + q8 + e + 1) * M + m0 + r];
+#pragma unroll
+          for (int li = 0; li < 4; li++)
+            l[li][e >> 1] = limb_bf16((x0 >> (8 * li)) & 255u) | (limb_bf16((x1 >> (8 * li)) & 255u) << 16);
+        }
+#pragma unroll
+        for (int li = 0; li < 4; li++)
+          *reinterpret_cast<uint4*>(sA + li * kALimbBytes + kmajor_off(r, q8)) =
+              make_uint4(l[li][0], l[li][1], l[li][2], l[li][3]);
+      }
+      if (r < kTileN) {
+        for (uint32_t q8 = 0; q8 < kChunkK; q8 += 8) {
+          uint32_t l[4][4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            const uint32_t x0 = B[(uint64_t)(k0 + q8 + e) * N + n0 + r];
+            const uint32_t x1 = B[(uint64_t)(k0 + q8 + e + 1) * N + n0 + r];
+#pragma unroll
+            for (int li = 0; li < 4; li++)
+              l[li][e >> 1] = limb_bf16((x0 >> (8 * li)) & 255u) | (limb_bf16((x1 >> (8 * li)) & 255u) << 16);
+          }
+#pragma unroll
+          for (int li = 0; li < 4; li++)
+            *reinterpret_cast<uint4*>(sB + li * kBLimbBytes + kmajor_off(r, q8)) =
+                make_uint4(l[li][0], l[li][1], l[li][2], l[li][3]);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      uint32_t written = 0;  // bit s: accumulator s already holds this chunk's partial sum
+      for (int li = 0; li < 4; li++)
+        for (int lj = 0; lj < 4; lj++) {
+          const int s = li + lj;
+          const uint32_t d = tmem + (uint32_t)s * kTileN;
+#pragma unroll
+          for (int ks = 0; ks < kChunkK / 16; ks++) {
+            // one MMA covers K = 16 = two core matrices along K (256 bytes)
+            const uint64_t ad = make_desc(smem_u32(sA + li * kALimbBytes) + ks * 256u, 128u, 1024u);
+            const uint64_t bd = make_desc(smem_u32(sB + lj * kBLimbBytes) + ks * 256u, 128u, 1024u);
+            mma_bf16(d, ad, bd, idesc, (written >> s) & 1u);
+            written |= 1u << s;
+          }
+        }
+      mma_commit(mbar);
+    }
+    const int waited = mbar_wait(mbar, phase) ? 1 : 0;
+    ok = __syncthreads_and(waited) != 0;  // every thread takes the same branch below
+    if (!ok && tid == 0) atomicExch(err, 1u);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      // fold the 7 accumulators of this chunk into the 32 residues of row tid
+#pragma unroll 1
+      for (int s = 0; s < 7; s++) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((warp * 32u) << 16) + (uint32_t)s * kTileN, v);
+        const uint32_t w = g->w256[s];
+#pragma unroll
+        for (int j = 0; j < kTileN; j++) acc[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) * w;
+      }
+#pragma unroll
+      for (int j = 0; j < kTileN; j++) acc[j] = tnc_dev::mod_reduce(acc[j], p, mu);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+
+  if (ok) {
+    // C[o(m, n)]: o = sum of the output weights of m's and n's bits
+    const uint32_t m = m0 + tid;
+    uint64_t om = 0;
+    for (uint32_t j = 0; j < g->fa; j++)
+      if ((m >> j) & 1u) om += g->wm[j];
+    uint32_t* C = arena + g->c_off;
+    uint64_t on0 = 0;  // column weights: n = n0 + jn, jn < 32 only touches bits 0..4
+    for (uint32_t j = 5; j < g->fb; j++)
+      if ((n0 >> j) & 1u) on0 += g->wn[j];
+#pragma unroll
+    for (int jn = 0; jn < kTileN; jn++) {
+      uint64_t on = on0;
+#pragma unroll
+      for (int j = 0; j < 5; j++)
+        if ((jn >> j) & 1) on += g->wn[j];
+      C[om + on] = (uint32_t)acc[jn];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace tnc_tc
+
+namespace tnc {
+
+// Can this step run on the tensor cores (possibly with A and B exchanged)?
+bool tc_eligible(const StepDesc& d) {
+  const int fa = d.ka, fb = d.kb;
+  return d.k >= 6 && ((fa >= 7 && fb >= 5) || (fb >= 7 && fa >= 5));
+}
+
+size_t tc_step_bytes() { return sizeof(tnc_tc::TcStep); }
+
+// Host-side descriptor for one dense step and residue prime p.
+void tc_make_step(const StepDesc& d, uint32_t p, void* out) {
+  using tnc_tc::TcStep;
+  TcStep t;
+  std::memset(&t, 0, sizeof(t));
+  int op[64] = {0}, dst[64] = {0};
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++)
+      for (int q = 0; q < d.map.runs.ra[i].len; q++) {
+        op[d.map.runs.ra[i].src + q] = 0;
+        dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
+      }
+    for (int i = 0; i < d.nrb; i++)
+      for (int q = 0; q < d.map.runs.rb[i].len; q++) {
+        op[d.map.runs.rb[i].src + q] = 1;
+        dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
+      }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      op[j] = d.map.bit[j] >> 7;
+      dst[j] = d.map.bit[j] & 63;
+    }
+  }
+  // row operand = the one with >= 7 free bits (A unless only B qualifies)
+  const bool swap = !(d.ka >= 7 && d.kb >= 5);
+  const int row_op = swap ? 1 : 0;
+  t.a_off = swap ? d.b_off : d.a_off;
+  t.b_off = swap ? d.a_off : d.b_off;
+  t.c_off = d.c_off;
+  t.fa = swap ? d.kb : d.ka;
+  t.fb = swap ? d.ka : d.kb;
+  t.k = d.k;
+  for (int j = 0; j < d.c; j++) {
+    if (op[j] == row_op) t.wm[dst[j]] = 1ull << j;
+    else t.wn[dst[j]] = 1ull << j;
+  }
+  t.p = p;
+  t.mu = ~0ull / p;
+  uint64_t w = 1;
+  for (int s = 0; s < 7; s++) {
+    t.w256[s] = (uint32_t)w;
+    w = w * 256 % p;
+  }
+  std::memcpy(out, &t, sizeof(t));
+}
+
+int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* dev_err, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tnc_tc::tc_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tnc_tc::kSmemBytes);
+    if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("tc attribute: ") + cudaGetErrorString(e));
+    attr_set = true;
+  }
+  const bool swap = !(d.ka >= 7 && d.kb >= 5);
+  const uint32_t fa = swap ? d.kb : d.ka, fb = swap ? d.ka : d.kb;
+  const uint64_t tiles = (1ull << (fa - 7)) * (1ull << (fb - 5));
+  if (tiles >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
+  tnc_tc::tc_step_kernel<<<(unsigned)tiles, tnc_tc::kThreads, tnc_tc::kSmemBytes, st>>>(
+      (const tnc_tc::TcStep*)dev_step, arena, dev_err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("tc launch: ") + cudaGetErrorString(e));
+  return TNC_OK;
+}
+
+}  // namespace tnc

@@ -121,4 +121,10 @@ constexpr uint32_t kDefaultPrimeBound = 1u << 30;
 std::vector<uint32_t> default_primes(int n);
 bool is_prime_u32(uint32_t n);
 
+// tc.cu: dense steps on the tensor cores (exact 8-bit-limb GEMMs)
+bool tc_eligible(const StepDesc& d);
+size_t tc_step_bytes();
+void tc_make_step(const StepDesc& d, uint32_t p, void* out);
+int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* dev_err, void* stream);
+
 }  // namespace tnc

@@ -25,7 +25,7 @@ TNC_OK = 0
 ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4: "TNC_ERR_BUFFER",
           -5: "TNC_ERR_TIMEOUT", -6: "TNC_ERR_NOMEM"}
 HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4}
-PATHS = {"int64": 0}
+PATHS = {"int64": 0, "tc": 1}
 TNC_MAYBE_WRAPPED = 1
 
 # every symbol include/tnc.h declares
@@ -62,7 +62,8 @@ class _PlanStats(ctypes.Structure):
     _fields_ = [("max_rank", ctypes.c_int32), ("n_steps", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("total_macs", ctypes.c_double),
                 ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double),
-                ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64)]
+                ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64),
+                ("n_dense_steps", ctypes.c_int32), ("dense_macs", ctypes.c_double)]
 
 
 class _ContractOpts(ctypes.Structure):
@@ -206,6 +207,8 @@ class PlanStats:
     log2_bound: float
     arena_entries: int = 0
     batch_arena_entries: int = 0
+    n_dense_steps: int = 0
+    dense_macs: float = 0.0
 
 
 class Plan:
@@ -242,7 +245,8 @@ def plan(network: Network, heuristic: str = "bisect", rank_cap: int = 32, tries:
 
 def _stats(st: _PlanStats) -> PlanStats:
     return PlanStats(st.max_rank, st.n_steps, st.n_leaves, st.depth, st.total_macs, st.total_entries,
-                     st.log2_bound, int(st.arena_entries), int(st.batch_arena_entries))
+                     st.log2_bound, int(st.arena_entries), int(st.batch_arena_entries), int(st.n_dense_steps),
+                     float(st.dense_macs))
 
 
 def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0

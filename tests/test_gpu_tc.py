@@ -1,0 +1,62 @@
+"""The tensor-core path (TNC_PATH_TC): dense steps as exact 8-bit-limb GEMMs
+on tcgen05.  Bit-exact against the CPU oracle where it finishes, and against
+the CUDA-core int64 path at larger sizes."""
+import pytest
+
+import oracle
+from paper_1805_00475_gb300 import build as tnc_build
+from paper_1805_00475_gb300 import instances as I
+from paper_1805_00475_gb300 import tnc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tnc_build.build()
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("h", ["greedy", "gn", "bisect"])
+def test_tc_matches_oracle_cubic_vc_n70(seed, h):
+    f = I.cubic_vertex_cover(70, seed)
+    p = tnc.plan_formula(f, heuristic=h, rank_cap=28)
+    exact = oracle.count(f, max_rank=28)
+    r = tnc.contract(p, n_residues=4, path="tc")
+    assert r.counts == exact and r.flags == 0
+    assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
+
+
+def test_tc_plans_really_have_dense_steps():
+    n_dense = [tnc.plan_formula(I.cubic_vertex_cover(70, s), heuristic="greedy").stats.n_dense_steps
+               for s in range(4)]
+    assert min(n_dense) >= 1
+
+
+@pytest.mark.parametrize("n,h,R", [(90, "greedy", 4), (100, "bisect", 3), (120, "greedy", 8), (140, "gn", 5)])
+def test_tc_matches_int64(n, h, R):
+    f = I.cubic_vertex_cover(n, 2)
+    p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
+    assert p.stats.n_dense_steps >= 1
+    a = tnc.contract(p, n_residues=R, path="int64")
+    b = tnc.contract(p, n_residues=R, path="tc")
+    assert a.counts == b.counts and a.residues.tolist() == b.residues.tolist()
+
+
+def test_tc_user_primes_near_2_31():
+    """Residues above 2^30 (caller's primes): the top limb is then up to 127
+    and the path must stay exact."""
+    f = I.cubic_vertex_cover(70, 1)
+    primes = [2147483647, 2147483629, 2147483587]
+    p = tnc.plan_formula(f, heuristic="greedy")
+    exact = oracle.count(f)[0]
+    r = tnc.contract(p, n_residues=3, primes=primes, path="tc")
+    assert [int(x) for x in r.residues[0]] == [exact % q for q in primes]
+
+
+def test_tc_one_in_three_with_open_bonds():
+    f = I.one_in_three(60, 40, 3)
+    f.open_vars = [0, 5, 9]
+    p = tnc.plan_formula(f, heuristic="greedy", rank_cap=28)
+    exact = oracle.count(f, max_rank=28)
+    assert tnc.contract(p, n_residues=4, path="tc").counts == exact
