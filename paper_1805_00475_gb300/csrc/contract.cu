@@ -148,7 +148,7 @@ int dispatch_rg(int rg, F&& f) {
 // ---------------------------------------------------------------- single formula
 
 struct SeqLayout {
-  size_t off_leaves, off_tables, off_steps, off_tc, off_err, off_results, off_limbs, off_arena, total;
+  size_t off_leaves, off_tables, off_steps, off_tc, off_err, off_part, off_results, off_limbs, off_arena, total;
   uint64_t n_out;
   size_t n_dense;
 };
@@ -162,6 +162,17 @@ void grid_shape(int c, int* threads, int* blocks, int* s) {
   *threads = 1 << t;
   *blocks = 1 << b;
   *s = t + b;
+}
+
+// Split-K for steps with at most 2^12 outputs and at least 2^9 shared values:
+// returns log2 of the number of K slices (0 = no split).  Each slice keeps at
+// least 256 shared values; outputs x slices stays at most 2^20.
+constexpr uint64_t kSplitPartEntries = 1ull << 20;
+uint32_t splitk_log(const StepDesc& d) {
+  if (d.c > 12 || d.k < 9) return 0;
+  uint32_t ls = d.k - 8;
+  while (ls > 0 && (1ull << (d.c + ls)) > kSplitPartEntries) ls--;
+  return ls;
 }
 
 GridStep make_grid_step(const StepDesc& d) {
@@ -222,6 +233,14 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
   o = align_up(o + s.n_dense * R * tc_step_bytes());
   s.off_err = o;
   o = align_up(o + 64);
+  uint64_t part_bytes = 0;
+  for (const StepDesc& d : p->low.seq_steps) {
+    if (splitk_log(d) > 0) part_bytes = std::max<uint64_t>(part_bytes, kSplitPartEntries * rg_max * sizeof(uint32_t));
+    if (tc_eligible(d) && tc_split_log(d) > 0)
+      part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
+  }
+  s.off_part = o;
+  o = align_up(o + part_bytes);
   s.off_results = o;
   o = align_up(o + s.n_out * R * sizeof(uint32_t));
   s.off_limbs = o;
@@ -335,8 +354,18 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
       for (size_t i = 0; i < gsteps.size(); i++) {
         if (RG == 1 && tc && dense_idx[i] >= 0) {
           const char* dstep = ws + L.off_tc + ((size_t)dense_idx[i] * a.R + groups.col[gi]) * tc_step_bytes();
-          int rc2 = tc_launch(dstep, plan->low.seq_steps[i], arena, d_err, st);
+          int rc2 = tc_launch(dstep, plan->low.seq_steps[i], arena, (uint32_t*)(ws + L.off_part), d_err, st);
           if (rc2) return rc2;
+          continue;
+        }
+        const uint32_t ls = splitk_log(gsteps[i].d);
+        if (ls > 0) {
+          uint32_t* part = (uint32_t*)(ws + L.off_part);
+          const uint64_t nblk = 1ull << (gsteps[i].d.c + ls);
+          tnc_dev::splitk_partial_kernel<RG><<<(unsigned)nblk, 256, 0, st>>>(d_steps + i, arena, part, ls, mg);
+          const uint64_t n = 1ull << gsteps[i].d.c;
+          tnc_dev::splitk_final_kernel<RG><<<(unsigned)std::max<uint64_t>(1, (n + 255) / 256), 256, 0, st>>>(
+              d_steps + i, arena, part, ls, mg);
           continue;
         }
         int threads, blocks, sh;

@@ -182,6 +182,78 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
   }
 }
 
+// Split-K for steps with few output entries and a long shared dimension (a
+// final dot product, a rank-19 tensor against a rank-19 tensor, ...): block
+// (o, part) sums A*B over its slice of the 2^k shared values, the block's
+// threads combine their residues with modular additions, and a second kernel
+// adds the parts of each output.  part[o * n_split + j] holds RG residues.
+template <int RG>
+__global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __restrict__ g, const uint32_t* arena,
+                                                             uint32_t* __restrict__ part, uint32_t log_split,
+                                                             ModGroup mg) {
+  __shared__ uint32_t red[256 * RG];
+  const uint32_t n_split = 1u << log_split;
+  const uint64_t o = blockIdx.x >> log_split;
+  const uint32_t j = blockIdx.x & (n_split - 1);
+  const uint32_t k = g->d.k, ka = g->d.ka, kb = g->d.kb, c = g->d.c;
+  uint64_t ia = 0, ib = 0;
+  for (uint32_t b = 0; b < c; b++)
+    if ((o >> b) & 1ull) {
+      ia += g->wA[b];
+      ib += g->wB[b];
+    }
+  const uint32_t* A = arena + (g->d.a_off + ia) * RG;
+  const uint32_t* B = arena + (g->d.b_off + ib) * RG;
+  const uint64_t per = (1ull << k) >> log_split;
+  uint64_t acc[RG];
+#pragma unroll
+  for (int r = 0; r < RG; r++) acc[r] = 0;
+  uint32_t cnt = 0;
+  for (uint64_t q = j * per + threadIdx.x; q < (j + 1) * per; q += blockDim.x) {
+    uint32_t va[RG], vb[RG];
+    load_entry<RG>(A + (q << ka) * RG, va);
+    load_entry<RG>(B + (q << kb) * RG, vb);
+#pragma unroll
+    for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+    if ((++cnt & mg.red_mask) == 0) {
+#pragma unroll
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  __syncthreads();
+  for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int r = 0; r < RG; r++) {
+        uint32_t x = red[threadIdx.x * RG + r] + red[(threadIdx.x + h) * RG + r];
+        if (x >= mg.p[r]) x -= mg.p[r];
+        red[threadIdx.x * RG + r] = x;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < RG) part[(uint64_t)blockIdx.x * RG + threadIdx.x] = red[threadIdx.x];
+}
+
+template <int RG>
+__global__ void splitk_final_kernel(const GridStep* __restrict__ g, uint32_t* arena, const uint32_t* __restrict__ part,
+                                    uint32_t log_split, ModGroup mg) {
+  const uint64_t n = 1ull << g->d.c;
+  uint32_t* C0 = arena + g->d.c_off * RG;
+  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v[RG];
+#pragma unroll
+    for (int r = 0; r < RG; r++) {
+      uint64_t s = 0;
+      for (uint32_t j = 0; j < (1u << log_split); j++) s += part[((o << log_split) + j) * RG + r];
+      v[r] = mod_reduce(s, mg.p[r], mg.mu[r]);
+    }
+    store_entry<RG>(C0 + o * RG, v);
+  }
+}
+
 struct RootMap {
   uint8_t perm[24];  // root bit j -> open variable index
   int n_open;

@@ -23,6 +23,7 @@
 // kernel records an error word, still frees its TMEM and returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -48,7 +49,7 @@ constexpr uint32_t kSmemBytes = 4 * kALimbBytes + 4 * kBLimbBytes + 1024;
 struct TcStep {
   uint64_t a_off, b_off, c_off;  // entries (one residue per entry)
   uint32_t fa, fb, k;            // M = 2^fa, N = 2^fb, K = 2^k
-  uint32_t pad;
+  uint32_t log_split;            // K split over 2^log_split CTAs per tile (partials summed after)
   uint64_t wm[32], wn[32];       // output address weight of row bit j / column bit j
   uint32_t p, red_pad;
   uint64_t mu;
@@ -139,14 +140,16 @@ __device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t q) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __restrict__ g, uint32_t* arena,
-                                                             uint32_t* err) {
+                                                             uint32_t* part, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t mbar_storage;
   __shared__ uint32_t tmem_base_s;
   const uint32_t tid = threadIdx.x, warp = tid >> 5;
   const uint32_t M = 1u << g->fa, N = 1u << g->fb, K = 1u << g->k;
   const uint32_t tiles_m = M / kTileM;
-  const uint32_t tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const uint32_t split = blockIdx.x & ((1u << g->log_split) - 1u), tile = blockIdx.x >> g->log_split;
+  const uint32_t tm = tile % tiles_m, tn = tile / tiles_m;
+  const uint32_t kbeg = split * (K >> g->log_split), kend = kbeg + (K >> g->log_split);
   const uint32_t m0 = tm * kTileM, n0 = tn * kTileN;
   uint8_t* sA = smem;                    // 4 limb tiles of 16 KiB
   uint8_t* sB = smem + 4 * kALimbBytes;  // 4 limb tiles of 4 KiB
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
   bool ok = true;
   uint32_t phase = 0;
 
-  for (uint32_t k0 = 0; k0 < K && ok; k0 += kChunkK) {
+  for (uint32_t k0 = kbeg; k0 < kend && ok; k0 += kChunkK) {
     // stage limbs: thread t covers rows t of A (all 64 q) and, for t < 32, row t of B
     {
       const uint32_t r = tid;
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
     uint64_t om = 0;
     for (uint32_t j = 0; j < g->fa; j++)
       if ((m >> j) & 1u) om += g->wm[j];
-    uint32_t* C = arena + g->c_off;
+    uint32_t* C = g->log_split ? part + ((uint64_t)split << (g->fa + g->fb)) : arena + g->c_off;
     uint64_t on0 = 0;  // column weights: n = n0 + jn, jn < 32 only touches bits 0..4
     for (uint32_t j = 5; j < g->fb; j++)
       if ((n0 >> j) & 1u) on0 += g->wn[j];
@@ -285,6 +288,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// Sum of the K-split partials of a dense step: C[o] = sum_j part[j][o] mod p.
+__global__ void tc_split_final_kernel(const TcStep* __restrict__ g, uint32_t* arena, const uint32_t* __restrict__ part) {
+  const uint64_t n = 1ull << (g->fa + g->fb);
+  uint32_t* C = arena + g->c_off;
+  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t s = 0;
+    for (uint32_t j = 0; j < (1u << g->log_split); j++) s += part[((uint64_t)j << (g->fa + g->fb)) + o];
+    C[o] = tnc_dev::mod_reduce(s, g->p, g->mu);
+  }
+}
+
 }  // namespace tnc_tc
 
 namespace tnc {
@@ -296,6 +310,19 @@ bool tc_eligible(const StepDesc& d) {
 }
 
 size_t tc_step_bytes() { return sizeof(tnc_tc::TcStep); }
+
+// K split of a dense step: double it while the tiles x splits stay below two
+// CTAs per SM of a 152-SM GPU, each split keeps >= 2 chunks of 64, and the
+// partials (2^c entries per split) stay within tc_part_entries().
+uint64_t tc_part_entries() { return 1ull << 24; }
+uint32_t tc_split_log(const StepDesc& d) {
+  const bool swap = !(d.ka >= 7 && d.kb >= 5);
+  const uint32_t fa = swap ? d.kb : d.ka, fb = swap ? d.ka : d.kb;
+  const uint64_t tiles = (1ull << (fa - 7)) << (fb - 5);
+  uint32_t ls = 0;
+  while ((tiles << ls) < 304 && d.k - ls > 7 && (1ull << (d.c + ls + 1)) <= tc_part_entries()) ls++;
+  return ls;
+}
 
 // Host-side descriptor for one dense step and residue prime p.
 void tc_make_step(const StepDesc& d, uint32_t p, void* out) {
@@ -329,6 +356,7 @@ void tc_make_step(const StepDesc& d, uint32_t p, void* out) {
   t.fa = swap ? d.kb : d.ka;
   t.fb = swap ? d.ka : d.kb;
   t.k = d.k;
+  t.log_split = tc_split_log(d);
   for (int j = 0; j < d.c; j++) {
     if (op[j] == row_op) t.wm[dst[j]] = 1ull << j;
     else t.wn[dst[j]] = 1ull << j;
@@ -343,7 +371,8 @@ void tc_make_step(const StepDesc& d, uint32_t p, void* out) {
   std::memcpy(out, &t, sizeof(t));
 }
 
-int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* dev_err, void* stream) {
+int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* part, uint32_t* dev_err,
+              void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   static bool attr_set = false;
   if (!attr_set) {
@@ -354,10 +383,16 @@ int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t
   }
   const bool swap = !(d.ka >= 7 && d.kb >= 5);
   const uint32_t fa = swap ? d.kb : d.ka, fb = swap ? d.ka : d.kb;
-  const uint64_t tiles = (1ull << (fa - 7)) * (1ull << (fb - 5));
+  const uint32_t ls = tc_split_log(d);
+  const uint64_t tiles = ((1ull << (fa - 7)) * (1ull << (fb - 5))) << ls;
   if (tiles >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
   tnc_tc::tc_step_kernel<<<(unsigned)tiles, tnc_tc::kThreads, tnc_tc::kSmemBytes, st>>>(
-      (const tnc_tc::TcStep*)dev_step, arena, dev_err);
+      (const tnc_tc::TcStep*)dev_step, arena, part, dev_err);
+  if (ls) {
+    const uint64_t n = 1ull << (fa + fb);
+    tnc_tc::tc_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 8192), 256, 0, st>>>(
+        (const tnc_tc::TcStep*)dev_step, arena, part);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("tc launch: ") + cudaGetErrorString(e));
   return TNC_OK;

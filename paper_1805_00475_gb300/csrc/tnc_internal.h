@@ -125,6 +125,9 @@ bool is_prime_u32(uint32_t n);
 bool tc_eligible(const StepDesc& d);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
-int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* dev_err, void* stream);
+uint32_t tc_split_log(const StepDesc& d);
+uint64_t tc_part_entries();
+int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t* part, uint32_t* dev_err,
+              void* stream);
 
 }  // namespace tnc

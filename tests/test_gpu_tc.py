@@ -35,7 +35,7 @@ def test_tc_plans_really_have_dense_steps():
 
 @pytest.mark.parametrize("n,h,R", [(90, "greedy", 4), (100, "bisect", 3), (120, "greedy", 8), (140, "gn", 5)])
 def test_tc_matches_int64(n, h, R):
-    f = I.cubic_vertex_cover(n, 2)
+    f = I.cubic_vertex_cover(n, 1)
     p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
     assert p.stats.n_dense_steps >= 1
     a = tnc.contract(p, n_residues=R, path="int64")
@@ -60,3 +60,34 @@ def test_tc_one_in_three_with_open_bonds():
     p = tnc.plan_formula(f, heuristic="greedy", rank_cap=28)
     exact = oracle.count(f, max_rank=28)
     assert tnc.contract(p, n_residues=4, path="tc").counts == exact
+
+
+def _step_shapes(f, p):
+    bonds, b = {}, 0
+    for c, vs in enumerate(f.clauses):
+        for v in vs:
+            bonds.setdefault(c, set()).add(b)
+            bonds.setdefault(f.n_cons + v, set()).add(b)
+            b += 1
+    nxt, out = f.n_cons + f.n_vars, []
+    for a, c in p.steps():
+        A, B = bonds.pop(a), bonds.pop(c)
+        k = len(A & B)
+        out.append((len(A) - k, len(B) - k, k))
+        bonds[nxt] = A ^ B
+        nxt += 1
+    return out
+
+
+@pytest.mark.parametrize("path", ["int64", "tc"])
+def test_split_k_final_dot_product(path):
+    """Plans whose last steps have few outputs and a long shared dimension
+    (here a full contraction of two rank-13+ tensors) run split over K."""
+    for seed in range(6):
+        f = I.cubic_vertex_cover(70, seed)
+        p = tnc.plan_formula(f, heuristic="greedy", rank_cap=28)
+        if any(fa + fb <= 12 and k >= 9 for fa, fb, k in _step_shapes(f, p)):
+            break
+    else:
+        pytest.skip("no split-K step among the seeds")
+    assert tnc.contract(p, n_residues=4, path=path).counts == oracle.count(f, max_rank=28)
