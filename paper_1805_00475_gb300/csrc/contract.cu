@@ -363,9 +363,8 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
           uint32_t* part = (uint32_t*)(ws + L.off_part);
           const uint64_t nblk = 1ull << (gsteps[i].d.c + ls);
           tnc_dev::splitk_partial_kernel<RG><<<(unsigned)nblk, 256, 0, st>>>(d_steps + i, arena, part, ls, mg);
-          const uint64_t n = 1ull << gsteps[i].d.c;
-          tnc_dev::splitk_final_kernel<RG><<<(unsigned)std::max<uint64_t>(1, (n + 255) / 256), 256, 0, st>>>(
-              d_steps + i, arena, part, ls, mg);
+          tnc_dev::splitk_final_kernel<RG><<<(unsigned)(1ull << gsteps[i].d.c), 256, 0, st>>>(d_steps + i, arena,
+                                                                                           part, ls, mg);
           continue;
         }
         int threads, blocks, sh;

@@ -237,21 +237,35 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
   if (threadIdx.x < RG) part[(uint64_t)blockIdx.x * RG + threadIdx.x] = red[threadIdx.x];
 }
 
+// One block per output entry: its threads add the parts, then combine.
 template <int RG>
-__global__ void splitk_final_kernel(const GridStep* __restrict__ g, uint32_t* arena, const uint32_t* __restrict__ part,
-                                    uint32_t log_split, ModGroup mg) {
-  const uint64_t n = 1ull << g->d.c;
-  uint32_t* C0 = arena + g->d.c_off * RG;
-  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t v[RG];
+__global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __restrict__ g, uint32_t* arena,
+                                                           const uint32_t* __restrict__ part, uint32_t log_split,
+                                                           ModGroup mg) {
+  __shared__ uint32_t red[256 * RG];
+  const uint64_t o = blockIdx.x;
+  uint64_t s[RG];
 #pragma unroll
-    for (int r = 0; r < RG; r++) {
-      uint64_t s = 0;
-      for (uint32_t j = 0; j < (1u << log_split); j++) s += part[((o << log_split) + j) * RG + r];
-      v[r] = mod_reduce(s, mg.p[r], mg.mu[r]);
-    }
-    store_entry<RG>(C0 + o * RG, v);
+  for (int r = 0; r < RG; r++) s[r] = 0;
+  for (uint32_t j = threadIdx.x; j < (1u << log_split); j += blockDim.x) {
+#pragma unroll
+    for (int r = 0; r < RG; r++) s[r] += part[((o << log_split) + j) * RG + r];  // < 2^31 each, < 2^20 of them
   }
+#pragma unroll
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(s[r], mg.p[r], mg.mu[r]);
+  __syncthreads();
+  for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+#pragma unroll
+      for (int r = 0; r < RG; r++) {
+        uint32_t x = red[threadIdx.x * RG + r] + red[(threadIdx.x + h) * RG + r];
+        if (x >= mg.p[r]) x -= mg.p[r];
+        red[threadIdx.x * RG + r] = x;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < RG) arena[(g->d.c_off + o) * RG + threadIdx.x] = red[threadIdx.x];
 }
 
 struct RootMap {

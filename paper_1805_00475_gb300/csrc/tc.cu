@@ -14,13 +14,15 @@
 // accumulate): on this GPU the 8-bit integer tensor rate is far below the
 // bf16 rate, and bf16 carries 8-bit limbs exactly.
 //
-// CTA tile: 128 rows of C (TMEM lanes) x 32 columns; one thread per row.  Per
-// K chunk all 128 threads stage A's and B's limbs into shared memory in the
-// canonical K-major, no-swizzle layout (8 x 16-byte core matrices), one
-// thread issues 16 pairs x 4 MMAs of 128 x 32 x 16 into 7 TMEM accumulators
-// (224 columns), commits to an mbarrier, and all threads fold the
-// accumulators into their 32 residues.  Every wait is bounded: on timeout the
-// kernel records an error word, still frees its TMEM and returns.
+// CTA tile: 128 rows of C (TMEM lanes) x 32 columns, 256 threads (8 warps);
+// warp w reads TMEM lane quarter w%4 and columns 16*(w/4) .. +16.  Pipeline:
+// two shared-memory stages of limbs (canonical K-major, no-swizzle layout: 8 x
+// 16-byte core matrices) and two sets of 7 TMEM accumulators (7 x 32 columns
+// each); while the MMAs of chunk c run, the threads stage chunk c+1 and fold
+// the accumulators of chunk c-1.  One thread issues the 16 limb pairs x 4 MMAs
+// of 128 x 32 x 16 per chunk and commits them to that stage's mbarrier.
+// Every wait is bounded: on timeout the kernel records an error word, frees
+// its TMEM and returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,14 +39,16 @@ namespace tnc_tc {
 constexpr int kTileM = 128;
 constexpr int kTileN = 32;
 constexpr int kChunkK = 64;
-constexpr int kThreads = 128;
-constexpr uint32_t kTmemCols = 256;  // 7 accumulators x 32 columns = 224
+constexpr int kThreads = 256;
+constexpr uint32_t kTmemCols = 512;  // 2 buffers x 7 accumulators x 32 columns = 448
+constexpr uint32_t kAccStride = 256; // columns between the two accumulator buffers
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-// Shared memory per CTA: A limbs 4 x (128 x 64 bf16) + B limbs 4 x (32 x 64 bf16).
+// Shared memory per stage: A limbs 4 x (128 x 64 bf16) + B limbs 4 x (32 x 64 bf16).
 constexpr uint32_t kALimbBytes = kTileM * kChunkK * 2;  // 16 KiB
 constexpr uint32_t kBLimbBytes = kTileN * kChunkK * 2;  // 4 KiB
-constexpr uint32_t kSmemBytes = 4 * kALimbBytes + 4 * kBLimbBytes + 1024;
+constexpr uint32_t kStageBytes = 4 * kALimbBytes + 4 * kBLimbBytes;  // 80 KiB
+constexpr uint32_t kSmemBytes = 2 * kStageBytes + 1024;
 
 struct TcStep {
   uint64_t a_off, b_off, c_off;  // entries (one residue per entry)
@@ -115,14 +119,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -139,21 +140,70 @@ __device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t q) {
   return (r >> 3) * 1024u + (q >> 3) * 128u + (r & 7u) * 16u + (q & 7u) * 2u;
 }
 
+// Stage chunk k0 of A's 128 rows and B's 32 rows as 8-bit limbs (bf16).
+// 1024 (row, 8-q group) pairs of A and 256 of B are shared by the 256 threads.
+__device__ __forceinline__ void stage_chunk(uint8_t* sA, uint8_t* sB, const uint32_t* A, const uint32_t* B, uint32_t M,
+                                            uint32_t N, uint32_t m0, uint32_t n0, uint32_t k0, uint32_t tid) {
+#pragma unroll 1
+  for (int it = 0; it < 5; it++) {
+    const uint32_t job = tid + it * kThreads;  // 0..1023: A, 1024..1279: B
+    const bool isA = job < 1024;
+    const uint32_t jj = isA ? job : job - 1024;
+    const uint32_t r = isA ? (jj & 127u) : (jj & 31u);
+    const uint32_t q8 = isA ? (jj >> 7) * 8u : (jj >> 5) * 8u;
+    const uint32_t* src = isA ? A + m0 + r : B + n0 + r;
+    const uint32_t ld = isA ? M : N;
+    uint32_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) x[e] = src[(uint64_t)(k0 + q8 + e) * ld];
+    uint8_t* base = isA ? sA : sB;
+    const uint32_t lbytes = isA ? kALimbBytes : kBLimbBytes;
+#pragma unroll
+    for (int li = 0; li < 4; li++) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2)
+        w[e >> 1] = limb_bf16((x[e] >> (8 * li)) & 255u) | (limb_bf16((x[e + 1] >> (8 * li)) & 255u) << 16);
+      *reinterpret_cast<uint4*>(base + li * lbytes + kmajor_off(r, q8)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_chunk(uint32_t acc_col, uint32_t sA, uint32_t sB) {
+  constexpr uint32_t idesc = make_idesc(kTileM, kTileN);
+  uint32_t written = 0;  // bit s: accumulator s already holds this chunk's partial sum
+  for (int li = 0; li < 4; li++)
+    for (int lj = 0; lj < 4; lj++) {
+      const int s = li + lj;
+#pragma unroll
+      for (int ks = 0; ks < kChunkK / 16; ks++) {
+        // one MMA covers K = 16 = two core matrices along K (256 bytes)
+        const uint64_t ad = make_desc(sA + li * kALimbBytes + ks * 256u, 128u, 1024u);
+        const uint64_t bd = make_desc(sB + lj * kBLimbBytes + ks * 256u, 128u, 1024u);
+        mma_bf16(acc_col + (uint32_t)s * kTileN, ad, bd, idesc, (written >> s) & 1u);
+        written |= 1u << s;
+      }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __restrict__ g, uint32_t* arena,
                                                              uint32_t* part, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar_storage;
+  __shared__ uint64_t mbar_storage[2];
   __shared__ uint32_t tmem_base_s;
-  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t quarter = warp & 3u, half = warp >> 2;
   const uint32_t M = 1u << g->fa, N = 1u << g->fb, K = 1u << g->k;
   const uint32_t tiles_m = M / kTileM;
   const uint32_t split = blockIdx.x & ((1u << g->log_split) - 1u), tile = blockIdx.x >> g->log_split;
   const uint32_t tm = tile % tiles_m, tn = tile / tiles_m;
-  const uint32_t kbeg = split * (K >> g->log_split), kend = kbeg + (K >> g->log_split);
+  const uint32_t kbeg = split * (K >> g->log_split);
+  const uint32_t n_chunks = (K >> g->log_split) / kChunkK;
   const uint32_t m0 = tm * kTileM, n0 = tn * kTileN;
-  uint8_t* sA = smem;                    // 4 limb tiles of 16 KiB
-  uint8_t* sB = smem + 4 * kALimbBytes;  // 4 limb tiles of 4 KiB
-  const uint32_t mbar = smem_u32(&mbar_storage);
+  // stage b: A limbs at smem + b*kStageBytes, B limbs right after them
+#define TC_SA(b) (smem + (b) * kStageBytes)
+#define TC_SB(b) (smem + (b) * kStageBytes + 4 * kALimbBytes)
+  const uint32_t mbar0 = smem_u32(&mbar_storage[0]), mbar1 = smem_u32(&mbar_storage[1]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
@@ -162,121 +212,75 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(mbar, 1);
+    mbar_init(mbar0, 1);
+    mbar_init(mbar1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const uint32_t* A = arena + g->a_off;
+  const uint32_t* B = arena + g->b_off;
+  stage_chunk(TC_SA(0), TC_SB(0), A, B, M, N, m0, n0, kbeg, tid);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
+  if (tid == 0) {
+    issue_chunk(tmem, smem_u32(TC_SA(0)), smem_u32(TC_SB(0)));
+    mma_commit(mbar0);
+  }
 
-  const uint32_t* A = arena + g->a_off;
-  const uint32_t* B = arena + g->b_off;
   const uint32_t p = g->p;
   const uint64_t mu = g->mu;
-  uint64_t acc[kTileN];
+  uint64_t acc[16];
 #pragma unroll
-  for (int j = 0; j < kTileN; j++) acc[j] = 0;
-  constexpr uint32_t idesc = make_idesc(kTileM, kTileN);
+  for (int j = 0; j < 16; j++) acc[j] = 0;
   bool ok = true;
-  uint32_t phase = 0;
-
-  for (uint32_t k0 = kbeg; k0 < kend && ok; k0 += kChunkK) {
-    // stage limbs: thread t covers rows t of A (all 64 q) and, for t < 32, row t of B
-    {
-      const uint32_t r = tid;
-      for (uint32_t q8 = 0; q8 < kChunkK; q8 += 8) {
-        uint32_t l[4][4];  // [limb][pair of bf16]
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          const uint32_t x0 = A[(uint64_t)(k0 + q8 + e) * M + m0 + r];
-          const uint32_t x1 = A[(uint64_t)(k0 + q8 + e + 1) * M + m0 + r];
-#pragma unroll
-          for (int li = 0; li < 4; li++)
-            l[li][e >> 1] = limb_bf16((x0 >> (8 * li)) & 255u) | (limb_bf16((x1 >> (8 * li)) & 255u) << 16);
-        }
-#pragma unroll
-        for (int li = 0; li < 4; li++)
-          *reinterpret_cast<uint4*>(sA + li * kALimbBytes + kmajor_off(r, q8)) =
-              make_uint4(l[li][0], l[li][1], l[li][2], l[li][3]);
-      }
-      if (r < kTileN) {
-        for (uint32_t q8 = 0; q8 < kChunkK; q8 += 8) {
-          uint32_t l[4][4];
-#pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            const uint32_t x0 = B[(uint64_t)(k0 + q8 + e) * N + n0 + r];
-            const uint32_t x1 = B[(uint64_t)(k0 + q8 + e + 1) * N + n0 + r];
-#pragma unroll
-            for (int li = 0; li < 4; li++)
-              l[li][e >> 1] = limb_bf16((x0 >> (8 * li)) & 255u) | (limb_bf16((x1 >> (8 * li)) & 255u) << 16);
-          }
-#pragma unroll
-          for (int li = 0; li < 4; li++)
-            *reinterpret_cast<uint4*>(sB + li * kBLimbBytes + kmajor_off(r, q8)) =
-                make_uint4(l[li][0], l[li][1], l[li][2], l[li][3]);
-        }
-      }
-    }
+  for (uint32_t c = 0; c < n_chunks; c++) {
+    const uint32_t b = c & 1u;
+    if (c + 1 < n_chunks)  // the buffer of chunk c-1 is free: its MMAs completed in the previous iteration
+      stage_chunk(TC_SA(b ^ 1u), TC_SB(b ^ 1u), A, B, M, N, m0, n0, kbeg + (c + 1) * kChunkK, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    const int waited = mbar_wait(b ? mbar1 : mbar0, (c >> 1) & 1u) ? 1 : 0;
+    ok = __syncthreads_and(waited) != 0;  // also: every thread has staged chunk c+1
+    if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-      uint32_t written = 0;  // bit s: accumulator s already holds this chunk's partial sum
-      for (int li = 0; li < 4; li++)
-        for (int lj = 0; lj < 4; lj++) {
-          const int s = li + lj;
-          const uint32_t d = tmem + (uint32_t)s * kTileN;
-#pragma unroll
-          for (int ks = 0; ks < kChunkK / 16; ks++) {
-            // one MMA covers K = 16 = two core matrices along K (256 bytes)
-            const uint64_t ad = make_desc(smem_u32(sA + li * kALimbBytes) + ks * 256u, 128u, 1024u);
-            const uint64_t bd = make_desc(smem_u32(sB + lj * kBLimbBytes) + ks * 256u, 128u, 1024u);
-            mma_bf16(d, ad, bd, idesc, (written >> s) & 1u);
-            written |= 1u << s;
-          }
-        }
-      mma_commit(mbar);
+    if (c + 1 < n_chunks && tid == 0) {
+      issue_chunk(tmem + (b ^ 1u) * kAccStride, smem_u32(TC_SA(b ^ 1u)), smem_u32(TC_SB(b ^ 1u)));
+      mma_commit(b ? mbar0 : mbar1);
     }
-    const int waited = mbar_wait(mbar, phase) ? 1 : 0;
-    ok = __syncthreads_and(waited) != 0;  // every thread takes the same branch below
-    if (!ok && tid == 0) atomicExch(err, 1u);
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      // fold the 7 accumulators of this chunk into the 32 residues of row tid
+    // fold the 7 accumulators of chunk c (this thread: one row, 16 columns)
 #pragma unroll 1
-      for (int s = 0; s < 7; s++) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((warp * 32u) << 16) + (uint32_t)s * kTileN, v);
-        const uint32_t w = g->w256[s];
+    for (int s = 0; s < 7; s++) {
+      uint32_t v[16];
+      tmem_ld16(tmem + ((quarter * 32u) << 16) + b * kAccStride + (uint32_t)s * kTileN + half * 16u, v);
+      const uint32_t w = g->w256[s];
 #pragma unroll
-        for (int j = 0; j < kTileN; j++) acc[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) * w;
-      }
-#pragma unroll
-      for (int j = 0; j < kTileN; j++) acc[j] = tnc_dev::mod_reduce(acc[j], p, mu);
+      for (int j = 0; j < 16; j++) acc[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) * w;
     }
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc[j] = tnc_dev::mod_reduce(acc[j], p, mu);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
+  if (!ok && tid == 0) atomicExch(err, 1u);
 
   if (ok) {
     // C[o(m, n)]: o = sum of the output weights of m's and n's bits
-    const uint32_t m = m0 + tid;
+    const uint32_t m = m0 + quarter * 32u + lane;
     uint64_t om = 0;
     for (uint32_t j = 0; j < g->fa; j++)
       if ((m >> j) & 1u) om += g->wm[j];
     uint32_t* C = g->log_split ? part + ((uint64_t)split << (g->fa + g->fb)) : arena + g->c_off;
-    uint64_t on0 = 0;  // column weights: n = n0 + jn, jn < 32 only touches bits 0..4
-    for (uint32_t j = 5; j < g->fb; j++)
-      if ((n0 >> j) & 1u) on0 += g->wn[j];
+    const uint32_t nb = n0 + half * 16u;  // columns nb .. nb+15: bits 0..3 vary
+    uint64_t on0 = 0;
+    for (uint32_t j = 4; j < g->fb; j++)
+      if ((nb >> j) & 1u) on0 += g->wn[j];
 #pragma unroll
-    for (int jn = 0; jn < kTileN; jn++) {
+    for (int jn = 0; jn < 16; jn++) {
       uint64_t on = on0;
 #pragma unroll
-      for (int j = 0; j < 5; j++)
+      for (int j = 0; j < 4; j++)
         if ((jn >> j) & 1) on += g->wn[j];
       C[om + on] = (uint32_t)acc[jn];
     }
@@ -286,6 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+#undef TC_SA
+#undef TC_SB
 }
 
 // Sum of the K-split partials of a dense step: C[o] = sum_j part[j][o] mod p.
