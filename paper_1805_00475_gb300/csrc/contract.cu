@@ -148,7 +148,8 @@ int dispatch_rg(int rg, F&& f) {
 // ---------------------------------------------------------------- single formula
 
 struct SeqLayout {
-  size_t off_leaves, off_tables, off_steps, off_tc, off_err, off_part, off_results, off_limbs, off_arena, total;
+  size_t off_leaves, off_tables, off_steps, off_small, off_tc, off_err, off_part, off_results, off_limbs, off_arena,
+      total;
   uint64_t n_out;
   size_t n_dense;
 };
@@ -227,6 +228,8 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
   o = align_up(o + p->low.leaf_tables.size() * sizeof(uint32_t));
   s.off_steps = o;
   o = align_up(o + p->low.seq_steps.size() * sizeof(GridStep));
+  s.off_small = o;
+  o = align_up(o + p->low.lvl_steps.size() * sizeof(StepDesc));
   s.n_dense = 0;
   for (const StepDesc& d : p->low.seq_steps) s.n_dense += tc_eligible(d) ? 1 : 0;
   s.off_tc = o;
@@ -234,7 +237,7 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
   s.off_err = o;
   o = align_up(o + 64);
   uint64_t part_bytes = 0;
-  for (const StepDesc& d : p->low.seq_steps) {
+  for (const StepDesc& d : p->low.lvl_steps) {
     if (splitk_log(d) > 0) part_bytes = std::max<uint64_t>(part_bytes, kSplitPartEntries * rg_max * sizeof(uint32_t));
     if (tc_eligible(d) && tc_split_log(d) > 0)
       part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
@@ -246,7 +249,7 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
   s.off_limbs = o;
   o = align_up(o + s.n_out * ((31 * R + 31) / 32) * sizeof(uint32_t));
   s.off_arena = o;
-  o = align_up(o + p->low.seq_arena_entries * rg_max * sizeof(uint32_t));
+  o = align_up(o + std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) * rg_max * sizeof(uint32_t));
   s.total = o;
   return s;
 }
@@ -293,50 +296,81 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   char* ws = (char*)dev_ws;
-  // leaves (offsets of the sequential schedule) and tables
-  std::vector<LeafDesc> leaves = plan->low.leaves;
-  for (size_t i = 0; i < leaves.size(); i++) leaves[i].off = plan->low.seq_leaf_off[i];
+  // The contraction runs level by level (the tree-level schedule of the
+  // lowering): per level, one launch for all its steps with fewer than 2^16
+  // outputs, and one launch each for its big steps, its split-K steps and, on
+  // the tensor-core path, its dense steps.
+  const Lowered& lw = plan->low;
+  std::vector<LeafDesc> leaves = lw.leaves;
+  for (size_t i = 0; i < leaves.size(); i++) leaves[i].off = lw.lvl_leaf_off[i];
   CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice, st));
-  if (!plan->low.leaf_tables.empty())
-    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, plan->low.leaf_tables.data(),
-                             plan->low.leaf_tables.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  if (!lw.leaf_tables.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, lw.leaf_tables.data(), lw.leaf_tables.size() * sizeof(uint32_t),
+                             cudaMemcpyHostToDevice, st));
+  const bool tc = opts->path == TNC_PATH_TC;
+  const size_t ns = lw.lvl_steps.size();
+  enum Kind { kSmall, kGrid, kSplit, kTc };
+  std::vector<int> kind(ns, kSmall), slot(ns, -1);
   std::vector<GridStep> gsteps;
-  gsteps.reserve(plan->low.seq_steps.size());
-  for (const StepDesc& d : plan->low.seq_steps) gsteps.push_back(make_grid_step(d));
+  std::vector<StepDesc> small;
+  std::vector<uint32_t> small_lo, small_hi, small_work;  // per level
+  std::vector<char> tcbuf;
+  size_t nd = 0;
+  for (size_t l = 0; l + 1 < lw.lvl_start.size(); l++) {
+    small_lo.push_back((uint32_t)small.size());
+    uint32_t work = 0;
+    for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
+      const StepDesc& d = lw.lvl_steps[i];
+      if (tc && tc_eligible(d)) {
+        kind[i] = kTc;
+        slot[i] = (int)nd++;
+      } else if (splitk_log(d) > 0 || d.c >= 16) {
+        kind[i] = splitk_log(d) > 0 ? kSplit : kGrid;
+        slot[i] = (int)gsteps.size();
+        gsteps.push_back(make_grid_step(d));
+      } else {
+        StepDesc e = d;
+        e.work_lo = work;
+        work += 1u << d.c;
+        small.push_back(e);
+      }
+    }
+    small_hi.push_back((uint32_t)small.size());
+    small_work.push_back(work);
+  }
   if (!gsteps.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_steps, gsteps.data(), gsteps.size() * sizeof(GridStep), cudaMemcpyHostToDevice,
                              st));
-  // tensor-core path: one pass per residue, dense steps on tcgen05
-  const bool tc = opts->path == TNC_PATH_TC;
+  if (!small.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_small, small.data(), small.size() * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
+  if (nd) {
+    tcbuf.assign(nd * a.R * tc_step_bytes(), 0);
+    for (size_t i = 0; i < ns; i++)
+      if (kind[i] == kTc)
+        for (int r = 0; r < a.R; r++)
+          tc_make_step(lw.lvl_steps[i], a.primes[r], tcbuf.data() + ((size_t)slot[i] * a.R + r) * tc_step_bytes());
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
+  }
+  // residue groups: tensor-core passes carry one residue per entry
   Groups groups = a.groups;
-  std::vector<int> dense_idx(plan->low.seq_steps.size(), -1);
-  std::vector<char> tcbuf;
   if (tc) {
     groups = Groups();
     for (int r = 0; r < a.R; r++) {
       groups.rg.push_back(1);
       groups.col.push_back(r);
     }
-    size_t nd = 0;
-    for (size_t i = 0; i < plan->low.seq_steps.size(); i++)
-      if (tc_eligible(plan->low.seq_steps[i])) dense_idx[i] = (int)nd++;
-    tcbuf.assign(nd * a.R * tc_step_bytes(), 0);
-    for (size_t i = 0; i < plan->low.seq_steps.size(); i++)
-      if (dense_idx[i] >= 0)
-        for (int r = 0; r < a.R; r++)
-          tc_make_step(plan->low.seq_steps[i], a.primes[r],
-                       tcbuf.data() + ((size_t)dense_idx[i] * a.R + r) * tc_step_bytes());
-    if (!tcbuf.empty())
-      CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
   }
   uint32_t* d_err = (uint32_t*)(ws + L.off_err);
   CUDA_TRY(cudaMemsetAsync(d_err, 0, 64, st));
   const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
+  const StepDesc* d_small = (const StepDesc*)(ws + L.off_small);
   uint32_t* arena = (uint32_t*)(ws + L.off_arena);
   uint32_t* results = (uint32_t*)(ws + L.off_results);
+  uint32_t* part = (uint32_t*)(ws + L.off_part);
   RootMap rm{};
   rm.n_open = (int)plan->net.open_vars.size();
-  for (int j = 0; j < rm.n_open; j++) rm.perm[j] = plan->low.root_perm[j];
+  for (int j = 0; j < rm.n_open; j++) rm.perm[j] = lw.root_perm[j];
+  const uint64_t root_off = lw.lvl_steps.empty() ? lw.lvl_leaf_off[plan->tree.root] : lw.lvl_root_off;
   const int sms = sm_count();
   for (size_t gi = 0; gi < groups.rg.size(); gi++) {
     ModGroup mg{};
@@ -351,29 +385,35 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
       const int nl = (int)leaves.size();
       tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
-      for (size_t i = 0; i < gsteps.size(); i++) {
-        if (RG == 1 && tc && dense_idx[i] >= 0) {
-          const char* dstep = ws + L.off_tc + ((size_t)dense_idx[i] * a.R + groups.col[gi]) * tc_step_bytes();
-          int rc2 = tc_launch(dstep, plan->low.seq_steps[i], arena, (uint32_t*)(ws + L.off_part), d_err, st);
-          if (rc2) return rc2;
-          continue;
+      for (size_t l = 0; l < small_lo.size(); l++) {
+        const uint32_t n_small = small_hi[l] - small_lo[l];
+        if (n_small) {
+          const uint32_t w = small_work[l];
+          const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, (uint64_t)sms * 8);
+          tnc_dev::level_kernel<RG><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
         }
-        const uint32_t ls = splitk_log(gsteps[i].d);
-        if (ls > 0) {
-          uint32_t* part = (uint32_t*)(ws + L.off_part);
-          const uint64_t nblk = 1ull << (gsteps[i].d.c + ls);
-          tnc_dev::splitk_partial_kernel<RG><<<(unsigned)nblk, 256, 0, st>>>(d_steps + i, arena, part, ls, mg);
-          tnc_dev::splitk_final_kernel<RG><<<(unsigned)(1ull << gsteps[i].d.c), 256, 0, st>>>(d_steps + i, arena,
-                                                                                           part, ls, mg);
-          continue;
+        for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
+          if (kind[i] == kSmall) continue;
+          if (kind[i] == kTc) {
+            if (RG != 1) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
+            const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
+            int rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);
+            if (rc2) return rc2;
+          } else if (kind[i] == kSplit) {
+            const uint32_t ls = splitk_log(lw.lvl_steps[i]);
+            const uint64_t nblk = 1ull << (lw.lvl_steps[i].c + ls);
+            tnc_dev::splitk_partial_kernel<RG><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls, mg);
+            tnc_dev::splitk_final_kernel<RG><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
+                d_steps + slot[i], arena, part, ls, mg);
+          } else {
+            int threads, blocks, sh;
+            grid_shape(lw.lvl_steps[i].c, &threads, &blocks, &sh);
+            tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
+          }
         }
-        int threads, blocks, sh;
-        grid_shape(gsteps[i].d.c, &threads, &blocks, &sh);
-        tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
       }
       tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
-          arena, plan->low.seq_steps.empty() ? plan->low.seq_leaf_off[plan->tree.root] : plan->low.seq_root_off, rm,
-          results, a.R, groups.col[gi]);
+          arena, root_off, rm, results, a.R, groups.col[gi]);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });

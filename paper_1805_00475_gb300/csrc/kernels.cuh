@@ -268,6 +268,24 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
   if (threadIdx.x < RG) arena[(g->d.c_off + o) * RG + threadIdx.x] = red[threadIdx.x];
 }
 
+// All the small steps of one tree level in one launch: they are independent,
+// so their output entries form one index space (step i owns [work_lo,
+// work_lo + 2^c)); each thread finds its step by binary search.
+template <int RG>
+__global__ void __launch_bounds__(256) level_kernel(const StepDesc* __restrict__ steps, uint32_t n_steps,
+                                                    uint32_t total, uint32_t* arena, ModGroup mg) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_steps - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (steps[mid].work_lo <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    const StepDesc& d = steps[lo];
+    step_entry<RG>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
+  }
+}
+
 struct RootMap {
   uint8_t perm[24];  // root bit j -> open variable index
   int n_open;

@@ -323,20 +323,23 @@ int validate_lowered(const Network& net, const Tree& tree, Lowered& low) {
     (void)net;
     if (root_off + root_n > arena) return set_error(TNC_ERR_INVALID, "internal: root outside");
   }
-  // level schedule (used only by the batch kernel, whose work offsets are
-  // 32-bit): outputs of a level must not overlap anything the level touches
+  // level schedule: outputs of a level must not overlap anything the level
+  // touches; its 32-bit work offsets (used by the batch kernel) must fit
+  bool fits = true;
   for (size_t l = 0; l + 1 < low.lvl_start.size(); l++) {
     uint64_t work = 0;
     for (uint32_t i = low.lvl_start[l]; i < low.lvl_start[l + 1]; i++) work += 1ull << low.lvl_steps[i].c;
-    if (work >= (1ull << 32)) return TNC_OK;  // lvl_fits stays false: batch refuses this plan
+    if (work >= (1ull << 32)) fits = false;
   }
   for (size_t l = 0; l + 1 < low.lvl_start.size(); l++) {
     for (uint32_t i = low.lvl_start[l]; i < low.lvl_start[l + 1]; i++) {
       const StepDesc& d = low.lvl_steps[i];
-      const uint64_t prev_end = i > low.lvl_start[l] ? (uint64_t)low.lvl_steps[i - 1].work_lo +
-                                                           (1ull << low.lvl_steps[i - 1].c)
-                                                     : 0;
-      if ((uint64_t)d.work_lo != prev_end) return set_error(TNC_ERR_INVALID, "internal: work offsets");
+      if (fits) {
+        const uint64_t prev_end = i > low.lvl_start[l] ? (uint64_t)low.lvl_steps[i - 1].work_lo +
+                                                             (1ull << low.lvl_steps[i - 1].c)
+                                                       : 0;
+        if ((uint64_t)d.work_lo != prev_end) return set_error(TNC_ERR_INVALID, "internal: work offsets");
+      }
       for (uint32_t j = low.lvl_start[l]; j < low.lvl_start[l + 1]; j++) {
         if (i == j) continue;
         const StepDesc& e = low.lvl_steps[j];
@@ -347,6 +350,7 @@ int validate_lowered(const Network& net, const Tree& tree, Lowered& low) {
       }
     }
   }
+  if (!fits) return TNC_OK;  // lvl_fits stays false: the batch kernel refuses this plan
   low.lvl_fits = true;
   return TNC_OK;
 }

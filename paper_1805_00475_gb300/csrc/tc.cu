@@ -141,21 +141,30 @@ __device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t q) {
 }
 
 // Stage chunk k0 of A's 128 rows and B's 32 rows as 8-bit limbs (bf16).
-// 1024 (row, 8-q group) pairs of A and 256 of B are shared by the 256 threads.
+// 1024 (row, 8-q group) pairs of A and 256 of B are shared by the 256 threads:
+// every thread first issues all 40 of its loads, then converts and stores.
 __device__ __forceinline__ void stage_chunk(uint8_t* sA, uint8_t* sB, const uint32_t* A, const uint32_t* B, uint32_t M,
                                             uint32_t N, uint32_t m0, uint32_t n0, uint32_t k0, uint32_t tid) {
-#pragma unroll 1
+  uint32_t x[5][8];
+#pragma unroll
   for (int it = 0; it < 5; it++) {
-    const uint32_t job = tid + it * kThreads;  // 0..1023: A, 1024..1279: B
-    const bool isA = job < 1024;
+    const uint32_t job = tid + it * kThreads;  // 0..1023: A, 1024..1279: B (warp-uniform per it)
+    const bool isA = it < 4;
     const uint32_t jj = isA ? job : job - 1024;
     const uint32_t r = isA ? (jj & 127u) : (jj & 31u);
     const uint32_t q8 = isA ? (jj >> 7) * 8u : (jj >> 5) * 8u;
     const uint32_t* src = isA ? A + m0 + r : B + n0 + r;
     const uint32_t ld = isA ? M : N;
-    uint32_t x[8];
 #pragma unroll
-    for (int e = 0; e < 8; e++) x[e] = src[(uint64_t)(k0 + q8 + e) * ld];
+    for (int e = 0; e < 8; e++) x[it][e] = src[(uint64_t)(k0 + q8 + e) * ld];
+  }
+#pragma unroll
+  for (int it = 0; it < 5; it++) {
+    const uint32_t job = tid + it * kThreads;
+    const bool isA = it < 4;
+    const uint32_t jj = isA ? job : job - 1024;
+    const uint32_t r = isA ? (jj & 127u) : (jj & 31u);
+    const uint32_t q8 = isA ? (jj >> 7) * 8u : (jj >> 5) * 8u;
     uint8_t* base = isA ? sA : sB;
     const uint32_t lbytes = isA ? kALimbBytes : kBLimbBytes;
 #pragma unroll
@@ -163,7 +172,7 @@ __device__ __forceinline__ void stage_chunk(uint8_t* sA, uint8_t* sB, const uint
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 8; e += 2)
-        w[e >> 1] = limb_bf16((x[e] >> (8 * li)) & 255u) | (limb_bf16((x[e + 1] >> (8 * li)) & 255u) << 16);
+        w[e >> 1] = limb_bf16((x[it][e] >> (8 * li)) & 255u) | (limb_bf16((x[it][e + 1] >> (8 * li)) & 255u) << 16);
       *reinterpret_cast<uint4*>(base + li * lbytes + kmajor_off(r, q8)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
