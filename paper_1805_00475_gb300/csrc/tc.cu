@@ -9,10 +9,11 @@
 // exactly in the fp32 tensor-core accumulators as long as it stays below
 // 2^24: at most 4 limb pairs share an s, 4 * 255^2 * 64 < 2^24, so K is
 // processed in chunks of 64 and every chunk's C_s is folded into 64-bit
-// integer accumulators, C += C_s * (256^s mod p), reduced mod p.  No
-// precision is lost.  The tensor cores run kind::f16 (bf16 inputs, fp32
-// accumulate): on this GPU the 8-bit integer tensor rate is far below the
-// bf16 rate, and bf16 carries 8-bit limbs exactly.
+// integer accumulators, C += sum_s 256^s C_s mod p.  No precision is lost.
+// The tensor cores run kind::f16 with fp16 inputs and fp32 accumulation: on
+// this GPU the 8-bit integer tensor rate is far below the 16-bit float rate,
+// and fp16 carries 8-bit limbs exactly (a limb v becomes the half 1024 + v by
+// bit operations, minus 1024 in one packed subtract).
 //
 // CTA tile: 128 rows of C (TMEM lanes) x 32 columns, 256 threads (8 warps);
 // warp w reads TMEM lane quarter w%4 and columns 16*(w/4) .. +16.  Pipeline:
@@ -57,7 +58,7 @@ struct TcStep {
   uint64_t wm[32], wn[32];       // output address weight of row bit j / column bit j
   uint32_t p, red_pad;
   uint64_t mu;
-  uint32_t w256[7];              // 256^s mod p
+  uint32_t w256[7];              // 256^s mod p (w256[5] = 2^40 mod p is used)
   uint32_t pad2;
 };
 
@@ -79,10 +80,10 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = F16
+// (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -128,8 +129,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// bf16 bit pattern of an integer 0..255 (exact: at most 8 significant bits).
-__device__ __forceinline__ uint32_t limb_bf16(uint32_t x) { return __float_as_uint((float)x) >> 16; }
+// Limb li (bits 8li..8li+7) of x0 and of x1 as a packed pair of fp16 values
+// (x0's in the low half): bytes placed at 0 and 2, exponent bits of 1024
+// or-ed in (half 1024 + v, exact for v < 1024), then 1024 subtracted.
+template <int li>
+__device__ __forceinline__ uint32_t limb_pair_f16(uint32_t x0, uint32_t x1) {
+  constexpr uint32_t sel = (uint32_t)li | ((uint32_t)(4 + li) << 8);
+  const uint32_t t = (__byte_perm(x0, x1, sel) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(0x64006400u));
+  return r;
+}
 
 // ---- the kernel ------------------------------------------------------------
 
@@ -167,14 +177,20 @@ __device__ __forceinline__ void stage_chunk(uint8_t* sA, uint8_t* sB, const uint
     const uint32_t q8 = isA ? (jj >> 7) * 8u : (jj >> 5) * 8u;
     uint8_t* base = isA ? sA : sB;
     const uint32_t lbytes = isA ? kALimbBytes : kBLimbBytes;
-#pragma unroll
-    for (int li = 0; li < 4; li++) {
-      uint32_t w[4];
-#pragma unroll
-      for (int e = 0; e < 8; e += 2)
-        w[e >> 1] = limb_bf16((x[it][e] >> (8 * li)) & 255u) | (limb_bf16((x[it][e + 1] >> (8 * li)) & 255u) << 16);
-      *reinterpret_cast<uint4*>(base + li * lbytes + kmajor_off(r, q8)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    const uint32_t off = kmajor_off(r, q8);
+    const uint32_t* v = x[it];
+    *reinterpret_cast<uint4*>(base + 0 * lbytes + off) =
+        make_uint4(limb_pair_f16<0>(v[0], v[1]), limb_pair_f16<0>(v[2], v[3]), limb_pair_f16<0>(v[4], v[5]),
+                   limb_pair_f16<0>(v[6], v[7]));
+    *reinterpret_cast<uint4*>(base + 1 * lbytes + off) =
+        make_uint4(limb_pair_f16<1>(v[0], v[1]), limb_pair_f16<1>(v[2], v[3]), limb_pair_f16<1>(v[4], v[5]),
+                   limb_pair_f16<1>(v[6], v[7]));
+    *reinterpret_cast<uint4*>(base + 2 * lbytes + off) =
+        make_uint4(limb_pair_f16<2>(v[0], v[1]), limb_pair_f16<2>(v[2], v[3]), limb_pair_f16<2>(v[4], v[5]),
+                   limb_pair_f16<2>(v[6], v[7]));
+    *reinterpret_cast<uint4*>(base + 3 * lbytes + off) =
+        make_uint4(limb_pair_f16<3>(v[0], v[1]), limb_pair_f16<3>(v[2], v[3]), limb_pair_f16<3>(v[4], v[5]),
+                   limb_pair_f16<3>(v[6], v[7]));
   }
 }
 
@@ -257,17 +273,36 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
       issue_chunk(tmem + (b ^ 1u) * kAccStride, smem_u32(TC_SA(b ^ 1u)), smem_u32(TC_SB(b ^ 1u)));
       mma_commit(b ? mbar0 : mbar1);
     }
-    // fold the 7 accumulators of chunk c (this thread: one row, 16 columns)
-#pragma unroll 1
-    for (int s = 0; s < 7; s++) {
+    // fold the 7 accumulators of chunk c (this thread: one row, 16 columns):
+    // lo = C0 + C1 2^8 + ... + C4 2^32 < 2^57, hi = C5 + C6 2^8 < 2^33,
+    // sum = lo + hi 2^40; acc < p + 2^57 + 2^33 (2^40 mod p) < 2^64
+    const uint32_t tl = tmem + ((quarter * 32u) << 16) + b * kAccStride + half * 16u;
+    uint64_t lo[16];
+    uint32_t hi[16];
+    {
       uint32_t v[16];
-      tmem_ld16(tmem + ((quarter * 32u) << 16) + b * kAccStride + (uint32_t)s * kTileN + half * 16u, v);
-      const uint32_t w = g->w256[s];
+      tmem_ld16(tl + 0 * kTileN, v);
 #pragma unroll
-      for (int j = 0; j < 16; j++) acc[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) * w;
+      for (int j = 0; j < 16; j++) lo[j] = __float2uint_rn(__uint_as_float(v[j]));
     }
 #pragma unroll
-    for (int j = 0; j < 16; j++) acc[j] = tnc_dev::mod_reduce(acc[j], p, mu);
+    for (int s = 1; s < 5; s++) {
+      uint32_t v[16];
+      tmem_ld16(tl + (uint32_t)s * kTileN, v);
+#pragma unroll
+      for (int j = 0; j < 16; j++) lo[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (8 * s);
+    }
+    {
+      uint32_t v[16], u[16];
+      tmem_ld16(tl + 5 * kTileN, v);
+      tmem_ld16(tl + 6 * kTileN, u);
+#pragma unroll
+      for (int j = 0; j < 16; j++)
+        hi[j] = __float2uint_rn(__uint_as_float(v[j])) + (__float2uint_rn(__uint_as_float(u[j])) << 8);
+    }
+    const uint32_t w40 = g->w256[5];  // 2^40 mod p
+#pragma unroll
+    for (int j = 0; j < 16; j++) acc[j] = tnc_dev::mod_reduce(acc[j] + lo[j] + (uint64_t)hi[j] * w40, p, mu);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
