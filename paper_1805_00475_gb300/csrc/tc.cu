@@ -86,7 +86,7 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N) {
   return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -118,6 +118,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+// Zero 16 TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -194,20 +202,23 @@ __device__ __forceinline__ void stage_chunk(uint8_t* sA, uint8_t* sB, const uint
   }
 }
 
+// B's four limb tiles are contiguous with the same core-matrix strides, so
+// together they are one K-major operand of 4 x 32 = 128 rows (row = 32 lj + n).
+// One MMA of 128 x 128 x 16 per A limb li then yields A_li B_lj for all lj;
+// written at column offset 32 li, the product of limbs (li, lj) lands in the
+// columns of accumulator s = li + lj.  Columns 0..127 are overwritten by the
+// first MMA of the chunk; 128..223 are zeroed beforehand.
 __device__ __forceinline__ void issue_chunk(uint32_t acc_col, uint32_t sA, uint32_t sB) {
-  constexpr uint32_t idesc = make_idesc(kTileM, kTileN);
-  uint32_t written = 0;  // bit s: accumulator s already holds this chunk's partial sum
-  for (int li = 0; li < 4; li++)
-    for (int lj = 0; lj < 4; lj++) {
-      const int s = li + lj;
+  constexpr uint32_t idesc = make_idesc(kTileM, 4 * kTileN);
+  const uint64_t a0 = make_desc(sA, 128u, 1024u), b0 = make_desc(sB, 128u, 1024u);
 #pragma unroll
-      for (int ks = 0; ks < kChunkK / 16; ks++) {
-        // one MMA covers K = 16 = two core matrices along K (256 bytes)
-        const uint64_t ad = make_desc(sA + li * kALimbBytes + ks * 256u, 128u, 1024u);
-        const uint64_t bd = make_desc(sB + lj * kBLimbBytes + ks * 256u, 128u, 1024u);
-        mma_bf16(acc_col + (uint32_t)s * kTileN, ad, bd, idesc, (written >> s) & 1u);
-        written |= 1u << s;
-      }
+  for (int li = 0; li < 4; li++)
+#pragma unroll
+    for (int ks = 0; ks < kChunkK / 16; ks++) {
+      // +16 bytes per unit of the descriptor's start-address field
+      const uint64_t ad = a0 + (uint64_t)((li * kALimbBytes + ks * 256u) >> 4);
+      const uint64_t bd = b0 + (uint64_t)((ks * 256u) >> 4);
+      mma_f16(acc_col + (uint32_t)li * kTileN, ad, bd, idesc, (li | ks) ? 1u : 0u);
     }
 }
 
@@ -249,6 +260,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
+  // zero accumulators s = 4..6 (columns 128..223) of both buffers; each warp
+  // owns one lane quarter and one 16-column half of every accumulator
+#pragma unroll
+  for (uint32_t bb = 0; bb < 2; bb++)
+#pragma unroll
+    for (uint32_t ss = 4; ss < 7; ss++)
+      tmem_zero16(tmem + ((quarter * 32u) << 16) + bb * kAccStride + ss * kTileN + half * 16u);
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (tid == 0) {
     issue_chunk(tmem, smem_u32(TC_SA(0)), smem_u32(TC_SB(0)));
     mma_commit(mbar0);
@@ -303,6 +325,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
     const uint32_t w40 = g->w256[5];  // 2^40 mod p
 #pragma unroll
     for (int j = 0; j < 16; j++) acc[j] = tnc_dev::mod_reduce(acc[j] + lo[j] + (uint64_t)hi[j] * w40, p, mu);
+    // the columns this warp just read of accumulators 4..6 start the chunk
+    // after next at zero
+#pragma unroll
+    for (uint32_t ss = 4; ss < 7; ss++) tmem_zero16(tl + ss * kTileN);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
