@@ -137,6 +137,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Exact integer value of a float holding an integer below 2^23.
+__device__ __forceinline__ uint32_t f2u_small(uint32_t fbits) {
+  return __float_as_uint(__uint_as_float(fbits) + 8388608.0f) - 0x4B000000u;
+}
+
 // Limb li (bits 8li..8li+7) of x0 and of x1 as a packed pair of fp16 values
 // (x0's in the low half): bytes placed at 0 and 2, exponent bits of 1024
 // or-ed in (half 1024 + v, exact for v < 1024), then 1024 subtracted.
@@ -278,9 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
 
   const uint32_t p = g->p;
   const uint64_t mu = g->mu;
-  uint64_t acc[16];
+  uint64_t lo[16], hi[16];
 #pragma unroll
-  for (int j = 0; j < 16; j++) acc[j] = 0;
+  for (int j = 0; j < 16; j++) lo[j] = hi[j] = 0;
   bool ok = true;
   for (uint32_t c = 0; c < n_chunks; c++) {
     const uint32_t b = c & 1u;
@@ -296,35 +301,41 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
       mma_commit(b ? mbar0 : mbar1);
     }
     // fold the 7 accumulators of chunk c (this thread: one row, 16 columns):
-    // lo = C0 + C1 2^8 + ... + C4 2^32 < 2^57, hi = C5 + C6 2^8 < 2^33,
-    // sum = lo + hi 2^40; acc < p + 2^57 + 2^33 (2^40 mod p) < 2^64
+    // lo += C0 + C1 2^8 + ... + C4 2^32 (< 2^57 per chunk), hi += C5 + C6 2^8
+    // (< 2^31 per chunk); count = lo + hi 2^40.  lo and hi are reduced mod p
+    // every 64 chunks (64 * 2^57 = 2^63) and at the end.  Accumulators with
+    // at most 2 limb pairs are below 2^23 and convert by a float add
+    // (x + 2^23 has x in its low mantissa bits); the others by F2I.
     const uint32_t tl = tmem + ((quarter * 32u) << 16) + b * kAccStride + half * 16u;
-    uint64_t lo[16];
-    uint32_t hi[16];
     {
-      uint32_t v[16];
-      tmem_ld16(tl + 0 * kTileN, v);
-#pragma unroll
-      for (int j = 0; j < 16; j++) lo[j] = __float2uint_rn(__uint_as_float(v[j]));
-    }
-#pragma unroll
-    for (int s = 1; s < 5; s++) {
-      uint32_t v[16];
-      tmem_ld16(tl + (uint32_t)s * kTileN, v);
-#pragma unroll
-      for (int j = 0; j < 16; j++) lo[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (8 * s);
-    }
-    {
-      uint32_t v[16], u[16];
-      tmem_ld16(tl + 5 * kTileN, v);
-      tmem_ld16(tl + 6 * kTileN, u);
+      uint32_t v0[16], v1[16];
+      tmem_ld16(tl + 0 * kTileN, v0);
+      tmem_ld16(tl + 1 * kTileN, v1);
 #pragma unroll
       for (int j = 0; j < 16; j++)
-        hi[j] = __float2uint_rn(__uint_as_float(v[j])) + (__float2uint_rn(__uint_as_float(u[j])) << 8);
+        lo[j] += (uint64_t)(f2u_small(v0[j]) + (f2u_small(v1[j]) << 8));
     }
-    const uint32_t w40 = g->w256[5];  // 2^40 mod p
 #pragma unroll
-    for (int j = 0; j < 16; j++) acc[j] = tnc_dev::mod_reduce(acc[j] + lo[j] + (uint64_t)hi[j] * w40, p, mu);
+    for (int ss = 2; ss < 5; ss++) {
+      uint32_t v[16];
+      tmem_ld16(tl + (uint32_t)ss * kTileN, v);
+#pragma unroll
+      for (int j = 0; j < 16; j++) lo[j] += (uint64_t)__float2uint_rn(__uint_as_float(v[j])) << (8 * ss);
+    }
+    {
+      uint32_t v5[16], v6[16];
+      tmem_ld16(tl + 5 * kTileN, v5);
+      tmem_ld16(tl + 6 * kTileN, v6);
+#pragma unroll
+      for (int j = 0; j < 16; j++) hi[j] += f2u_small(v5[j]) + (f2u_small(v6[j]) << 8);
+    }
+    if ((c & 63u) == 63u) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        lo[j] = tnc_dev::mod_reduce(lo[j], p, mu);
+        hi[j] = tnc_dev::mod_reduce(hi[j], p, mu);
+      }
+    }
     // the columns this warp just read of accumulators 4..6 start the chunk
     // after next at zero
 #pragma unroll
@@ -336,6 +347,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
   }
   if (!ok && tid == 0) atomicExch(err, 1u);
 
+  uint32_t res[16];
+  {
+    const uint32_t w40 = g->w256[5];  // 2^40 mod p
+#pragma unroll
+    for (int j = 0; j < 16; j++)
+      res[j] = tnc_dev::mod_reduce(tnc_dev::mod_reduce(lo[j], p, mu) +
+                                       (uint64_t)tnc_dev::mod_reduce(hi[j], p, mu) * w40,
+                                   p, mu);
+  }
   if (ok) {
     // C[o(m, n)]: o = sum of the output weights of m's and n's bits
     const uint32_t m = m0 + quarter * 32u + lane;
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
 #pragma unroll
       for (int j = 0; j < 4; j++)
         if ((jn >> j) & 1) on += g->wn[j];
-      C[om + on] = (uint32_t)acc[jn];
+      C[om + on] = res[jn];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
