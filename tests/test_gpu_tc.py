@@ -91,3 +91,41 @@ def test_split_k_final_dot_product(path):
     else:
         pytest.skip("no split-K step among the seeds")
     assert tnc.contract(p, n_residues=4, path=path).counts == oracle.count(f, max_rank=28)
+
+
+# ---------------------------------------------------------------- full C4 size
+# #Cubic-Vertex-Cover on 180 vertices (counts near 2^125, 8 residues): the
+# oracle cannot finish these contractions, so parity rests on properties that
+# hold at any size, each able to expose a wrong residue or a wrong CRT.
+
+def _c4(seed=0):
+    f = I.cubic_vertex_cover(180, seed)
+    return f, tnc.plan_formula(f, heuristic="best", rank_cap=30)
+
+
+def test_c4_tc_equals_int64_and_primes_agree():
+    f, p = _c4(0)
+    a = tnc.contract(p, n_residues=8, path="tc")
+    b = tnc.contract(p, n_residues=8, path="int64")
+    assert a.counts == b.counts and a.flags == 0
+    # a disjoint set of 8 primes (below 2^31, near 2^31) must rebuild the same integer
+    other = [2147483647, 2147483629, 2147483587, 2147483579, 2147483563, 2147483549, 2147483543, 2147483497]
+    c = tnc.contract(p, n_residues=8, primes=other, path="tc")
+    assert c.counts == a.counts and c.flags == 0
+    assert 2 ** 100 < a.counts[0] < 2 ** 180
+
+
+def test_c4_vertex_covers_equal_independent_sets():
+    f, p = _c4(0)
+    g = I.independent_set_formula(180, I.random_cubic_graph(180, 0))
+    q = tnc.plan_formula(g, heuristic="best", rank_cap=30)
+    assert tnc.contract(p, n_residues=8, path="tc").counts == tnc.contract(q, n_residues=8, path="tc").counts
+
+
+def test_c4_order_independence():
+    f = I.cubic_vertex_cover(180, 4)
+    counts = set()
+    for h in ("gn", "bisect", "best"):
+        p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
+        counts.add(tnc.contract(p, n_residues=8, path="tc").counts[0])
+    assert len(counts) == 1
