@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--planner", default="best")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c4"],
-                    help="c2: batch of cubic VC n=60 (default); c4: cubic VC n=180, 8 residues, "
-                         "tensor-core vs CUDA-core path")
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
+                         "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
+    ap.add_argument("--formulas", type=int, default=0, help="c3/c4: number of formulas (0 = the config's)")
     return ap.parse_args()
 
 
@@ -198,6 +199,71 @@ def c4_workload(count=16, n=180):
     return kept
 
 
+def run_c3(args):
+    """4096 monotone 1-in-3 formulas, n ~ U{50..150}, m = round(n U[0.5, 0.8)),
+    2 residues.  Formulas whose best plan stays at rank <= 14 are counted in one
+    persistent, graph-captured launch; ranks 15..26 one by one on the
+    tensor-core path; plans above rank 26 (tensors beyond 2^26 entries) are
+    left out and reported."""
+    import torch
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import tnc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    Rc, n_total = 2, args.formulas or 4096
+    forms = I.batch_one_in_three(n_total, 2026)
+    t = time.perf_counter()
+    plans = tnc.plan_many(forms, heuristic="best", rank_cap=64)
+    plan_s = time.perf_counter() - t
+    light = [p for p in plans if p.stats.max_rank <= 14]
+    heavy = [p for p in plans if 14 < p.stats.max_rank <= 26]
+    left = [p.stats.max_rank for p in plans if p.stats.max_rank > 26]
+    batch = tnc.Batch(light, n_residues=Rc)
+    ws_b = torch.empty(batch.workspace_bytes(), dtype=torch.uint8, device=dev)
+    ws_h = torch.empty(max([tnc.workspace_bytes(p, Rc) for p in heavy] + [256]), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    batch.upload(ws_b, stream)
+    tuned = batch.autotune(ws_b, stream)
+    macs = sum(p.stats.total_macs for p in light + heavy) * Rc
+
+    def one_step():
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        batch.launch(ws_b, stream)
+        for p in heavy:
+            tnc.contract(p, n_residues=Rc, path="tc", workspace=ws_h, stream=stream)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0
+
+    for _ in range(max(args.warmup, 1)):
+        one_step()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    times = [one_step() for _ in range(args.steps)]
+    clk = clocks.stop()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        batch.launch(ws_b, stream)
+        ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    s = sum(times) / len(times)
+    done = len(light) + len(heavy)
+    line = {
+        "metric": "exact model counts/s", "value": done / s, "unit": "counts/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": s * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 residues (int64 batch; fp16-limb tensor cores for dense steps)",
+        "data": "synthetic",
+        "config": {"workload": f"one_in_three_batch{n_total}_R2", "light_rank_le_14_batched": len(light),
+                   "heavy_rank_15_26_tc": len(heavy), "left_out_rank_gt_26": len(left),
+                   "left_out_ranks": sorted(left), "planner": "best", "autotune": tuned},
+        "modular_macs_per_s": macs / s,
+        "batch_launch_ms": ev0.elapsed_time(ev1), "clocks": clk, "plan_s": plan_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_c4(args):
     """16 #Cubic-VC formulas on 180 vertices, 8 residues: exact counts through
     tnc_contract on the tensor-core path; the CUDA-core path timed once beside it."""
@@ -207,7 +273,7 @@ def run_c4(args):
     torch.cuda.set_device(dev)
     Rc = 8
     t = time.perf_counter()
-    kept = c4_workload()
+    kept = c4_workload(args.formulas or 16)
     plan_s = time.perf_counter() - t
     plans = [k[2] for k in kept]
     ws = torch.empty(max(tnc.workspace_bytes(p, Rc) for p in plans), dtype=torch.uint8, device=dev)
@@ -244,7 +310,7 @@ def run_c4(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1000.0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 residues; fp16 8-bit limbs, fp32 accumulate (exact)",
         "data": "synthetic",
-        "config": {"workload": "cubic_vertex_cover_n180_R8_16formulas", "seeds": [k[0] for k in kept],
+        "config": {"workload": f"cubic_vertex_cover_n180_R8_{len(kept)}formulas", "seeds": [k[0] for k in kept],
                    "max_ranks": [p.stats.max_rank for p in plans], "planner": "best", "path": "tc",
                    "l2": "inputs (up to 18 GB of tensors) far above L2"},
         "modular_macs_per_s": macs / s,
@@ -399,6 +465,8 @@ def main():
         run_reference(args)
     elif args.config == "c4":
         run_c4(args)
+    elif args.config == "c3":
+        run_c3(args)
     else:
         run_tnc(args)
 
