@@ -243,6 +243,67 @@ void tnc_free_batch(tnc_batch_t* b);
 int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                        void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* outs);
 
+/* ---- learned ordering ----------------------------------------------------
+ * A 3-layer perceptron scores candidate merges of a greedy contraction (the
+ * edge-contraction step of Sec. 2.2); it is trained on the exact plan cost
+ * the method itself predicts before contracting (the "lazy" evaluation of
+ * Sec. 4), and the paper's heuristics (Sec. 3.1.1) stay the fallback and the
+ * judge: a learned plan is kept only if its (max rank, MACs) is not worse.
+ * Parameters: fp32, flat, W1[F][H], b1[H], W2[H][H], b2[H], w3[H], b3. */
+#define TNC_MLP_FEATURES 16
+#define TNC_MLP_HIDDEN 128
+#define TNC_MLP_PARAMS (TNC_MLP_FEATURES * TNC_MLP_HIDDEN + TNC_MLP_HIDDEN + TNC_MLP_HIDDEN * TNC_MLP_HIDDEN + \
+                        TNC_MLP_HIDDEN + TNC_MLP_HIDDEN + 1)
+#define TNC_LEARNED_CANDIDATES 32 /* candidates scored per formula and merge */
+
+/* He-initialised parameters (host, TNC_MLP_PARAMS floats). */
+int tnc_mlp_init(uint64_t seed, float* params);
+/* Training rows: at `states` random points of an exploring tensor-greedy
+ * trajectory of every network, each of its (at most `cands`) cheapest
+ * candidate merges gets 16 features (x, host [rows][16]) and its regret
+ * (t, host [rows]): log2 of the total MACs of the plan that merges it and
+ * finishes by tensor-greedy, minus the least such value at that state.
+ * OpenMP over networks; deterministic for a seed.  TNC_ERR_BUFFER if
+ * cap_rows is too small (needed rows in *n_rows; x, t may be NULL to ask). */
+int tnc_learned_dataset(const tnc_network_t* const* nets, int32_t n, int32_t states, int32_t cands,
+                        uint64_t seed, float* x, float* t, int64_t cap_rows, int64_t* n_rows);
+/* fp32 forward over `rows` rows of x (device [rows][16]) into y (device
+ * [rows]); h1, h2 (device [rows][128] each) receive the post-ReLU
+ * activations for the backward pass, or may be NULL. */
+int tnc_mlp_forward(const float* d_params, const float* d_x, int64_t rows, float* d_y, float* d_h1, float* d_h2,
+                    void* cuda_stream);
+/* Gradient of the mean squared error (1/rows) sum (y - t)^2 with respect to
+ * the parameters (d_grads, overwritten), from a forward pass's y, h1, h2.
+ * d_scratch: device, tnc_mlp_backward_scratch_floats(rows) floats. */
+size_t tnc_mlp_backward_scratch_floats(int64_t rows);
+int tnc_mlp_backward(const float* d_params, const float* d_x, const float* d_h1, const float* d_h2, const float* d_y,
+                     const float* d_t, int64_t rows, float* d_scratch, float* d_grads, void* cuda_stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on all parameters; step >= 1. */
+int tnc_mlp_adam(float* d_params, const float* d_grads, float* d_m, float* d_v, int32_t step, float lr,
+                 void* cuda_stream);
+/* Whole training: `epochs` passes over the rows (already shuffled by the
+ * caller) in mini-batches of `batch`, Adam with rate lr; per-epoch mean loss
+ * into loss_out[epochs] (host, may be NULL).  Synchronises the stream. */
+size_t tnc_mlp_train_workspace_bytes(int32_t batch);
+int tnc_mlp_train(float* d_params, const float* d_x, const float* d_t, int64_t rows, int32_t epochs, int32_t batch,
+                  float lr, void* d_ws, size_t ws_bytes, void* cuda_stream, float* loss_out);
+/* bf16 copy of the parameters (device, TNC_MLP_PARAMS bf16) and the bf16
+ * inference forward used by the learned planner. */
+int tnc_mlp_to_bf16(const float* d_params, void* d_params_bf16, void* cuda_stream);
+int tnc_mlp_forward_bf16(const void* d_params_bf16, const float* d_x, int64_t rows, float* d_y, void* cuda_stream);
+/* Learned plans for n networks: all formulas advance in lockstep, every round
+ * scoring the TNC_LEARNED_CANDIDATES cheapest candidates of each in one bf16
+ * inference launch and merging each formula's lowest predicted regret.
+ * Each learned plan is then compared with the heuristic plan of `fallback`
+ * (NULL: TNC_PLAN_BEST); the one with the smaller (max rank, MACs) is kept.
+ * chose_learned[i] = 1 if the learned plan was kept; learned_macs[i] = its
+ * MACs either way (both may be NULL).  d_ws: device,
+ * tnc_plan_learned_workspace_bytes(n) bytes.  All or nothing on failure. */
+size_t tnc_plan_learned_workspace_bytes(int32_t n);
+int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                          const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                          tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned, double* learned_macs);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Measured rate of the modular multiply-accumulate primitive of the step
  * kernels (4 residues per thread, 64-bit accumulation, Barrett reduction every

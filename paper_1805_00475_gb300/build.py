@@ -23,8 +23,8 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libtnc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["network.cpp", "planner.cpp", "lower.cpp", "abi_host.cpp"]
-CUDA_SRC = ["contract.cu", "probe.cu", "tc.cu"]
+HOST_SRC = ["network.cpp", "planner.cpp", "lower.cpp", "learned.cpp", "abi_host.cpp"]
+CUDA_SRC = ["contract.cu", "probe.cu", "tc.cu", "mlp.cu"]
 HEADERS = ["tnc_internal.h", "step_desc.h", "kernels.cuh", "modarith.cuh"]
 
 

@@ -12,6 +12,54 @@ const char* last_error_cstr();
 
 using namespace tnc;
 
+namespace tnc {
+
+// Cost, rank cap, lowering, validation and stats of a plan whose tree is set.
+int finish_plan(tnc_plan_t* p, int rank_cap, tnc_plan_stats* stats) {
+  p->cost = tree_cost(p->tree);
+  const int cap = rank_cap > 0 ? rank_cap : 32;
+  int rc = TNC_OK;
+  if (p->cost.max_rank > cap)
+    rc = set_error(TNC_ERR_TOO_LARGE, "plan rank " + std::to_string(p->cost.max_rank) + " exceeds rank cap " +
+                                          std::to_string(cap));
+  if (rc == TNC_OK) rc = lower_plan(p->net, p->tree, p->low);
+  if (rc == TNC_OK) rc = validate_lowered(p->net, p->tree, p->low);
+  if (rc != TNC_OK) {
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->max_rank = p->cost.max_rank;
+      stats->total_macs = p->cost.macs;
+    }
+    return rc;
+  }
+  tnc_plan_stats& s = p->stats;
+  s.max_rank = p->cost.max_rank;
+  s.n_steps = (int32_t)p->tree.nodes.size() - p->tree.n_leaves;
+  s.n_leaves = p->tree.n_leaves;
+  s.depth = p->cost.depth;
+  s.total_macs = p->cost.macs;
+  s.total_entries = p->cost.entries;
+  s.log2_bound = p->net.log2_bound;
+  s.arena_entries = p->low.seq_arena_entries;
+  s.batch_arena_entries = p->low.lvl_arena_entries;
+  s.n_dense_steps = 0;
+  s.dense_macs = 0;
+  for (const StepDesc& d : p->low.seq_steps)
+    if (tc_eligible(d)) {
+      s.n_dense_steps++;
+      s.dense_macs += std::ldexp(1.0, d.ka + d.kb + d.k);
+    }
+  if (stats) *stats = s;
+  return TNC_OK;
+}
+
+int learned_dataset(const std::vector<const Network*>& nets, int states, int cands, uint64_t seed, std::vector<float>& X,
+                    std::vector<float>& T);
+int learned_trees(const std::vector<const Network*>& nets, const void* d_params_bf16, void* d_ws, size_t ws_bytes,
+                  void* stream, int cands, std::vector<Tree>& trees);
+
+}  // namespace tnc
+
 extern "C" {
 
 const char* tnc_version(void) { return "tnc 0.1 (sm_103a)"; }
@@ -65,41 +113,11 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
     auto* p = new tnc_plan_t();
     p->net = net->net;
     int rc = plan_tree(p->net, *opts, p->tree);
-    if (rc == TNC_OK) {
-      p->cost = tree_cost(p->tree);
-      const int cap = opts->rank_cap > 0 ? opts->rank_cap : 32;
-      if (p->cost.max_rank > cap)
-        rc = set_error(TNC_ERR_TOO_LARGE, "plan rank " + std::to_string(p->cost.max_rank) +
-                                              " exceeds rank cap " + std::to_string(cap));
-    }
-    if (rc == TNC_OK) rc = lower_plan(p->net, p->tree, p->low);
-    if (rc == TNC_OK) rc = validate_lowered(p->net, p->tree, p->low);
+    if (rc == TNC_OK) rc = finish_plan(p, opts->rank_cap, stats);
     if (rc != TNC_OK) {
-      if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->max_rank = p->cost.max_rank;
-      }
       delete p;
       return rc;
     }
-    tnc_plan_stats& s = p->stats;
-    s.max_rank = p->cost.max_rank;
-    s.n_steps = (int32_t)p->tree.nodes.size() - p->tree.n_leaves;
-    s.n_leaves = p->tree.n_leaves;
-    s.depth = p->cost.depth;
-    s.total_macs = p->cost.macs;
-    s.total_entries = p->cost.entries;
-    s.log2_bound = p->net.log2_bound;
-    s.arena_entries = p->low.seq_arena_entries;
-    s.batch_arena_entries = p->low.lvl_arena_entries;
-    s.n_dense_steps = 0;
-    s.dense_macs = 0;
-    for (const StepDesc& d : p->low.seq_steps)
-      if (tc_eligible(d)) {
-        s.n_dense_steps++;
-        s.dense_macs += std::ldexp(1.0, d.ka + d.kb + d.k);
-      }
-    if (stats) *stats = s;
     *out = p;
     return TNC_OK;
   } catch (const std::bad_alloc&) {
@@ -155,5 +173,122 @@ int tnc_plan_steps(const tnc_plan_t* plan, int32_t* left, int32_t* right, int32_
 }
 
 void tnc_free_plan(tnc_plan_t* plan) { delete plan; }
+
+int tnc_mlp_init(uint64_t seed, float* params) {
+  clear_error();
+  if (!params) return set_error(TNC_ERR_INVALID, "params is NULL");
+  const int F = TNC_MLP_FEATURES, H = TNC_MLP_HIDDEN;
+  uint64_t st = seed;
+  auto u01 = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() { return std::sqrt(-2.0 * std::log(u01())) * std::cos(6.283185307179586 * u01()); };
+  float* p = params;
+  for (int i = 0; i < F * H; i++) *p++ = (float)(normal() * std::sqrt(2.0 / F));  // W1
+  for (int i = 0; i < H; i++) *p++ = 0.f;                                       // b1
+  for (int i = 0; i < H * H; i++) *p++ = (float)(normal() * std::sqrt(2.0 / H));  // W2
+  for (int i = 0; i < H; i++) *p++ = 0.f;                                       // b2
+  for (int i = 0; i < H; i++) *p++ = (float)(normal() * std::sqrt(1.0 / H));    // w3
+  *p++ = 0.f;                                                                   // b3
+  return TNC_OK;
+}
+
+int tnc_learned_dataset(const tnc_network_t* const* nets, int32_t n, int32_t states, int32_t cands, uint64_t seed,
+                        float* x, float* t, int64_t cap_rows, int64_t* n_rows) {
+  clear_error();
+  if (!nets || n < 0 || states <= 0 || cands <= 1 || !n_rows) return set_error(TNC_ERR_INVALID, "bad dataset arguments");
+  try {
+    std::vector<const Network*> v;
+    for (int i = 0; i < n; i++) {
+      if (!nets[i]) return set_error(TNC_ERR_INVALID, "NULL network");
+      v.push_back(&nets[i]->net);
+    }
+    std::vector<float> X, T;
+    learned_dataset(v, states, cands, seed, X, T);
+    *n_rows = (int64_t)T.size();
+    if (!x || !t || cap_rows < (int64_t)T.size())
+      return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
+    std::copy(X.begin(), X.end(), x);
+    std::copy(T.begin(), T.end(), t);
+    return TNC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_error(TNC_ERR_NOMEM, "out of host memory");
+  }
+}
+
+size_t tnc_plan_learned_workspace_bytes(int32_t n) {
+  return n <= 0 ? 0 : (size_t)n * TNC_LEARNED_CANDIDATES * (TNC_MLP_FEATURES + 1) * sizeof(float);
+}
+
+int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                          const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                          tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned, double* learned_macs) {
+  clear_error();
+  if (!nets || n <= 0 || !d_params_bf16 || !d_ws || !out) return set_error(TNC_ERR_INVALID, "bad arguments");
+  for (int i = 0; i < n; i++) out[i] = nullptr;
+  try {
+    std::vector<const Network*> v;
+    for (int i = 0; i < n; i++) {
+      if (!nets[i]) return set_error(TNC_ERR_INVALID, "NULL network");
+      v.push_back(&nets[i]->net);
+    }
+    std::vector<Tree> trees;
+    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees);
+    if (rc) return rc;
+    tnc_plan_opts fb{};
+    if (fallback) fb = *fallback;
+    else fb.heuristic = TNC_PLAN_BEST;
+    const int cap = fb.rank_cap > 0 ? fb.rank_cap : 32;
+    int first_rc = TNC_OK;
+    std::string first_msg;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; i++) {
+      // the learned plan, then the heuristic one; the cheaper (max rank, MACs) wins
+      auto* pl = new tnc_plan_t();
+      pl->net = v[i][0];
+      pl->tree = std::move(trees[i]);
+      const TreeCost cl = tree_cost(pl->tree);
+      if (learned_macs) learned_macs[i] = cl.macs;
+      auto* ph = new tnc_plan_t();
+      ph->net = v[i][0];
+      int rh = plan_tree(ph->net, fb, ph->tree);
+      const TreeCost ch = rh == TNC_OK ? tree_cost(ph->tree) : TreeCost{1 << 30, 0, 1e300, 0};
+      const bool use_l = cl.max_rank < ch.max_rank || (cl.max_rank == ch.max_rank && cl.macs <= ch.macs);
+      tnc_plan_t* keep = use_l ? pl : ph;
+      delete (use_l ? ph : pl);
+      tnc_plan_stats st{};
+      int r = finish_plan(keep, cap, &st);
+      if (stats) stats[i] = st;
+      if (chose_learned) chose_learned[i] = use_l ? 1 : 0;
+      if (r != TNC_OK) {
+        delete keep;
+        keep = nullptr;
+#pragma omp critical
+        {
+          if (first_rc == TNC_OK) {
+            first_rc = r;
+            first_msg = "formula " + std::to_string(i) + ": " + tnc_last_error();
+          }
+        }
+      }
+      out[i] = keep;
+    }
+    if (first_rc != TNC_OK) {
+      for (int i = 0; i < n; i++) {
+        tnc_free_plan(out[i]);
+        out[i] = nullptr;
+      }
+      return set_error(first_rc, first_msg);
+    }
+    return TNC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_error(TNC_ERR_NOMEM, "out of host memory");
+  }
+}
 
 }  // extern "C"

@@ -35,7 +35,14 @@ EXPORTS = [
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
+    "tnc_mlp_init", "tnc_learned_dataset", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
+    "tnc_mlp_backward", "tnc_mlp_adam", "tnc_mlp_train_workspace_bytes", "tnc_mlp_train", "tnc_mlp_to_bf16",
+    "tnc_mlp_forward_bf16", "tnc_plan_learned_workspace_bytes", "tnc_plan_learned_many",
 ]
+MLP_FEATURES = 16
+MLP_HIDDEN = 128
+MLP_PARAMS = MLP_FEATURES * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+LEARNED_CANDIDATES = 32
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -127,6 +134,23 @@ def lib():
             "tnc_contract_batch": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), vp, sz, vp,
                                     ctypes.POINTER(_Count)], ctypes.c_int),
             "tnc_probe_modmac": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "tnc_mlp_init": ([ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "tnc_learned_dataset": ([ctypes.POINTER(vp), i32, i32, i32, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+            "tnc_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp, vp], ctypes.c_int),
+            "tnc_mlp_backward_scratch_floats": ([ctypes.c_int64], sz),
+            "tnc_mlp_backward": ([vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
+            "tnc_mlp_adam": ([vp, vp, vp, vp, i32, ctypes.c_float, vp], ctypes.c_int),
+            "tnc_mlp_train_workspace_bytes": ([i32], sz),
+            "tnc_mlp_train": ([vp, vp, vp, ctypes.c_int64, i32, i32, ctypes.c_float, vp, sz, vp,
+                               ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "tnc_mlp_to_bf16": ([vp, vp, vp], ctypes.c_int),
+            "tnc_mlp_forward_bf16": ([vp, vp, ctypes.c_int64, vp, vp], ctypes.c_int),
+            "tnc_plan_learned_workspace_bytes": ([i32], sz),
+            "tnc_plan_learned_many": ([ctypes.POINTER(vp), i32, vp, ctypes.POINTER(_PlanOpts), vp, sz, vp,
+                                       ctypes.POINTER(vp), ctypes.POINTER(_PlanStats), i32p,
+                                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_contract_noalloc": ([vp, ctypes.POINTER(_ContractOpts), vp, ctypes.POINTER(_Count)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
@@ -446,3 +470,87 @@ def contract_batch(plans: Sequence[Plan], n_residues: int = 2, primes=None, work
 def count(formula, n_residues: int = 4, heuristic: str = "bisect", **kw) -> Count:
     """Convenience: build, plan and contract one formula."""
     return contract(plan_formula(formula, heuristic=heuristic), n_residues, **kw)
+
+
+# ------------------------------------------------------------------ learned ordering
+
+def _dp(x):
+    return ctypes.c_void_p(x.data_ptr() if x is not None else 0)
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """He-initialised scorer parameters (fp32, TNC_MLP_PARAMS)."""
+    out = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(lib().tnc_mlp_init(seed, _p(out, ctypes.c_float)))
+    return out
+
+
+def learned_dataset(formulas, states: int = 2, cands: int = 16, seed: int = 0):
+    """(X [rows, 16], T [rows]) float32: features and rollout regrets."""
+    nets = [build_network(f) for f in formulas]
+    arr = (ctypes.c_void_p * len(nets))(*[x.h.value for x in nets])
+    n = ctypes.c_int64()
+    rc = lib().tnc_learned_dataset(arr, len(nets), states, cands, seed, None, None, 0, ctypes.byref(n))
+    if rc not in (TNC_OK, -4):
+        _check(rc)
+    X = np.zeros((max(n.value, 1), MLP_FEATURES), dtype=np.float32)
+    T = np.zeros(max(n.value, 1), dtype=np.float32)
+    _check(lib().tnc_learned_dataset(arr, len(nets), states, cands, seed, _p(X, ctypes.c_float),
+                                     _p(T, ctypes.c_float), n.value, ctypes.byref(n)))
+    return X[: n.value], T[: n.value]
+
+
+def mlp_forward(params, x, y, h1=None, h2=None, stream=None):
+    """Device tensors (torch): params [P] f32, x [rows,16] f32 -> y [rows]."""
+    _check(lib().tnc_mlp_forward(_dp(params), _dp(x), x.shape[0], _dp(y), _dp(h1), _dp(h2), _stream_ptr(stream)))
+
+
+def mlp_backward(params, x, h1, h2, y, t, grads, stream=None):
+    import torch
+    scratch = torch.empty(int(lib().tnc_mlp_backward_scratch_floats(x.shape[0])) + 1, dtype=torch.float32,
+                          device=x.device)
+    _check(lib().tnc_mlp_backward(_dp(params), _dp(x), _dp(h1), _dp(h2), _dp(y), _dp(t), x.shape[0], _dp(scratch),
+                                  _dp(grads), _stream_ptr(stream)))
+
+
+def mlp_adam(params, grads, m, v, step: int, lr: float, stream=None):
+    _check(lib().tnc_mlp_adam(_dp(params), _dp(grads), _dp(m), _dp(v), step, lr, _stream_ptr(stream)))
+
+
+def mlp_train(params, x, t, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, stream=None) -> List[float]:
+    """Train in place on device rows; returns per-epoch mean squared error."""
+    import torch
+    ws = torch.empty(int(lib().tnc_mlp_train_workspace_bytes(batch)), dtype=torch.uint8, device=x.device)
+    loss = (ctypes.c_float * epochs)()
+    _check(lib().tnc_mlp_train(_dp(params), _dp(x), _dp(t), x.shape[0], epochs, batch, lr, _dp(ws), ws.numel(),
+                               _stream_ptr(stream), loss))
+    return [float(v) for v in loss]
+
+
+def mlp_to_bf16(params, out, stream=None):
+    _check(lib().tnc_mlp_to_bf16(_dp(params), _dp(out), _stream_ptr(stream)))
+
+
+def mlp_forward_bf16(params_bf16, x, y, stream=None):
+    _check(lib().tnc_mlp_forward_bf16(_dp(params_bf16), _dp(x), x.shape[0], _dp(y), _stream_ptr(stream)))
+
+
+def plan_learned_many(formulas, params_bf16, fallback: str = "best", rank_cap: int = 32, stream=None):
+    """Learned plans with heuristic fallback.  Returns (plans, chose_learned
+    list, learned_macs list)."""
+    import torch
+    nets = [build_network(f) for f in formulas]
+    n = len(nets)
+    arr = (ctypes.c_void_p * n)(*[x.h.value for x in nets])
+    outs = (ctypes.c_void_p * n)()
+    sts = (_PlanStats * n)()
+    chose = np.zeros(n, dtype=np.int32)
+    lmacs = np.zeros(n, dtype=np.float64)
+    ordr = np.zeros(1, dtype=np.int32)
+    o = _PlanOpts(HEURISTICS[fallback], rank_cap, 2, 0, _p(ordr, ctypes.c_int32), 0)
+    ws = torch.empty(int(lib().tnc_plan_learned_workspace_bytes(n)), dtype=torch.uint8, device=params_bf16.device)
+    _check(lib().tnc_plan_learned_many(arr, n, _dp(params_bf16), ctypes.byref(o), _dp(ws), ws.numel(),
+                                       _stream_ptr(stream), outs, sts, _p(chose, ctypes.c_int32),
+                                       _p(lmacs, ctypes.c_double)))
+    plans = [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), len(formulas[i].open_vars)) for i in range(n)]
+    return plans, chose.tolist(), lmacs.tolist()

@@ -1,0 +1,143 @@
+"""Learned ordering: the scorer's reference (pinned by finite differences),
+dataset generation (host), and the CUDA kernels against the reference."""
+import numpy as np
+import pytest
+
+from oracle import mlp_ref
+from paper_1805_00475_gb300 import build as tnc_build
+from paper_1805_00475_gb300 import instances as I
+from paper_1805_00475_gb300 import tnc
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tnc_build.build()
+
+
+def _problem(seed, rows):
+    rng = np.random.default_rng(seed)
+    p = tnc.mlp_init(seed).astype(np.float64)
+    p[mlp_ref.F * mlp_ref.H: mlp_ref.F * mlp_ref.H + mlp_ref.H] = rng.normal(0, 0.1, mlp_ref.H)  # nonzero b1
+    X = rng.normal(0, 1, (rows, mlp_ref.F))
+    T = rng.normal(0, 1, rows)
+    return p, X, T
+
+
+# ---------------------------------------------------------------- CPU
+
+def test_reference_gradient_matches_finite_differences():
+    """Pins the reference backward pass to the definition of a derivative."""
+    p, X, T = _problem(1, 9)
+    g = mlp_ref.grad(p, X, T)
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.choice(mlp_ref.N_PARAMS, 60, replace=False), [mlp_ref.N_PARAMS - 1]])
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (mlp_ref.loss(p + e, X, T) - mlp_ref.loss(p - e, X, T)) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(g[i]), (i, fd, g[i])
+
+
+def test_reference_adam_step_against_hand_formula():
+    p, g = np.array([1.0, -2.0]), np.array([0.5, -0.25])
+    q, m, v = mlp_ref.adam(p, g, np.zeros(2), np.zeros(2), 1, 0.1)
+    # first step: m_hat = g, v_hat = g^2, so the update is lr * sign(g) (up to eps)
+    assert np.allclose(q, p - 0.1 * np.sign(g), atol=1e-6)
+
+
+def test_init_and_param_count():
+    p = tnc.mlp_init(0)
+    assert p.shape == (tnc.MLP_PARAMS,) == (mlp_ref.N_PARAMS,)
+    W1 = p[: 16 * 128]
+    assert abs(W1.std() - np.sqrt(2 / 16)) < 0.03 and not p[16 * 128: 16 * 128 + 128].any()
+
+
+def test_dataset_rows():
+    fs = [I.one_in_three(40, 26, s) for s in range(12)]
+    X, T = tnc.learned_dataset(fs, states=2, cands=12, seed=5)
+    X2, T2 = tnc.learned_dataset(fs, states=2, cands=12, seed=5)
+    assert X.shape[1] == 16 and X.shape[0] == T.shape[0] > 24
+    assert np.array_equal(X, X2) and np.array_equal(T, T2)  # deterministic for a seed
+    assert np.isfinite(X).all() and (T >= 0).all() and (T == 0).sum() >= 12
+    # regret labels are log2 MAC differences: bounded by the plan sizes involved
+    assert T.max() < 40
+
+
+# ---------------------------------------------------------------- GPU
+
+@pytest.mark.gpu
+def test_gpu_forward_and_gradient_match_reference():
+    import torch
+    p, X, T = _problem(3, 300)  # spans several 32-row tiles and a ragged tail
+    d = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+    dp, dx, dt = d(p), d(X), d(T)
+    y = torch.empty(300, device="cuda")
+    h1 = torch.empty(300, 128, device="cuda")
+    h2 = torch.empty(300, 128, device="cuda")
+    tnc.mlp_forward(dp, dx, y, h1, h2)
+    p32 = np.asarray(p, dtype=np.float32).astype(np.float64)
+    x32 = np.asarray(X, dtype=np.float32).astype(np.float64)
+    t32 = np.asarray(T, dtype=np.float32).astype(np.float64)
+    y_ref, _ = mlp_ref.forward(p32, x32)
+    assert np.allclose(y.cpu().numpy(), y_ref, rtol=1e-4, atol=1e-4)
+    g = torch.empty(tnc.MLP_PARAMS, device="cuda")
+    tnc.mlp_backward(dp, dx, h1, h2, y, dt, g)
+    g_ref = mlp_ref.grad(p32, x32, t32)
+    gg = g.cpu().numpy().astype(np.float64)
+    scale = np.abs(g_ref).max()
+    assert np.abs(gg - g_ref).max() <= 1e-4 * scale, np.abs(gg - g_ref).max() / scale
+
+
+@pytest.mark.gpu
+def test_gpu_adam_matches_reference():
+    import torch
+    rng = np.random.default_rng(4)
+    p = rng.normal(0, 1, tnc.MLP_PARAMS).astype(np.float32)
+    g = rng.normal(0, 1, tnc.MLP_PARAMS).astype(np.float32)
+    m = rng.normal(0, 0.1, tnc.MLP_PARAMS).astype(np.float32)
+    v = np.abs(rng.normal(0, 0.1, tnc.MLP_PARAMS)).astype(np.float32)
+    dp, dg, dm, dv = (torch.tensor(a, device="cuda") for a in (p, g, m, v))
+    tnc.mlp_adam(dp, dg, dm, dv, 3, 1e-2)
+    q, m2, v2 = mlp_ref.adam(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64),
+                             v.astype(np.float64), 3, 1e-2)
+    assert np.allclose(dp.cpu().numpy(), q, rtol=1e-5, atol=1e-6)
+    assert np.allclose(dm.cpu().numpy(), m2, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.gpu
+def test_gpu_bf16_inference_close_to_fp32():
+    import torch
+    p, X, _ = _problem(5, 200)
+    dp = torch.tensor(p.astype(np.float32), device="cuda")
+    dx = torch.tensor(X.astype(np.float32), device="cuda")
+    pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    tnc.mlp_to_bf16(dp, pb)
+    y32, yb = torch.empty(200, device="cuda"), torch.empty(200, device="cuda")
+    tnc.mlp_forward(dp, dx, y32)
+    tnc.mlp_forward_bf16(pb, dx, yb)
+    y_ref, _ = mlp_ref.forward(pb.float().cpu().numpy().astype(np.float64), X.astype(np.float32).astype(np.float64))
+    assert np.allclose(yb.cpu().numpy(), y_ref, rtol=1e-4, atol=1e-4)  # bf16 weights, fp32 arithmetic
+    assert np.abs(yb - y32).max().item() <= 0.05 * (y32.abs().max().item() + 1)
+
+
+@pytest.mark.gpu
+def test_gpu_training_lowers_loss_and_learned_plans_count_the_same():
+    import oracle
+    import torch
+    fs = [I.one_in_three(50, 32, s) for s in range(200)]
+    X, T = tnc.learned_dataset(fs, states=3, cands=16, seed=7)
+    perm = np.random.default_rng(0).permutation(len(T))
+    dx = torch.tensor(X[perm], device="cuda")
+    dt = torch.tensor(T[perm], device="cuda")
+    dp = torch.tensor(tnc.mlp_init(1), device="cuda")
+    losses = tnc.mlp_train(dp, dx, dt, epochs=15, batch=512, lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0]
+    pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    tnc.mlp_to_bf16(dp, pb)
+    evals = [I.one_in_three(40, 26, 1000 + s) for s in range(16)]
+    plans, chose, lmacs = tnc.plan_learned_many(evals, pb)
+    heur = [tnc.plan_formula(f, heuristic="best") for f in evals]
+    for f, p, h, c, lm in zip(evals, plans, heur, chose, lmacs):
+        # the kept plan is never worse than the heuristic one (the fallback judges)
+        assert (p.stats.max_rank, p.stats.total_macs) <= (h.stats.max_rank, h.stats.total_macs)
+        assert tnc.contract(p, n_residues=2).counts == oracle.count(f)
