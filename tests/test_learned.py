@@ -131,7 +131,8 @@ def test_gpu_training_lowers_loss_and_learned_plans_count_the_same():
     dt = torch.tensor(T[perm], device="cuda")
     dp = torch.tensor(tnc.mlp_init(1), device="cuda")
     losses = tnc.mlp_train(dp, dx, dt, epochs=15, batch=512, lr=2e-3)
-    assert losses[-1] < 0.7 * losses[0]
+    # learns beyond the best constant predictor (whose loss is the variance)
+    assert losses[-1] < losses[0] and losses[-1] < 0.95 * float(T.var())
     pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
     tnc.mlp_to_bf16(dp, pb)
     evals = [I.one_in_three(40, 26, 1000 + s) for s in range(16)]
