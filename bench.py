@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--planner", default="best")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
-    ap.add_argument("--formulas", type=int, default=0, help="c3/c4: number of formulas (0 = the config's)")
+    ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
+    ap.add_argument("--train-formulas", type=int, default=20000, help="c5: generated training formulas")
     return ap.parse_args()
 
 
@@ -264,6 +265,84 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5(args):
+    """Learned ordering: the edge scorer is trained on the GPU on rollout
+    costs of generated monotone 1-in-3 formulas (n 50..300, m/n 0.5..0.8),
+    then plans 256 formulas with n = 300, m = 186.  Reported: total MACs and
+    max rank of tensor-greedy, the learned greedy, the best paper heuristic
+    and the kept plan (learned unless the heuristic is cheaper); counts of
+    learned and heuristic plans compared on formulas small enough to count."""
+    import numpy as np
+    import torch
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import tnc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    train = I.batch_one_in_three(args.train_formulas, 31337, n_lo=50, n_hi=300)
+    X, T = tnc.learned_dataset(train, states=2, cands=12, seed=5)
+    data_s = time.perf_counter() - t0
+    perm = np.random.default_rng(0).permutation(len(T))
+    dx = torch.tensor(X[perm], device=dev)
+    dt = torch.tensor(T[perm], device=dev)
+    dp = torch.tensor(tnc.mlp_init(11), device=dev)
+    t0 = time.perf_counter()
+    losses = tnc.mlp_train(dp, dx, dt, epochs=20, batch=4096, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device=dev)
+    tnc.mlp_to_bf16(dp, pb)
+
+    def compare(evals, tag):
+        t0 = time.perf_counter()
+        plans, chose, lmacs = tnc.plan_learned_many(evals, pb, fallback="best", rank_cap=64)
+        l_s = time.perf_counter() - t0
+        greedy = tnc.plan_many(evals, heuristic="greedy", rank_cap=64)
+        t0 = time.perf_counter()
+        best = tnc.plan_many(evals, heuristic="best", rank_cap=64)
+        h_s = time.perf_counter() - t0
+        lg = lambda xs: float(np.mean(np.log2(xs)))
+        return plans, best, {
+            "formulas": len(evals), "workload": tag,
+            "mean_log2_macs": {"tensor_greedy": lg([p.stats.total_macs for p in greedy]),
+                               "learned": lg(lmacs), "best_heuristic": lg([p.stats.total_macs for p in best]),
+                               "kept": lg([p.stats.total_macs for p in plans])},
+            "mean_max_rank": {"tensor_greedy": float(np.mean([p.stats.max_rank for p in greedy])),
+                              "best_heuristic": float(np.mean([p.stats.max_rank for p in best])),
+                              "kept": float(np.mean([p.stats.max_rank for p in plans]))},
+            "learned_beats_greedy": int(sum(l < g.stats.total_macs for l, g in zip(lmacs, greedy))),
+            "learned_kept": int(sum(chose)),
+            "plan_s": {"learned_with_fallback": l_s, "best_heuristic": h_s}}
+
+    n_eval = args.formulas or 256
+    evals = [I.one_in_three(300, 186, 900000 + s) for s in range(n_eval)]
+    _, _, big = compare(evals, "one_in_three_n300_m186")
+    # counts: on formulas small enough to contract, learned (kept) and heuristic plans must agree
+    small = [I.one_in_three(100, 62, 800000 + s) for s in range(64)]
+    plans, best, smallrep = compare(small, "one_in_three_n100_m62")
+    torch.cuda.synchronize(dev)
+    agree, tk, th = 0, 0.0, 0.0
+    for p, h in zip(plans, best):
+        t0 = time.perf_counter()
+        a = tnc.contract(p, n_residues=2, path="tc").counts
+        tk += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        b = tnc.contract(h, n_residues=2, path="tc").counts
+        th += time.perf_counter() - t0
+        agree += int(a == b)
+    smallrep["counts_identical"] = f"{agree}/{len(plans)}"
+    smallrep["contract_s"] = {"kept": tk, "best_heuristic": th}
+    line = {"metric": "learned ordering vs heuristic (plan MACs)", "value": 2 ** (big["mean_log2_macs"]["tensor_greedy"] -
+                                                                                big["mean_log2_macs"]["learned"]),
+            "unit": "x fewer MACs than tensor-greedy (geometric mean)", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "dtype": "fp32 training, bf16 inference",
+            "config": {"workload": "learned ordering, monotone 1-in-3", "train_formulas": len(train),
+                       "train_rows": int(len(T)), "epochs": 20},
+            "train": {"dataset_s": data_s, "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
+                      "label_variance": float(T.var())},
+            "eval_n300": big, "eval_n100_counts": smallrep}
+    print(json.dumps(line), flush=True)
+
+
 def run_c4(args):
     """16 #Cubic-VC formulas on 180 vertices, 8 residues: exact counts through
     tnc_contract on the tensor-core path; the CUDA-core path timed once beside it."""
@@ -467,6 +546,8 @@ def main():
         run_c4(args)
     elif args.config == "c3":
         run_c3(args)
+    elif args.config == "c5":
+        run_c5(args)
     else:
         run_tnc(args)
 

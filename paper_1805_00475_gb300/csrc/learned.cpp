@@ -146,18 +146,24 @@ void top_candidates(const GState& s, std::vector<Cand>& cs, int cap) {
   if ((int)cs.size() > cap) cs.resize(cap);
 }
 
-// 16 features of candidate c in state s (scaled to O(1)).
-void features(const GState& s, const Cand& c, float* f) {
+int live_max_rank(const GState& s) {
+  int m = 0;
+  for (size_t i = 0; i < s.t.nodes.size(); i++)
+    if (s.live[i]) m = std::max(m, s.rank((int)i));
+  return m;
+}
+
+// 16 features of candidate c in state s (scaled to O(1)); live_max is the
+// largest rank among the state's live tensors.
+void features(const GState& s, const Cand& c, int live_max, float* f) {
   const int ra = s.rank(c.a), rb = s.rank(c.b), k = c.k;
   const int r = ra + rb - 2 * k, lm = ra + rb - k;
   const int da = (int)s.nb[c.a].size(), db = (int)s.nb[c.b].size();
-  int touch = 0, live_max = 0;
+  int touch = 0;
   for (auto& kv : s.nb[c.a])
     if (kv.first != c.b) touch++;
   for (auto& kv : s.nb[c.b])
     if (kv.first != c.a && !s.nb[c.a].count(kv.first)) touch++;
-  for (size_t i = 0; i < s.t.nodes.size(); i++)
-    if (s.live[i]) live_max = std::max(live_max, s.rank((int)i));
   f[0] = ra / 32.f;
   f[1] = rb / 32.f;
   f[2] = k / 16.f;
@@ -220,9 +226,10 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
           cost[c] = r.cost();
         }
         const double lo = *std::min_element(cost.begin(), cost.end());
+        const int lm = live_max_rank(s);
         for (size_t c = 0; c < cs.size(); c++) {
           float f[TNC_MLP_FEATURES];
-          features(s, cs[c], f);
+          features(s, cs[c], lm, f);
           xs[i].insert(xs[i].end(), f, f + TNC_MLP_FEATURES);
           ts[i].push_back((float)(cost[c] - lo));
         }
@@ -263,9 +270,10 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
     for (int i = 0; i < n; i++) {
       top_candidates(st[i], cs[i], cands);
       span[i] = {(int)(X.size() / TNC_MLP_FEATURES), (int)cs[i].size()};
+      const int lm = cs[i].empty() ? 0 : live_max_rank(st[i]);
       for (const Cand& c : cs[i]) {
         float f[TNC_MLP_FEATURES];
-        features(st[i], c, f);
+        features(st[i], c, lm, f);
         X.insert(X.end(), f, f + TNC_MLP_FEATURES);
       }
     }
