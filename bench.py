@@ -280,17 +280,27 @@ def run_c5(args):
     torch.cuda.set_device(dev)
     t0 = time.perf_counter()
     train = I.batch_one_in_three(args.train_formulas, 31337, n_lo=50, n_hi=300)
-    X, T = tnc.learned_dataset(train, states=2, cands=12, seed=5)
+    X, T = tnc.learned_dataset(train, states=2, cands=tnc.LEARNED_CANDIDATES, seed=5)
     data_s = time.perf_counter() - t0
-    perm = np.random.default_rng(0).permutation(len(T))
-    dx = torch.tensor(X[perm], device=dev)
-    dt = torch.tensor(T[perm], device=dev)
     dp = torch.tensor(tnc.mlp_init(11), device=dev)
-    t0 = time.perf_counter()
-    losses = tnc.mlp_train(dp, dx, dt, epochs=20, batch=4096, lr=2e-3)
-    train_s = time.perf_counter() - t0
     pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device=dev)
-    tnc.mlp_to_bf16(dp, pb)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    losses = []
+    for rnd in range(2):
+        # round 0: states of exploring tensor-greedy trajectories; round 1 adds
+        # the states the learned planner itself visits (on a quarter of the formulas)
+        if rnd == 1:
+            t1 = time.perf_counter()
+            X2, T2 = tnc.learned_dataset_on_policy(train[: len(train) // 4], pb, states=2, seed=6)
+            data_s += time.perf_counter() - t1
+            X, T = np.concatenate([X, X2]), np.concatenate([T, T2])
+        perm = rng.permutation(len(T))
+        dx = torch.tensor(X[perm], device=dev)
+        dt = torch.tensor(T[perm], device=dev)
+        losses += tnc.mlp_train(dp, dx, dt, epochs=20, batch=4096, lr=2e-3 if rnd == 0 else 1e-3)
+        tnc.mlp_to_bf16(dp, pb)
+    train_s = time.perf_counter() - t0
 
     def compare(evals, tag):
         t0 = time.perf_counter()
@@ -336,7 +346,7 @@ def run_c5(args):
             "unit": "x fewer MACs than tensor-greedy (geometric mean)", "n_gpus": 1, "higher_is_better": True,
             "data": "synthetic", "dtype": "fp32 training, bf16 inference",
             "config": {"workload": "learned ordering, monotone 1-in-3", "train_formulas": len(train),
-                       "train_rows": int(len(T)), "epochs": 20},
+                       "train_rows": int(len(T)), "epochs": "2 rounds x 20", "candidates": tnc.LEARNED_CANDIDATES},
             "train": {"dataset_s": data_s, "train_s": train_s, "loss_first": losses[0], "loss_last": losses[-1],
                       "label_variance": float(T.var())},
             "eval_n300": big, "eval_n100_counts": smallrep}

@@ -254,7 +254,8 @@ int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_cont
 #define TNC_MLP_HIDDEN 128
 #define TNC_MLP_PARAMS (TNC_MLP_FEATURES * TNC_MLP_HIDDEN + TNC_MLP_HIDDEN + TNC_MLP_HIDDEN * TNC_MLP_HIDDEN + \
                         TNC_MLP_HIDDEN + TNC_MLP_HIDDEN + 1)
-#define TNC_LEARNED_CANDIDATES 32 /* candidates scored per formula and merge */
+#define TNC_LEARNED_CANDIDATES 8 /* candidates scored per formula and merge: the cheapest
+                                      by result rank (then MACs), greedy's choice first */
 
 /* He-initialised parameters (host, TNC_MLP_PARAMS floats). */
 int tnc_mlp_init(uint64_t seed, float* params);
@@ -267,6 +268,13 @@ int tnc_mlp_init(uint64_t seed, float* params);
  * cap_rows is too small (needed rows in *n_rows; x, t may be NULL to ask). */
 int tnc_learned_dataset(const tnc_network_t* const* nets, int32_t n, int32_t states, int32_t cands,
                         uint64_t seed, float* x, float* t, int64_t cap_rows, int64_t* n_rows);
+/* As tnc_learned_dataset, but the trajectories follow the learned planner's
+ * own choices (scorer d_params_bf16, TNC_LEARNED_CANDIDATES candidates), so
+ * that a second round of training sees the states the planner visits.
+ * d_ws: tnc_plan_learned_workspace_bytes(n) device bytes. */
+int tnc_learned_dataset_on_policy(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                                  void* d_ws, size_t ws_bytes, void* cuda_stream, int32_t states, uint64_t seed,
+                                  float* x, float* t, int64_t cap_rows, int64_t* n_rows);
 /* fp32 forward over `rows` rows of x (device [rows][16]) into y (device
  * [rows]); h1, h2 (device [rows][128] each) receive the post-ReLU
  * activations for the backward pass, or may be NULL. */

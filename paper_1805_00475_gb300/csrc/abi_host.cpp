@@ -54,9 +54,9 @@ int finish_plan(tnc_plan_t* p, int rank_cap, tnc_plan_stats* stats) {
 }
 
 int learned_dataset(const std::vector<const Network*>& nets, int states, int cands, uint64_t seed, std::vector<float>& X,
-                    std::vector<float>& T);
+                    std::vector<float>& T, const std::vector<std::vector<int>>* policy);
 int learned_trees(const std::vector<const Network*>& nets, const void* d_params_bf16, void* d_ws, size_t ws_bytes,
-                  void* stream, int cands, std::vector<Tree>& trees);
+                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen);
 
 }  // namespace tnc
 
@@ -209,7 +209,36 @@ int tnc_learned_dataset(const tnc_network_t* const* nets, int32_t n, int32_t sta
       v.push_back(&nets[i]->net);
     }
     std::vector<float> X, T;
-    learned_dataset(v, states, cands, seed, X, T);
+    learned_dataset(v, states, cands, seed, X, T, nullptr);
+    *n_rows = (int64_t)T.size();
+    if (!x || !t || cap_rows < (int64_t)T.size())
+      return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
+    std::copy(X.begin(), X.end(), x);
+    std::copy(T.begin(), T.end(), t);
+    return TNC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_error(TNC_ERR_NOMEM, "out of host memory");
+  }
+}
+
+int tnc_learned_dataset_on_policy(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                                  void* d_ws, size_t ws_bytes, void* cuda_stream, int32_t states, uint64_t seed,
+                                  float* x, float* t, int64_t cap_rows, int64_t* n_rows) {
+  clear_error();
+  if (!nets || n <= 0 || !d_params_bf16 || !d_ws || states <= 0 || !n_rows)
+    return set_error(TNC_ERR_INVALID, "bad dataset arguments");
+  try {
+    std::vector<const Network*> v;
+    for (int i = 0; i < n; i++) {
+      if (!nets[i]) return set_error(TNC_ERR_INVALID, "NULL network");
+      v.push_back(&nets[i]->net);
+    }
+    std::vector<Tree> trees;
+    std::vector<std::vector<int>> chosen;
+    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, &chosen);
+    if (rc) return rc;
+    std::vector<float> X, T;
+    learned_dataset(v, states, TNC_LEARNED_CANDIDATES, seed, X, T, &chosen);
     *n_rows = (int64_t)T.size();
     if (!x || !t || cap_rows < (int64_t)T.size())
       return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
@@ -238,7 +267,7 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
       v.push_back(&nets[i]->net);
     }
     std::vector<Tree> trees;
-    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees);
+    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, nullptr);
     if (rc) return rc;
     tnc_plan_opts fb{};
     if (fallback) fb = *fallback;

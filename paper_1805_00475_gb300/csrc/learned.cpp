@@ -154,8 +154,9 @@ int live_max_rank(const GState& s) {
 }
 
 // 16 features of candidate c in state s (scaled to O(1)); live_max is the
-// largest rank among the state's live tensors.
-void features(const GState& s, const Cand& c, int live_max, float* f) {
+// largest rank among the state's live tensors, pos the candidate's position in
+// the tensor-greedy order of the state's candidates (0 = greedy's choice).
+void features(const GState& s, const Cand& c, int live_max, int pos, int n_cands, float* f) {
   const int ra = s.rank(c.a), rb = s.rank(c.b), k = c.k;
   const int r = ra + rb - 2 * k, lm = ra + rb - k;
   const int da = (int)s.nb[c.a].size(), db = (int)s.nb[c.b].size();
@@ -172,14 +173,14 @@ void features(const GState& s, const Cand& c, int live_max, float* f) {
   f[5] = (r - std::max(ra, rb)) / 16.f;
   f[6] = da / 16.f;
   f[7] = db / 16.f;
-  f[8] = s.max_rank / 32.f;
+  f[8] = pos == 0 ? 1.f : 0.f;
   f[9] = (r - s.max_rank) / 16.f;
   f[10] = 1.f - (float)s.n_live / (float)std::max(1, s.n_leaves);
   f[11] = c.a < s.n_leaves ? 1.f : 0.f;
   f[12] = c.b < s.n_leaves ? 1.f : 0.f;
   f[13] = touch / 16.f;
   f[14] = (r - live_max) / 16.f;
-  f[15] = (float)std::log2(s.macs + 1.0) / 64.f;
+  f[15] = (float)pos / (float)std::max(1, n_cands);
 }
 
 struct Rng {
@@ -198,8 +199,11 @@ struct Rng {
 
 // Training rows: at `states` points of an exploring greedy trajectory of each
 // formula, every candidate (at most `cands`) gets its features and its regret.
+// With `policy` set, the trajectory follows instead the choices recorded in
+// policy[i] (merge sequences of a previous learned plan, as candidate
+// positions), so that the scorer also learns on the states it visits itself.
 int learned_dataset(const std::vector<const Network*>& nets, int states, int cands, uint64_t seed, std::vector<float>& X,
-                    std::vector<float>& T) {
+                    std::vector<float>& T, const std::vector<std::vector<int>>* policy = nullptr) {
   const int n = (int)nets.size();
   std::vector<std::vector<float>> xs(n), ts(n);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -229,13 +233,14 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
         const int lm = live_max_rank(s);
         for (size_t c = 0; c < cs.size(); c++) {
           float f[TNC_MLP_FEATURES];
-          features(s, cs[c], lm, f);
+          features(s, cs[c], lm, (int)c, (int)cs.size(), f);
           xs[i].insert(xs[i].end(), f, f + TNC_MLP_FEATURES);
           ts[i].push_back((float)(cost[c] - lo));
         }
       }
-      // explore: mostly the greedy choice, sometimes one of the next three
+      // explore: mostly the greedy choice (or the recorded policy's), sometimes one of the next three
       size_t pick = 0;
+      if (policy && step < (int)(*policy)[i].size()) pick = std::min<size_t>((size_t)(*policy)[i][step], cs.size() - 1);
       if (cs.size() > 1 && rng.next() % 4 == 0) pick = 1 + rng.next() % std::min<size_t>(3, cs.size() - 1);
       s.merge(cs[pick].a, cs[pick].b);
     }
@@ -253,10 +258,11 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
 // candidates of all unfinished formulas, scores them in one bf16 inference
 // launch, and merges each formula's lowest predicted regret.
 int learned_trees(const std::vector<const Network*>& nets, const void* d_params_bf16, void* d_ws, size_t ws_bytes,
-                  void* stream, int cands, std::vector<Tree>& trees) {
+                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen = nullptr) {
   const int n = (int)nets.size();
   std::vector<GState> st(n);
   for (int i = 0; i < n; i++) st[i].init(*nets[i]);
+  if (chosen) chosen->assign(n, {});
   std::vector<std::vector<Cand>> cs(n);
   std::vector<float> X, Y;
   const size_t max_rows = (size_t)n * cands;
@@ -271,9 +277,9 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
       top_candidates(st[i], cs[i], cands);
       span[i] = {(int)(X.size() / TNC_MLP_FEATURES), (int)cs[i].size()};
       const int lm = cs[i].empty() ? 0 : live_max_rank(st[i]);
-      for (const Cand& c : cs[i]) {
+      for (size_t c = 0; c < cs[i].size(); c++) {
         float f[TNC_MLP_FEATURES];
-        features(st[i], c, lm, f);
+        features(st[i], cs[i][c], lm, (int)c, (int)cs[i].size(), f);
         X.insert(X.end(), f, f + TNC_MLP_FEATURES);
       }
     }
@@ -292,6 +298,7 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
       int best = 0;
       for (int c = 1; c < span[i].second; c++)
         if (Y[span[i].first + c] < Y[span[i].first + best]) best = c;
+      if (chosen) (*chosen)[i].push_back(best);
       st[i].merge(cs[i][best].a, cs[i][best].b);
     }
   }

@@ -35,14 +35,14 @@ EXPORTS = [
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
-    "tnc_mlp_init", "tnc_learned_dataset", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
+    "tnc_mlp_init", "tnc_learned_dataset", "tnc_learned_dataset_on_policy", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
     "tnc_mlp_backward", "tnc_mlp_adam", "tnc_mlp_train_workspace_bytes", "tnc_mlp_train", "tnc_mlp_to_bf16",
     "tnc_mlp_forward_bf16", "tnc_plan_learned_workspace_bytes", "tnc_plan_learned_many",
 ]
 MLP_FEATURES = 16
 MLP_HIDDEN = 128
 MLP_PARAMS = MLP_FEATURES * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
-LEARNED_CANDIDATES = 32
+LEARNED_CANDIDATES = 8
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -138,6 +138,9 @@ def lib():
             "tnc_learned_dataset": ([ctypes.POINTER(vp), i32, i32, i32, ctypes.c_uint64,
                                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+            "tnc_learned_dataset_on_policy": ([ctypes.POINTER(vp), i32, vp, vp, sz, vp, i32, ctypes.c_uint64,
+                                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                               ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
             "tnc_mlp_forward": ([vp, vp, ctypes.c_int64, vp, vp, vp, vp], ctypes.c_int),
             "tnc_mlp_backward_scratch_floats": ([ctypes.c_int64], sz),
             "tnc_mlp_backward": ([vp, vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp], ctypes.c_int),
@@ -498,6 +501,26 @@ def learned_dataset(formulas, states: int = 2, cands: int = 16, seed: int = 0):
     _check(lib().tnc_learned_dataset(arr, len(nets), states, cands, seed, _p(X, ctypes.c_float),
                                      _p(T, ctypes.c_float), n.value, ctypes.byref(n)))
     return X[: n.value], T[: n.value]
+
+
+def learned_dataset_on_policy(formulas, params_bf16, states: int = 2, seed: int = 0, stream=None):
+    """Rows along the learned planner's own trajectories (second training round)."""
+    import torch
+    nets = [build_network(f) for f in formulas]
+    n = len(nets)
+    arr = (ctypes.c_void_p * n)(*[x.h.value for x in nets])
+    ws = torch.empty(int(lib().tnc_plan_learned_workspace_bytes(n)), dtype=torch.uint8, device=params_bf16.device)
+    cnt = ctypes.c_int64()
+    rc = lib().tnc_learned_dataset_on_policy(arr, n, _dp(params_bf16), _dp(ws), ws.numel(), _stream_ptr(stream),
+                                             states, seed, None, None, 0, ctypes.byref(cnt))
+    if rc not in (TNC_OK, -4):
+        _check(rc)
+    X = np.zeros((max(cnt.value, 1), MLP_FEATURES), dtype=np.float32)
+    T = np.zeros(max(cnt.value, 1), dtype=np.float32)
+    _check(lib().tnc_learned_dataset_on_policy(arr, n, _dp(params_bf16), _dp(ws), ws.numel(), _stream_ptr(stream),
+                                               states, seed, _p(X, ctypes.c_float), _p(T, ctypes.c_float),
+                                               cnt.value, ctypes.byref(cnt)))
+    return X[: cnt.value], T[: cnt.value]
 
 
 def mlp_forward(params, x, y, h1=None, h2=None, stream=None):

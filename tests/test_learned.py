@@ -125,7 +125,7 @@ def test_gpu_training_lowers_loss_and_learned_plans_count_the_same():
     import oracle
     import torch
     fs = [I.one_in_three(50, 32, s) for s in range(200)]
-    X, T = tnc.learned_dataset(fs, states=3, cands=16, seed=7)
+    X, T = tnc.learned_dataset(fs, states=3, cands=tnc.LEARNED_CANDIDATES, seed=7)
     perm = np.random.default_rng(0).permutation(len(T))
     dx = torch.tensor(X[perm], device="cuda")
     dt = torch.tensor(T[perm], device="cuda")
