@@ -63,9 +63,24 @@ def dist_env():
     return rank, world, local
 
 
+def shard_seeds(rank: int, batch: int):
+    """Seeds of one rank's formulas: ranks own disjoint, contiguous seed ranges
+    (weak scaling: every rank counts `batch` formulas of its own)."""
+    return range(rank * batch, (rank + 1) * batch)
+
+
 def workload(rank: int, batch: int):
     from paper_1805_00475_gb300 import instances as I
-    return [I.cubic_vertex_cover(N_VERTS, rank * batch + i) for i in range(batch)]
+    return [I.cubic_vertex_cover(N_VERTS, s) for s in shard_seeds(rank, batch)]
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time: the one all-reduce of the multi-GPU run (it
+    carries timings only; no formula data moves between ranks)."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def config(args, world):
@@ -475,9 +490,7 @@ def run_tnc(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
     ms = total_ms / args.steps
     value = args.batch * world / (ms / 1000.0)
 
