@@ -564,26 +564,61 @@ int batch_pack(tnc_batch_t* b) {
       }
       steps.push_back(bs);
     }
-    // segments per level: steps of 32+ entries get whole-warp segments, the
-    // smaller ones share packed segments lane by lane
+    // segments per level.  An entry of a step with a long shared sum is split
+    // over 2^sh lanes, so that no lane sums much more than the level's share
+    // per lane of a 256-thread CTA (at least 16 products); steps whose
+    // entries take 32+ lanes get whole-warp segments, the others share packed
+    // segments lane by lane.  Segments are ordered by cost, longest first.
     std::vector<Seg> segs;
     std::vector<uint32_t> items, lvl{0};
     const uint32_t nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
     for (uint32_t l = 0; l < nlev; l++) {
-      std::vector<uint32_t> small;
+      uint64_t work = 0;
+      for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++)
+        work += 1ull << (lw.lvl_steps[si].c + lw.lvl_steps[si].k);
+      uint32_t log_t = 4;
+      while (log_t < 24 && (1ull << log_t) * 256 < work) log_t++;
+      struct Group {
+        uint32_t si, o, sh, cost;
+      };
+      std::vector<Group> small;
+      std::vector<std::pair<uint32_t, Seg>> lsegs;  // (cost, segment)
       for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
-        const uint32_t nout = 1u << lw.lvl_steps[si].c;
-        if (nout < 32) {
-          for (uint32_t o = 0; o < nout; o++) small.push_back(si | (o << 16));
+        const StepDesc& d = lw.lvl_steps[si];
+        uint32_t sh = 0;
+        while (sh < 5 && sh < d.k && d.k - sh > log_t) sh++;
+        const uint32_t cost = 1u << (d.k - sh);
+        const uint32_t nout = 1u << d.c;
+        if ((nout << sh) < 32) {
+          for (uint32_t o = 0; o < nout; o++) small.push_back(Group{si, o, sh, cost});
           continue;
         }
-        for (uint32_t o0 = 0; o0 < nout; o0 += 32) segs.push_back(Seg{o0, (uint16_t)si, 32});
+        for (uint32_t o0 = 0; o0 < nout; o0 += 32u >> sh)
+          lsegs.push_back({cost, Seg{o0, (uint16_t)si, 32, (uint8_t)sh}});
       }
-      for (size_t i0 = 0; i0 < small.size(); i0 += 32) {
-        const uint16_t cnt = (uint16_t)std::min<size_t>(32, small.size() - i0);
-        segs.push_back(Seg{(uint32_t)items.size(), tnc_dev::kPacked, cnt});
-        items.insert(items.end(), small.begin() + i0, small.begin() + i0 + cnt);
+      // widest groups first: each group then starts at a multiple of its size
+      // and never crosses a 32-lane boundary
+      std::stable_sort(small.begin(), small.end(), [](const Group& x, const Group& y) {
+        return x.sh != y.sh ? x.sh > y.sh : x.cost > y.cost;
+      });
+      for (size_t g = 0; g < small.size();) {
+        const uint32_t first = (uint32_t)items.size();
+        uint32_t lanes = 0, cost = 0;
+        const uint8_t sh0 = (uint8_t)small[g].sh;
+        while (g < small.size() && lanes + (1u << small[g].sh) <= 32) {
+          const Group& q = small[g];
+          for (uint32_t j = 0; j < (1u << q.sh); j++) items.push_back(q.si | q.o << 16 | j << 21 | q.sh << 26);
+          lanes += 1u << q.sh;
+          cost = std::max(cost, q.cost);
+          g++;
+        }
+        lsegs.push_back({cost, Seg{first, tnc_dev::kPacked, (uint8_t)lanes, sh0}});
       }
+      std::stable_sort(lsegs.begin(), lsegs.end(),
+                       [](const std::pair<uint32_t, Seg>& x, const std::pair<uint32_t, Seg>& y) {
+                         return x.first > y.first;
+                       });
+      for (const auto& x : lsegs) segs.push_back(x.second);
       lvl.push_back((uint32_t)segs.size());
     }
     // the blob

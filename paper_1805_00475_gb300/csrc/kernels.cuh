@@ -71,16 +71,14 @@ __device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uin
   }
 }
 
-// One output entry of a pairwise step: the sum over the 2^k shared-bond
-// values of A*B, for every residue of the group.  A product of residues is
-// below (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64
-// bits: reduce after every (red_mask+1)-th product and once at the end.
+// Sum over the 2^k shared-bond values of A*B for every residue of the group
+// (A, B point at the operands' first shared-bond entry; consecutive shared
+// values are 2^ka and 2^kb entries apart).  A product of residues is below
+// (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64 bits:
+// reduce after every (red_mask+1)-th product and once at the end.
 template <int RG>
-__device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
-                                              uint64_t ib, const uint32_t* A0, const uint32_t* B0, uint32_t* C0,
-                                              const ModGroup& mg) {
-  const uint32_t* A = A0 + ia * RG;
-  const uint32_t* B = B0 + ib * RG;
+__device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, const uint32_t* A, const uint32_t* B,
+                                         const ModGroup& mg, uint32_t (&out)[RG]) {
   const uint64_t sa = (uint64_t)RG << ka, sb = (uint64_t)RG << kb;
   const uint32_t K = 1u << k;
   uint64_t acc[RG];
@@ -108,9 +106,18 @@ __device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t 
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
-  uint32_t out[RG];
 #pragma unroll
   for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+}
+
+// One output entry of a pairwise step (Sec. 2.1: the permuted operands
+// multiplied as matrices): entry o of C from the operand entries ia, ib.
+template <int RG>
+__device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
+                                              uint64_t ib, const uint32_t* A0, const uint32_t* B0, uint32_t* C0,
+                                              const ModGroup& mg) {
+  uint32_t out[RG];
+  step_sum<RG>(k, ka, kb, A0 + ia * RG, B0 + ib * RG, mg, out);
   store_entry<RG>(C0 + o * RG, out);
 }
 
@@ -365,15 +372,22 @@ struct BStep {
   uint8_t nra, nrb, pad0, pad1;
 };
 
-// The unit of work of one warp.  Either 32 consecutive output entries of one
-// step: step = step index, o0 = first entry; or, for steps of fewer than 32
-// entries, up to 32 entries of several such steps packed lane by lane:
-// step = kPacked, o0 = first of n items (item = step | entry << 16).
+// The unit of work of one warp.  An output entry whose sum runs over 2^k
+// shared values may be split over 2^sh lanes (sh <= min(k, 5)): lane slice j
+// sums the shared values j, j + 2^sh, ..., and the lanes of the entry add
+// their residues with butterfly shuffles.  A segment is either 32 lanes of one
+// step: step = step index, o0 = first entry, lane L takes entry o0 + (L >> sh),
+// slice L & (2^sh - 1); or, for steps whose entries need fewer than 32 lanes,
+// the lanes of several such entries packed side by side: step = kPacked, o0 =
+// first of n lane items, each item = step | entry << 16 | slice << 21 |
+// sh << 26, the entries' lane groups aligned to their size; sh is then the
+// largest split in the segment.
 constexpr uint16_t kPacked = 0xFFFF;
 struct Seg {
   uint32_t o0;
   uint16_t step;
-  uint16_t n;  // active lanes, 1..32
+  uint8_t n;   // active lanes, 1..32
+  uint8_t sh;  // log2 lanes per entry (packed: the largest)
 };
 
 struct BLeaf {
@@ -461,20 +475,44 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       const uint32_t s1 = lvl[l + 1];
       for (uint32_t sg = lvl[l] + warp; sg < s1; sg += nwarps) {
         const Seg seg = segs[sg];
-        if (lane < seg.n) {
-          uint32_t st = seg.step, o = seg.o0 + lane;
-          if (st == kPacked) {
-            const uint32_t it = items[o];
-            st = it & 0xFFFFu;
-            o = it >> 16;
-          }
-          const BStep d = steps[st];
-          const uint16_t* runs = runs_all + d.run0;
-          const uint32_t ia = map_runs(o, runs, d.nra);
-          const uint32_t ib = map_runs(o, runs + d.nra, d.nrb);
-          step_entry_at<RG>(d.k, d.ka, d.kb, o, ia, ib, arena + (uint64_t)d.a_off * RG,
-                            arena + (uint64_t)d.b_off * RG, arena + (uint64_t)d.c_off * RG, mg);
+        uint32_t st = seg.step, o, slice, sh = seg.sh;
+        bool active = true;
+        if (st != kPacked) {
+          o = seg.o0 + (lane >> sh);
+          slice = lane & ((1u << sh) - 1u);
+        } else {
+          active = lane < seg.n;
+          const uint32_t it = items[seg.o0 + (active ? lane : 0)];
+          st = it & 0xFFFFu;
+          o = (it >> 16) & 31u;
+          slice = (it >> 21) & 31u;
+          sh = it >> 26;
         }
+        const BStep d = steps[st];
+        uint32_t out[RG];
+        if (active) {
+          const uint16_t* runs = runs_all + d.run0;
+          const uint32_t ia = map_runs(o, runs, d.nra) + (slice << d.ka);
+          const uint32_t ib = map_runs(o, runs + d.nra, d.nrb) + (slice << d.kb);
+          step_sum<RG>(d.k - sh, d.ka + sh, d.kb + sh, arena + ((uint64_t)d.a_off + ia) * RG,
+                       arena + ((uint64_t)d.b_off + ib) * RG, mg, out);
+        } else {
+#pragma unroll
+          for (int r = 0; r < RG; r++) out[r] = 0;
+        }
+        // lanes of one entry add their partial sums (all lanes take part in
+        // every shuffle; a lane keeps only its own group's partners)
+        for (uint32_t m = 1; m < (1u << seg.sh); m <<= 1) {
+#pragma unroll
+          for (int r = 0; r < RG; r++) {
+            const uint32_t v = __shfl_xor_sync(0xFFFFFFFFu, out[r], m);
+            if (m < (1u << sh)) {
+              const uint32_t t = out[r] + v;
+              out[r] = t >= mg.p[r] ? t - mg.p[r] : t;
+            }
+          }
+        }
+        if (active && slice == 0) store_entry<RG>(arena + ((uint64_t)d.c_off + o) * RG, out);
       }
       __syncthreads();
     }
