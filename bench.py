@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--planner", default="best")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", default="", help="c2: fixed launch shape THREADS,SMEM_BYTES[,CTAS_PER_SM] instead of the autotuner")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
@@ -369,8 +370,10 @@ def run_c5(args):
 
 
 def run_c4(args):
-    """16 #Cubic-VC formulas on 180 vertices, 8 residues: exact counts through
-    tnc_contract on the tensor-core path; the CUDA-core path timed once beside it."""
+    """16 #Cubic-VC formulas on 180 vertices: exact counts through tnc_contract
+    on the 8-bit-prime tensor-core path (timed steps); the 30-bit-prime limb
+    tensor-core path (8 residues) and the CUDA-core int64 path (8 residues)
+    timed once beside it; all three must give the same counts."""
     import torch
     from paper_1805_00475_gb300 import tnc
     dev = torch.device("cuda", 0)
@@ -380,47 +383,68 @@ def run_c4(args):
     kept = c4_workload(args.formulas or 16)
     plan_s = time.perf_counter() - t
     plans = [k[2] for k in kept]
-    ws = torch.empty(max(tnc.workspace_bytes(p, Rc) for p in plans), dtype=torch.uint8, device=dev)
+    # 8-bit primes: the fewest whose product exceeds every certified bound
+    bound = max(p.stats.log2_bound for p in plans)
+    p8_primes, bits = [], 0.0
+    for q in tnc.default_primes(53, "tc_p8"):
+        if bits > bound + 1:
+            break
+        p8_primes.append(q)
+        bits += math.log2(q)
+    R8 = len(p8_primes)
+    ws = torch.empty(max(max(tnc.workspace_bytes(p, Rc) for p in plans),
+                         max(tnc.workspace_bytes(p, R8, "tc_p8") for p in plans)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    macs = sum(p.stats.total_macs for p in plans) * Rc
-    dense = sum(p.stats.dense_macs for p in plans) * Rc
+    macs = sum(p.stats.total_macs for p in plans)
+    dense = sum(p.stats.dense_macs for p in plans)
 
     def one_pass(path):
+        R = R8 if path == "tc_p8" else Rc
         counts = []
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for p in plans:
-            counts.append(tnc.contract(p, n_residues=Rc, path=path, workspace=ws, stream=stream).counts[0])
+            r = tnc.contract(p, n_residues=R, path=path, workspace=ws, stream=stream)
+            assert r.flags == 0
+            counts.append(r.counts[0])
         torch.cuda.synchronize(dev)
         return time.perf_counter() - t0, counts
 
     for _ in range(max(args.warmup, 1)):
-        one_pass("tc")
+        one_pass("tc_p8")
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
     times, counts = [], None
     for _ in range(args.steps):
-        dt, counts = one_pass("tc")
+        dt, counts = one_pass("tc_p8")
         times.append(dt)
     clk = clocks.stop()
+    ttc, counts_tc = one_pass("tc")
     t64, counts64 = one_pass("int64")
-    assert counts == counts64, "tensor-core and CUDA-core paths disagree"
+    assert counts == counts_tc == counts64, "the three arithmetic paths disagree"
     s = sum(times) / len(times)
     pk, pk_kind = peaks()
-    limb_flops = dense * 16 * 2  # 16 limb products of 2 flops per modular MAC on the dense steps
+    # p8 dense steps: one fp16 product (2 flops) per MAC and residue; limb
+    # path: 16 limb products per MAC and residue
+    p8_flops = dense * R8 * 2
     line = {
         "metric": "exact model counts/s", "value": len(plans) / s, "unit": "counts/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1000.0, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32 residues; fp16 8-bit limbs, fp32 accumulate (exact)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 residues mod primes <= 251; dense steps fp16 (exact), fp32 accumulate reduced every 1024",
         "data": "synthetic",
-        "config": {"workload": f"cubic_vertex_cover_n180_R8_{len(kept)}formulas", "seeds": [k[0] for k in kept],
-                   "max_ranks": [p.stats.max_rank for p in plans], "planner": "best", "path": "tc",
+        "config": {"workload": f"cubic_vertex_cover_n180_{len(kept)}formulas", "seeds": [k[0] for k in kept],
+                   "max_ranks": [p.stats.max_rank for p in plans], "planner": "best", "path": "tc_p8",
+                   "residues": R8, "primes": p8_primes, "log2_bound_max": round(bound, 2),
                    "l2": "inputs (up to 18 GB of tensors) far above L2"},
-        "modular_macs_per_s": macs / s,
-        "int64_path": {"ms_per_step": t64 * 1000.0, "modular_macs_per_s": macs / t64, "speedup_tc": t64 / s},
-        "roofline": {"bound": "tensor", "achieved": limb_flops / s / 1e12, "peak": pk["bf16_tflops"],
-                     "unit": "TFLOP/s", "frac": limb_flops / s / 1e12 / pk["bf16_tflops"], "traffic": None,
+        "modular_macs_per_s": macs * R8 / s,
+        "tc_limb_path": {"residues": Rc, "ms_per_step": ttc * 1000.0, "speedup_tc_p8": ttc / s,
+                         "limb_tflops": dense * Rc * 16 * 2 / ttc / 1e12},
+        "int64_path": {"residues": Rc, "ms_per_step": t64 * 1000.0, "modular_macs_per_s": macs * Rc / t64,
+                       "speedup_tc_p8": t64 / s, "speedup_tc_limb": t64 / ttc},
+        "roofline": {"bound": "tensor", "achieved": p8_flops / s / 1e12, "peak": pk["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": p8_flops / s / 1e12 / pk["bf16_tflops"], "traffic": None,
                      "peak_source": f"{pk_kind} bf16 burst (MEASURED_PEAKS.json); fp16 has the same dense rate",
                      "note": "achieved over the whole contraction time, not the dense kernels alone"},
         "clocks": clk, "plan_s": plan_s,
@@ -454,7 +478,12 @@ def run_tnc(args):
     stream = torch.cuda.Stream(device=dev)
     batch.upload(ws, stream)
     t = time.perf_counter()
-    tuned_threads, tuned_smem = batch.autotune(ws, stream)
+    if args.launch:
+        shape = [int(x) for x in args.launch.split(",")] + [0]
+        tuned_threads, tuned_smem, tuned_ctas = shape[:3]
+        batch.set_launch(tuned_threads, tuned_smem, tuned_ctas)
+    else:
+        tuned_threads, tuned_smem, tuned_ctas = batch.autotune(ws, stream)
     tune_s = time.perf_counter() - t
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -544,7 +573,8 @@ def run_tnc(args):
                      "measured_primitive_peak": probe / 1e12,
                      "kernel": "batch_kernel<4>", "algorithmic_macs_per_launch": macs,
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_s_vs_hbm": achieved_gbs / pk["hbm_gbs"]},
-        "autotune": {"threads": tuned_threads, "smem_arena_bytes": tuned_smem, "seconds": tune_s},
+        "autotune": {"threads": tuned_threads, "smem_arena_bytes": tuned_smem, "ctas_per_sm_cap": tuned_ctas,
+                     "seconds": tune_s},
         "clocks": clk,
         "gpu_launches": kpl * args.steps,
         "plan_s": plan_s,

@@ -73,6 +73,15 @@ extern "C" {
                             tcgen05 tensor cores (bf16 limbs, fp32 accumulation below
                             2^24, K chunks of 64); other steps as TNC_PATH_INT64; one
                             pass per residue.  tnc_contract only. */
+#define TNC_PATH_TC_P8 2 /* residues modulo primes p <= 251 (Sec. 3.2's exact counts
+                            from more, smaller residues): each residue is one 8-bit
+                            limb, taken balanced (|r| <= 125) and exact in fp16.
+                            Dense steps (k >= 6, one side >= 2^7 and the other >= 2^4
+                            free entries) run as fp16 GEMMs on tcgen05, operand tiles
+                            by TMA, fp32 accumulation in TMEM reduced mod p in place
+                            every 1024 shared values (1024 * 125^2 + 125 < 2^24: exact);
+                            other steps as TNC_PATH_INT64; one pass per residue.
+                            Workspace: tnc_workspace_bytes_opts.  tnc_contract only. */
 
 /* ---- result flags -------------------------------------------------------- */
 #define TNC_MAYBE_WRAPPED 1u /* the certified bound on the count is not below the
@@ -137,10 +146,12 @@ typedef struct {
 
 typedef struct {
   int32_t path;          /* TNC_PATH_*                                           */
-  int32_t n_residues;    /* R, 1..16                                             */
+  int32_t n_residues;    /* R, 1..16 (TNC_PATH_TC_P8: 1..53)                     */
   const uint32_t* primes;/* host, R distinct primes in (2^29, 2^31); NULL = the R
                             largest primes below 2^30 (16 residue products fit a
-                            64-bit accumulator between reductions; 4 near 2^31) */
+                            64-bit accumulator between reductions; 4 near 2^31).
+                            TNC_PATH_TC_P8: R distinct primes in [3, 251]; NULL =
+                            the R largest (tnc_default_primes_p8)                */
 } tnc_contract_opts;
 
 /* One formula's result.  Caller-allocated host buffers.
@@ -167,6 +178,9 @@ const char* tnc_last_error(void);
 /* The default primes: the n largest below 2^30, descending (deterministic
  * Miller-Rabin). */
 int tnc_default_primes(int32_t n, uint32_t* out /* host, n */);
+/* The default primes of TNC_PATH_TC_P8: the n (<= 53) largest primes <= 251,
+ * descending. */
+int tnc_default_primes_p8(int32_t n, uint32_t* out /* host, n */);
 
 /* ---- network (Sec. 2.1): formula -> COPY + clause tensors, bonds --------- */
 int tnc_build_network(const tnc_formula* f, tnc_network_t** out);
@@ -192,10 +206,16 @@ int tnc_plan_steps(const tnc_plan_t* plan, int32_t* left, int32_t* right, int32_
 void tnc_free_plan(tnc_plan_t* plan);
 
 /* ---- single formula (Sec. 2.1 contraction; one launch per step) --------- */
-/* Device workspace needed by tnc_contract for R residues. */
+/* Device workspace needed by tnc_contract for R residues on TNC_PATH_INT64 or
+ * TNC_PATH_TC. */
 size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues);
+/* Device workspace needed by tnc_contract with these options (any path; adds
+ * TNC_PATH_TC_P8's packed fp16 operands and K-split partials); 0 if the options
+ * are invalid. */
+size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts);
 /* Contracts the plan on the GPU and returns the count(s) in `out` (host).
- * dev_ws: device buffer of at least tnc_workspace_bytes(plan, R) bytes, 256-byte
+ * dev_ws: device buffer of at least tnc_workspace_bytes_opts(plan, opts) bytes
+ * (= tnc_workspace_bytes(plan, R) on TNC_PATH_INT64 and TNC_PATH_TC), 256-byte
  * aligned, owned by the caller, free for the library's use during the call.
  * Synchronises `cuda_stream` before returning. */
 int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws,
@@ -219,13 +239,21 @@ int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, void* cuda_s
  * Requires a prior tnc_batch_upload to the same dev_ws.  The launch sequence is
  * captured once into a CUDA graph per (dev_ws, stream) and replayed. */
 int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream);
-/* Autotuner: times the batch's launch for every CTA size in {64, 128, 256} and
- * shared-memory arena capacity in {0, 16, 32, 48, 64, 96, 128, 200} KiB (capped
- * at the largest formula's arena), keeps the fastest and reports it.  Needs a
- * prior tnc_batch_upload to dev_ws; leaves the results of the last trial in
- * dev_ws; synchronises the stream.  Either out pointer may be NULL. */
+/* Autotuner: times the batch's launch for every CTA size in {128, 256, 512,
+ * 1024}, shared-memory arena capacity in {0, 16, 32, 48, 64, 96, 128, 192} KiB
+ * (capped at the largest formula's arena) and cap on CTAs per SM in {as many
+ * as fit, 2, 1} (fewer CTAs leave more of the SM's memory to L1), keeps the
+ * fastest and reports it.  Needs a prior tnc_batch_upload to dev_ws; leaves
+ * the results of the last trial in dev_ws; synchronises the stream.  Any out
+ * pointer may be NULL. */
 int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t* threads_out,
-                       int32_t* smem_bytes_out);
+                       int32_t* smem_bytes_out, int32_t* ctas_per_sm_out);
+/* Sets the launch shape without timing (threads per CTA in {128, 256, 512,
+ * 1024}, shared-memory arena bytes per CTA, CTAs per SM cap, 0 = as many as
+ * fit; e.g. a shape an earlier autotune chose).  TNC_ERR_INVALID for another
+ * CTA size, TNC_ERR_TOO_LARGE if the CTA does not fit on an SM.  Host only: no
+ * device work is queued. */
+int tnc_batch_set_launch(tnc_batch_t* b, int32_t threads, int32_t smem_bytes, int32_t ctas_per_sm);
 /* Device -> host copy of the results; synchronises the stream.  outs: n counts. */
 int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs);
 /* Bulk form of tnc_batch_download: residues [E][R] and CRT limbs

@@ -24,7 +24,7 @@ LIB = os.path.join(LIBDIR, "libtnc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRC = ["network.cpp", "planner.cpp", "lower.cpp", "learned.cpp", "abi_host.cpp"]
-CUDA_SRC = ["contract.cu", "probe.cu", "tc.cu", "mlp.cu"]
+CUDA_SRC = ["contract.cu", "probe.cu", "tc.cu", "tc_p8.cu", "mlp.cu"]
 HEADERS = ["tnc_internal.h", "step_desc.h", "kernels.cuh", "modarith.cuh"]
 
 

@@ -74,6 +74,14 @@ int tnc_default_primes(int32_t n, uint32_t* out) {
   return TNC_OK;
 }
 
+int tnc_default_primes_p8(int32_t n, uint32_t* out) {
+  clear_error();
+  if (n < 0 || n > kP8MaxResidues || (n > 0 && !out)) return set_error(TNC_ERR_INVALID, "n must be in [0, 53]");
+  std::vector<uint32_t> p = default_primes_p8(n);
+  std::copy(p.begin(), p.end(), out);
+  return TNC_OK;
+}
+
 int tnc_build_network(const tnc_formula* f, tnc_network_t** out) {
   clear_error();
   if (!out) return set_error(TNC_ERR_INVALID, "out is NULL");

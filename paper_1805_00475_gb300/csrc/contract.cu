@@ -66,20 +66,6 @@ Groups split_groups(int R) {
   return g;
 }
 
-// Largest power of two n (<= 16) with n (p-1)^2 + p < 2^64 for every prime of
-// the group: the number of products a 64-bit accumulator takes between
-// reductions.
-uint32_t red_mask_for(const uint32_t* p, int n) {
-  uint32_t best = 16;
-  for (int i = 0; i < n; i++) {
-    const unsigned __int128 sq = (unsigned __int128)(p[i] - 1) * (p[i] - 1);
-    uint32_t m = 16;
-    while (m > 1 && (unsigned __int128)m * sq + p[i] >= ((unsigned __int128)1 << 64)) m >>= 1;
-    best = std::min(best, m);
-  }
-  return best - 1;
-}
-
 struct Arith {
   int R = 0;
   std::vector<uint32_t> primes;
@@ -87,33 +73,33 @@ struct Arith {
   double log2_prod = 0;
   Groups groups;
   ModGroup group(int gi) const {
-    ModGroup m{};
-    for (int r = 0; r < 4; r++) {
-      uint32_t p = r < groups.rg[gi] ? primes[groups.col[gi] + r] : primes[groups.col[gi]];
-      m.p[r] = p;
-      m.mu[r] = ~0ull / p;
-    }
-    m.red_mask = red_mask_for(m.p, 4);
-    return m;
+    uint32_t p[4];
+    for (int r = 0; r < 4; r++) p[r] = r < groups.rg[gi] ? primes[groups.col[gi] + r] : primes[groups.col[gi]];
+    return tnc_dev::make_mod_group(p);
   }
 };
 
 int make_arith(const tnc_contract_opts* o, Arith& a) {
   if (!o) return set_error(TNC_ERR_INVALID, "contract opts NULL");
-  if (o->path != TNC_PATH_INT64 && o->path != TNC_PATH_TC) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
-  if (o->n_residues < 1 || o->n_residues > 16) return set_error(TNC_ERR_INVALID, "n_residues must be in [1, 16]");
+  if (o->path != TNC_PATH_INT64 && o->path != TNC_PATH_TC && o->path != TNC_PATH_TC_P8)
+    return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
+  const bool p8 = o->path == TNC_PATH_TC_P8;
+  const int max_r = p8 ? kP8MaxResidues : 16;
+  if (o->n_residues < 1 || o->n_residues > max_r)
+    return set_error(TNC_ERR_INVALID, p8 ? "n_residues must be in [1, 53]" : "n_residues must be in [1, 16]");
   a.R = o->n_residues;
   if (o->primes) {
     a.primes.assign(o->primes, o->primes + a.R);
     for (int i = 0; i < a.R; i++) {
       uint32_t p = a.primes[i];
-      if (p <= (1u << 29) || p >= (1u << 31) || !is_prime_u32(p))
-        return set_error(TNC_ERR_INVALID, "primes must be primes in (2^29, 2^31)");
+      if (p8 ? (p < 3 || p > kP8PrimeMax || !is_prime_u32(p))
+             : (p <= (1u << 29) || p >= (1u << 31) || !is_prime_u32(p)))
+        return set_error(TNC_ERR_INVALID, p8 ? "primes must be primes in [3, 251]" : "primes must be primes in (2^29, 2^31)");
       for (int j = 0; j < i; j++)
         if (a.primes[j] == p) return set_error(TNC_ERR_INVALID, "primes must be distinct");
     }
   } else {
-    a.primes = default_primes(a.R);
+    a.primes = p8 ? default_primes_p8(a.R) : default_primes(a.R);
   }
   a.crt = CrtConsts{};
   a.crt.R = a.R;
@@ -127,7 +113,8 @@ int make_arith(const tnc_contract_opts* o, Arith& a) {
     a.crt.inv[i] = i == 0 ? 1u : powmod(prod, p - 2, p);
     a.log2_prod += std::log2((double)p);
   }
-  a.crt.n_limbs = (31 * a.R + 31) / 32;
+  // limbs of the CRT value: enough for prod p < 2^(32 n_limbs)
+  a.crt.n_limbs = p8 ? (int)std::floor(a.log2_prod / 32.0) + 1 : (31 * a.R + 31) / 32;
   a.groups = split_groups(a.R);
   return TNC_OK;
 }
@@ -148,8 +135,8 @@ int dispatch_rg(int rg, F&& f) {
 // ---------------------------------------------------------------- single formula
 
 struct SeqLayout {
-  size_t off_leaves, off_tables, off_steps, off_small, off_tc, off_err, off_part, off_results, off_limbs, off_arena,
-      total;
+  size_t off_leaves, off_tables, off_steps, off_small, off_tc, off_err, off_part, off_results, off_limbs, off_p8,
+      off_arena, total;
   uint64_t n_out;
   size_t n_dense;
 };
@@ -217,7 +204,7 @@ GridStep make_grid_step(const StepDesc& d) {
   return g;
 }
 
-SeqLayout seq_layout(const tnc_plan_t* p, int R) {
+SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
   SeqLayout s{};
   const int rg_max = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
   s.n_out = 1ull << p->net.open_vars.size();
@@ -241,13 +228,21 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R) {
     if (splitk_log(d) > 0) part_bytes = std::max<uint64_t>(part_bytes, kSplitPartEntries * rg_max * sizeof(uint32_t));
     if (tc_eligible(d) && tc_split_log(d) > 0)
       part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
+    if (path == TNC_PATH_TC_P8 && p8_eligible(d))
+      part_bytes = std::max<uint64_t>(part_bytes, p8_part_entries(d) * sizeof(uint32_t));
   }
+  uint64_t p8_bytes = 0;
+  if (path == TNC_PATH_TC_P8)
+    for (const StepDesc& d : p->low.lvl_steps)
+      if (p8_eligible(d)) p8_bytes = std::max<uint64_t>(p8_bytes, p8_scratch_bytes(d));
   s.off_part = o;
   o = align_up(o + part_bytes);
   s.off_results = o;
   o = align_up(o + s.n_out * R * sizeof(uint32_t));
   s.off_limbs = o;
   o = align_up(o + s.n_out * ((31 * R + 31) / 32) * sizeof(uint32_t));
+  s.off_p8 = o;
+  o = align_up(o + p8_bytes);
   s.off_arena = o;
   o = align_up(o + std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) * rg_max * sizeof(uint32_t));
   s.total = o;
@@ -278,6 +273,13 @@ extern "C" size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues
   return seq_layout(plan, n_residues).total;
 }
 
+extern "C" size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts) {
+  clear_error();
+  Arith a;
+  if (!plan || make_arith(opts, a)) return 0;
+  return seq_layout(plan, a.R, opts->path).total;
+}
+
 extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
                             void* cuda_stream, tnc_count* out) {
   clear_error();
@@ -285,7 +287,7 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   Arith a;
   int rc = make_arith(opts, a);
   if (rc) return rc;
-  const SeqLayout L = seq_layout(plan, a.R);
+  const SeqLayout L = seq_layout(plan, a.R, opts->path);
   const uint32_t flags = result_flags(plan, a);
   if (plan->tree.nodes.empty()) {  // empty network: the empty product, 1
     std::vector<uint32_t> res(a.R, 1u), limbs(a.crt.n_limbs, 0u);
@@ -307,7 +309,8 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   if (!lw.leaf_tables.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, lw.leaf_tables.data(), lw.leaf_tables.size() * sizeof(uint32_t),
                              cudaMemcpyHostToDevice, st));
-  const bool tc = opts->path == TNC_PATH_TC;
+  const bool p8 = opts->path == TNC_PATH_TC_P8;
+  const bool tc = opts->path == TNC_PATH_TC || p8;
   const size_t ns = lw.lvl_steps.size();
   enum Kind { kSmall, kGrid, kSplit, kTc };
   std::vector<int> kind(ns, kSmall), slot(ns, -1);
@@ -321,7 +324,7 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
     uint32_t work = 0;
     for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
       const StepDesc& d = lw.lvl_steps[i];
-      if (tc && tc_eligible(d)) {
+      if (tc && (p8 ? p8_eligible(d) : tc_eligible(d))) {
         kind[i] = kTc;
         slot[i] = (int)nd++;
       } else if (splitk_log(d) > 0 || d.c >= 16) {
@@ -343,7 +346,7 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
                              st));
   if (!small.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_small, small.data(), small.size() * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
-  if (nd) {
+  if (nd && !p8) {
     tcbuf.assign(nd * a.R * tc_step_bytes(), 0);
     for (size_t i = 0; i < ns; i++)
       if (kind[i] == kTc)
@@ -373,13 +376,9 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   const uint64_t root_off = lw.lvl_steps.empty() ? lw.lvl_leaf_off[plan->tree.root] : lw.lvl_root_off;
   const int sms = sm_count();
   for (size_t gi = 0; gi < groups.rg.size(); gi++) {
-    ModGroup mg{};
-    for (int r = 0; r < 4; r++) {
-      const uint32_t p = r < groups.rg[gi] ? a.primes[groups.col[gi] + r] : a.primes[groups.col[gi]];
-      mg.p[r] = p;
-      mg.mu[r] = ~0ull / p;
-    }
-    mg.red_mask = red_mask_for(mg.p, 4);
+    uint32_t gp[4];
+    for (int r = 0; r < 4; r++) gp[r] = r < groups.rg[gi] ? a.primes[groups.col[gi] + r] : a.primes[groups.col[gi]];
+    const ModGroup mg = tnc_dev::make_mod_group(gp);
     rc = dispatch_rg(groups.rg[gi], [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
       const int nl = (int)leaves.size();
@@ -396,8 +395,13 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
           if (kind[i] == kSmall) continue;
           if (kind[i] == kTc) {
             if (RG != 1) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
-            const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
-            int rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);
+            int rc2;
+            if (p8) {
+              rc2 = p8_launch(lw.lvl_steps[i], a.primes[groups.col[gi]], arena, ws + L.off_p8, part, d_err, sms, st);
+            } else {
+              const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
+              rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);
+            }
             if (rc2) return rc2;
           } else if (kind[i] == kSplit) {
             const uint32_t ls = splitk_log(lw.lvl_steps[i]);
@@ -457,6 +461,7 @@ struct tnc_batch_s {
   uint64_t garena_entries = 0;
   // launch configuration (autotuned)
   int threads = 128;
+  int cta_cap = 0;           // CTAs per SM cap (0: as many as fit)
   size_t smem_bytes = 0;     // dynamic shared memory for arenas (per CTA), beyond the blob
   std::vector<int> grid;     // per residue group
   // graph cache
@@ -473,22 +478,41 @@ namespace {
 
 constexpr size_t kSmemMax = 227 * 1024;
 
+// CTAs of batch_kernel<RG> per SM for (threads, dynamic shared memory),
+// capped at `cap` (0: no cap).  The L1 / shared-memory split is then set to
+// the smallest shared-memory share that holds those CTAs, so that the rest of
+// the SM's 256 KiB serves as L1 for the formulas' global arenas.
 template <int RG>
-int occupancy(int threads, size_t smem, int* blocks) {
-  CUDA_TRY(cudaFuncSetAttribute(tnc_dev::batch_kernel<RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)std::max<size_t>(smem, 1)));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tnc_dev::batch_kernel<RG>, threads, smem));
+int occupancy(int threads, size_t smem, int cap, int* blocks) {
+  auto k = tnc_dev::batch_kernel<RG>;
+  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
+  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  int occ = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem));
+  if (cap > 0) occ = std::min(occ, cap);
+  int dev = 0, per_sm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  if (occ > 0 && per_sm > 0) {
+    const size_t need = (size_t)occ * (smem + 1024 + 64);
+    const int pct = (int)std::min<size_t>(100, (need * 100 + per_sm - 1) / per_sm);
+    CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    int occ2 = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k, threads, smem));
+    if (occ2 < occ) CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  }
+  *blocks = occ;
   return TNC_OK;
 }
 
-// Launch shape for (threads, smem) on every residue group.
-int batch_configure(tnc_batch_t* b, int threads, size_t smem) {
+// Launch shape for (threads, smem, CTAs per SM cap) on every residue group.
+int batch_configure(tnc_batch_t* b, int threads, size_t smem, int cap) {
   const int sms = sm_count();
   std::vector<int> grid;
   for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
     int occ = 0;
     int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
-      return occupancy<decltype(rgc)::value>(threads, b->max_blob + smem, &occ);
+      return occupancy<decltype(rgc)::value>(threads, b->max_blob + smem, cap, &occ);
     });
     if (rc) return rc;
     if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
@@ -496,6 +520,7 @@ int batch_configure(tnc_batch_t* b, int threads, size_t smem) {
   }
   b->threads = threads;
   b->smem_bytes = smem;
+  b->cta_cap = cap;
   b->grid = grid;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
@@ -702,10 +727,10 @@ int batch_pack(tnc_batch_t* b) {
   put(b->off_tables, tables.data(), tables.size() * sizeof(uint32_t));
   put(b->off_perms, perms.data(), perms.size());
   put(b->off_order, order.data(), order.size() * sizeof(uint32_t));
-  // default launch shape: 128 threads, shared-memory arenas up to 64 KiB
+  // default launch shape (the autotuner's usual pick): 256 threads, arenas in
+  // global memory, as many CTAs per SM as fit
   if (b->max_blob > kSmemMax) return set_error(TNC_ERR_TOO_LARGE, "a formula's descriptors exceed shared memory");
-  return batch_configure(b, 128, std::min<size_t>(std::min<size_t>(64 * 1024, kSmemMax - b->max_blob),
-                                                  b->max_arena * rg_max * sizeof(uint32_t)));
+  return batch_configure(b, 256, 0, 0);
 }
 
 int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
@@ -757,6 +782,8 @@ extern "C" int tnc_batch_create(const tnc_plan_t* const* plans, int32_t n, const
   try {
     auto* b = new tnc_batch_t();
     int rc = make_arith(opts, b->a);
+    if (!rc && opts->path == TNC_PATH_TC_P8)
+      rc = set_error(TNC_ERR_INVALID, "TNC_PATH_TC_P8 is a tnc_contract path; batches run TNC_PATH_INT64");
     if (!rc) {
       for (int i = 0; i < n; i++) {
         if (!plans[i]) rc = set_error(TNC_ERR_INVALID, "NULL plan in batch");
@@ -832,7 +859,7 @@ extern "C" int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream)
 }
 
 extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t* threads_out,
-                                  int32_t* smem_out) {
+                                  int32_t* smem_out, int32_t* ctas_out) {
   clear_error();
   if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -847,43 +874,62 @@ extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_strea
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_t = b->threads;
+  int best_t = b->threads, best_c = b->cta_cap;
   size_t best_s = b->smem_bytes;
   int rc = TNC_OK;
-  for (int threads : {64, 128, 256}) {
+  for (int threads : {128, 256, 512, 1024}) {
     for (size_t sm : smems) {
-      rc = batch_configure(b, threads, sm);
-      if (rc == TNC_ERR_TOO_LARGE) {
-        rc = TNC_OK;
-        continue;
+      int prev_grid = -1;
+      for (int cap : {0, 2, 1}) {
+        rc = batch_configure(b, threads, sm, cap);
+        if (rc == TNC_ERR_TOO_LARGE) {
+          rc = TNC_OK;
+          break;
+        }
+        if (rc) break;
+        if (b->grid[0] == prev_grid) continue;  // the cap changes nothing
+        prev_grid = b->grid[0];
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && !rc; rep++) {
+          cudaEventRecord(e0, st);
+          rc = batch_enqueue(b, dev_ws, st);
+          cudaEventRecord(e1, st);
+          if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(TNC_ERR_CUDA, "autotune launch failed");
+          float t = 0;
+          if (!rc) cudaEventElapsedTime(&t, e0, e1);
+          if (rep == 1) ms = t;
+        }
+        if (rc) break;
+        if (ms < best) {
+          best = ms;
+          best_t = threads;
+          best_s = sm;
+          best_c = cap;
+        }
       }
       if (rc) break;
-      float ms = 1e30f;
-      for (int rep = 0; rep < 2 && !rc; rep++) {
-        cudaEventRecord(e0, st);
-        rc = batch_enqueue(b, dev_ws, st);
-        cudaEventRecord(e1, st);
-        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(TNC_ERR_CUDA, "autotune launch failed");
-        float t = 0;
-        if (!rc) cudaEventElapsedTime(&t, e0, e1);
-        if (rep == 1) ms = t;
-      }
-      if (rc) break;
-      if (ms < best) {
-        best = ms;
-        best_t = threads;
-        best_s = sm;
-      }
     }
     if (rc) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  rc = batch_configure(b, best_t, best_s);
+  rc = batch_configure(b, best_t, best_s, best_c);
   if (threads_out) *threads_out = best_t;
   if (smem_out) *smem_out = (int32_t)best_s;
+  if (ctas_out) *ctas_out = best_c;
   return rc;
+}
+
+extern "C" int tnc_batch_set_launch(tnc_batch_t* b, int32_t threads, int32_t smem_bytes, int32_t ctas_per_sm) {
+  clear_error();
+  if (!b) return set_error(TNC_ERR_INVALID, "NULL argument");
+  if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+    return set_error(TNC_ERR_INVALID, "threads must be 128, 256, 512 or 1024");
+  if (ctas_per_sm < 0) return set_error(TNC_ERR_INVALID, "ctas_per_sm must be >= 0");
+  if (smem_bytes < 0 || (size_t)smem_bytes + b->max_blob > kSmemMax)
+    return set_error(TNC_ERR_TOO_LARGE, "shared-memory arena too large");
+  return batch_configure(b, threads, (size_t)smem_bytes, ctas_per_sm);
 }
 
 extern "C" int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs) {
@@ -1094,13 +1140,9 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
   const uint64_t root_off =
       plan->low.seq_steps.empty() ? plan->low.seq_leaf_off[plan->tree.root] : plan->low.seq_root_off;
   for (int gi = 0; gi < n_groups; gi++) {
-    ModGroup mg{};
-    for (int r = 0; r < 4; r++) {
-      const uint32_t p = r < grp_rg[gi] ? primes[grp_col[gi] + r] : primes[grp_col[gi]];
-      mg.p[r] = p;
-      mg.mu[r] = ~0ull / p;
-    }
-    mg.red_mask = red_mask_for(mg.p, 4);
+    uint32_t gp[4];
+    for (int r = 0; r < 4; r++) gp[r] = r < grp_rg[gi] ? primes[grp_col[gi] + r] : primes[grp_col[gi]];
+    const ModGroup mg = tnc_dev::make_mod_group(gp);
     rc = dispatch_rg(grp_rg[gi], [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
       tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(

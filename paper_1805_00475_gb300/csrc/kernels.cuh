@@ -96,7 +96,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     }
     if (((q + 4) & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce_g(acc[r], mg, r);
     }
   }
   for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
@@ -107,7 +107,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) out[r] = mod_reduce_g(acc[r], mg, r);
 }
 
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     if ((++cnt & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce_g(acc[r], mg, r);
     }
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce_g(acc[r], mg, r);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
     for (int r = 0; r < RG; r++) s[r] += part[((o << log_split) + j) * RG + r];  // < 2^31 each, < 2^20 of them
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(s[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce_g(s[r], mg, r);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -316,19 +316,21 @@ __global__ void extract_kernel(const uint32_t* __restrict__ arena, uint64_t root
 // Chinese remaindering by Garner's mixed radix:
 //   v0 = r0,  v_i = (r_i - (v0 + v1 p0 + ... + v_{i-1} p0..p_{i-2})) * inv_i  mod p_i,
 //   X = v0 + p0 (v1 + p1 (v2 + ...)),  0 <= X < p0 p1 ... p_{R-1}.
+constexpr int kCrtMaxResidues = 64;
+constexpr int kCrtMaxLimbs = 17;
 struct CrtConsts {
-  uint32_t p[16];
-  uint64_t mu[16];
-  uint32_t inv[16];  // (p0 ... p_{i-1})^{-1} mod p_i
+  uint32_t p[kCrtMaxResidues];
+  uint64_t mu[kCrtMaxResidues];
+  uint32_t inv[kCrtMaxResidues];  // (p0 ... p_{i-1})^{-1} mod p_i
   int R;
-  int n_limbs;
+  int n_limbs;                    // <= kCrtMaxLimbs
 };
 
 __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_entries, CrtConsts cc,
                            uint32_t* __restrict__ limbs) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_entries;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t v[16];
+    uint32_t v[kCrtMaxResidues];
     const uint32_t* r = residues + e * cc.R;
     for (int i = 0; i < cc.R; i++) {
       const uint32_t p = cc.p[i];
@@ -343,8 +345,8 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
       const uint32_t diff = ri >= t ? ri - t : ri + (p - t);
       v[i] = mod_reduce((uint64_t)diff * cc.inv[i], p, mu);
     }
-    uint32_t x[17];
-    for (int l = 0; l < 17; l++) x[l] = 0;
+    uint32_t x[kCrtMaxLimbs];
+    for (int l = 0; l < kCrtMaxLimbs; l++) x[l] = 0;
     x[0] = v[cc.R - 1];
     for (int i = cc.R - 2; i >= 0; i--) {
       uint64_t carry = v[i];
@@ -364,7 +366,7 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
 // one contiguous, 16-byte aligned blob (steps, segments, packed items, bit-map
 // runs, level table), copied to shared memory in one coalesced pass when a
 // CTA starts the formula.  Offsets are relative to the formula's own arena;
-// a run is a u16: src | dst << 5 | len << 10.
+// a run is a u16 (map_runs).
 struct BStep {
   uint32_t a_off, b_off, c_off;
   uint32_t run0;  // first run of A's map (blob-relative); B's map follows
@@ -422,6 +424,8 @@ struct BatchArgs {
   int col;                // first residue column of this group
 };
 
+// A run of the bit map of an operand, a u16: output bits src .. src+len-1 are
+// the operand's bits dst .. dst+len-1 (src | dst << 5 | len << 10).
 __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, int n) {
   uint32_t a = 0;
   for (int i = 0; i < n; i++) {
@@ -439,7 +443,7 @@ __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, i
 // live in shared memory when the formula's arena fits, else in its own region
 // of global memory.
 template <int RG>
-__global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
+__global__ void __launch_bounds__(1024) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

@@ -70,6 +70,13 @@ std::vector<uint32_t> default_primes(int n) {
   return out;
 }
 
+std::vector<uint32_t> default_primes_p8(int n) {
+  std::vector<uint32_t> out;
+  for (uint32_t x = kP8PrimeMax; (int)out.size() < n && x > 2; x -= 2)
+    if (is_prime_u32(x)) out.push_back(x);
+  return out;
+}
+
 // ---------------------------------------------------------------- network
 
 static int find_root(std::vector<int>& p, int x) {

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) modmac_probe_kernel(uint32_t seed, uint32
     }
     if ((it & 3u) == 3u) {
 #pragma unroll
-      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce_g(acc[r], mg, r);
     }
 #pragma unroll
     for (int i = 0; i < 8; i++) x[i] = (x[i] ^ (x[(i + 1) & 7] >> 3)) & 0x3FFFFFFFu;
@@ -56,12 +56,8 @@ extern "C" int tnc_probe_modmac(void* cuda_stream, int32_t iters, double* macs_p
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, modmac_probe_kernel, 256, 0);
   if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("probe setup: ") + cudaGetErrorString(e));
-  tnc_dev::ModGroup mg{};
   const uint32_t ps[4] = {1073741789u, 1073741783u, 1073741741u, 1073741723u};
-  for (int r = 0; r < 4; r++) {
-    mg.p[r] = ps[r];
-    mg.mu[r] = ~0ull / ps[r];
-  }
+  const tnc_dev::ModGroup mg = tnc_dev::make_mod_group(ps);
   const int blocks = sms * occ;
   cudaEvent_t a = nullptr, b = nullptr;
   unsigned long long* sink = nullptr;

@@ -1,0 +1,593 @@
+// Dense pairwise steps on the 5th-generation tensor cores with residues
+// modulo primes below 2^8 (the TNC_PATH_TC_P8 arithmetic).
+//
+// A step C[m,n] = sum_q A[m,q] B[n,q] mod p (Sec. 2.1: the two tensors
+// permuted and reshaped to matrices over their shared bonds) with p <= 251.
+// Residues are taken balanced, |a|, |b| <= (p-1)/2 <= 125, and are exact as
+// fp16; a product is at most 125^2 = 15625, so 1024 of them plus a residue
+// left from an earlier reduction stay below 2^24 in magnitude, where every
+// fp32 partial sum is an exact integer.  The fp32 tensor-core accumulator
+// therefore takes K in chunks of 1024 exactly; after each chunk the epilogue
+// warps read it from TMEM, reduce it modulo p (in fp32, exactly) and write the
+// residue back, and the next chunk accumulates on top.  One residue is one
+// 8-bit limb: one fp16 MMA per residue instead of the 16 limb pairs of a
+// 30-bit residue (about 7.8 bits of the count per MMA against 1.9).
+//
+// Data path: a pack kernel turns each operand (u32 residues, the lowering's
+// column-major layout: row index low, shared index high) into balanced fp16
+// in a [q/8][row][q%8] layout; one 3-D TMA box {8, rows, 8} of it is exactly
+// the canonical K-major no-swizzle tile (core matrices of 8 rows x 16 bytes).
+// Persistent CTAs (one per SM) run three warp roles:
+//   warp 0, lane 0: TMA producer over a 4-stage shared-memory ring;
+//   warp 1, lane 0: MMA issuer (kind::f16, 128 x TN x 16, fp32 in TMEM);
+//   warps 2..5: epilogue (TMEM lane quarter = warp % 4).
+// A CTA takes its output tiles two at a time, with one TMEM accumulator each,
+// and alternates their K chunks, so one tile's reduction overlaps the other
+// tile's MMAs.  Every wait is bounded (about 2 s); on timeout the kernel
+// records an error word, drains its own copies and MMAs, frees its TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "tnc_internal.h"
+
+namespace tnc_p8 {
+
+constexpr uint32_t kTileM = 128;
+constexpr uint32_t kStageK = 64;
+constexpr uint32_t kChunkK = 1024;
+constexpr uint32_t kStages = 4;
+constexpr uint32_t kThreads = 192;
+constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
+constexpr uint32_t kStageBytes = 48 * 1024;         // A + B (B up to 256 x 64 fp16)
+constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+struct P8Args {
+  uint32_t fa, fb, k, log_split;  // rows 2^fa, columns 2^fb, shared 2^k, K split 2^log_split
+  uint32_t n_items, tiles_m;      // work items (tiles x splits); row tiles
+  uint32_t p, pad;
+  float pf, invp;
+  uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
+  uint32_t* out;            // C, or the split partials [split][2^(fa+fb)]
+};
+
+// ---- PTX helpers -----------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of parity `parity`; false after ~2 s (or 2^26
+// polls if the timer were not to advance).
+__device__ __noinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 0; i < (1u << 26); i++) {
+    if (mbar_try(mbar, parity)) return true;
+    if ((i & 63u) == 63u && gtimer() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 3-D tiled TMA load of box {8, rows, 8} at (0, y, z) into shared memory,
+// completing on mbar with its byte count.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t y, int32_t z,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+// Canonical K-major, no-swizzle shared-memory matrix descriptor: core matrices
+// of 8 rows x 16 bytes; LBO = byte distance between core matrices adjacent in
+// K, SBO = between core matrices adjacent in M/N; version 1; layout 0.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// x (an exact integer of magnitude below 2^24, as fp32) reduced modulo p to
+// a representative of magnitude below 1.2 p: q is x/p rounded to nearest up
+// to the rounding of x * (1/p) (off by at most one), and the fma is exact.
+__device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
+  const float q = rintf(x * invp);
+  return fmaf(-q, pf, x);
+}
+
+// The canonical residue in [0, p) of such a representative.
+__device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
+  int v = __float2int_rn(r);
+  if (v < 0) v += (int)p;
+  if (v < 0) v += (int)p;
+  if (v >= (int)p) v -= (int)p;
+  return (uint32_t)v;
+}
+
+// ---- operand packing ------------------------------------------------------
+
+// X: u32 residues in [0, p), X[q * R + r] (R = 2^f rows, K = 2^k shared
+// values); Y: balanced fp16 residues, Y[((q >> 3) * R + r) * 8 + (q & 7)].
+// Thread i packs row r = i mod R of the 8-group g = i / R: eight loads that
+// are coalesced across the warp, one 16-byte store.
+__global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
+                                                      uint32_t f, uint32_t k, uint32_t p) {
+  const uint64_t R = 1ull << f, n = R << (k - 3);
+  const int hp = (int)(p - 1) / 2;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = i & (R - 1), g = i >> f;
+    uint32_t h[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      int v0 = (int)X[(g * 8 + e) * R + r], v1 = (int)X[(g * 8 + e + 1) * R + r];
+      v0 = v0 > hp ? v0 - (int)p : v0;
+      v1 = v1 > hp ? v1 - (int)p : v1;
+      const __half2 t = __halves2half2(__int2half_rn(v0), __int2half_rn(v1));
+      h[e / 2] = *reinterpret_cast<const uint32_t*>(&t);
+    }
+    *reinterpret_cast<uint4*>(Y + i * 8) = make_uint4(h[0], h[1], h[2], h[3]);
+  }
+}
+
+// Sum of the K-split partials: C[o] = sum_j part[j][o] mod p.
+__global__ void p8_split_final_kernel(const uint32_t* __restrict__ part, uint32_t* __restrict__ C, uint32_t c,
+                                      uint32_t log_split, uint32_t p) {
+  const uint64_t n = 1ull << c;
+  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t s = 0;
+    for (uint32_t j = 0; j < (1u << log_split); j++) s += part[((uint64_t)j << c) + o];
+    C[o] = s % p;
+  }
+}
+
+// ---- the GEMM -------------------------------------------------------------
+
+// Output address weights of the low four column bits for column offset jj.
+__device__ __forceinline__ uint64_t col_lo(const P8Args& g, uint32_t jj) {
+  uint64_t o = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < 4; j++)
+    if ((jj >> j) & 1u) o += g.wn[j];
+  return o;
+}
+
+template <uint32_t TN>
+__global__ void __launch_bounds__(kThreads, 1)
+    p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ P8Args g, uint32_t* err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 5];
+  __shared__ uint32_t tmem_base_s;
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]);
+  const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + 2]);
+  const uint32_t drain = smem_u32(&bars[2 * kStages + 4]);
+  constexpr uint32_t kCols = 2 * TN < 32 ? 32 : 2 * TN;  // two accumulators of TN columns
+  if (threadIdx.x == 0) {
+    for (uint32_t s = 0; s < kStages; s++) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf0, 1);
+    mbar_init(accf0 + 8, 1);
+    mbar_init(acce0, 128);
+    mbar_init(acce0 + 8, 128);
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  // this CTA's work items: bid, bid + G, ... taken two at a time; for each
+  // pair the K chunks alternate between the two (accumulator u = 0, 1)
+  const uint32_t G = gridDim.x, bid = blockIdx.x;
+  const uint32_t T = g.n_items > bid ? (g.n_items - bid + G - 1) / G : 0;
+  const uint32_t Ks = (1u << g.k) >> g.log_split;
+  const uint32_t chunk = Ks < kChunkK ? Ks : kChunkK;
+  const uint32_t n_chunks = Ks / chunk;
+  const uint32_t spc = chunk / kStageK;  // stages per chunk
+  const uint32_t split_mask = (1u << g.log_split) - 1u;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      uint32_t s = 0, ph = 0, issued = 0;
+      for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
+        const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
+        for (uint32_t c = 0; c < n_chunks && ok; c++)
+          for (uint32_t u = 0; u < nu && ok; u++) {
+            const uint32_t item = bid + (t0 + u) * G;
+            const uint32_t split = item & split_mask, tile = item >> g.log_split;
+            const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+            const uint32_t q0 = split * Ks + c * chunk;
+            for (uint32_t j = 0; j < spc; j++) {
+              if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+                ok = false;
+                break;
+              }
+              const uint32_t sa = smem_u32(smem + s * kStageBytes);
+              const int32_t z = (int32_t)((q0 + j * kStageK) >> 3);
+              mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
+              tma_load_3d(sa, &tmA, (int32_t)m0, z, full0 + 8 * s);
+              tma_load_3d(sa + kABytes, &tmB, (int32_t)n0, z, full0 + 8 * s);
+              issued++;
+              if (++s == kStages) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+          }
+      }
+      // every copy issued has landed before the CTA can exit
+      for (uint32_t s2 = 0; s2 < kStages && s2 < issued; s2++) {
+        const uint32_t uses = issued / kStages + (s2 < issued % kStages ? 1u : 0u);
+        if (!mbar_wait(full0 + 8 * s2, (uses - 1u) & 1u)) ok = false;
+      }
+      if (!ok) atomicExch(err, 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = make_idesc(kTileM, TN);
+      uint32_t s = 0, ph = 0, na[2] = {0, 0};
+      for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
+        const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
+        for (uint32_t c = 0; c < n_chunks && ok; c++)
+          for (uint32_t u = 0; u < nu && ok; u++) {
+            if (!mbar_wait(acce0 + 8 * u, (na[u] & 1u) ^ 1u)) {  // the epilogue is done with accumulator u
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + u * TN;
+            for (uint32_t j = 0; j < spc; j++) {
+              if (!mbar_wait(full0 + 8 * s, ph)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(smem + s * kStageBytes), sb = sa + kABytes;
+#pragma unroll
+              for (uint32_t ks = 0; ks < kStageK / 16; ks++) {
+                // 16 K values = two core matrices along K
+                const uint64_t ad = make_desc(sa + ks * 2u * (kTileM * 16u), kTileM * 16u, 128u);
+                const uint64_t bd = make_desc(sb + ks * 2u * (TN * 16u), TN * 16u, 128u);
+                mma_f16(d, ad, bd, idesc, (c | j | ks) ? 1u : 0u);
+              }
+              mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
+              if (++s == kStages) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
+            mma_commit(accf0 + 8 * u);
+            na[u]++;
+          }
+      }
+      // every MMA issued has completed before the TMEM is freed
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) ok = false;
+      if (!ok) atomicExch(err, 1u);
+    }
+  } else {  // epilogue: warps 2..5, TMEM lanes 32 (warp % 4) ..
+    const uint32_t quarter = warp & 3u;
+    const uint32_t row = quarter * 32u + lane;
+    uint32_t na[2] = {0, 0};
+    for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
+      const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
+      for (uint32_t c = 0; c < n_chunks && ok; c++)
+        for (uint32_t u = 0; u < nu && ok; u++) {
+          if (!mbar_wait(accf0 + 8 * u, na[u] & 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tb = tmem + ((quarter * 32u) << 16) + u * TN;
+          if (c + 1 < n_chunks) {  // reduce in place; the next chunk accumulates on top
+            for (uint32_t col = 0; col < TN; col += 16) {
+              uint32_t v[16];
+              tmem_ld16(tb + col, v);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int jj = 0; jj < 16; jj++) v[jj] = __float_as_uint(reduce_p(__uint_as_float(v[jj]), g.pf, g.invp));
+              tmem_st16(tb + col, v);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          } else {  // last chunk: canonical residues to C (or to this split's partials)
+            const uint32_t item = bid + (t0 + u) * G;
+            const uint32_t split = item & split_mask, tile = item >> g.log_split;
+            const uint32_t m = (tile % g.tiles_m) * kTileM + row, n0 = (tile / g.tiles_m) * TN;
+            uint64_t om = 0;
+            for (uint32_t j = 0; j < g.fa; j++)
+              if ((m >> j) & 1u) om += g.wm[j];
+            uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) : 0ull);
+            for (uint32_t col = 0; col < TN; col += 16) {
+              uint32_t v[16];
+              tmem_ld16(tb + col, v);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              uint64_t on = om;
+              for (uint32_t j = 4; j < g.fb; j++)
+                if (((n0 + col) >> j) & 1u) on += g.wn[j];
+#pragma unroll
+              for (uint32_t jj = 0; jj < 16; jj++)
+                outp[on + col_lo(g, jj)] =
+                    canonical(reduce_p(__uint_as_float(v[jj]), g.pf, g.invp), g.p);
+            }
+          }
+          tc_fence_before();
+          mbar_arrive(acce0 + 8 * u);
+          na[u]++;
+        }
+    }
+    if (!ok) atomicExch(err, 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+}  // namespace tnc_p8
+
+namespace tnc {
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, fetched once through the runtime (no
+// link-time dependency on the driver library).
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of a packed operand (rows x K fp16 in [K/8][rows][8] order) with
+// boxes of {8, box_rows, 8}: one box is one K-major no-swizzle tile of 64 K.
+int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
+  EncodeTiled fn = encoder();
+  if (!fn) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[3] = {8, rows, K / 8};
+  const cuuint64_t strides[2] = {16, rows * 16};
+  const cuuint32_t box[3] = {8, box_rows, 8};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return TNC_OK;
+}
+
+struct Shape {
+  bool swap;              // rows come from B
+  uint32_t fa, fb, k, tn;  // row bits, column bits, shared bits, columns per tile
+  uint64_t tiles;
+};
+
+Shape shape_of(const StepDesc& d) {
+  Shape s;
+  s.swap = !(d.ka >= 7 && d.kb >= 4);
+  s.fa = s.swap ? d.kb : d.ka;
+  s.fb = s.swap ? d.ka : d.kb;
+  s.k = d.k;
+  s.tn = std::min<uint32_t>(1u << s.fb, 256u);
+  s.tiles = ((1ull << s.fa) / tnc_p8::kTileM) * ((1ull << s.fb) / s.tn);
+  return s;
+}
+
+template <uint32_t TN>
+int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid, uint32_t* err,
+                cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tnc_p8::kSmemBytes);
+    if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
+    attr = true;
+  }
+  tnc_p8::p8_gemm_kernel<TN><<<grid, tnc_p8::kThreads, tnc_p8::kSmemBytes, st>>>(ma, mb, g, err);
+  return TNC_OK;
+}
+
+}  // namespace
+
+bool p8_eligible(const StepDesc& d) {
+  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
+}
+
+// K split of a dense step: double it while the work items stay below
+// kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
+// (2^c entries per split) stay within 2^26 entries.
+constexpr uint64_t kP8SplitTarget = 160;
+uint32_t p8_split_log(const StepDesc& d) {
+  const Shape s = shape_of(d);
+  uint32_t ls = 0;
+  while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
+  return ls;
+}
+
+uint64_t p8_scratch_bytes(const StepDesc& d) {
+  return 2ull * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
+}
+
+uint64_t p8_part_entries(const StepDesc& d) {
+  const uint32_t ls = p8_split_log(d);
+  return ls ? 1ull << (d.c + ls) : 0;
+}
+
+int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uint32_t* part, uint32_t* dev_err,
+              int sms, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p < 3 || p > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
+  const Shape s = shape_of(d);
+  const uint32_t ls = p8_split_log(d);
+  __half* a16 = (__half*)scratch;
+  __half* b16 = a16 + (1ull << (s.fa + s.k));
+  const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
+  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
+    const uint64_t n = (1ull << f) << (s.k - 3);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
+    tnc_p8::p8_pack_kernel<<<blocks, 256, 0, st>>>(arena + off, dst, f, s.k, p);
+  };
+  pack(a_off, a16, s.fa);
+  pack(b_off, b16, s.fb);
+  CUtensorMap ma, mb;
+  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, tnc_p8::kTileM);
+  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, s.tn);
+  if (rc) return rc;
+  tnc_p8::P8Args g;
+  std::memset(&g, 0, sizeof(g));
+  g.fa = s.fa;
+  g.fb = s.fb;
+  g.k = s.k;
+  g.log_split = ls;
+  g.tiles_m = (1u << s.fa) / tnc_p8::kTileM;
+  if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
+  g.n_items = (uint32_t)(s.tiles << ls);
+  g.p = p;
+  g.pf = (float)p;
+  g.invp = 1.0f / (float)p;
+  // output address weights (the output bit j comes from one operand's free bit)
+  int op[64] = {0}, dst[64] = {0};
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++)
+      for (int q = 0; q < d.map.runs.ra[i].len; q++) {
+        op[d.map.runs.ra[i].src + q] = 0;
+        dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
+      }
+    for (int i = 0; i < d.nrb; i++)
+      for (int q = 0; q < d.map.runs.rb[i].len; q++) {
+        op[d.map.runs.rb[i].src + q] = 1;
+        dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
+      }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      op[j] = d.map.bit[j] >> 7;
+      dst[j] = d.map.bit[j] & 63;
+    }
+  }
+  const int row_op = s.swap ? 1 : 0;
+  for (int j = 0; j < d.c; j++) {
+    if (op[j] == row_op) g.wm[dst[j]] = 1ull << j;
+    else g.wn[dst[j]] = 1ull << j;
+  }
+  g.out = ls ? part : arena + d.c_off;
+  const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
+  switch (s.tn) {
+    case 16: rc = launch_gemm<16>(ma, mb, g, grid, dev_err, st); break;
+    case 32: rc = launch_gemm<32>(ma, mb, g, grid, dev_err, st); break;
+    case 64: rc = launch_gemm<64>(ma, mb, g, grid, dev_err, st); break;
+    case 128: rc = launch_gemm<128>(ma, mb, g, grid, dev_err, st); break;
+    default: rc = launch_gemm<256>(ma, mb, g, grid, dev_err, st); break;
+  }
+  if (rc) return rc;
+  if (ls) {
+    const uint64_t n = 1ull << d.c;
+    tnc_p8::p8_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
+        part, arena + d.c_off, d.c, ls, p);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 launch: ") + cudaGetErrorString(e));
+  return TNC_OK;
+}
+
+}  // namespace tnc

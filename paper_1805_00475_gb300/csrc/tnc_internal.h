@@ -119,10 +119,21 @@ int validate_lowered(const Network& net, const Tree& tree, Lowered& low);
 // 64-bit accumulator between reductions (4 for primes near 2^31).
 constexpr uint32_t kDefaultPrimeBound = 1u << 30;
 std::vector<uint32_t> default_primes(int n);
+// Largest prime of the TNC_PATH_TC_P8 arithmetic, and its default primes.
+constexpr uint32_t kP8PrimeMax = 251;
+constexpr int kP8MaxResidues = 53;  // odd primes in [3, 251]
+std::vector<uint32_t> default_primes_p8(int n);
 bool is_prime_u32(uint32_t n);
 
 // tc.cu: dense steps on the tensor cores (exact 8-bit-limb GEMMs)
 bool tc_eligible(const StepDesc& d);
+// TNC_PATH_TC_P8 dense steps (tc_p8.cu).
+bool p8_eligible(const StepDesc& d);
+uint32_t p8_split_log(const StepDesc& d);
+uint64_t p8_scratch_bytes(const StepDesc& d);
+uint64_t p8_part_entries(const StepDesc& d);
+int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uint32_t* part, uint32_t* dev_err,
+              int sms, void* stream);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
 uint32_t tc_split_log(const StepDesc& d);

@@ -25,14 +25,14 @@ TNC_OK = 0
 ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4: "TNC_ERR_BUFFER",
           -5: "TNC_ERR_TIMEOUT", -6: "TNC_ERR_NOMEM"}
 HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4}
-PATHS = {"int64": 0, "tc": 1}
+PATHS = {"int64": 0, "tc": 1, "tc_p8": 2}
 TNC_MAYBE_WRAPPED = 1
 
 # every symbol include/tnc.h declares
 EXPORTS = [
-    "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes",
-    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune",
+    "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts",
+    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
     "tnc_mlp_init", "tnc_learned_dataset", "tnc_learned_dataset_on_policy", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
@@ -107,6 +107,7 @@ def lib():
             "tnc_version": ([], ctypes.c_char_p),
             "tnc_last_error": ([], ctypes.c_char_p),
             "tnc_default_primes": ([i32, u32p], ctypes.c_int),
+            "tnc_default_primes_p8": ([i32, u32p], ctypes.c_int),
             "tnc_build_network": ([ctypes.POINTER(_Formula), ctypes.POINTER(vp)], ctypes.c_int),
             "tnc_network_info": ([vp, i32p, i32p, i32p], ctypes.c_int),
             "tnc_free_network": ([vp], None),
@@ -117,6 +118,7 @@ def lib():
             "tnc_plan_steps": ([vp, i32p, i32p, i32], ctypes.c_int),
             "tnc_free_plan": ([vp], None),
             "tnc_workspace_bytes": ([vp, i32], sz),
+            "tnc_workspace_bytes_opts": ([vp, vp], sz),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
@@ -126,7 +128,8 @@ def lib():
                                 i32p], ctypes.c_int),
             "tnc_batch_upload": ([vp, vp, sz, vp], ctypes.c_int),
             "tnc_batch_launch": ([vp, vp, vp], ctypes.c_int),
-            "tnc_batch_autotune": ([vp, vp, vp, i32p, i32p], ctypes.c_int),
+            "tnc_batch_autotune": ([vp, vp, vp, i32p, i32p, i32p], ctypes.c_int),
+            "tnc_batch_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
             "tnc_batch_download": ([vp, vp, vp, ctypes.POINTER(_Count)], ctypes.c_int),
             "tnc_batch_download_flat": ([vp, vp, vp, u32p, u32p, u32p], ctypes.c_int),
             "tnc_batch_status": ([vp, vp, vp], ctypes.c_int),
@@ -177,9 +180,11 @@ def version() -> str:
     return lib().tnc_version().decode()
 
 
-def default_primes(n: int) -> List[int]:
+def default_primes(n: int, path: str = "int64") -> List[int]:
+    """The path's default primes (tnc_default_primes; tnc_default_primes_p8 for "tc_p8")."""
     out = np.zeros(max(n, 1), dtype=np.uint32)
-    _check(lib().tnc_default_primes(n, _p(out, ctypes.c_uint32)))
+    fn = lib().tnc_default_primes_p8 if path == "tc_p8" else lib().tnc_default_primes
+    _check(fn(n, _p(out, ctypes.c_uint32)))
     return [int(x) for x in out[:n]]
 
 
@@ -311,7 +316,7 @@ class Count:
 
 
 def _opts(n_residues: int, primes: Optional[Sequence[int]], path: str = "int64"):
-    pr = np.array(list(primes) if primes is not None else default_primes(n_residues), dtype=np.uint32)
+    pr = np.array(list(primes) if primes is not None else default_primes(n_residues, path), dtype=np.uint32)
     o = _ContractOpts(PATHS[path], n_residues, _p(pr, ctypes.c_uint32))
     return o, pr
 
@@ -349,14 +354,19 @@ def _workspace(nbytes: int, ws=None):
     return torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
 
 
-def workspace_bytes(p: Plan, n_residues: int) -> int:
-    return int(lib().tnc_workspace_bytes(p.h, n_residues))
+def workspace_bytes(p: Plan, n_residues: int, path: str = "int64", primes=None) -> int:
+    """tnc_workspace_bytes_opts for the path (tnc_workspace_bytes on int64 / tc)."""
+    o, _ = _opts(n_residues, primes, path)
+    nb = int(lib().tnc_workspace_bytes_opts(p.h, ctypes.byref(o)))
+    if nb == 0:
+        raise TncError(-1, lib().tnc_last_error().decode() or "invalid contract options")
+    return nb
 
 
 def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=None, path: str = "int64") -> Count:
     """Contract one plan on the GPU (tnc_contract); returns exact counts."""
     o, pr = _opts(n_residues, primes, path)
-    nb = workspace_bytes(p, n_residues)
+    nb = workspace_bytes(p, n_residues, path, primes)
     ws = _workspace(nb, workspace)
     c, res, limbs = _count_buffers(1 << p.n_open, n_residues)
     _check(lib().tnc_contract(p.h, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream),
@@ -415,12 +425,17 @@ class Batch:
     def launch(self, ws, stream=None):
         _check(lib().tnc_batch_launch(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
 
-    def autotune(self, ws, stream=None) -> Tuple[int, int]:
-        """tnc_batch_autotune: returns (threads per CTA, shared-memory arena bytes)."""
-        a, b = ctypes.c_int32(), ctypes.c_int32()
+    def autotune(self, ws, stream=None) -> Tuple[int, int, int]:
+        """tnc_batch_autotune: returns (threads per CTA, shared-memory arena
+        bytes, CTAs-per-SM cap with 0 = as many as fit)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib().tnc_batch_autotune(self.h, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream),
-                                        ctypes.byref(a), ctypes.byref(b)))
-        return a.value, b.value
+                                        ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_launch(self, threads: int, smem_bytes: int, ctas_per_sm: int = 0):
+        """tnc_batch_set_launch: fix the launch shape without timing."""
+        _check(lib().tnc_batch_set_launch(self.h, int(threads), int(smem_bytes), int(ctas_per_sm)))
 
     def download(self, ws, stream=None) -> List[Count]:
         n = len(self.plans)

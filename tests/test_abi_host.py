@@ -61,6 +61,27 @@ def test_version_and_primes():
             assert not isprime(x)
 
 
+def test_p8_primes_and_options():
+    """TNC_PATH_TC_P8: its default primes are the odd primes <= 251, largest
+    first (checked by trial division); bad options are refused on the host."""
+    odd_primes = [n for n in range(251, 2, -2) if all(n % d for d in range(3, int(n ** 0.5) + 1, 2))]
+    assert len(odd_primes) == 53
+    assert tnc.default_primes(53, "tc_p8") == odd_primes
+    assert tnc.default_primes(5, "tc_p8") == [251, 241, 239, 233, 229]
+    with pytest.raises(tnc.TncError):
+        tnc.default_primes(54, "tc_p8")
+    p = tnc.plan_formula(I.cubic_vertex_cover(30, 0))
+    assert tnc.workspace_bytes(p, 20, "tc_p8") > 0
+    assert tnc.workspace_bytes(p, 4, "int64") == tnc.lib().tnc_workspace_bytes(p.h, 4)
+    for bad in ([257], [1], [4], [1073741789]):
+        with pytest.raises(tnc.TncError):
+            tnc.workspace_bytes(p, 1, "tc_p8", primes=bad)
+    with pytest.raises(tnc.TncError):
+        tnc.workspace_bytes(p, 54, "tc_p8")
+    with pytest.raises(tnc.TncError):
+        tnc.Batch([p], n_residues=4, path="tc_p8")
+
+
 def test_network_info_and_components():
     f = I.cubic_vertex_cover(20, 0)
     n, bonds, comps = tnc.build_network(f).info()

@@ -1,0 +1,131 @@
+"""The 8-bit-prime tensor-core path (TNC_PATH_TC_P8): residues modulo primes
+<= 251, one fp16 limb each, dense steps as TMA-fed tcgen05 GEMMs with the fp32
+accumulator reduced in place every 1024 shared values.  Residues are compared
+with the CPU oracle's exact count reduced mod each prime, and the CRT values
+with the oracle (small cases) or with the int64 path (large cases)."""
+import pytest
+
+import oracle
+from paper_1805_00475_gb300 import build as tnc_build
+from paper_1805_00475_gb300 import instances as I
+from paper_1805_00475_gb300 import tnc
+
+from test_gpu_tc import _step_shapes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tnc_build.build()
+
+
+def _p8_shape(fa, fb, k):
+    """(rows from B, columns per tile, K chunks, log2 K split) of a step the
+    path runs on the tensor cores, else None (the library's rule restated)."""
+    if not (k >= 6 and ((fa >= 7 and fb >= 4) or (fb >= 7 and fa >= 4))):
+        return None
+    swap = not (fa >= 7 and fb >= 4)
+    r, c = (fb, fa) if swap else (fa, fb)
+    tn = min(1 << c, 256)
+    tiles = (1 << r) // 128 * ((1 << c) // tn)
+    ls = 0
+    while (tiles << ls) < 160 and k - ls - 1 >= 10 and (1 << (fa + fb + ls + 1)) <= (1 << 26):
+        ls += 1
+    return swap, tn, max(1, (1 << (k - ls)) // 1024), ls
+
+
+ORACLE_CASES = [(70, "greedy", 0), (70, "greedy", 1), (70, "greedy", 2), (70, "gn", 1), (70, "bisect", 0),
+                (70, "bisect", 1), (80, "greedy", 0), (80, "gn", 2), (80, "bisect", 2)]
+
+
+@pytest.mark.parametrize("n,h,seed", ORACLE_CASES)
+def test_p8_matches_oracle(n, h, seed):
+    f = I.cubic_vertex_cover(n, seed)
+    p = tnc.plan_formula(f, heuristic=h, rank_cap=28)
+    assert any(_p8_shape(*s) for s in _step_shapes(f, p))
+    exact = oracle.count(f, max_rank=28)
+    r = tnc.contract(p, n_residues=12, path="tc_p8")
+    assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
+    assert r.flags == 0 and r.counts == exact
+
+
+def test_p8_oracle_cases_cover_every_tile_width_and_both_orientations():
+    seen = set()
+    for n, h, seed in ORACLE_CASES:
+        f = I.cubic_vertex_cover(n, seed)
+        p = tnc.plan_formula(f, heuristic=h, rank_cap=28)
+        for s in _step_shapes(f, p):
+            sh = _p8_shape(*s)
+            if sh:
+                seen.add(("tn", sh[1]))
+                seen.add(("swap", sh[0]))
+    assert {("tn", t) for t in (16, 32, 64, 128, 256)} <= seen
+    assert {("swap", True), ("swap", False)} <= seen
+
+
+@pytest.mark.parametrize("n,h,seed", [(100, "greedy", 0), (100, "greedy", 2), (120, "greedy", 2), (120, "bisect", 2)])
+def test_p8_matches_int64_with_k_split(n, h, seed):
+    f = I.cubic_vertex_cover(n, seed)
+    p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
+    shapes = [_p8_shape(*s) for s in _step_shapes(f, p)]
+    assert any(s for s in shapes)
+    a = tnc.contract(p, n_residues=5, path="int64")
+    b = tnc.contract(p, n_residues=20, path="tc_p8")
+    assert a.flags == 0 and b.flags == 0
+    assert a.counts == b.counts
+
+
+def test_p8_k_split_cases_really_split():
+    splits = []
+    for n, h, seed in [(100, "greedy", 2), (120, "greedy", 2)]:
+        f = I.cubic_vertex_cover(n, seed)
+        p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
+        splits += [s[3] for s in map(lambda x: _p8_shape(*x), _step_shapes(f, p)) if s]
+    assert max(splits) >= 2
+
+
+def test_p8_many_chunks_match_int64():
+    """A dense step with 2^16 shared values over 2^2 K slices: 16 chunks of
+    1024 per tile, each reduced in place in TMEM before the next."""
+    f = I.cubic_vertex_cover(180, 1)
+    p = tnc.plan_formula(f, heuristic="best", rank_cap=30)
+    assert max(sh[2] for sh in (_p8_shape(*s) for s in _step_shapes(f, p)) if sh) >= 8
+    a = tnc.contract(p, n_residues=7, path="int64")
+    b = tnc.contract(p, n_residues=26, path="tc_p8")
+    assert a.flags == 0 and b.flags == 0
+    assert a.counts == b.counts
+
+
+def test_p8_one_in_three_with_open_bonds():
+    f = I.one_in_three(60, 40, 3)
+    f.open_vars = [0, 5, 9]
+    p = tnc.plan_formula(f, heuristic="greedy", rank_cap=28)
+    exact = oracle.count(f, max_rank=28)
+    r = tnc.contract(p, n_residues=10, path="tc_p8")
+    assert r.counts == exact
+    for e, row in zip(exact, r.residues):
+        assert [int(x) for x in row] == [e % q for q in r.primes]
+
+
+def test_p8_smallest_primes():
+    """p = 3 (residues -1, 0, 1) up to 251, given by the caller."""
+    f = I.cubic_vertex_cover(70, 1)
+    p = tnc.plan_formula(f, heuristic="greedy", rank_cap=28)
+    primes = [3, 5, 7, 11, 13, 127, 251]
+    exact = oracle.count(f, max_rank=28)[0]
+    r = tnc.contract(p, n_residues=len(primes), primes=primes, path="tc_p8")
+    assert [int(x) for x in r.residues[0]] == [exact % q for q in primes]
+
+
+def test_p8_rejects_bad_options():
+    f = I.cubic_vertex_cover(20, 0)
+    p = tnc.plan_formula(f)
+    with pytest.raises(tnc.TncError):
+        tnc.contract(p, n_residues=2, primes=[257, 251], path="tc_p8")
+    with pytest.raises(tnc.TncError):
+        tnc.contract(p, n_residues=2, primes=[1073741789, 251], path="tc_p8")
+    with pytest.raises(tnc.TncError):
+        tnc.contract(p, n_residues=2, primes=[251, 251], path="tc_p8")
+    with pytest.raises(tnc.TncError):
+        tnc.Batch([p], n_residues=4, path="tc_p8")
