@@ -142,6 +142,8 @@ typedef struct {
   uint64_t batch_arena_entries; /* same for the level-by-level batch schedule     */
   int32_t n_dense_steps;  /* steps TNC_PATH_TC runs on the tensor cores            */
   double dense_macs;      /* their share of total_macs                             */
+  int32_t n_dense_steps_p8; /* steps TNC_PATH_TC_P8 runs on the tensor cores       */
+  double dense_macs_p8;     /* their share of total_macs                           */
 } tnc_plan_stats;
 
 typedef struct {
@@ -213,6 +215,12 @@ size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues);
  * TNC_PATH_TC_P8's packed fp16 operands and K-split partials); 0 if the options
  * are invalid. */
 size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts);
+/* Measurement aid (calling thread only; off by default): with on != 0, every
+ * later tnc_contract brackets each dense (tensor-core) step with CUDA events
+ * on its stream, and tnc_last_dense_time returns the summed device time (ms)
+ * and the number of dense step launches of the last tnc_contract. */
+void tnc_set_step_timing(int32_t on);
+int tnc_last_dense_time(double* ms, int32_t* n_steps);
 /* Contracts the plan on the GPU and returns the count(s) in `out` (host).
  * dev_ws: device buffer of at least tnc_workspace_bytes_opts(plan, opts) bytes
  * (= tnc_workspace_bytes(plan, R) on TNC_PATH_INT64 and TNC_PATH_TC), 256-byte

@@ -44,11 +44,18 @@ int finish_plan(tnc_plan_t* p, int rank_cap, tnc_plan_stats* stats) {
   s.batch_arena_entries = p->low.lvl_arena_entries;
   s.n_dense_steps = 0;
   s.dense_macs = 0;
-  for (const StepDesc& d : p->low.seq_steps)
+  s.n_dense_steps_p8 = 0;
+  s.dense_macs_p8 = 0;
+  for (const StepDesc& d : p->low.seq_steps) {
     if (tc_eligible(d)) {
       s.n_dense_steps++;
       s.dense_macs += std::ldexp(1.0, d.ka + d.kb + d.k);
     }
+    if (p8_eligible(d)) {
+      s.n_dense_steps_p8++;
+      s.dense_macs_p8 += std::ldexp(1.0, d.ka + d.kb + d.k);
+    }
+  }
   if (stats) *stats = s;
   return TNC_OK;
 }

@@ -29,6 +29,11 @@ namespace {
   } while (0)
 
 constexpr size_t kAlign = 256;
+
+// Dense-step timing of tnc_contract (off unless tnc_set_step_timing(1)).
+thread_local bool g_time_dense = false;
+thread_local double g_dense_ms = 0.0;
+thread_local int g_dense_launches = 0;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int sm_count() {
@@ -273,6 +278,14 @@ extern "C" size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues
   return seq_layout(plan, n_residues).total;
 }
 
+extern "C" void tnc_set_step_timing(int32_t on) { g_time_dense = on != 0; }
+
+extern "C" int tnc_last_dense_time(double* ms, int32_t* n_steps) {
+  if (ms) *ms = g_dense_ms;
+  if (n_steps) *n_steps = g_dense_launches;
+  return TNC_OK;
+}
+
 extern "C" size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts) {
   clear_error();
   Arith a;
@@ -365,6 +378,16 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   }
   uint32_t* d_err = (uint32_t*)(ws + L.off_err);
   CUDA_TRY(cudaMemsetAsync(d_err, 0, 64, st));
+  // dense-step events (tnc_set_step_timing), destroyed on every return
+  std::vector<cudaEvent_t> dense_events;
+  struct EventGuard {
+    std::vector<cudaEvent_t>& v;
+    ~EventGuard() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } event_guard{dense_events};
+  g_dense_ms = 0.0;
+  g_dense_launches = 0;
   const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
   const StepDesc* d_small = (const StepDesc*)(ws + L.off_small);
   uint32_t* arena = (uint32_t*)(ws + L.off_arena);
@@ -396,11 +419,22 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
           if (kind[i] == kTc) {
             if (RG != 1) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
             int rc2;
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            if (g_time_dense) {
+              CUDA_TRY(cudaEventCreate(&ev[0]));
+              CUDA_TRY(cudaEventCreate(&ev[1]));
+              CUDA_TRY(cudaEventRecord(ev[0], st));
+            }
             if (p8) {
               rc2 = p8_launch(lw.lvl_steps[i], a.primes[groups.col[gi]], arena, ws + L.off_p8, part, d_err, sms, st);
             } else {
               const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
               rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);
+            }
+            if (g_time_dense) {
+              CUDA_TRY(cudaEventRecord(ev[1], st));
+              dense_events.push_back(ev[0]);
+              dense_events.push_back(ev[1]);
             }
             if (rc2) return rc2;
           } else if (kind[i] == kSplit) {
@@ -434,6 +468,12 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   if (h_err) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
+  for (size_t e = 0; e + 1 < dense_events.size(); e += 2) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, dense_events[e], dense_events[e + 1]));
+    g_dense_ms += ms;
+    g_dense_launches++;
+  }
   return fill_count(out, L.n_out, a, h_res.data(), h_limbs.data(), flags);
 }
 

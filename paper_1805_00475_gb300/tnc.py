@@ -31,7 +31,7 @@ TNC_MAYBE_WRAPPED = 1
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -70,7 +70,8 @@ class _PlanStats(ctypes.Structure):
                 ("depth", ctypes.c_int32), ("total_macs", ctypes.c_double),
                 ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double),
                 ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64),
-                ("n_dense_steps", ctypes.c_int32), ("dense_macs", ctypes.c_double)]
+                ("n_dense_steps", ctypes.c_int32), ("dense_macs", ctypes.c_double),
+                ("n_dense_steps_p8", ctypes.c_int32), ("dense_macs_p8", ctypes.c_double)]
 
 
 class _ContractOpts(ctypes.Structure):
@@ -119,6 +120,8 @@ def lib():
             "tnc_free_plan": ([vp], None),
             "tnc_workspace_bytes": ([vp, i32], sz),
             "tnc_workspace_bytes_opts": ([vp, vp], sz),
+            "tnc_set_step_timing": ([i32], None),
+            "tnc_last_dense_time": ([ctypes.POINTER(ctypes.c_double), i32p], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
@@ -241,6 +244,8 @@ class PlanStats:
     batch_arena_entries: int = 0
     n_dense_steps: int = 0
     dense_macs: float = 0.0
+    n_dense_steps_p8: int = 0
+    dense_macs_p8: float = 0.0
 
 
 class Plan:
@@ -278,7 +283,7 @@ def plan(network: Network, heuristic: str = "bisect", rank_cap: int = 32, tries:
 def _stats(st: _PlanStats) -> PlanStats:
     return PlanStats(st.max_rank, st.n_steps, st.n_leaves, st.depth, st.total_macs, st.total_entries,
                      st.log2_bound, int(st.arena_entries), int(st.batch_arena_entries), int(st.n_dense_steps),
-                     float(st.dense_macs))
+                     float(st.dense_macs), int(st.n_dense_steps_p8), float(st.dense_macs_p8))
 
 
 def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0
@@ -372,6 +377,18 @@ def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=N
     _check(lib().tnc_contract(p.h, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream),
                               ctypes.byref(c)))
     return _to_count(c, res, limbs, pr)
+
+
+def set_step_timing(on: bool):
+    """tnc_set_step_timing: time every dense step of later contractions (this thread)."""
+    lib().tnc_set_step_timing(1 if on else 0)
+
+
+def last_dense_time() -> Tuple[float, int]:
+    """tnc_last_dense_time: (device ms of the dense steps, their count) of the last contraction."""
+    ms, n = ctypes.c_double(), ctypes.c_int32()
+    _check(lib().tnc_last_dense_time(ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def probe_modmac(iters: int = 4096, stream=None) -> float:
