@@ -367,9 +367,10 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
           tc_make_step(lw.lvl_steps[i], a.primes[r], tcbuf.data() + ((size_t)slot[i] * a.R + r) * tc_step_bytes());
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
   }
-  // residue groups: tensor-core passes carry one residue per entry
+  // residue groups: limb tensor-core passes carry one residue per entry; the
+  // 8-bit-prime path keeps groups of 4 and runs its dense steps per residue
   Groups groups = a.groups;
-  if (tc) {
+  if (tc && !p8) {
     groups = Groups();
     for (int r = 0; r < a.R; r++) {
       groups.rg.push_back(1);
@@ -417,8 +418,8 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
         for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
           if (kind[i] == kSmall) continue;
           if (kind[i] == kTc) {
-            if (RG != 1) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
-            int rc2;
+            if (RG != 1 && !p8) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
+            int rc2 = TNC_OK;
             cudaEvent_t ev[2] = {nullptr, nullptr};
             if (g_time_dense) {
               CUDA_TRY(cudaEventCreate(&ev[0]));
@@ -426,7 +427,9 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
               CUDA_TRY(cudaEventRecord(ev[0], st));
             }
             if (p8) {
-              rc2 = p8_launch(lw.lvl_steps[i], a.primes[groups.col[gi]], arena, ws + L.off_p8, part, d_err, sms, st);
+              for (int r = 0; r < RG && !rc2; r++)
+                rc2 = p8_launch(lw.lvl_steps[i], a.primes[groups.col[gi] + r], RG, r, arena, ws + L.off_p8, part, d_err,
+                                sms, st);
             } else {
               const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
               rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);

@@ -43,7 +43,8 @@ constexpr uint32_t kTileM = 128;
 constexpr uint32_t kStageK = 64;
 constexpr uint32_t kChunkK = 1024;
 constexpr uint32_t kStages = 4;
-constexpr uint32_t kThreads = 192;
+constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
+constexpr uint32_t kEpiThreads = 256;
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
 constexpr uint32_t kStageBytes = 48 * 1024;         // A + B (B up to 256 x 64 fp16)
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024;
@@ -55,7 +56,8 @@ struct P8Args {
   uint32_t p, pad;
   float pf, invp;
   uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
-  uint32_t* out;            // C, or the split partials [split][2^(fa+fb)]
+  uint32_t* out;            // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb)]
+  uint32_t rg, pad2;        // entry stride of C in u32 (residues per entry of the pass)
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -104,8 +106,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// 3-D tiled TMA load of box {8, rows, 8} at (0, y, z) into shared memory,
-// completing on mbar with its byte count.
+// 3-D tiled TMA load of the box at (0, y, z) into shared memory, completing
+// on mbar with its byte count.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t y, int32_t z,
                                             uint32_t mbar) {
   asm volatile(
@@ -186,12 +188,13 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 
 // ---- operand packing ------------------------------------------------------
 
-// X: u32 residues in [0, p), X[q * R + r] (R = 2^f rows, K = 2^k shared
-// values); Y: balanced fp16 residues, Y[((q >> 3) * R + r) * 8 + (q & 7)].
+// X: u32 residues in [0, p), entry q * R + r at X[(q * R + r) * rg] (R = 2^f
+// rows, K = 2^k shared values; rg residues per entry, X points at this
+// prime's); Y: balanced fp16 residues, Y[((q >> 3) * R + r) * 8 + (q & 7)].
 // Thread i packs row r = i mod R of the 8-group g = i / R: eight loads that
 // are coalesced across the warp, one 16-byte store.
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
-                                                      uint32_t f, uint32_t k, uint32_t p) {
+                                                      uint32_t f, uint32_t k, uint32_t p, uint32_t rg) {
   const uint64_t R = 1ull << f, n = R << (k - 3);
   const int hp = (int)(p - 1) / 2;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
     uint32_t h[4];
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
-      int v0 = (int)X[(g * 8 + e) * R + r], v1 = (int)X[(g * 8 + e + 1) * R + r];
+      int v0 = (int)X[((g * 8 + e) * R + r) * rg], v1 = (int)X[((g * 8 + e + 1) * R + r) * rg];
       v0 = v0 > hp ? v0 - (int)p : v0;
       v1 = v1 > hp ? v1 - (int)p : v1;
       const __half2 t = __halves2half2(__int2half_rn(v0), __int2half_rn(v1));
@@ -209,14 +212,14 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
   }
 }
 
-// Sum of the K-split partials: C[o] = sum_j part[j][o] mod p.
+// Sum of the K-split partials: C[o * rg] = sum_j part[j][o] mod p.
 __global__ void p8_split_final_kernel(const uint32_t* __restrict__ part, uint32_t* __restrict__ C, uint32_t c,
-                                      uint32_t log_split, uint32_t p) {
+                                      uint32_t log_split, uint32_t p, uint32_t rg) {
   const uint64_t n = 1ull << c;
   for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s = 0;
     for (uint32_t j = 0; j < (1u << log_split); j++) s += part[((uint64_t)j << c) + o];
-    C[o] = s % p;
+    C[o * rg] = s % p;
   }
 }
 
@@ -251,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(accf0, 1);
     mbar_init(accf0 + 8, 1);
-    mbar_init(acce0, 128);
-    mbar_init(acce0 + 8, 128);
+    mbar_init(acce0, kEpiThreads);
+    mbar_init(acce0 + 8, kEpiThreads);
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -297,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t sa = smem_u32(smem + s * kStageBytes);
               const int32_t z = (int32_t)((q0 + j * kStageK) >> 3);
               mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
-              tma_load_3d(sa, &tmA, (int32_t)m0, z, full0 + 8 * s);
-              tma_load_3d(sa + kABytes, &tmB, (int32_t)n0, z, full0 + 8 * s);
+              tma_load_3d(sa, &tmA, (int32_t)(m0 >> 3), z, full0 + 8 * s);
+              tma_load_3d(sa + kABytes, &tmB, (int32_t)(n0 >> 3), z, full0 + 8 * s);
               issued++;
               if (++s == kStages) {
                 s = 0;
@@ -358,9 +361,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(drain, 0)) ok = false;
       if (!ok) atomicExch(err, 1u);
     }
-  } else {  // epilogue: warps 2..5, TMEM lanes 32 (warp % 4) ..
+  } else {  // epilogue: warps 2..9; TMEM lanes 32 (warp % 4) .., column half (warp - 2) / 4
     const uint32_t quarter = warp & 3u;
     const uint32_t row = quarter * 32u + lane;
+    constexpr uint32_t kHalf = TN >= 32 ? TN / 2 : TN;  // columns per epilogue warp
+    constexpr uint32_t kBatch = kHalf >= 32 ? 32 : 16;  // columns per TMEM load batch
+    const uint32_t cbeg = ((warp - 2u) >> 2) * kHalf;
+    const bool idle = cbeg >= TN;                         // second half when TN = 16
     uint32_t na[2] = {0, 0};
     for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
       const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
@@ -371,36 +378,52 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t tb = tmem + ((quarter * 32u) << 16) + u * TN;
-          if (c + 1 < n_chunks) {  // reduce in place; the next chunk accumulates on top
-            for (uint32_t col = 0; col < TN; col += 16) {
-              uint32_t v[16];
-              tmem_ld16(tb + col, v);
+          const uint32_t tb = tmem + ((quarter * 32u) << 16) + u * TN + cbeg;
+          if (idle) {
+          } else if (c + 1 < n_chunks) {  // reduce in place; the next chunk accumulates on top
+#pragma unroll 1
+            for (uint32_t col = 0; col < kHalf; col += kBatch) {
+              uint32_t v[kBatch / 16][16];
+#pragma unroll
+              for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
               asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-              for (int jj = 0; jj < 16; jj++) v[jj] = __float_as_uint(reduce_p(__uint_as_float(v[jj]), g.pf, g.invp));
-              tmem_st16(tb + col, v);
+              for (uint32_t b = 0; b < kBatch / 16; b++) {
+#pragma unroll
+                for (int jj = 0; jj < 16; jj++)
+                  v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), g.pf, g.invp));
+                tmem_st16(tb + col + 16 * b, v[b]);
+              }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           } else {  // last chunk: canonical residues to C (or to this split's partials)
             const uint32_t item = bid + (t0 + u) * G;
             const uint32_t split = item & split_mask, tile = item >> g.log_split;
-            const uint32_t m = (tile % g.tiles_m) * kTileM + row, n0 = (tile / g.tiles_m) * TN;
+            const uint32_t m = (tile % g.tiles_m) * kTileM + row, n0 = (tile / g.tiles_m) * TN + cbeg;
             uint64_t om = 0;
             for (uint32_t j = 0; j < g.fa; j++)
               if ((m >> j) & 1u) om += g.wm[j];
+            const uint64_t stride = g.log_split ? 1u : g.rg;
             uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) : 0ull);
-            for (uint32_t col = 0; col < TN; col += 16) {
-              uint32_t v[16];
-              tmem_ld16(tb + col, v);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-              uint64_t on = om;
-              for (uint32_t j = 4; j < g.fb; j++)
-                if (((n0 + col) >> j) & 1u) on += g.wn[j];
+            uint64_t lo[16];
 #pragma unroll
-              for (uint32_t jj = 0; jj < 16; jj++)
-                outp[on + col_lo(g, jj)] =
-                    canonical(reduce_p(__uint_as_float(v[jj]), g.pf, g.invp), g.p);
+            for (uint32_t jj = 0; jj < 16; jj++) lo[jj] = col_lo(g, jj) * stride;
+#pragma unroll 1
+            for (uint32_t col = 0; col < kHalf; col += kBatch) {
+              uint32_t v[kBatch / 16][16];
+#pragma unroll
+              for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (uint32_t b = 0; b < kBatch / 16; b++) {
+                uint64_t on = om;
+                for (uint32_t j = 4; j < g.fb; j++)
+                  if (((n0 + col + 16 * b) >> j) & 1u) on += g.wn[j];
+                uint32_t* dst = outp + on * stride;
+#pragma unroll
+                for (uint32_t jj = 0; jj < 16; jj++)
+                  dst[lo[jj]] = canonical(reduce_p(__uint_as_float(v[b][jj]), g.pf, g.invp), g.p);
+              }
             }
           }
           tc_fence_before();
@@ -441,14 +464,16 @@ EncodeTiled encoder() {
   return fn;
 }
 
-// Tensor map of a packed operand (rows x K fp16 in [K/8][rows][8] order) with
-// boxes of {8, box_rows, 8}: one box is one K-major no-swizzle tile of 64 K.
+// Tensor map of a packed operand (rows x K fp16 in [K/8][rows][8] order),
+// viewed as {64 (8 rows x 8 values, 128 bytes), rows/8, K/8} so that TMA moves
+// whole 128-byte lines; a box {64, box_rows/8, 8} is one K-major no-swizzle
+// tile of box_rows x 64 K.
 int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
   EncodeTiled fn = encoder();
   if (!fn) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const cuuint64_t dims[3] = {8, rows, K / 8};
-  const cuuint64_t strides[2] = {16, rows * 16};
-  const cuuint32_t box[3] = {8, box_rows, 8};
+  const cuuint64_t dims[3] = {64, rows / 8, K / 8};
+  const cuuint64_t strides[2] = {128, rows * 16};
+  const cuuint32_t box[3] = {64, box_rows / 8, 8};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -514,8 +539,8 @@ uint64_t p8_part_entries(const StepDesc& d) {
   return ls ? 1ull << (d.c + ls) : 0;
 }
 
-int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uint32_t* part, uint32_t* dev_err,
-              int sms, void* stream) {
+int p8_launch(const StepDesc& d, uint32_t p, uint32_t rg, uint32_t r, uint32_t* arena, void* scratch, uint32_t* part,
+              uint32_t* dev_err, int sms, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (p < 3 || p > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
   const Shape s = shape_of(d);
@@ -526,7 +551,7 @@ int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uin
   auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
     const uint64_t n = (1ull << f) << (s.k - 3);
     const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
-    tnc_p8::p8_pack_kernel<<<blocks, 256, 0, st>>>(arena + off, dst, f, s.k, p);
+    tnc_p8::p8_pack_kernel<<<blocks, 256, 0, st>>>(arena + off * rg + r, dst, f, s.k, p, rg);
   };
   pack(a_off, a16, s.fa);
   pack(b_off, b16, s.fb);
@@ -570,7 +595,8 @@ int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uin
     if (op[j] == row_op) g.wm[dst[j]] = 1ull << j;
     else g.wn[dst[j]] = 1ull << j;
   }
-  g.out = ls ? part : arena + d.c_off;
+  g.out = ls ? part : arena + d.c_off * rg + r;
+  g.rg = rg;
   const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
   switch (s.tn) {
     case 16: rc = launch_gemm<16>(ma, mb, g, grid, dev_err, st); break;
@@ -583,7 +609,7 @@ int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uin
   if (ls) {
     const uint64_t n = 1ull << d.c;
     tnc_p8::p8_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
-        part, arena + d.c_off, d.c, ls, p);
+        part, arena + d.c_off * rg + r, d.c, ls, p, rg);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 launch: ") + cudaGetErrorString(e));

@@ -132,8 +132,9 @@ bool p8_eligible(const StepDesc& d);
 uint32_t p8_split_log(const StepDesc& d);
 uint64_t p8_scratch_bytes(const StepDesc& d);
 uint64_t p8_part_entries(const StepDesc& d);
-int p8_launch(const StepDesc& d, uint32_t p, uint32_t* arena, void* scratch, uint32_t* part, uint32_t* dev_err,
-              int sms, void* stream);
+// One dense step for residue r of a pass whose entries hold rg residues.
+int p8_launch(const StepDesc& d, uint32_t p, uint32_t rg, uint32_t r, uint32_t* arena, void* scratch, uint32_t* part,
+              uint32_t* dev_err, int sms, void* stream);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
 uint32_t tc_split_log(const StepDesc& d);
