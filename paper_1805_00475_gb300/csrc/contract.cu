@@ -239,7 +239,7 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
   uint64_t p8_bytes = 0;
   if (path == TNC_PATH_TC_P8)
     for (const StepDesc& d : p->low.lvl_steps)
-      if (p8_eligible(d)) p8_bytes = std::max<uint64_t>(p8_bytes, p8_scratch_bytes(d));
+      if (p8_eligible(d)) p8_bytes = std::max<uint64_t>(p8_bytes, p8_scratch_bytes(d, rg_max));
   s.off_part = o;
   o = align_up(o + part_bytes);
   s.off_results = o;
@@ -427,9 +427,8 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
               CUDA_TRY(cudaEventRecord(ev[0], st));
             }
             if (p8) {
-              for (int r = 0; r < RG && !rc2; r++)
-                rc2 = p8_launch(lw.lvl_steps[i], a.primes[groups.col[gi] + r], RG, r, arena, ws + L.off_p8, part, d_err,
-                                sms, st);
+              rc2 = p8_launch(lw.lvl_steps[i], a.primes.data() + groups.col[gi], RG, arena, ws + L.off_p8, part, d_err,
+                              sms, st);
             } else {
               const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
               rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);

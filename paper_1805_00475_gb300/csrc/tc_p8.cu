@@ -14,9 +14,11 @@
 // 30-bit residue (about 7.8 bits of the count per MMA against 1.9).
 //
 // Data path: a pack kernel turns each operand (u32 residues, the lowering's
-// column-major layout: row index low, shared index high) into balanced fp16
-// in a [q/8][row][q%8] layout; one 3-D TMA box {8, rows, 8} of it is exactly
-// the canonical K-major no-swizzle tile (core matrices of 8 rows x 16 bytes).
+// column-major layout: row index low, shared index high; all residues of the
+// pass at once) into balanced fp16 matrices, one per residue, row-major with
+// the shared index contiguous.  TMA moves tiles of rows x 64 values (128-byte
+// lines) into shared memory with the 128-byte swizzle, the canonical K-major
+// SWIZZLE_128B layout of the MMA operand descriptors.
 // Persistent CTAs (one per SM) run three warp roles:
 //   warp 0, lane 0: TMA producer over a 4-stage shared-memory ring;
 //   warp 1, lane 0: MMA issuer (kind::f16, 128 x TN x 16, fp32 in TMEM);
@@ -106,26 +108,30 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// 3-D tiled TMA load of the box at (0, y, z) into shared memory, completing
-// on mbar with its byte count.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t y, int32_t z,
+// 2-D tiled TMA load of the box at (x, y) into shared memory, completing on
+// mbar with its byte count.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
                                             uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-          "r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(z), "r"(mbar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
       : "memory");
 }
 
-// Canonical K-major, no-swizzle shared-memory matrix descriptor: core matrices
-// of 8 rows x 16 bytes; LBO = byte distance between core matrices adjacent in
-// K, SBO = between core matrices adjacent in M/N; version 1; layout 0.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzle layout: rows of 64 fp16 (128 bytes), 8-row atoms of 1024 bytes
+// (SBO = 1024; LBO unused for this layout, set to 16 bytes); version 1;
+// layout type 2 (SWIZZLE_128B).  The tile base is 1024-byte aligned; the
+// K-th group of 16 values starts 32 K bytes further (the swizzle applies to
+// the address bits, so the start simply advances within the atom).
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -188,27 +194,57 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 
 // ---- operand packing ------------------------------------------------------
 
-// X: u32 residues in [0, p), entry q * R + r at X[(q * R + r) * rg] (R = 2^f
-// rows, K = 2^k shared values; rg residues per entry, X points at this
-// prime's); Y: balanced fp16 residues, Y[((q >> 3) * R + r) * 8 + (q & 7)].
-// Thread i packs row r = i mod R of the 8-group g = i / R: eight loads that
-// are coalesced across the warp, one 16-byte store.
+// X: the operand's u32 residues in [0, p_i), entry q * R + r at
+// X + (q * R + r) * RG (R = 2^f rows, K = 2^k shared values, RG residues per
+// entry); Y_i (i < RG, Y_i = Y + i * R * K): balanced fp16 residues mod p_i,
+// row-major, Y_i[r * K + q].  A block transposes a tile of 32 rows x 64 shared
+// values through shared memory: reads of whole entries coalesced along r,
+// 16-byte writes coalesced along q.
+struct PackPrimes {
+  uint32_t p[4];
+};
+
+template <int RG>
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
-                                                      uint32_t f, uint32_t k, uint32_t p, uint32_t rg) {
-  const uint64_t R = 1ull << f, n = R << (k - 3);
-  const int hp = (int)(p - 1) / 2;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t r = i & (R - 1), g = i >> f;
-    uint32_t h[4];
+                                                      uint32_t f, uint32_t k, PackPrimes pp) {
+  __shared__ __align__(16) __half tile[RG][32][72];
+  const uint32_t R = 1u << f, K = 1u << k;
+  const uint32_t tiles_r = (R + 31) / 32;
+  const uint64_t n_tiles = (uint64_t)tiles_r << (k - 6);
+  const uint32_t t = threadIdx.x;
+  for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+    const uint32_t r0 = (uint32_t)(b % tiles_r) * 32u, q0 = (uint32_t)(b / tiles_r) * 64u;
 #pragma unroll
-    for (int e = 0; e < 8; e += 2) {
-      int v0 = (int)X[((g * 8 + e) * R + r) * rg], v1 = (int)X[((g * 8 + e + 1) * R + r) * rg];
-      v0 = v0 > hp ? v0 - (int)p : v0;
-      v1 = v1 > hp ? v1 - (int)p : v1;
-      const __half2 t = __halves2half2(__int2half_rn(v0), __int2half_rn(v1));
-      h[e / 2] = *reinterpret_cast<const uint32_t*>(&t);
+    for (int j = 0; j < 8; j++) {
+      const uint32_t rr = t & 31u, qq = (t >> 5) + 8u * j;
+      if (r0 + rr < R) {
+        const uint32_t* src = X + ((uint64_t)(q0 + qq) * R + r0 + rr) * RG;
+        uint32_t v[RG];
+        if constexpr (RG == 4) {
+          const uint4 w = *reinterpret_cast<const uint4*>(src);
+          v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+        } else if constexpr (RG == 2) {
+          const uint2 w = *reinterpret_cast<const uint2*>(src);
+          v[0] = w.x; v[1] = w.y;
+        } else {
+          v[0] = src[0];
+        }
+#pragma unroll
+        for (int i = 0; i < RG; i++) {
+          const int x = (int)v[i], hp = (int)(pp.p[i] - 1) / 2;
+          tile[i][rr][qq] = __int2half_rn(x > hp ? x - (int)pp.p[i] : x);
+        }
+      }
     }
-    *reinterpret_cast<uint4*>(Y + i * 8) = make_uint4(h[0], h[1], h[2], h[3]);
+    __syncthreads();
+    const uint32_t rr = t >> 3, c8 = (t & 7u) * 8u;
+    if (r0 + rr < R) {
+#pragma unroll
+      for (int i = 0; i < RG; i++)
+        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)(r0 + rr) * K + q0 + c8) =
+            *reinterpret_cast<const uint4*>(&tile[i][rr][c8]);
+    }
+    __syncthreads();
   }
 }
 
@@ -298,10 +334,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
               }
               const uint32_t sa = smem_u32(smem + s * kStageBytes);
-              const int32_t z = (int32_t)((q0 + j * kStageK) >> 3);
+              const int32_t x = (int32_t)(q0 + j * kStageK);
               mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
-              tma_load_3d(sa, &tmA, (int32_t)(m0 >> 3), z, full0 + 8 * s);
-              tma_load_3d(sa + kABytes, &tmB, (int32_t)(n0 >> 3), z, full0 + 8 * s);
+              tma_load_2d(sa, &tmA, x, (int32_t)m0, full0 + 8 * s);
+              tma_load_2d(sa + kABytes, &tmB, x, (int32_t)n0, full0 + 8 * s);
               issued++;
               if (++s == kStages) {
                 s = 0;
@@ -340,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t sa = smem_u32(smem + s * kStageBytes), sb = sa + kABytes;
 #pragma unroll
               for (uint32_t ks = 0; ks < kStageK / 16; ks++) {
-                // 16 K values = two core matrices along K
-                const uint64_t ad = make_desc(sa + ks * 2u * (kTileM * 16u), kTileM * 16u, 128u);
-                const uint64_t bd = make_desc(sb + ks * 2u * (TN * 16u), TN * 16u, 128u);
+                // the ks-th 16 K values: 32 bytes into every 128-byte row
+                const uint64_t ad = make_desc_sw128(sa + ks * 32u);
+                const uint64_t bd = make_desc_sw128(sb + ks * 32u);
                 mma_f16(d, ad, bd, idesc, (c | j | ks) ? 1u : 0u);
               }
               mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
@@ -464,19 +500,17 @@ EncodeTiled encoder() {
   return fn;
 }
 
-// Tensor map of a packed operand (rows x K fp16 in [K/8][rows][8] order),
-// viewed as {64 (8 rows x 8 values, 128 bytes), rows/8, K/8} so that TMA moves
-// whole 128-byte lines; a box {64, box_rows/8, 8} is one K-major no-swizzle
-// tile of box_rows x 64 K.
+// Tensor map of a packed operand (rows x K fp16, row-major) with boxes of
+// box_rows x 64 values (128-byte lines) and the 128-byte swizzle.
 int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
   EncodeTiled fn = encoder();
   if (!fn) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const cuuint64_t dims[3] = {64, rows / 8, K / 8};
-  const cuuint64_t strides[2] = {128, rows * 16};
-  const cuuint32_t box[3] = {64, box_rows / 8, 8};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  const cuuint64_t dims[2] = {K, rows};
+  const cuuint64_t strides[1] = {K * 2};
+  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return TNC_OK;
@@ -513,48 +547,9 @@ int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Ar
   return TNC_OK;
 }
 
-}  // namespace
-
-bool p8_eligible(const StepDesc& d) {
-  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
-}
-
-// K split of a dense step: double it while the work items stay below
-// kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
-// (2^c entries per split) stay within 2^26 entries.
-constexpr uint64_t kP8SplitTarget = 160;
-uint32_t p8_split_log(const StepDesc& d) {
-  const Shape s = shape_of(d);
-  uint32_t ls = 0;
-  while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
-  return ls;
-}
-
-uint64_t p8_scratch_bytes(const StepDesc& d) {
-  return 2ull * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
-}
-
-uint64_t p8_part_entries(const StepDesc& d) {
-  const uint32_t ls = p8_split_log(d);
-  return ls ? 1ull << (d.c + ls) : 0;
-}
-
-int p8_launch(const StepDesc& d, uint32_t p, uint32_t rg, uint32_t r, uint32_t* arena, void* scratch, uint32_t* part,
-              uint32_t* dev_err, int sms, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (p < 3 || p > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
-  const Shape s = shape_of(d);
-  const uint32_t ls = p8_split_log(d);
-  __half* a16 = (__half*)scratch;
-  __half* b16 = a16 + (1ull << (s.fa + s.k));
-  const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
-  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
-    const uint64_t n = (1ull << f) << (s.k - 3);
-    const unsigned blocks = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8);
-    tnc_p8::p8_pack_kernel<<<blocks, 256, 0, st>>>(arena + off * rg + r, dst, f, s.k, p, rg);
-  };
-  pack(a_off, a16, s.fa);
-  pack(b_off, b16, s.fb);
+// One residue of a dense step: the GEMM on packed operands (+ the split sum).
+int p8_gemm_one(const StepDesc& d, const Shape& s, uint32_t ls, uint32_t p, uint32_t rg, uint32_t r, __half* a16,
+                __half* b16, uint32_t* arena, uint32_t* part, uint32_t* dev_err, int sms, cudaStream_t st) {
   CUtensorMap ma, mb;
   int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, tnc_p8::kTileM);
   if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, s.tn);
@@ -614,6 +609,62 @@ int p8_launch(const StepDesc& d, uint32_t p, uint32_t rg, uint32_t r, uint32_t* 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 launch: ") + cudaGetErrorString(e));
   return TNC_OK;
+}
+
+}  // namespace
+
+bool p8_eligible(const StepDesc& d) {
+  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
+}
+
+// K split of a dense step: double it while the work items stay below
+// kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
+// (2^c entries per split) stay within 2^26 entries.
+constexpr uint64_t kP8SplitTarget = 160;
+uint32_t p8_split_log(const StepDesc& d) {
+  const Shape s = shape_of(d);
+  uint32_t ls = 0;
+  while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
+  return ls;
+}
+
+uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
+  return 2ull * (uint64_t)rg * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
+}
+
+uint64_t p8_part_entries(const StepDesc& d) {
+  const uint32_t ls = p8_split_log(d);
+  return ls ? 1ull << (d.c + ls) : 0;
+}
+
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
+              uint32_t* dev_err, int sms, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rg != 1 && rg != 2 && rg != 4) return set_error(TNC_ERR_INVALID, "internal: residues per pass must be 1, 2 or 4");
+  tnc_p8::PackPrimes pp{};
+  for (uint32_t i = 0; i < 4; i++) pp.p[i] = primes[i < rg ? i : 0];
+  for (uint32_t i = 0; i < rg; i++)
+    if (primes[i] < 3 || primes[i] > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
+  const Shape s = shape_of(d);
+  const uint32_t ls = p8_split_log(d);
+  const uint64_t a_elems = 1ull << (s.fa + s.k), b_elems = 1ull << (s.fb + s.k);
+  __half* a16 = (__half*)scratch;           // rg planes of a_elems
+  __half* b16 = a16 + rg * a_elems;         // rg planes of b_elems
+  const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
+  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
+    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.k - 6);
+    const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
+    const uint32_t* src = arena + off * rg;
+    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+  };
+  pack(a_off, a16, s.fa);
+  pack(b_off, b16, s.fb);
+  int rc = TNC_OK;
+  for (uint32_t r = 0; r < rg && !rc; r++) rc = p8_gemm_one(d, s, ls, primes[r], rg, r, a16 + r * a_elems,
+                                                             b16 + r * b_elems, arena, part, dev_err, sms, st);
+  return rc;
 }
 
 }  // namespace tnc

@@ -130,10 +130,11 @@ bool tc_eligible(const StepDesc& d);
 // TNC_PATH_TC_P8 dense steps (tc_p8.cu).
 bool p8_eligible(const StepDesc& d);
 uint32_t p8_split_log(const StepDesc& d);
-uint64_t p8_scratch_bytes(const StepDesc& d);
+uint64_t p8_scratch_bytes(const StepDesc& d, int rg);
 uint64_t p8_part_entries(const StepDesc& d);
-// One dense step for residue r of a pass whose entries hold rg residues.
-int p8_launch(const StepDesc& d, uint32_t p, uint32_t rg, uint32_t r, uint32_t* arena, void* scratch, uint32_t* part,
+// One dense step for all rg residues (primes[0..rg)) of a pass whose entries
+// hold rg residues: both operands packed once, then one GEMM per residue.
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
               uint32_t* dev_err, int sms, void* stream);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
