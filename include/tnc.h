@@ -247,8 +247,8 @@ int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, void* cuda_s
  * Requires a prior tnc_batch_upload to the same dev_ws.  The launch sequence is
  * captured once into a CUDA graph per (dev_ws, stream) and replayed. */
 int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream);
-/* Autotuner: times the batch's launch for every CTA size in {128, 256, 512,
- * 1024}, shared-memory arena capacity in {0, 16, 32, 48, 64, 96, 128, 192} KiB
+/* Autotuner: times the batch's launch for every CTA size in {64, 128, 256},
+ * shared-memory arena capacity in {0, 16, 32, 48, 64, 96, 128, 192} KiB
  * (capped at the largest formula's arena) and cap on CTAs per SM in {as many
  * as fit, 2, 1} (fewer CTAs leave more of the SM's memory to L1), keeps the
  * fastest and reports it.  Needs a prior tnc_batch_upload to dev_ws; leaves
@@ -256,8 +256,8 @@ int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream);
  * pointer may be NULL. */
 int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t* threads_out,
                        int32_t* smem_bytes_out, int32_t* ctas_per_sm_out);
-/* Sets the launch shape without timing (threads per CTA in {128, 256, 512,
- * 1024}, shared-memory arena bytes per CTA, CTAs per SM cap, 0 = as many as
+/* Sets the launch shape without timing (threads per CTA in {64, 128, 256},
+ * shared-memory arena bytes per CTA, CTAs per SM cap, 0 = as many as
  * fit; e.g. a shape an earlier autotune chose).  TNC_ERR_INVALID for another
  * CTA size, TNC_ERR_TOO_LARGE if the CTA does not fit on an SM.  Host only: no
  * device work is queued. */

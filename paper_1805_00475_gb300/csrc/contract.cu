@@ -919,7 +919,7 @@ extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_strea
   int best_t = b->threads, best_c = b->cta_cap;
   size_t best_s = b->smem_bytes;
   int rc = TNC_OK;
-  for (int threads : {128, 256, 512, 1024}) {
+  for (int threads : {64, 128, 256}) {
     for (size_t sm : smems) {
       int prev_grid = -1;
       for (int cap : {0, 2, 1}) {
@@ -966,8 +966,8 @@ extern "C" int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_strea
 extern "C" int tnc_batch_set_launch(tnc_batch_t* b, int32_t threads, int32_t smem_bytes, int32_t ctas_per_sm) {
   clear_error();
   if (!b) return set_error(TNC_ERR_INVALID, "NULL argument");
-  if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
-    return set_error(TNC_ERR_INVALID, "threads must be 128, 256, 512 or 1024");
+  if (threads != 64 && threads != 128 && threads != 256)
+    return set_error(TNC_ERR_INVALID, "threads must be 64, 128 or 256");
   if (ctas_per_sm < 0) return set_error(TNC_ERR_INVALID, "ctas_per_sm must be >= 0");
   if (smem_bytes < 0 || (size_t)smem_bytes + b->max_blob > kSmemMax)
     return set_error(TNC_ERR_TOO_LARGE, "shared-memory arena too large");

@@ -96,7 +96,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     }
     if (((q + 4) & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce_g(acc[r], mg, r);
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
     }
   }
   for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
@@ -107,7 +107,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) out[r] = mod_reduce_g(acc[r], mg, r);
+  for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
 }
 
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
@@ -224,11 +224,11 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     if ((++cnt & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce_g(acc[r], mg, r);
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce_g(acc[r], mg, r);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
     for (int r = 0; r < RG; r++) s[r] += part[((o << log_split) + j) * RG + r];  // < 2^31 each, < 2^20 of them
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce_g(s[r], mg, r);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(s[r], mg.p[r], mg.mu[r]);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -366,7 +366,7 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
 // one contiguous, 16-byte aligned blob (steps, segments, packed items, bit-map
 // runs, level table), copied to shared memory in one coalesced pass when a
 // CTA starts the formula.  Offsets are relative to the formula's own arena;
-// a run is a u16 (map_runs).
+// a run is a u16: src | dst << 5 | len << 10.
 struct BStep {
   uint32_t a_off, b_off, c_off;
   uint32_t run0;  // first run of A's map (blob-relative); B's map follows
@@ -424,8 +424,6 @@ struct BatchArgs {
   int col;                // first residue column of this group
 };
 
-// A run of the bit map of an operand, a u16: output bits src .. src+len-1 are
-// the operand's bits dst .. dst+len-1 (src | dst << 5 | len << 10).
 __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, int n) {
   uint32_t a = 0;
   for (int i = 0; i < n; i++) {
@@ -443,7 +441,7 @@ __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, i
 // live in shared memory when the formula's arena fits, else in its own region
 // of global memory.
 template <int RG>
-__global__ void __launch_bounds__(1024) batch_kernel(BatchArgs a, ModGroup mg) {
+__global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) modmac_probe_kernel(uint32_t seed, uint32
     }
     if ((it & 3u) == 3u) {
 #pragma unroll
-      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce_g(acc[r], mg, r);
+      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce(acc[r], mg.p[r], mg.mu[r]);
     }
 #pragma unroll
     for (int i = 0; i < 8; i++) x[i] = (x[i] ^ (x[(i + 1) & 7] >> 3)) & 0x3FFFFFFFu;
