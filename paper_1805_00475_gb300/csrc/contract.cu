@@ -234,7 +234,7 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
     if (tc_eligible(d) && tc_split_log(d) > 0)
       part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
     if (path == TNC_PATH_TC_P8 && p8_eligible(d))
-      part_bytes = std::max<uint64_t>(part_bytes, p8_part_entries(d) * sizeof(uint32_t));
+      part_bytes = std::max<uint64_t>(part_bytes, p8_part_entries(d, rg_max) * sizeof(uint32_t));
   }
   uint64_t p8_bytes = 0;
   if (path == TNC_PATH_TC_P8)

@@ -47,19 +47,22 @@ constexpr uint32_t kChunkK = 1024;
 constexpr uint32_t kStages = 4;
 constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
 constexpr uint32_t kEpiThreads = 256;
+constexpr uint32_t kMaxTN = 128;                    // columns per tile (TMEM: RG x TN <= 512)
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
-constexpr uint32_t kStageBytes = 48 * 1024;         // A + B (B up to 256 x 64 fp16)
-constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint32_t kStageBytes = 32 * 1024;         // A + B (B up to 128 x 64 fp16)
+constexpr uint32_t kStagePitch = kTileM + 1;        // u32 words per staged column (+1: no bank conflicts)
+constexpr uint32_t kStagingBytes = kMaxTN * kStagePitch * 4;
+constexpr uint32_t kSmemBytes = kStages * kStageBytes + kStagingBytes + 1024;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct P8Args {
   uint32_t fa, fb, k, log_split;  // rows 2^fa, columns 2^fb, shared 2^k, K split 2^log_split
   uint32_t n_items, tiles_m;      // work items (tiles x splits); row tiles
-  uint32_t p, pad;
-  float pf, invp;
+  uint32_t rg, pad;               // residues per entry (1, 2 or 4), computed together
+  uint32_t p[4];
+  float pf[4], invp[4];
   uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
-  uint32_t* out;            // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb)]
-  uint32_t rg, pad2;        // entry stride of C in u32 (residues per entry of the pass)
+  uint32_t* out;            // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -106,6 +109,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 3-D tiled TMA load of the box at (x, y, z) into shared memory, completing
+// on mbar with its byte count.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
 }
 
 // 2-D tiled TMA load of the box at (x, y) into shared memory, completing on
@@ -248,50 +262,55 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
   }
 }
 
-// Sum of the K-split partials: C[o * rg] = sum_j part[j][o] mod p.
+// Sum of the K-split partials: C[i] = sum_j part[j][i] mod p_(i mod rg) for
+// the n = 2^c * rg residues of the step's output.
 __global__ void p8_split_final_kernel(const uint32_t* __restrict__ part, uint32_t* __restrict__ C, uint32_t c,
-                                      uint32_t log_split, uint32_t p, uint32_t rg) {
-  const uint64_t n = 1ull << c;
-  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (uint64_t)gridDim.x * blockDim.x) {
+                                      uint32_t log_split, uint32_t rg, uint4 primes) {
+  const uint64_t n = (uint64_t)rg << c;
+  const uint32_t pr[4] = {primes.x, primes.y, primes.z, primes.w};
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s = 0;
-    for (uint32_t j = 0; j < (1u << log_split); j++) s += part[((uint64_t)j << c) + o];
-    C[o * rg] = s % p;
+    for (uint32_t j = 0; j < (1u << log_split); j++) s += part[(uint64_t)j * n + i];
+    C[i] = s % pr[i % rg];
   }
 }
 
 // ---- the GEMM -------------------------------------------------------------
 
-// Output address weights of the low four column bits for column offset jj.
-__device__ __forceinline__ uint64_t col_lo(const P8Args& g, uint32_t jj) {
-  uint64_t o = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < 4; j++)
-    if ((jj >> j) & 1u) o += g.wn[j];
-  return o;
-}
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-template <uint32_t TN>
+// One CTA per SM.  Work item = (output tile of 128 rows x TN columns, K
+// slice); for each item, each K chunk and each residue r < RG (in that order)
+// the MMA warp accumulates chunk c of C_r = A_r B_r^T into TMEM accumulator r
+// (columns r TN ..).  The epilogue reduces accumulator r in place after every
+// chunk but the last; after the last it turns it into canonical residues,
+// staged in shared memory as one byte per residue of each entry, and frees the
+// accumulator at once, so the next item's MMAs start while the staged entries
+// are written out whole (RG u32 residues per entry, the pass's layout).
+template <uint32_t TN, uint32_t RG>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ P8Args g, uint32_t* err) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * kStages + 5];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * RG + 1];
   __shared__ uint32_t tmem_base_s;
+  __shared__ uint64_t om_tab[kTileM], on_tab[TN];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint32_t* staging = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);  // [col][kStagePitch]
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]);
-  const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + 2]);
-  const uint32_t drain = smem_u32(&bars[2 * kStages + 4]);
-  constexpr uint32_t kCols = 2 * TN < 32 ? 32 : 2 * TN;  // two accumulators of TN columns
+  const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + RG]);
+  const uint32_t drain = smem_u32(&bars[2 * kStages + 2 * RG]);
+  constexpr uint32_t kCols = RG * TN < 32 ? 32 : RG * TN;  // RG accumulators of TN columns
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kStages; s++) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(accf0, 1);
-    mbar_init(accf0 + 8, 1);
-    mbar_init(acce0, kEpiThreads);
-    mbar_init(acce0 + 8, kEpiThreads);
+    for (uint32_t r = 0; r < RG; r++) {
+      mbar_init(accf0 + 8 * r, 1);
+      mbar_init(acce0 + 8 * r, kEpiThreads);
+    }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -306,8 +325,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
 
-  // this CTA's work items: bid, bid + G, ... taken two at a time; for each
-  // pair the K chunks alternate between the two (accumulator u = 0, 1)
   const uint32_t G = gridDim.x, bid = blockIdx.x;
   const uint32_t T = g.n_items > bid ? (g.n_items - bid + G - 1) / G : 0;
   const uint32_t Ks = (1u << g.k) >> g.log_split;
@@ -320,13 +337,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
       uint32_t s = 0, ph = 0, issued = 0;
-      for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
-        const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
+      for (uint32_t t = 0; t < T && ok; t++) {
+        const uint32_t item = bid + t * G;
+        const uint32_t split = item & split_mask, tile = item >> g.log_split;
+        const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
         for (uint32_t c = 0; c < n_chunks && ok; c++)
-          for (uint32_t u = 0; u < nu && ok; u++) {
-            const uint32_t item = bid + (t0 + u) * G;
-            const uint32_t split = item & split_mask, tile = item >> g.log_split;
-            const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+          for (uint32_t r = 0; r < RG && ok; r++) {
             const uint32_t q0 = split * Ks + c * chunk;
             for (uint32_t j = 0; j < spc; j++) {
               if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
@@ -336,8 +352,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t sa = smem_u32(smem + s * kStageBytes);
               const int32_t x = (int32_t)(q0 + j * kStageK);
               mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
-              tma_load_2d(sa, &tmA, x, (int32_t)m0, full0 + 8 * s);
-              tma_load_2d(sa + kABytes, &tmB, x, (int32_t)n0, full0 + 8 * s);
+              tma_load_3d(sa, &tmA, x, (int32_t)m0, (int32_t)r, full0 + 8 * s);
+              tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
               issued++;
               if (++s == kStages) {
                 s = 0;
@@ -356,17 +372,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       constexpr uint32_t idesc = make_idesc(kTileM, TN);
-      uint32_t s = 0, ph = 0, na[2] = {0, 0};
-      for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
-        const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
+      uint32_t s = 0, ph = 0, na[RG];
+      for (uint32_t r = 0; r < RG; r++) na[r] = 0;
+      for (uint32_t t = 0; t < T && ok; t++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
-          for (uint32_t u = 0; u < nu && ok; u++) {
-            if (!mbar_wait(acce0 + 8 * u, (na[u] & 1u) ^ 1u)) {  // the epilogue is done with accumulator u
+          for (uint32_t r = 0; r < RG && ok; r++) {
+            if (!mbar_wait(acce0 + 8 * r, (na[r] & 1u) ^ 1u)) {  // the epilogue is done with accumulator r
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t d = tmem + u * TN;
+            const uint32_t d = tmem + r * TN;
             for (uint32_t j = 0; j < spc; j++) {
               if (!mbar_wait(full0 + 8 * s, ph)) {
                 ok = false;
@@ -375,12 +391,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * kStageBytes), sb = sa + kABytes;
 #pragma unroll
-              for (uint32_t ks = 0; ks < kStageK / 16; ks++) {
-                // the ks-th 16 K values: 32 bytes into every 128-byte row
-                const uint64_t ad = make_desc_sw128(sa + ks * 32u);
-                const uint64_t bd = make_desc_sw128(sb + ks * 32u);
-                mma_f16(d, ad, bd, idesc, (c | j | ks) ? 1u : 0u);
-              }
+              for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values: 32 bytes into each row
+                mma_f16(d, make_desc_sw128(sa + ks * 32u), make_desc_sw128(sb + ks * 32u), idesc,
+                        (c | j | ks) ? 1u : 0u);
               mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
               if (++s == kStages) {
                 s = 0;
@@ -388,84 +401,101 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
             if (!ok) break;
-            mma_commit(accf0 + 8 * u);
-            na[u]++;
+            mma_commit(accf0 + 8 * r);
+            na[r]++;
           }
-      }
       // every MMA issued has completed before the TMEM is freed
       mma_commit(drain);
       if (!mbar_wait(drain, 0)) ok = false;
       if (!ok) atomicExch(err, 1u);
     }
-  } else {  // epilogue: warps 2..9; TMEM lanes 32 (warp % 4) .., column half (warp - 2) / 4
+  } else {
+    // epilogue: warps 2..9; TMEM lanes 32 (warp % 4) .., column half (warp - 2) / 4.
+    // Every epilogue thread runs the same loop trips and named barriers; a
+    // failed wait only turns the thread's work off.
+    const uint32_t et = threadIdx.x - 64u;
     const uint32_t quarter = warp & 3u;
     const uint32_t row = quarter * 32u + lane;
     constexpr uint32_t kHalf = TN >= 32 ? TN / 2 : TN;  // columns per epilogue warp
     constexpr uint32_t kBatch = kHalf >= 32 ? 32 : 16;  // columns per TMEM load batch
     const uint32_t cbeg = ((warp - 2u) >> 2) * kHalf;
     const bool idle = cbeg >= TN;                         // second half when TN = 16
-    uint32_t na[2] = {0, 0};
-    for (uint32_t t0 = 0; t0 < T && ok; t0 += 2) {
-      const uint32_t nu = T - t0 < 2u ? T - t0 : 2u;
-      for (uint32_t c = 0; c < n_chunks && ok; c++)
-        for (uint32_t u = 0; u < nu && ok; u++) {
-          if (!mbar_wait(accf0 + 8 * u, na[u] & 1u)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t tb = tmem + ((quarter * 32u) << 16) + u * TN + cbeg;
-          if (idle) {
-          } else if (c + 1 < n_chunks) {  // reduce in place; the next chunk accumulates on top
-#pragma unroll 1
-            for (uint32_t col = 0; col < kHalf; col += kBatch) {
-              uint32_t v[kBatch / 16][16];
-#pragma unroll
-              for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-              for (uint32_t b = 0; b < kBatch / 16; b++) {
-#pragma unroll
-                for (int jj = 0; jj < 16; jj++)
-                  v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), g.pf, g.invp));
-                tmem_st16(tb + col + 16 * b, v[b]);
-              }
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-          } else {  // last chunk: canonical residues to C (or to this split's partials)
-            const uint32_t item = bid + (t0 + u) * G;
-            const uint32_t split = item & split_mask, tile = item >> g.log_split;
-            const uint32_t m = (tile % g.tiles_m) * kTileM + row, n0 = (tile / g.tiles_m) * TN + cbeg;
-            uint64_t om = 0;
+    const bool rows_low = g.wm[0] < g.wn[0];              // entries of consecutive rows are adjacent in C
+    uint8_t* stage8 = reinterpret_cast<uint8_t*>(staging);
+    uint32_t na[RG];
+    for (uint32_t r = 0; r < RG; r++) na[r] = 0;
+    for (uint32_t t = 0; t < T; t++) {
+      const uint32_t item = bid + t * G;
+      const uint32_t split = item & split_mask, tile = item >> g.log_split;
+      const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+      for (uint32_t c = 0; c < n_chunks; c++) {
+        const bool last = c + 1 == n_chunks;
+        if (last) {
+          epi_bar();  // the previous item's entries are out: staging and tables are free
+          if (et < kTileM) {
+            uint64_t o = 0;
             for (uint32_t j = 0; j < g.fa; j++)
-              if ((m >> j) & 1u) om += g.wm[j];
-            const uint64_t stride = g.log_split ? 1u : g.rg;
-            uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) : 0ull);
-            uint64_t lo[16];
-#pragma unroll
-            for (uint32_t jj = 0; jj < 16; jj++) lo[jj] = col_lo(g, jj) * stride;
+              if (((m0 + et) >> j) & 1u) o += g.wm[j];
+            om_tab[et] = o;
+          } else if (et - kTileM < TN) {
+            uint64_t o = 0;
+            for (uint32_t j = 0; j < g.fb; j++)
+              if (((n0 + et - kTileM) >> j) & 1u) o += g.wn[j];
+            on_tab[et - kTileM] = o;
+          }
+        }
+        for (uint32_t r = 0; r < RG; r++) {
+          if (ok && !mbar_wait(accf0 + 8 * r, na[r] & 1u)) ok = false;
+          tc_fence_after();
+          const uint32_t tb = tmem + ((quarter * 32u) << 16) + r * TN + cbeg;
+          if (ok && !idle) {
+            const float pf = g.pf[r], invp = g.invp[r];
 #pragma unroll 1
             for (uint32_t col = 0; col < kHalf; col += kBatch) {
               uint32_t v[kBatch / 16][16];
 #pragma unroll
               for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
               asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              if (!last) {  // reduce in place; the next chunk accumulates on top
 #pragma unroll
-              for (uint32_t b = 0; b < kBatch / 16; b++) {
-                uint64_t on = om;
-                for (uint32_t j = 4; j < g.fb; j++)
-                  if (((n0 + col + 16 * b) >> j) & 1u) on += g.wn[j];
-                uint32_t* dst = outp + on * stride;
+                for (uint32_t b = 0; b < kBatch / 16; b++) {
 #pragma unroll
-                for (uint32_t jj = 0; jj < 16; jj++)
-                  dst[lo[jj]] = canonical(reduce_p(__uint_as_float(v[b][jj]), g.pf, g.invp), g.p);
+                  for (int jj = 0; jj < 16; jj++)
+                    v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), pf, invp));
+                  tmem_st16(tb + col + 16 * b, v[b]);
+                }
+              } else {  // canonical residue, one byte per residue of the staged entry
+#pragma unroll
+                for (uint32_t b = 0; b < kBatch / 16; b++)
+#pragma unroll
+                  for (uint32_t jj = 0; jj < 16; jj++)
+                    stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * 4 + r] =
+                        (uint8_t)canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]);
               }
             }
+            if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           }
           tc_fence_before();
-          mbar_arrive(acce0 + 8 * u);
-          na[u]++;
+          mbar_arrive(acce0 + 8 * r);  // accumulator r is free (its values are in registers or staged)
+          na[r]++;
         }
+      }
+      epi_bar();  // every residue of the item is staged
+      if (ok) {
+        uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull);
+        for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
+          const uint32_t rr = rows_low ? e % kTileM : e / TN, cc = rows_low ? e / kTileM : e % TN;
+          const uint32_t w = staging[cc * kStagePitch + rr];
+          uint32_t* dst = outp + (om_tab[rr] + on_tab[cc]) * RG;
+          if constexpr (RG == 4) {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w & 0xFFu, (w >> 8) & 0xFFu, (w >> 16) & 0xFFu, w >> 24);
+          } else if constexpr (RG == 2) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2(w & 0xFFu, (w >> 8) & 0xFFu);
+          } else {
+            *dst = w & 0xFFu;
+          }
+        }
+      }
     }
     if (!ok) atomicExch(err, 1u);
   }
@@ -500,16 +530,17 @@ EncodeTiled encoder() {
   return fn;
 }
 
-// Tensor map of a packed operand (rows x K fp16, row-major) with boxes of
-// box_rows x 64 values (128-byte lines) and the 128-byte swizzle.
-int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t box_rows) {
+// Tensor map of the packed operand planes (rg planes of rows x K fp16,
+// row-major) with boxes of box_rows x 64 values (128-byte lines) of one plane,
+// 128-byte swizzle.
+int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t rg, uint32_t box_rows) {
   EncodeTiled fn = encoder();
   if (!fn) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  const cuuint64_t dims[2] = {K, rows};
-  const cuuint64_t strides[1] = {K * 2};
-  const cuuint32_t box[2] = {64, box_rows};
-  const cuuint32_t es[2] = {1, 1};
-  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint64_t dims[3] = {K, rows, rg};
+  const cuuint64_t strides[2] = {K * 2, rows * K * 2};
+  const cuuint32_t box[3] = {64, box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -517,7 +548,7 @@ int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t box
 }
 
 struct Shape {
-  bool swap;              // rows come from B
+  bool swap;               // rows come from B
   uint32_t fa, fb, k, tn;  // row bits, column bits, shared bits, columns per tile
   uint64_t tiles;
 };
@@ -528,31 +559,89 @@ Shape shape_of(const StepDesc& d) {
   s.fa = s.swap ? d.kb : d.ka;
   s.fb = s.swap ? d.ka : d.kb;
   s.k = d.k;
-  s.tn = std::min<uint32_t>(1u << s.fb, 256u);
+  s.tn = std::min<uint32_t>(1u << s.fb, tnc_p8::kMaxTN);
   s.tiles = ((1ull << s.fa) / tnc_p8::kTileM) * ((1ull << s.fb) / s.tn);
   return s;
 }
 
-template <uint32_t TN>
+template <uint32_t TN, uint32_t RG>
 int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid, uint32_t* err,
                 cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tnc_p8::kSmemBytes);
     if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
     attr = true;
   }
-  tnc_p8::p8_gemm_kernel<TN><<<grid, tnc_p8::kThreads, tnc_p8::kSmemBytes, st>>>(ma, mb, g, err);
+  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::kSmemBytes, st>>>(ma, mb, g, err);
   return TNC_OK;
 }
 
-// One residue of a dense step: the GEMM on packed operands (+ the split sum).
-int p8_gemm_one(const StepDesc& d, const Shape& s, uint32_t ls, uint32_t p, uint32_t rg, uint32_t r, __half* a16,
-                __half* b16, uint32_t* arena, uint32_t* part, uint32_t* dev_err, int sms, cudaStream_t st) {
+template <uint32_t RG>
+int launch_gemm_rg(uint32_t tn, const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid,
+                   uint32_t* err, cudaStream_t st) {
+  switch (tn) {
+    case 16: return launch_gemm<16, RG>(ma, mb, g, grid, err, st);
+    case 32: return launch_gemm<32, RG>(ma, mb, g, grid, err, st);
+    case 64: return launch_gemm<64, RG>(ma, mb, g, grid, err, st);
+    default: return launch_gemm<128, RG>(ma, mb, g, grid, err, st);
+  }
+}
+
+}  // namespace
+
+bool p8_eligible(const StepDesc& d) {
+  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
+}
+
+// K split of a dense step: double it while the work items stay below
+// kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
+// (2^c entries per split, each of up to 4 residues) stay within 2^26 entries.
+constexpr uint64_t kP8SplitTarget = 160;
+uint32_t p8_split_log(const StepDesc& d) {
+  const Shape s = shape_of(d);
+  uint32_t ls = 0;
+  while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
+  return ls;
+}
+
+uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
+  return 2ull * (uint64_t)rg * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
+}
+
+uint64_t p8_part_entries(const StepDesc& d, int rg) {
+  const uint32_t ls = p8_split_log(d);
+  return ls ? (uint64_t)rg << (d.c + ls) : 0;
+}
+
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
+              uint32_t* dev_err, int sms, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rg != 1 && rg != 2 && rg != 4) return set_error(TNC_ERR_INVALID, "internal: residues per pass must be 1, 2 or 4");
+  tnc_p8::PackPrimes pp{};
+  for (uint32_t i = 0; i < 4; i++) pp.p[i] = primes[i < rg ? i : 0];
+  for (uint32_t i = 0; i < rg; i++)
+    if (primes[i] < 3 || primes[i] > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
+  const Shape s = shape_of(d);
+  const uint32_t ls = p8_split_log(d);
+  const uint64_t a_elems = 1ull << (s.fa + s.k);
+  __half* a16 = (__half*)scratch;    // rg planes of a_elems
+  __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
+  const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
+  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
+    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.k - 6);
+    const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
+    const uint32_t* src = arena + off * rg;
+    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+  };
+  pack(a_off, a16, s.fa);
+  pack(b_off, b16, s.fb);
   CUtensorMap ma, mb;
-  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, tnc_p8::kTileM);
-  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, s.tn);
+  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, rg, tnc_p8::kTileM);
+  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, rg, s.tn);
   if (rc) return rc;
   tnc_p8::P8Args g;
   std::memset(&g, 0, sizeof(g));
@@ -563,9 +652,12 @@ int p8_gemm_one(const StepDesc& d, const Shape& s, uint32_t ls, uint32_t p, uint
   g.tiles_m = (1u << s.fa) / tnc_p8::kTileM;
   if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
   g.n_items = (uint32_t)(s.tiles << ls);
-  g.p = p;
-  g.pf = (float)p;
-  g.invp = 1.0f / (float)p;
+  g.rg = rg;
+  for (uint32_t i = 0; i < 4; i++) {
+    g.p[i] = pp.p[i];
+    g.pf[i] = (float)pp.p[i];
+    g.invp[i] = 1.0f / (float)pp.p[i];
+  }
   // output address weights (the output bit j comes from one operand's free bit)
   int op[64] = {0}, dst[64] = {0};
   if (d.nra != TNC_BITMAP) {
@@ -590,81 +682,20 @@ int p8_gemm_one(const StepDesc& d, const Shape& s, uint32_t ls, uint32_t p, uint
     if (op[j] == row_op) g.wm[dst[j]] = 1ull << j;
     else g.wn[dst[j]] = 1ull << j;
   }
-  g.out = ls ? part : arena + d.c_off * rg + r;
-  g.rg = rg;
+  g.out = ls ? part : arena + d.c_off * rg;
   const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
-  switch (s.tn) {
-    case 16: rc = launch_gemm<16>(ma, mb, g, grid, dev_err, st); break;
-    case 32: rc = launch_gemm<32>(ma, mb, g, grid, dev_err, st); break;
-    case 64: rc = launch_gemm<64>(ma, mb, g, grid, dev_err, st); break;
-    case 128: rc = launch_gemm<128>(ma, mb, g, grid, dev_err, st); break;
-    default: rc = launch_gemm<256>(ma, mb, g, grid, dev_err, st); break;
-  }
+  if (rg == 4) rc = launch_gemm_rg<4>(s.tn, ma, mb, g, grid, dev_err, st);
+  else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, ma, mb, g, grid, dev_err, st);
+  else rc = launch_gemm_rg<1>(s.tn, ma, mb, g, grid, dev_err, st);
   if (rc) return rc;
   if (ls) {
-    const uint64_t n = 1ull << d.c;
+    const uint64_t n = (uint64_t)rg << d.c;
     tnc_p8::p8_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
-        part, arena + d.c_off * rg + r, d.c, ls, p, rg);
+        part, arena + d.c_off * rg, d.c, ls, rg, make_uint4(pp.p[0], pp.p[1], pp.p[2], pp.p[3]));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 launch: ") + cudaGetErrorString(e));
   return TNC_OK;
-}
-
-}  // namespace
-
-bool p8_eligible(const StepDesc& d) {
-  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
-}
-
-// K split of a dense step: double it while the work items stay below
-// kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
-// (2^c entries per split) stay within 2^26 entries.
-constexpr uint64_t kP8SplitTarget = 160;
-uint32_t p8_split_log(const StepDesc& d) {
-  const Shape s = shape_of(d);
-  uint32_t ls = 0;
-  while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
-  return ls;
-}
-
-uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
-  return 2ull * (uint64_t)rg * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
-}
-
-uint64_t p8_part_entries(const StepDesc& d) {
-  const uint32_t ls = p8_split_log(d);
-  return ls ? 1ull << (d.c + ls) : 0;
-}
-
-int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
-              uint32_t* dev_err, int sms, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (rg != 1 && rg != 2 && rg != 4) return set_error(TNC_ERR_INVALID, "internal: residues per pass must be 1, 2 or 4");
-  tnc_p8::PackPrimes pp{};
-  for (uint32_t i = 0; i < 4; i++) pp.p[i] = primes[i < rg ? i : 0];
-  for (uint32_t i = 0; i < rg; i++)
-    if (primes[i] < 3 || primes[i] > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
-  const Shape s = shape_of(d);
-  const uint32_t ls = p8_split_log(d);
-  const uint64_t a_elems = 1ull << (s.fa + s.k), b_elems = 1ull << (s.fb + s.k);
-  __half* a16 = (__half*)scratch;           // rg planes of a_elems
-  __half* b16 = a16 + rg * a_elems;         // rg planes of b_elems
-  const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
-  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
-    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.k - 6);
-    const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
-    const uint32_t* src = arena + off * rg;
-    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
-    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
-    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
-  };
-  pack(a_off, a16, s.fa);
-  pack(b_off, b16, s.fb);
-  int rc = TNC_OK;
-  for (uint32_t r = 0; r < rg && !rc; r++) rc = p8_gemm_one(d, s, ls, primes[r], rg, r, a16 + r * a_elems,
-                                                             b16 + r * b_elems, arena, part, dev_err, sms, st);
-  return rc;
 }
 
 }  // namespace tnc
