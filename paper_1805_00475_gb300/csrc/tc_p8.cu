@@ -36,6 +36,8 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "tnc_internal.h"
 
@@ -62,6 +64,9 @@ struct P8Args {
   uint32_t p[4];
   float pf[4], invp[4];
   uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
+  uint8_t ebit[16];         // the tile's row and column bits by output weight, lightest first
+                            // (column bit j: 0x80 | j; row bit j: j); bits 0..4 go to lanes
+  uint32_t n_ebits, pad3;
   uint32_t* out;            // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
 };
 
@@ -221,7 +226,9 @@ struct PackPrimes {
 template <int RG>
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
                                                       uint32_t f, uint32_t k, PackPrimes pp) {
-  __shared__ __align__(16) __half tile[RG][32][72];
+  // a row of the tile is 64 values + 2 of padding: 33 words, so the 32 lanes of
+  // a warp (32 rows) hit 32 different banks in both phases
+  __shared__ __align__(16) __half2 tile[RG][32][33];
   const uint32_t R = 1u << f, K = 1u << k;
   const uint32_t tiles_r = (R + 31) / 32;
   const uint64_t n_tiles = (uint64_t)tiles_r << (k - 6);
@@ -229,34 +236,44 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
   for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
     const uint32_t r0 = (uint32_t)(b % tiles_r) * 32u, q0 = (uint32_t)(b / tiles_r) * 64u;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const uint32_t rr = t & 31u, qq = (t >> 5) + 8u * j;
+    for (int j = 0; j < 4; j++) {  // 1024 pairs (row, q..q+1) of the tile
+      const uint32_t pi = t + 256u * j, rr = pi & 31u, qp = pi >> 5;
       if (r0 + rr < R) {
-        const uint32_t* src = X + ((uint64_t)(q0 + qq) * R + r0 + rr) * RG;
-        uint32_t v[RG];
-        if constexpr (RG == 4) {
-          const uint4 w = *reinterpret_cast<const uint4*>(src);
-          v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
-        } else if constexpr (RG == 2) {
-          const uint2 w = *reinterpret_cast<const uint2*>(src);
-          v[0] = w.x; v[1] = w.y;
-        } else {
-          v[0] = src[0];
+        uint32_t v[2][RG];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const uint32_t* src = X + ((uint64_t)(q0 + 2 * qp + h) * R + r0 + rr) * RG;
+          if constexpr (RG == 4) {
+            const uint4 w = *reinterpret_cast<const uint4*>(src);
+            v[h][0] = w.x; v[h][1] = w.y; v[h][2] = w.z; v[h][3] = w.w;
+          } else if constexpr (RG == 2) {
+            const uint2 w = *reinterpret_cast<const uint2*>(src);
+            v[h][0] = w.x; v[h][1] = w.y;
+          } else {
+            v[h][0] = src[0];
+          }
         }
 #pragma unroll
         for (int i = 0; i < RG; i++) {
-          const int x = (int)v[i], hp = (int)(pp.p[i] - 1) / 2;
-          tile[i][rr][qq] = __int2half_rn(x > hp ? x - (int)pp.p[i] : x);
+          const int hp = (int)(pp.p[i] - 1) / 2, p = (int)pp.p[i];
+          const int x0 = (int)v[0][i], x1 = (int)v[1][i];
+          tile[i][rr][qp] = __halves2half2(__int2half_rn(x0 > hp ? x0 - p : x0), __int2half_rn(x1 > hp ? x1 - p : x1));
         }
       }
     }
     __syncthreads();
-    const uint32_t rr = t >> 3, c8 = (t & 7u) * 8u;
+    const uint32_t rr = t >> 3, c4 = (t & 7u) * 4u;  // 4 pairs = 8 values = 16 bytes of one row
     if (r0 + rr < R) {
 #pragma unroll
-      for (int i = 0; i < RG; i++)
-        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)(r0 + rr) * K + q0 + c8) =
-            *reinterpret_cast<const uint4*>(&tile[i][rr][c8]);
+      for (int i = 0; i < RG; i++) {
+        const __half2* src = &tile[i][rr][c4];
+        uint4 w;
+        w.x = *reinterpret_cast<const uint32_t*>(src + 0);
+        w.y = *reinterpret_cast<const uint32_t*>(src + 1);
+        w.z = *reinterpret_cast<const uint32_t*>(src + 2);
+        w.w = *reinterpret_cast<const uint32_t*>(src + 3);
+        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)(r0 + rr) * K + q0 + 2 * c4) = w;
+      }
     }
     __syncthreads();
   }
@@ -295,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * RG + 1];
   __shared__ uint32_t tmem_base_s;
   __shared__ uint64_t om_tab[kTileM], on_tab[TN];
+  __shared__ uint16_t hi_tab[kTileM * TN / 32];  // row | col << 8 of the entry bits above the lane bits
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint32_t* staging = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);  // [col][kStagePitch]
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (uint32_t r = 0; r < RG && ok; r++) {
             const uint32_t q0 = split * Ks + c * chunk;
             for (uint32_t j = 0; j < spc; j++) {
-              if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+              if (!mbar_try(empty0 + 8 * s, ph ^ 1u) && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
                 ok = false;
                 break;
               }
@@ -384,16 +402,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t d = tmem + r * TN;
             for (uint32_t j = 0; j < spc; j++) {
-              if (!mbar_wait(full0 + 8 * s, ph)) {
+              if (!mbar_try(full0 + 8 * s, ph) && !mbar_wait(full0 + 8 * s, ph)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * kStageBytes), sb = sa + kABytes;
+              const uint64_t ad = make_desc_sw128(sa), bd = make_desc_sw128(sb);
 #pragma unroll
               for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values: 32 bytes into each row
-                mma_f16(d, make_desc_sw128(sa + ks * 32u), make_desc_sw128(sb + ks * 32u), idesc,
-                        (c | j | ks) ? 1u : 0u);
+                mma_f16(d, ad + 2u * ks, bd + 2u * ks, idesc, (c | j | ks) ? 1u : 0u);
               mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
               if (++s == kStages) {
                 s = 0;
@@ -420,8 +438,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr uint32_t kBatch = kHalf >= 32 ? 32 : 16;  // columns per TMEM load batch
     const uint32_t cbeg = ((warp - 2u) >> 2) * kHalf;
     const bool idle = cbeg >= TN;                         // second half when TN = 16
-    const bool rows_low = g.wm[0] < g.wn[0];              // entries of consecutive rows are adjacent in C
     uint8_t* stage8 = reinterpret_cast<uint8_t*>(staging);
+    // write order of a tile's entries: entry index e has the tile's row and
+    // column bits ordered by output weight, so consecutive e are as close in C
+    // as the step's bit map allows (lane bits: the five lightest)
+    uint32_t lane_row = 0, lane_col = 0;
+    for (uint32_t i = 0; i < 5; i++) {
+      const uint32_t b = g.ebit[i], v = (lane >> i) & 1u;
+      if (b & 0x80u) lane_col |= v << (b & 31u);
+      else lane_row |= v << b;
+    }
+    for (uint32_t h = et; h < kTileM * TN / 32; h += kEpiThreads) {
+      uint32_t rw = 0, cl = 0;
+      for (uint32_t i = 5; i < g.n_ebits; i++) {
+        const uint32_t b = g.ebit[i], v = (h >> (i - 5)) & 1u;
+        if (b & 0x80u) cl |= v << (b & 31u);
+        else rw |= v << b;
+      }
+      hi_tab[h] = (uint16_t)(rw | cl << 8);
+    }
     uint32_t na[RG];
     for (uint32_t r = 0; r < RG; r++) na[r] = 0;
     for (uint32_t t = 0; t < T; t++) {
@@ -484,7 +519,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (ok) {
         uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull);
         for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
-          const uint32_t rr = rows_low ? e % kTileM : e / TN, cc = rows_low ? e / kTileM : e % TN;
+          const uint32_t hc = hi_tab[e >> 5];
+          const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
           const uint32_t w = staging[cc * kStagePitch + rr];
           uint32_t* dst = outp + (om_tab[rr] + on_tab[cc]) * RG;
           if constexpr (RG == 4) {
@@ -681,6 +717,15 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
   for (int j = 0; j < d.c; j++) {
     if (op[j] == row_op) g.wm[dst[j]] = 1ull << j;
     else g.wn[dst[j]] = 1ull << j;
+  }
+  // the tile's bits by output weight (ties cannot occur: distinct bits)
+  {
+    std::vector<std::pair<uint64_t, uint8_t>> bits;
+    for (uint32_t j = 0; j < 7; j++) bits.push_back({g.wm[j], (uint8_t)j});
+    for (uint32_t j = 0; (1u << j) < s.tn; j++) bits.push_back({g.wn[j], (uint8_t)(0x80u | j)});
+    std::sort(bits.begin(), bits.end());
+    g.n_ebits = (uint32_t)bits.size();
+    for (size_t i = 0; i < bits.size(); i++) g.ebit[i] = bits[i].second;
   }
   g.out = ls ? part : arena + d.c_off * rg;
   const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
