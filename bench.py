@@ -219,7 +219,8 @@ def c4_workload(count=16, n=180):
 def run_c3(args):
     """4096 monotone 1-in-3 formulas, n ~ U{50..150}, m = round(n U[0.5, 0.8)).
     Counted modulo about 2^60 like 2 residues below 2^30: formulas whose best
-    plan needs few MACs go through one persistent, graph-captured batch launch
+    plan needs few MACs (<= 2^24, rank <= 16: the descriptors of a formula fit
+    in shared memory) go through one persistent, graph-captured batch launch
     (2 residues below 2^30); the others one by one through tnc_contract on the
     8-bit-prime tensor-core path (8 primes <= 251, product 2^62.8), spread over
     host threads with a stream and a workspace each; plans above rank 28 are
@@ -236,7 +237,7 @@ def run_c3(args):
     t = time.perf_counter()
     plans = tnc.plan_many(forms, heuristic="best", rank_cap=64)
     plan_s = time.perf_counter() - t
-    is_light = [p.stats.total_macs <= light_macs and p.stats.max_rank <= 24 for p in plans]
+    is_light = [p.stats.total_macs <= light_macs and p.stats.max_rank <= 16 for p in plans]
     light = [p for p, l in zip(plans, is_light) if l]
     heavy = [p for p, l in zip(plans, is_light) if not l and p.stats.max_rank <= rank_max]
     left = [p.stats.max_rank for p in plans if p.stats.max_rank > rank_max]
@@ -295,7 +296,7 @@ def run_c3(args):
         "vs_baseline": None,
         "dtype": "u32 residues: batch 2 primes < 2^30 (int64); heavy 8 primes <= 251 (fp16 tensor-core dense steps)",
         "data": "synthetic",
-        "config": {"workload": f"one_in_three_batch{n_total}", "batched_macs_le_2^24": len(light),
+        "config": {"workload": f"one_in_three_batch{n_total}", "batched_macs_le_2^24_rank_le_16": len(light),
                    "heavy_tc_p8_rank_le_28": len(heavy), "left_out_rank_gt_28": len(left),
                    "left_out_ranks": sorted(left), "planner": "best", "autotune": tuned, "host_threads": workers,
                    "modulus_bits": {"batch": round(sum(math.log2(q) for q in tnc.default_primes(Rc)), 1),
