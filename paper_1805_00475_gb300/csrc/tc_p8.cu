@@ -216,30 +216,16 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 // X: the operand's u32 residues in [0, p_i), entry q * R + r at
 // X + (q * R + r) * RG (R = 2^f rows, K = 2^k shared values, RG residues per
 // entry); Y_i (i < RG, Y_i = Y + i * R * K): balanced fp16 residues mod p_i,
-// row-major, Y_i[pi(r) * K + q] with pi the row order of RowPerm.  A block transposes a tile of 32 rows x 64 shared
+// row-major, Y_i[r * K + q].  A block transposes a tile of 32 rows x 64 shared
 // values through shared memory: reads of whole entries coalesced along r,
 // 16-byte writes coalesced along q.
 struct PackPrimes {
   uint32_t p[4];
 };
 
-// Row order of a packed operand: bit j of an operand row index becomes bit
-// pos[j] of its packed row index (the bits sorted by their weight in the
-// step's output, lightest first, so that an output tile of consecutive packed
-// rows and columns covers a compact range of the output).
-struct RowPerm {
-  uint8_t pos[32];
-};
-
-__device__ __forceinline__ uint32_t permute_row(uint32_t r, uint32_t f, const RowPerm& rp) {
-  uint32_t o = 0;
-  for (uint32_t j = 0; j < f; j++) o |= ((r >> j) & 1u) << rp.pos[j];
-  return o;
-}
-
 template <int RG>
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
-                                                      uint32_t f, uint32_t k, PackPrimes pp, RowPerm rp) {
+                                                      uint32_t f, uint32_t k, PackPrimes pp) {
   // a row of the tile is 64 values + 2 of padding: 33 words, so the 32 lanes of
   // a warp (32 rows) hit 32 different banks in both phases
   __shared__ __align__(16) __half2 tile[RG][32][33];
@@ -286,7 +272,7 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
         w.y = *reinterpret_cast<const uint32_t*>(src + 1);
         w.z = *reinterpret_cast<const uint32_t*>(src + 2);
         w.w = *reinterpret_cast<const uint32_t*>(src + 3);
-        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)permute_row(r0 + rr, f, rp) * K + q0 + 2 * c4) = w;
+        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)(r0 + rr) * K + q0 + 2 * c4) = w;
       }
     }
     __syncthreads();
@@ -679,57 +665,16 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
   __half* a16 = (__half*)scratch;    // rg planes of a_elems
   __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
   const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
-  // output address weight of each operand bit (row operand first)
-  uint64_t wrow[32] = {0}, wcol[32] = {0};
-  {
-    int op[64] = {0}, dst[64] = {0};
-    if (d.nra != TNC_BITMAP) {
-      for (int i = 0; i < d.nra; i++)
-        for (int q = 0; q < d.map.runs.ra[i].len; q++) {
-          op[d.map.runs.ra[i].src + q] = 0;
-          dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
-        }
-      for (int i = 0; i < d.nrb; i++)
-        for (int q = 0; q < d.map.runs.rb[i].len; q++) {
-          op[d.map.runs.rb[i].src + q] = 1;
-          dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
-        }
-    } else {
-      for (int j = 0; j < d.c; j++) {
-        op[j] = d.map.bit[j] >> 7;
-        dst[j] = d.map.bit[j] & 63;
-      }
-    }
-    const int row_op = s.swap ? 1 : 0;
-    for (int j = 0; j < d.c; j++) {
-      if (op[j] == row_op) wrow[dst[j]] = 1ull << j;
-      else wcol[dst[j]] = 1ull << j;
-    }
-  }
-  // packed row order: operand bits by output weight, lightest first
-  auto order = [](const uint64_t* w, uint32_t f, tnc_p8::RowPerm& rp, uint64_t* wpacked) {
-    std::vector<std::pair<uint64_t, uint32_t>> b;
-    for (uint32_t j = 0; j < f; j++) b.push_back({w[j], j});
-    std::sort(b.begin(), b.end());
-    for (uint32_t i = 0; i < f; i++) {
-      rp.pos[b[i].second] = (uint8_t)i;
-      wpacked[i] = b[i].first;
-    }
-  };
-  tnc_p8::RowPerm rp_a{}, rp_b{};
-  uint64_t wm_packed[32] = {0}, wn_packed[32] = {0};
-  order(wrow, s.fa, rp_a, wm_packed);
-  order(wcol, s.fb, rp_b, wn_packed);
-  auto pack = [&](uint64_t off, __half* dst, uint32_t f, const tnc_p8::RowPerm& rp) {
+  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
     const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.k - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
     const uint32_t* src = arena + off * rg;
-    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp, rp);
-    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp, rp);
-    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp, rp);
+    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
   };
-  pack(a_off, a16, s.fa, rp_a);
-  pack(b_off, b16, s.fb, rp_b);
+  pack(a_off, a16, s.fa);
+  pack(b_off, b16, s.fb);
   CUtensorMap ma, mb;
   int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, rg, tnc_p8::kTileM);
   if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, rg, s.tn);
@@ -749,9 +694,30 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
     g.pf[i] = (float)pp.p[i];
     g.invp[i] = 1.0f / (float)pp.p[i];
   }
-  // output address weights of the packed row and column bits
-  for (uint32_t j = 0; j < s.fa; j++) g.wm[j] = wm_packed[j];
-  for (uint32_t j = 0; j < s.fb; j++) g.wn[j] = wn_packed[j];
+  // output address weights (the output bit j comes from one operand's free bit)
+  int op[64] = {0}, dst[64] = {0};
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++)
+      for (int q = 0; q < d.map.runs.ra[i].len; q++) {
+        op[d.map.runs.ra[i].src + q] = 0;
+        dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
+      }
+    for (int i = 0; i < d.nrb; i++)
+      for (int q = 0; q < d.map.runs.rb[i].len; q++) {
+        op[d.map.runs.rb[i].src + q] = 1;
+        dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
+      }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      op[j] = d.map.bit[j] >> 7;
+      dst[j] = d.map.bit[j] & 63;
+    }
+  }
+  const int row_op = s.swap ? 1 : 0;
+  for (int j = 0; j < d.c; j++) {
+    if (op[j] == row_op) g.wm[dst[j]] = 1ull << j;
+    else g.wn[dst[j]] = 1ull << j;
+  }
   // the tile's bits by output weight (ties cannot occur: distinct bits)
   {
     std::vector<std::pair<uint64_t, uint8_t>> bits;
