@@ -246,34 +246,46 @@ def run_c3(args):
     stream = torch.cuda.Stream(device=dev)
     batch.upload(ws_b, stream)
     tuned = batch.autotune(ws_b, stream)
-    # heavy formulas: longest first onto the least loaded worker
-    heavy.sort(key=lambda p: -p.stats.total_macs)
-    bins, load = [[] for _ in range(workers)], [0.0] * workers
-    for p in heavy:
-        w = load.index(min(load))
-        bins[w].append(p)
-        load[w] += p.stats.total_macs
-    wss = [torch.empty(max([tnc.workspace_bytes(p, R8, "tc_p8") for p in b] + [256]), dtype=torch.uint8, device=dev)
-           for b in bins]
+    # heavy formulas in two phases (rank <= 26, then 27..28), each spread
+    # longest first onto the least loaded of the workers
+    phases = [[p for p in heavy if p.stats.max_rank <= 26], [p for p in heavy if p.stats.max_rank > 26]]
+    bins = []
+    for ph in phases:
+        b, load = [[] for _ in range(workers)], [0.0] * workers
+        for p in sorted(ph, key=lambda p: -p.stats.total_macs):
+            w = load.index(min(load))
+            b[w].append(p)
+            load[w] += p.stats.total_macs
+        bins.append(b)
+    wss = [torch.empty(max([tnc.workspace_bytes(p, R8, "tc_p8") for ph in bins for p in ph[w]] + [256]),
+                       dtype=torch.uint8, device=dev) for w in range(workers)]
     streams = [torch.cuda.Stream(device=dev) for _ in range(workers)]
     macs_light = sum(p.stats.total_macs for p in light) * Rc
     macs_heavy = sum(p.stats.total_macs for p in heavy) * R8
+    phase_s = [[], [], []]
 
-    def work(w):
-        for p in bins[w]:
+    def work(ph, w):
+        for p in bins[ph][w]:
             tnc.contract(p, n_residues=R8, path="tc_p8", workspace=wss[w], stream=streams[w])
 
     def one_step():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         batch.launch(ws_b, stream)
-        th = [threading.Thread(target=work, args=(w,)) for w in range(workers)]
-        for x in th:
-            x.start()
-        for x in th:
-            x.join()
-        torch.cuda.synchronize(dev)
-        return time.perf_counter() - t0
+        stream.synchronize()
+        t1 = time.perf_counter()
+        marks = [t0, t1]
+        for ph in range(2):
+            th = [threading.Thread(target=work, args=(ph, w)) for w in range(workers)]
+            for x in th:
+                x.start()
+            for x in th:
+                x.join()
+            torch.cuda.synchronize(dev)
+            marks.append(time.perf_counter())
+        for i in range(3):
+            phase_s[i].append(marks[i + 1] - marks[i])
+        return marks[-1] - t0
 
     for _ in range(max(args.warmup, 1)):
         one_step()
@@ -303,6 +315,11 @@ def run_c3(args):
                                     "heavy": round(sum(math.log2(q) for q in tnc.default_primes(R8, "tc_p8")), 1)}},
         "modular_macs_per_s": (macs_light + macs_heavy) / s,
         "batch_launch_ms": ev0.elapsed_time(ev1), "clocks": clk, "plan_s": plan_s,
+        "phases_ms": {"batch": 1000 * statistics.mean(phase_s[0][-args.steps:]),
+                      "heavy_rank_le_26": 1000 * statistics.mean(phase_s[1][-args.steps:]),
+                      "heavy_rank_27_28": 1000 * statistics.mean(phase_s[2][-args.steps:])},
+        "counts_per_s_rank_le_26": (len(light) + len(phases[0])) /
+                                   (statistics.mean(phase_s[0][-args.steps:]) + statistics.mean(phase_s[1][-args.steps:])),
     }
     print(json.dumps(line), flush=True)
 
@@ -425,11 +442,11 @@ def run_c4(args):
     dense = sum(p.stats.dense_macs for p in plans)
     dense8 = sum(p.stats.dense_macs_p8 for p in plans)
 
-    dense_ms = []
+    dense_ms, device_ms = [], []
 
     def one_pass(path, timed=False):
         R = R8 if path == "tc_p8" else Rc
-        counts, dms = [], 0.0
+        counts, dms, gms = [], 0.0, 0.0
         tnc.set_step_timing(timed)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -438,11 +455,13 @@ def run_c4(args):
             assert r.flags == 0
             counts.append(r.counts[0])
             dms += tnc.last_dense_time()[0]
+            gms += tnc.last_contract_time()
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         tnc.set_step_timing(False)
         if timed:
             dense_ms.append(dms)
+            device_ms.append(gms)
         return dt, counts
 
     for _ in range(max(args.warmup, 1)):
@@ -484,6 +503,7 @@ def run_c4(args):
                      "peak_source": f"{pk_kind} bf16 burst (MEASURED_PEAKS.json); fp16 has the same dense rate",
                      "kernel": "dense steps: p8_pack x2 + p8_gemm_kernel (+ split sum)",
                      "dense_ms_per_step": dms, "dense_share_of_step": dms / (s * 1000.0),
+                     "device_ms_per_step": sum(device_ms) / len(device_ms),
                      "whole_contraction_tflops": p8_flops / s / 1e12,
                      "algorithmic_flops_per_step": p8_flops},
         "clocks": clk, "plan_s": plan_s,

@@ -221,6 +221,9 @@ size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts*
  * and the number of dense step launches of the last tnc_contract. */
 void tnc_set_step_timing(int32_t on);
 int tnc_last_dense_time(double* ms, int32_t* n_steps);
+/* Same mode: device time (ms) of the last tnc_contract's kernels, from its
+ * first launch to its CRT (host work and the final copies excluded). */
+int tnc_last_contract_time(double* device_ms);
 /* Contracts the plan on the GPU and returns the count(s) in `out` (host).
  * dev_ws: device buffer of at least tnc_workspace_bytes_opts(plan, opts) bytes
  * (= tnc_workspace_bytes(plan, R) on TNC_PATH_INT64 and TNC_PATH_TC), 256-byte

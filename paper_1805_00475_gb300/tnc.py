@@ -31,7 +31,7 @@ TNC_MAYBE_WRAPPED = 1
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -122,6 +122,7 @@ def lib():
             "tnc_workspace_bytes_opts": ([vp, vp], sz),
             "tnc_set_step_timing": ([i32], None),
             "tnc_last_dense_time": ([ctypes.POINTER(ctypes.c_double), i32p], ctypes.c_int),
+            "tnc_last_contract_time": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
@@ -389,6 +390,13 @@ def last_dense_time() -> Tuple[float, int]:
     ms, n = ctypes.c_double(), ctypes.c_int32()
     _check(lib().tnc_last_dense_time(ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def last_contract_time() -> float:
+    """tnc_last_contract_time: device ms of the last contraction's kernels (timing mode)."""
+    ms = ctypes.c_double()
+    _check(lib().tnc_last_contract_time(ctypes.byref(ms)))
+    return ms.value
 
 
 def probe_modmac(iters: int = 4096, stream=None) -> float:
