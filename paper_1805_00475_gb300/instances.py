@@ -243,6 +243,48 @@ def cubic_one_in_three(n_vertices: int, seed: int) -> Formula:
                    name=f"cubic1in3_v{n_vertices}_s{seed}")
 
 
+def cnf_formula(n_vars: int, clauses: Sequence[Sequence[int]], name: str = "") -> Formula:
+    """General CNF with negated literals (Sec. 2.1: a clause tensor is 1 on the
+    assignments that satisfy the clause; a negated literal reverses its bond's
+    index).  Literals are DIMACS-style: +(v+1) is x_v, -(v+1) is not x_v.  A
+    clause becomes a TABLE tensor over its distinct variables (index bit i =
+    value of the i-th), 1 everywhere except the one assignment that falsifies
+    every literal; a clause with x and not x is the all-ones table."""
+    cl, tabs = [], []
+    for lits in clauses:
+        sign = {}
+        taut = False
+        for lit in lits:
+            if lit == 0 or abs(lit) > n_vars:
+                raise ValueError(f"literal {lit} out of range")
+            v, neg = abs(lit) - 1, lit < 0
+            if v in sign and sign[v] != neg:
+                taut = True
+            sign[v] = neg
+        vs = tuple(sign)
+        table = [1] * (1 << len(vs))
+        if not taut:
+            table[sum(1 << i for i, v in enumerate(vs) if sign[v])] = 0
+        cl.append(vs)
+        tabs.append(table)
+    return Formula(n_vars, cl, [KIND_TABLE] * len(cl), tables=tabs, name=name or f"cnf{n_vars}")
+
+
+def random_k_cnf(n: int, m: int, k: int, seed: int) -> Formula:
+    """m clauses of k distinct variables drawn uniformly, each literal negated
+    with probability 1/2 (seeded splitmix64)."""
+    g = SplitMix64(seed)
+    clauses = []
+    for _ in range(m):
+        vs: List[int] = []
+        while len(vs) < k:
+            v = g.below(n)
+            if v not in vs:
+                vs.append(v)
+        clauses.append([(v + 1) * (-1 if g.below(2) else 1) for v in vs])
+    return cnf_formula(n, clauses, name=f"cnf{k}_{n}_{m}_{seed}")
+
+
 def batch_one_in_three(count: int, master_seed: int, n_lo: int = 50, n_hi: int = 150,
                        d_lo: float = 0.5, d_hi: float = 0.8) -> List[Formula]:
     """Uneven batch: n ~ U{n_lo..n_hi}, m = round(n * U[d_lo, d_hi))."""

@@ -249,3 +249,46 @@ def test_contract_rejects_bad_order():
         oracle.count(f, order=[(0, 0)])
     with pytest.raises(RuntimeError):
         oracle.count(f, order=[(0, 99)])
+
+
+def _cnf_bruteforce(n, lit_clauses):
+    """Satisfying assignments of a CNF evaluated literal by literal (no clause
+    tensors involved)."""
+    total = 0
+    for x in range(1 << n):
+        if all(any(((x >> (abs(l) - 1)) & 1) == (1 if l > 0 else 0) for l in c) for c in lit_clauses):
+            total += 1
+    return total
+
+
+def _cnf_literals(n, m, k, seed):
+    rng = random.Random(seed)
+    return [[rng.choice([1, -1]) * (v + 1) for v in rng.sample(range(n), k)] for _ in range(m)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cnf_with_negations_matches_literal_bruteforce(seed):
+    """General CNF (negated literals as reversed bond indices, Sec. 2.1): the
+    oracle's contraction equals the count of assignments satisfying every
+    clause, evaluated directly on the literals."""
+    n, lits = 13, _cnf_literals(13, 20, 3, seed)
+    f = I.cnf_formula(n, lits)
+    assert oracle.count(f) == [_cnf_bruteforce(n, lits)]
+
+
+def test_cnf_count_invariant_under_flipping_a_variable():
+    """Negating every literal of one variable permutes the assignments: the
+    count is unchanged (and a clause with x and not x changes nothing)."""
+    lits = _cnf_literals(12, 18, 3, 99)
+    base = oracle.count(I.cnf_formula(12, lits))
+    for v in (1, 5, 12):
+        flipped = [[-l if abs(l) == v else l for l in c] for c in lits]
+        assert oracle.count(I.cnf_formula(12, flipped)) == base
+    assert oracle.count(I.cnf_formula(12, lits + [[3, -3, 7]])) == base
+
+
+def test_positive_cnf_equals_or_clauses():
+    """A CNF without negations is the OR-clause formula of the same scopes."""
+    lits = [[abs(l) for l in c] for c in _cnf_literals(14, 12, 3, 7)]
+    f_or = I.Formula(14, [tuple(abs(l) - 1 for l in c) for c in lits], [I.KIND_OR] * len(lits))
+    assert oracle.count(I.cnf_formula(14, lits)) == oracle.count(f_or)
