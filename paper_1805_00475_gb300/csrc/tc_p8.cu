@@ -216,7 +216,8 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 // X: the operand's u32 residues in [0, p_i), entry q * R + r at
 // X + (q * R + r) * RG (R = 2^f rows, K = 2^k shared values, RG residues per
 // entry); Y_i (i < RG, Y_i = Y + i * R * K): balanced fp16 residues mod p_i,
-// row-major, Y_i[r * K + q].  A block transposes a tile of 32 rows x 64 shared
+// row-major, Y_i[r * Kp + q] with rows padded to Kp = max(K, 64) values by
+// zeros.  A block transposes a tile of 32 rows x 64 shared
 // values through shared memory: reads of whole entries coalesced along r,
 // 16-byte writes coalesced along q.
 struct PackPrimes {
@@ -225,13 +226,14 @@ struct PackPrimes {
 
 template <int RG>
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
-                                                      uint32_t f, uint32_t k, PackPrimes pp) {
+                                                      uint32_t f, uint32_t k, uint32_t kp, PackPrimes pp) {
   // a row of the tile is 64 values + 2 of padding: 33 words, so the 32 lanes of
   // a warp (32 rows) hit 32 different banks in both phases
   __shared__ __align__(16) __half2 tile[RG][32][33];
-  const uint32_t R = 1u << f, K = 1u << k;
+  // rows of Y hold Kp = 2^kp >= K values: shared values q >= K are zero
+  const uint32_t R = 1u << f, K = 1u << k, Kp = 1u << kp;
   const uint32_t tiles_r = (R + 31) / 32;
-  const uint64_t n_tiles = (uint64_t)tiles_r << (k - 6);
+  const uint64_t n_tiles = (uint64_t)tiles_r << (kp - 6);
   const uint32_t t = threadIdx.x;
   for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
     const uint32_t r0 = (uint32_t)(b % tiles_r) * 32u, q0 = (uint32_t)(b / tiles_r) * 64u;
@@ -242,6 +244,11 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
         uint32_t v[2][RG];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
+          if (q0 + 2 * qp + h >= K) {
+#pragma unroll
+            for (int i = 0; i < RG; i++) v[h][i] = 0;
+            continue;
+          }
           const uint32_t* src = X + ((uint64_t)(q0 + 2 * qp + h) * R + r0 + rr) * RG;
           if constexpr (RG == 4) {
             const uint4 w = *reinterpret_cast<const uint4*>(src);
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
         w.y = *reinterpret_cast<const uint32_t*>(src + 1);
         w.z = *reinterpret_cast<const uint32_t*>(src + 2);
         w.w = *reinterpret_cast<const uint32_t*>(src + 3);
-        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * K + (uint64_t)(r0 + rr) * K + q0 + 2 * c4) = w;
+        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * Kp + (uint64_t)(r0 + rr) * Kp + q0 + 2 * c4) = w;
       }
     }
     __syncthreads();
@@ -584,8 +591,8 @@ int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t rg,
 }
 
 struct Shape {
-  bool swap;               // rows come from B
-  uint32_t fa, fb, k, tn;  // row bits, column bits, shared bits, columns per tile
+  bool swap;                   // rows come from B
+  uint32_t fa, fb, k, kp, tn;  // row bits, column bits, shared bits (padded to >= 6), columns per tile
   uint64_t tiles;
 };
 
@@ -595,6 +602,7 @@ Shape shape_of(const StepDesc& d) {
   s.fa = s.swap ? d.kb : d.ka;
   s.fb = s.swap ? d.ka : d.kb;
   s.k = d.k;
+  s.kp = std::max<uint32_t>(d.k, 6);
   s.tn = std::min<uint32_t>(1u << s.fb, tnc_p8::kMaxTN);
   s.tiles = ((1ull << s.fa) / tnc_p8::kTileM) * ((1ull << s.fb) / s.tn);
   return s;
@@ -628,7 +636,7 @@ int launch_gemm_rg(uint32_t tn, const CUtensorMap& ma, const CUtensorMap& mb, co
 }  // namespace
 
 bool p8_eligible(const StepDesc& d) {
-  return d.k >= 6 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
+  return d.k >= 4 && ((d.ka >= 7 && d.kb >= 4) || (d.kb >= 7 && d.ka >= 4));
 }
 
 // K split of a dense step: double it while the work items stay below
@@ -643,7 +651,8 @@ uint32_t p8_split_log(const StepDesc& d) {
 }
 
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
-  return 2ull * (uint64_t)rg * ((1ull << (d.ka + d.k)) + (1ull << (d.kb + d.k)));
+  const uint32_t kp = std::max<uint32_t>(d.k, 6);
+  return 2ull * (uint64_t)rg * ((1ull << (d.ka + kp)) + (1ull << (d.kb + kp)));
 }
 
 uint64_t p8_part_entries(const StepDesc& d, int rg) {
@@ -661,29 +670,29 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
     if (primes[i] < 3 || primes[i] > 251) return set_error(TNC_ERR_INVALID, "tensor-core p8 steps need primes in [3, 251]");
   const Shape s = shape_of(d);
   const uint32_t ls = p8_split_log(d);
-  const uint64_t a_elems = 1ull << (s.fa + s.k);
+  const uint64_t a_elems = 1ull << (s.fa + s.kp);
   __half* a16 = (__half*)scratch;    // rg planes of a_elems
   __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
   const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
   auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
-    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.k - 6);
+    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.kp - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
     const uint32_t* src = arena + off * rg;
-    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
-    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
-    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, pp);
+    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
+    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
+    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
   };
   pack(a_off, a16, s.fa);
   pack(b_off, b16, s.fb);
   CUtensorMap ma, mb;
-  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.k, rg, tnc_p8::kTileM);
-  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.k, rg, s.tn);
+  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
+  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
   if (rc) return rc;
   tnc_p8::P8Args g;
   std::memset(&g, 0, sizeof(g));
   g.fa = s.fa;
   g.fb = s.fb;
-  g.k = s.k;
+  g.k = s.kp;  // zero-padded shared values contribute nothing
   g.log_split = ls;
   g.tiles_m = (1u << s.fa) / tnc_p8::kTileM;
   if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");

@@ -21,18 +21,19 @@ def built():
 
 
 def _p8_shape(fa, fb, k):
-    """(rows from B, columns per tile, K chunks, log2 K split) of a step the
-    path runs on the tensor cores, else None (the library's rule restated)."""
-    if not (k >= 6 and ((fa >= 7 and fb >= 4) or (fb >= 7 and fa >= 4))):
+    """(rows from B, columns per tile, K chunks, log2 K split, shared values
+    zero-padded) of a step the path runs on the tensor cores, else None (the
+    library's rule restated)."""
+    if not (k >= 4 and ((fa >= 7 and fb >= 4) or (fb >= 7 and fa >= 4))):
         return None
     swap = not (fa >= 7 and fb >= 4)
     r, c = (fb, fa) if swap else (fa, fb)
-    tn = min(1 << c, 256)
+    tn = min(1 << c, 128)
     tiles = (1 << r) // 128 * ((1 << c) // tn)
     ls = 0
     while (tiles << ls) < 160 and k - ls - 1 >= 10 and (1 << (fa + fb + ls + 1)) <= (1 << 26):
         ls += 1
-    return swap, tn, max(1, (1 << (k - ls)) // 1024), ls
+    return swap, tn, max(1, (1 << (max(k, 6) - ls)) // 1024), ls, k < 6
 
 
 ORACLE_CASES = [(70, "greedy", 0), (70, "greedy", 1), (70, "greedy", 2), (70, "gn", 1), (70, "bisect", 0),
@@ -60,8 +61,10 @@ def test_p8_oracle_cases_cover_every_tile_width_and_both_orientations():
             if sh:
                 seen.add(("tn", sh[1]))
                 seen.add(("swap", sh[0]))
-    assert {("tn", t) for t in (16, 32, 64, 128, 256)} <= seen
+                seen.add(("padded", sh[4]))
+    assert {("tn", t) for t in (16, 32, 64, 128)} <= seen
     assert {("swap", True), ("swap", False)} <= seen
+    assert ("padded", True) in seen and ("padded", False) in seen
 
 
 @pytest.mark.parametrize("n,h,seed", [(100, "greedy", 0), (100, "greedy", 2), (120, "greedy", 2), (120, "bisect", 2)])
