@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default="", help="c2: fixed launch shape THREADS,SMEM_BYTES[,CTAS_PER_SM] instead of the autotuner")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
@@ -412,6 +412,64 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_slicing(args):
+    """Bond slicing on the rank-29 networks of C4 (#Cubic-VC, n = 180, seeds 3
+    and 15): each counted whole and as 2^s slices (s = 1..4) on the
+    8-bit-prime tensor-core path; reported: time, peak tensor size and
+    workspace, identical counts."""
+    import torch
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import slicing as S
+    from paper_1805_00475_gb300 import tnc
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    R8 = 20
+    stream = torch.cuda.Stream(device=dev)
+    rows = []
+    for seed in (3, 15):
+        f = I.cubic_vertex_cover(180, seed)
+        whole = tnc.plan_formula(f, heuristic="best", rank_cap=30)
+        cases = [("whole", [whole], [])]
+        for s in range(1, 5):
+            vs = S.choose_slice_vars(f, s)
+            cases.append((f"s={s}", S.sliced_plans(f, vs)[0], vs))
+        ref = None
+        for name, plans, vs in cases:
+            if name == "whole":
+                nb = tnc.workspace_bytes(plans[0], R8, "tc_p8")
+                run = lambda ws: tnc.contract(plans[0], n_residues=R8, path="tc_p8", workspace=ws, stream=stream)
+            else:
+                o, _ = tnc._opts(R8, None, "tc_p8")
+                arr = (tnc.ctypes.c_void_p * len(plans))(*[p.h.value for p in plans])
+                nb = int(tnc.lib().tnc_workspace_bytes_sliced(arr, len(plans), tnc.ctypes.byref(o)))
+                run = lambda ws, plans=plans: tnc.contract_sliced(plans, n_residues=R8, path="tc_p8", workspace=ws,
+                                                                  stream=stream)
+            ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            for _ in range(max(args.warmup, 1)):
+                r = run(ws)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                r = run(ws)
+            torch.cuda.synchronize(dev)
+            ms = 1000 * (time.perf_counter() - t0) / args.steps
+            ref = r.counts if ref is None else ref
+            assert r.counts == ref and r.flags == 0, "slices disagree with the whole network"
+            rows.append({"seed": seed, "case": name, "fixed_vars": vs, "slices": len(plans),
+                         "max_rank": max(p.stats.max_rank for p in plans),
+                         "log2_macs": round(math.log2(sum(p.stats.total_macs for p in plans)), 2),
+                         "workspace_gb": round(nb / 1e9, 2), "ms": ms})
+            del ws
+            torch.cuda.empty_cache()
+    best = {seed: min((x for x in rows if x["seed"] == seed), key=lambda x: x["ms"]) for seed in (3, 15)}
+    line = {"metric": "bond slicing on rank-29 networks", "value": sum(x["ms"] for x in rows if x["case"] == "whole") /
+            sum(b["ms"] for b in best.values()), "unit": "x (whole-network time / best sliced time)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "u32 residues mod 20 primes <= 251",
+            "config": {"workload": "cubic_vertex_cover_n180_seeds_3_15", "path": "tc_p8", "residues": R8},
+            "cases": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_c4(args):
     """16 #Cubic-VC formulas on 180 vertices: exact counts through tnc_contract
     on the 8-bit-prime tensor-core path (timed steps); the 30-bit-prime limb
@@ -656,6 +714,8 @@ def main():
         run_reference(args)
     elif args.config == "c4":
         run_c4(args)
+    elif args.config == "slicing":
+        run_slicing(args)
     elif args.config == "c3":
         run_c3(args)
     elif args.config == "c5":

@@ -215,6 +215,17 @@ size_t tnc_workspace_bytes(const tnc_plan_t* plan, int32_t n_residues);
  * TNC_PATH_TC_P8's packed fp16 operands and K-split partials); 0 if the options
  * are invalid. */
 size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts);
+/* Sliced contraction (bond slicing: fixing s variables of a formula splits its
+ * count into 2^s counts of smaller networks, each with at most the original
+ * ranks; the paper leaves memory as the bottleneck of its method, Sec. 4).
+ * plans[i] are the networks of the slices (same open variables); the result
+ * is the sum of their counts, exact: each slice's residues are added on the
+ * device modulo the primes, then one CRT.  `flags` certifies the sum (the sum
+ * of the slices' bounds).  dev_ws: tnc_workspace_bytes_sliced bytes, 256-byte
+ * aligned.  Synchronises `cuda_stream`. */
+size_t tnc_workspace_bytes_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts);
+int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts, void* dev_ws,
+                        size_t ws_bytes, void* cuda_stream, tnc_count* out);
 /* Measurement aid (calling thread only; off by default): with on != 0, every
  * later tnc_contract brackets each dense (tensor-core) step with CUDA events
  * on its stream, and tnc_last_dense_time returns the summed device time (ms)

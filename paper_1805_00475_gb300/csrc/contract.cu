@@ -299,10 +299,22 @@ extern "C" size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_con
   return seq_layout(plan, a.R, opts->path).total;
 }
 
-extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
-                            void* cuda_stream, tnc_count* out) {
-  clear_error();
-  if (!plan || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
+// Residues r of a sum of contractions: acc[e R + r] = (acc + src) mod p_r.
+__global__ void residue_add_kernel(uint32_t* __restrict__ acc, const uint32_t* __restrict__ src, uint64_t n, int R,
+                                   CrtConsts cc) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = cc.p[i % R];
+    const uint32_t s = acc[i] + src[i];  // both below p < 2^31
+    acc[i] = s >= p ? s - p : s;
+  }
+}
+
+// The contraction of one plan.  With sum_into == nullptr the count is
+// finished (CRT, copy to `out`); otherwise the residues [2^n_open][R] are
+// added into the device buffer sum_into and nothing else is returned.
+static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
+                         void* cuda_stream, tnc_count* out, uint32_t* sum_into) {
+  if (!plan || (!out && !sum_into)) return set_error(TNC_ERR_INVALID, "NULL argument");
   Arith a;
   int rc = make_arith(opts, a);
   if (rc) return rc;
@@ -311,6 +323,15 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   if (plan->tree.nodes.empty()) {  // empty network: the empty product, 1
     std::vector<uint32_t> res(a.R, 1u), limbs(a.crt.n_limbs, 0u);
     limbs[0] = 1;
+    if (sum_into) {
+      if (!dev_ws || ws_bytes < (size_t)a.R * 4) return set_error(TNC_ERR_BUFFER, "workspace too small");
+      cudaStream_t st0 = (cudaStream_t)cuda_stream;
+      CUDA_TRY(cudaMemcpyAsync(dev_ws, res.data(), a.R * sizeof(uint32_t), cudaMemcpyHostToDevice, st0));
+      residue_add_kernel<<<1, 64, 0, st0>>>(sum_into, (const uint32_t*)dev_ws, (uint64_t)a.R, a.R, a.crt);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaStreamSynchronize(st0));
+      return TNC_OK;
+    }
     return fill_count(out, 1, a, res.data(), limbs.data(), 0);
   }
   if (!dev_ws || ws_bytes < L.total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_workspace_bytes");
@@ -474,6 +495,17 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
     });
     if (rc) return rc;
   }
+  if (sum_into) {  // one term of a sum: add the residues, check the device status
+    const uint64_t n = L.n_out * (uint64_t)a.R;
+    residue_add_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 1024), 256, 0, st>>>(sum_into, results, n, a.R,
+                                                                                           a.crt);
+    CUDA_TRY(cudaGetLastError());
+    uint32_t h_err0 = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h_err0, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err0) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
+    return TNC_OK;
+  }
   uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((L.n_out + 127) / 128, 1024), 128, 0, st>>>(results, L.n_out, a.crt,
                                                                                                   limbs);
@@ -497,6 +529,68 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
     g_dense_launches++;
   }
   return fill_count(out, L.n_out, a, h_res.data(), h_limbs.data(), flags);
+}
+
+extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
+                            void* cuda_stream, tnc_count* out) {
+  clear_error();
+  return contract_core(plan, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
+}
+
+// Slices of one count: the sum of the plans' counts (each plan the network of
+// the formula with some variables fixed), exact as residues, one CRT at the end.
+static size_t sliced_head_bytes(uint64_t n_out, const Arith& a) {
+  return align_up(n_out * a.R * sizeof(uint32_t)) + align_up(n_out * a.crt.n_limbs * sizeof(uint32_t));
+}
+
+extern "C" size_t tnc_workspace_bytes_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts) {
+  clear_error();
+  Arith a;
+  if (!plans || n <= 0 || make_arith(opts, a)) return 0;
+  size_t body = 256;
+  for (int i = 0; i < n; i++) {
+    if (!plans[i]) return 0;
+    body = std::max(body, seq_layout(plans[i], a.R, opts->path).total);
+  }
+  return sliced_head_bytes(1ull << plans[0]->net.open_vars.size(), a) + body;
+}
+
+extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                                   void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* out) {
+  clear_error();
+  if (!plans || n <= 0 || !out || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
+  Arith a;
+  int rc = make_arith(opts, a);
+  if (rc) return rc;
+  const size_t n_open = plans[0] ? plans[0]->net.open_vars.size() : 0;
+  double bound = 0;  // log2 of the sum of the slices' certified bounds
+  for (int i = 0; i < n; i++) {
+    if (!plans[i]) return set_error(TNC_ERR_INVALID, "NULL plan");
+    if (plans[i]->net.open_vars.size() != n_open) return set_error(TNC_ERR_INVALID, "slices differ in open variables");
+    const double b = plans[i]->net.log2_bound;
+    bound = i == 0 ? b : std::max(bound, b) + std::log2(1.0 + std::exp2(-std::fabs(bound - b)));
+  }
+  const size_t need = tnc_workspace_bytes_sliced(plans, n, opts);
+  if (!dev_ws || ws_bytes < need) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_workspace_bytes_sliced");
+  if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const uint64_t n_out = 1ull << n_open;
+  char* ws = (char*)dev_ws;
+  uint32_t* acc = (uint32_t*)ws;
+  uint32_t* limbs = (uint32_t*)(ws + align_up(n_out * a.R * sizeof(uint32_t)));
+  const size_t head = sliced_head_bytes(n_out, a);
+  CUDA_TRY(cudaMemsetAsync(acc, 0, n_out * a.R * sizeof(uint32_t), st));
+  for (int i = 0; i < n; i++) {
+    rc = contract_core(plans[i], opts, ws + head, ws_bytes - head, cuda_stream, nullptr, acc);
+    if (rc) return rc;
+  }
+  tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((n_out + 127) / 128, 1024), 128, 0, st>>>(acc, n_out, a.crt, limbs);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<uint32_t> h_res(n_out * a.R), h_limbs(n_out * a.crt.n_limbs);
+  CUDA_TRY(cudaMemcpyAsync(h_res.data(), acc, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return fill_count(out, n_out, a, h_res.data(), h_limbs.data(), bound >= a.log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u);
 }
 
 // ======================================================================= batch

@@ -31,7 +31,7 @@ TNC_MAYBE_WRAPPED = 1
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -123,6 +123,8 @@ def lib():
             "tnc_set_step_timing": ([i32], None),
             "tnc_last_dense_time": ([ctypes.POINTER(ctypes.c_double), i32p], ctypes.c_int),
             "tnc_last_contract_time": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "tnc_workspace_bytes_sliced": ([vp, i32, vp], sz),
+            "tnc_contract_sliced": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
@@ -397,6 +399,22 @@ def last_contract_time() -> float:
     ms = ctypes.c_double()
     _check(lib().tnc_last_contract_time(ctypes.byref(ms)))
     return ms.value
+
+
+def contract_sliced(plans: Sequence[Plan], n_residues: int = 4, primes=None, workspace=None, stream=None,
+                    path: str = "int64") -> Count:
+    """tnc_contract_sliced: the sum of the plans' counts (the slices of one
+    formula), added as residues on the device, one CRT."""
+    o, pr = _opts(n_residues, primes, path)
+    arr = (ctypes.c_void_p * len(plans))(*[pp.h.value for pp in plans])
+    nb = int(lib().tnc_workspace_bytes_sliced(arr, len(plans), ctypes.byref(o)))
+    if nb == 0:
+        raise TncError(-1, lib().tnc_last_error().decode() or "invalid slices")
+    ws = _workspace(nb, workspace)
+    c, res, limbs = _count_buffers(1 << plans[0].n_open, n_residues)
+    _check(lib().tnc_contract_sliced(arr, len(plans), ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb,
+                                     _stream_ptr(stream), ctypes.byref(c)))
+    return _to_count(c, res, limbs, pr)
 
 
 def probe_modmac(iters: int = 4096, stream=None) -> float:
