@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch", default="", help="c2: fixed launch shape THREADS,SMEM_BYTES[,CTAS_PER_SM] instead of the autotuner")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing", "fig4c"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
@@ -412,6 +412,32 @@ def run_c5(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fig4c(args):
+    """Planner only (the exact cost before any contraction, Sec. 4): mean max
+    rank of the best heuristic plan for #Cubic-Vertex-Cover on random cubic
+    graphs and on random planar cubic graphs, n = 20..200 (the comparison of
+    the paper's Fig. 4c; its sizes, our own generators and planners)."""
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import tnc
+    seeds = args.formulas or 8
+    rows = []
+    t0 = time.perf_counter()
+    for n in range(20, 201, 20):
+        un = tnc.plan_many([I.cubic_vertex_cover(n, s) for s in range(seeds)], heuristic="best", rank_cap=64)
+        pl = tnc.plan_many([I.vertex_cover_formula(n, I.random_planar_cubic_graph(n, s)) for s in range(seeds)],
+                           heuristic="best", rank_cap=64)
+        rows.append({"n": n, "unrestricted_mean_max_rank": statistics.mean(p.stats.max_rank for p in un),
+                     "planar_mean_max_rank": statistics.mean(p.stats.max_rank for p in pl),
+                     "unrestricted_mean_log2_macs": statistics.mean(math.log2(p.stats.total_macs) for p in un),
+                     "planar_mean_log2_macs": statistics.mean(math.log2(p.stats.total_macs) for p in pl)})
+    line = {"metric": "mean max rank vs n (planner only)", "value": rows[-1]["unrestricted_mean_max_rank"] /
+            rows[-1]["planar_mean_max_rank"], "unit": "x (unrestricted / planar at n = 200)", "higher_is_better": True,
+            "data": "synthetic", "config": {"workload": "cubic_vertex_cover, random vs random planar cubic graphs",
+                                            "seeds_per_n": seeds, "planner": "best"},
+            "plan_s": time.perf_counter() - t0, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_slicing(args):
     """Bond slicing on the rank-29 networks of C4 (#Cubic-VC, n = 180, seeds 3
     and 15): each counted whole and as 2^s slices (s = 1..4) on the
@@ -716,6 +742,8 @@ def main():
         run_c4(args)
     elif args.config == "slicing":
         run_slicing(args)
+    elif args.config == "fig4c":
+        run_fig4c(args)
     elif args.config == "c3":
         run_c3(args)
     elif args.config == "c5":

@@ -169,6 +169,58 @@ def random_cubic_graph(n: int, seed: int, max_tries: int = 100000) -> List[Tuple
     raise RuntimeError("no simple connected cubic graph found")
 
 
+def random_planar_cubic_graph(n: int, seed: int, flips_per_edge: int = 20) -> List[Tuple[int, int]]:
+    """A seeded random simple connected planar cubic graph on n vertices (n
+    even, >= 4): the dual of a random triangulation of the sphere with n/2 + 2
+    vertices.  The triangulation starts as a bipyramid over a cycle and is
+    mixed by random edge flips (an edge ab between triangles abc and abd
+    becomes cd when c and d are not adjacent and a and b keep degree >= 3);
+    its triangles are the graph's vertices and two triangles sharing an edge
+    are adjacent.  Flips keep the triangulation simple, so the dual is simple
+    and 3-connected."""
+    if n < 4 or n % 2:
+        raise ValueError("a cubic graph needs an even n >= 4")
+    V = n // 2 + 2
+    g = SplitMix64(seed)
+    top, bottom, ring = V - 2, V - 1, V - 2
+    tris = []
+    for i in range(ring):
+        j = (i + 1) % ring
+        tris.append((top, i, j))
+        tris.append((bottom, j, i))
+    if ring == 2:  # V = 4: the tetrahedron
+        tris = [(0, 1, 2), (0, 3, 1), (1, 3, 2), (2, 3, 0)]
+    for _ in range(flips_per_edge * 3 * V):
+        # edge -> its two triangles
+        owner = {}
+        for ti, (a, b, c) in enumerate(tris):
+            for u, v in ((a, b), (b, c), (c, a)):
+                owner.setdefault((min(u, v), max(u, v)), []).append(ti)
+        edges = sorted(owner)
+        a, b = edges[g.below(len(edges))]
+        t1, t2 = owner[(a, b)]
+        c = [x for x in tris[t1] if x not in (a, b)][0]
+        d = [x for x in tris[t2] if x not in (a, b)][0]
+        deg = {}
+        for u, v in edges:
+            deg[u] = deg.get(u, 0) + 1
+            deg[v] = deg.get(v, 0) + 1
+        if c == d or (min(c, d), max(c, d)) in owner or deg[a] <= 3 or deg[b] <= 3:
+            continue
+        # keep the orientation: triangle t1 = (a, b, c) in some rotation
+        r = tris[t1]
+        k = r.index(a)
+        if r[(k + 1) % 3] != b:
+            a, b = b, a
+        tris[t1] = (a, d, c)
+        tris[t2] = (b, c, d)
+    owner = {}
+    for ti, (a, b, c) in enumerate(tris):
+        for u, v in ((a, b), (b, c), (c, a)):
+            owner.setdefault((min(u, v), max(u, v)), []).append(ti)
+    return sorted((min(t), max(t)) for t in owner.values())
+
+
 def cycle_graph(n: int) -> List[Tuple[int, int]]:
     return [(i, (i + 1) % n) for i in range(n)]
 

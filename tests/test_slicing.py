@@ -57,3 +57,23 @@ def test_slicing_lowers_the_rank_of_a_large_network():
     assert len(plans) == 8 and len(set(vs)) == 3
     assert max(p.stats.max_rank for p in plans) <= full.stats.max_rank - 2
     assert max(p.stats.arena_entries for p in plans) * 4 <= full.stats.arena_entries
+
+
+def test_random_planar_cubic_graphs():
+    """The planar generator: simple, cubic, connected, planar (networkx's
+    planarity test), seeded; and the planner finds far lower max ranks on
+    them than on unrestricted cubic graphs of the same size (the trend of the
+    paper's Fig. 4c)."""
+    nx = pytest.importorskip("networkx")
+    for n, seed in ((4, 0), (10, 1), (40, 2), (100, 3)):
+        e = I.random_planar_cubic_graph(n, seed)
+        assert e == I.random_planar_cubic_graph(n, seed)
+        g = nx.Graph(e)
+        assert len(e) == 3 * n // 2 and g.number_of_edges() == len(e) and all(u != v for u, v in e)
+        assert all(d == 3 for _, d in g.degree()) and nx.is_connected(g) and nx.check_planarity(g)[0]
+    n = 160
+    planar = [tnc.plan_formula(I.vertex_cover_formula(n, I.random_planar_cubic_graph(n, s)), heuristic="best",
+                               rank_cap=64).stats.max_rank for s in range(3)]
+    free = [tnc.plan_formula(I.cubic_vertex_cover(n, s), heuristic="best", rank_cap=64).stats.max_rank
+            for s in range(3)]
+    assert max(planar) + 8 <= min(free)
