@@ -46,15 +46,24 @@ namespace tnc_p8 {
 constexpr uint32_t kTileM = 128;
 constexpr uint32_t kStageK = 64;
 constexpr uint32_t kChunkK = 1024;
-constexpr uint32_t kStages = 4;
 constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
 constexpr uint32_t kEpiThreads = 256;
 constexpr uint32_t kMaxTN = 128;                    // columns per tile (TMEM: RG x TN <= 512)
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
-constexpr uint32_t kStageBytes = 32 * 1024;         // A + B (B up to 128 x 64 fp16)
 constexpr uint32_t kStagePitch = kTileM + 1;        // u32 words per staged column (+1: no bank conflicts)
-constexpr uint32_t kStagingBytes = kMaxTN * kStagePitch * 4;
-constexpr uint32_t kSmemBytes = kStages * kStageBytes + kStagingBytes + 1024;
+
+// Shared-memory plan of a tile width: stages of A (16 KiB) + B (TN x 64 fp16),
+// 1 KiB aligned for the 128-byte swizzle; as many stages (up to 8) as fit
+// next to the output staging in about 200 KiB (4 for TN = 128, 8 for narrow
+// tiles, whose steps stream a tall operand and need more bytes in flight).
+template <uint32_t TN>
+struct Cfg {
+  static constexpr uint32_t kStageBytes = (kABytes + TN * kStageK * 2 + 1023u) / 1024u * 1024u;
+  static constexpr uint32_t kStagingBytes = TN * kStagePitch * 4;
+  static constexpr uint32_t kFit = (200u * 1024u - kStagingBytes) / kStageBytes;
+  static constexpr uint32_t kStages = kFit > 8 ? 8 : kFit;
+  static constexpr uint32_t kSmemBytes = kStages * kStageBytes + kStagingBytes + 1024;
+};
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct P8Args {
@@ -315,6 +324,7 @@ template <uint32_t TN, uint32_t RG>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ P8Args g, uint32_t* err) {
+  constexpr uint32_t kStages = Cfg<TN>::kStages, kStageBytes = Cfg<TN>::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * RG + 1];
   __shared__ uint32_t tmem_base_s;
@@ -614,11 +624,11 @@ int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Ar
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tnc_p8::kSmemBytes);
+                                         (int)tnc_p8::Cfg<TN>::kSmemBytes);
     if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
     attr = true;
   }
-  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::kSmemBytes, st>>>(ma, mb, g, err);
+  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::Cfg<TN>::kSmemBytes, st>>>(ma, mb, g, err);
   return TNC_OK;
 }
 
