@@ -489,7 +489,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
         }
       }
       tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
-          arena, root_off, rm, results, a.R, groups.col[gi], mg);
+          arena, root_off, rm, results, a.R, groups.col[gi]);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });
@@ -1309,7 +1309,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
         tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
       }
       tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((n_out + 255) / 256, 1024), 256, 0, st>>>(
-          arena, root_off, rm, results, R, grp_col[gi], mg);
+          arena, root_off, rm, results, R, grp_col[gi]);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });

@@ -73,9 +73,9 @@ __device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uin
 
 // Sum over the 2^k shared-bond values of A*B for every residue of the group
 // (A, B point at the operands' first shared-bond entry; consecutive shared
-// values are 2^ka and 2^kb entries apart), in Montgomery form: products
-// (a R)(b R) are summed in 64 bits, every red_mask+1 of them the sum is
-// REDC-reduced to (sum a b) R mod p and added mod p to the total.
+// values are 2^ka and 2^kb entries apart).  A product of residues is below
+// (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64 bits:
+// reduce after every (red_mask+1)-th product and once at the end.
 template <int RG>
 __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, const uint32_t* A, const uint32_t* B,
                                          const ModGroup& mg, uint32_t (&out)[RG]) {
@@ -83,19 +83,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
   const uint32_t K = 1u << k;
   uint64_t acc[RG];
 #pragma unroll
-  for (int r = 0; r < RG; r++) {
-    acc[r] = 0;
-    out[r] = 0;
-  }
-  bool pending = false;
-  auto flush = [&]() {
-#pragma unroll
-    for (int r = 0; r < RG; r++) {
-      out[r] = add_mod(out[r], redc(acc[r], mg.p[r], mg.pinv[r]), mg.p[r]);
-      acc[r] = 0;
-    }
-    pending = false;
-  };
+  for (int r = 0; r < RG; r++) acc[r] = 0;
   uint32_t q = 0;
   for (; q + 4 <= K; q += 4) {
 #pragma unroll
@@ -105,20 +93,21 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
       load_entry<RG>(B + (uint64_t)(q + u) * sb, vb);
 #pragma unroll
       for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
-      if (u == 1 && mg.red_mask == 1) flush();
     }
-    pending = true;
-    if (((q + 4) & mg.red_mask) == 0) flush();
+    if (((q + 4) & mg.red_mask) == 0) {
+#pragma unroll
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+    }
   }
-  for (; q < K; q++) {  // K < 4 here: at most 2 products
+  for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
     uint32_t va[RG], vb[RG];
     load_entry<RG>(A + (uint64_t)q * sa, va);
     load_entry<RG>(B + (uint64_t)q * sb, vb);
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
-    pending = true;
   }
-  if (pending) flush();
+#pragma unroll
+  for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
 }
 
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
@@ -153,8 +142,7 @@ __global__ void __launch_bounds__(256) leaf_fill_kernel(const LeafDesc* __restri
     for (uint64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
       uint32_t v[RG];
 #pragma unroll
-      for (int r = 0; r < RG; r++)
-        v[r] = to_mont(leaf_value(ld.kind, ld.rank, (uint32_t)idx, tables, ld.table_off, mg.p[r]), mg, r);
+      for (int r = 0; r < RG; r++) v[r] = leaf_value(ld.kind, ld.rank, (uint32_t)idx, tables, ld.table_off, mg.p[r]);
       store_entry<RG>(dst + idx * RG, v);
     }
   }
@@ -225,9 +213,8 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
   const uint32_t* B = arena + (g->d.b_off + ib) * RG;
   const uint64_t per = (1ull << k) >> log_split;
   uint64_t acc[RG];
-  uint32_t tot[RG];
 #pragma unroll
-  for (int r = 0; r < RG; r++) acc[r] = tot[r] = 0;
+  for (int r = 0; r < RG; r++) acc[r] = 0;
   uint32_t cnt = 0;
   for (uint64_t q = j * per + threadIdx.x; q < (j + 1) * per; q += blockDim.x) {
     uint32_t va[RG], vb[RG];
@@ -235,17 +222,13 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
     load_entry<RG>(B + (q << kb) * RG, vb);
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
-    if ((++cnt & mg.red_mask) == 0) {  // Montgomery sums of red_mask+1 products
+    if ((++cnt & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) {
-        tot[r] = add_mod(tot[r], redc(acc[r], mg.p[r], mg.pinv[r]), mg.p[r]);
-        acc[r] = 0;
-      }
+      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
     }
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++)
-    red[threadIdx.x * RG + r] = add_mod(tot[r], redc(acc[r], mg.p[r], mg.pinv[r]), mg.p[r]);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -315,11 +298,10 @@ struct RootMap {
   int n_open;
 };
 
-// Root tensor -> result residues [entry][R] (canonical, out of Montgomery
-// form), entry index bit i = open var i.
+// Root tensor -> result residues [entry][R], entry index bit i = open var i.
 template <int RG>
 __global__ void extract_kernel(const uint32_t* __restrict__ arena, uint64_t root_off, RootMap rm,
-                               uint32_t* __restrict__ results, int R, int col, ModGroup mg) {
+                               uint32_t* __restrict__ results, int R, int col) {
   const uint32_t n_out = 1u << rm.n_open;
   for (uint32_t J = blockIdx.x * blockDim.x + threadIdx.x; J < n_out; J += gridDim.x * blockDim.x) {
     uint64_t a = 0;
@@ -327,8 +309,7 @@ __global__ void extract_kernel(const uint32_t* __restrict__ arena, uint64_t root
     for (int j = 0; j < 24; j++)
       if (j < rm.n_open) a |= (uint64_t)((J >> rm.perm[j]) & 1u) << j;
 #pragma unroll
-    for (int r = 0; r < RG; r++)  // leave Montgomery form: x R^{-1}
-      results[(uint64_t)J * R + col + r] = redc(arena[(root_off + a) * RG + r], mg.p[r], mg.pinv[r]);
+    for (int r = 0; r < RG; r++) results[(uint64_t)J * R + col + r] = arena[(root_off + a) * RG + r];
   }
 }
 
@@ -481,7 +462,7 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       for (uint32_t idx = 0; idx < n; idx++) {
         uint32_t v[RG];
 #pragma unroll
-        for (int r = 0; r < RG; r++) v[r] = to_mont(leaf_value(ld.kind, ld.rank, idx, a.tables, ld.table_off, mg.p[r]), mg, r);
+        for (int r = 0; r < RG; r++) v[r] = leaf_value(ld.kind, ld.rank, idx, a.tables, ld.table_off, mg.p[r]);
         store_entry<RG>(dst + (uint64_t)idx * RG, v);
       }
     }
@@ -541,9 +522,8 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
       uint32_t ad = 0;
       for (uint32_t j = 0; j < f.n_open; j++) ad |= ((J >> a.perms[f.perm_off + j]) & 1u) << j;
 #pragma unroll
-      for (int r = 0; r < RG; r++)  // out of Montgomery form
-        a.results[((uint64_t)f.res_off + J) * a.R + a.col + r] =
-            redc(arena[((uint64_t)f.root_off + ad) * RG + r], mg.p[r], mg.pinv[r]);
+      for (int r = 0; r < RG; r++)
+        a.results[((uint64_t)f.res_off + J) * a.R + a.col + r] = arena[((uint64_t)f.root_off + ad) * RG + r];
     }
     __syncthreads();
   }

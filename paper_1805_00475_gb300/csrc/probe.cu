@@ -24,26 +24,23 @@ __global__ void __launch_bounds__(256) modmac_probe_kernel(uint32_t seed, uint32
     h ^= h << 13;
     h ^= h >> 17;
     h ^= h << 5;
-    x[i] = h & 0x1FFFFFFFu;  // below 2^29: 4 products stay below p 2^32
+    x[i] = h & 0x3FFFFFFFu;  // below 2^30
   }
   uint64_t acc[4] = {0, 0, 0, 0};
-  uint32_t tot[4] = {0, 0, 0, 0};
   for (uint32_t it = 0; it < iters; it++) {
 #pragma unroll
     for (int u = 0; u < 4; u++) {
 #pragma unroll
       for (int r = 0; r < 4; r++) acc[r] += (uint64_t)x[(u + r) & 7] * x[(u + r + 3) & 7];
     }
-    // the step kernels' pattern: a Montgomery reduction per 4 products
+    if ((it & 3u) == 3u) {
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
-      tot[r] = tnc_dev::add_mod(tot[r], tnc_dev::redc(acc[r], mg.p[r], mg.pinv[r]), mg.p[r]);
-      acc[r] = 0;
+      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce(acc[r], mg.p[r], mg.mu[r]);
     }
 #pragma unroll
-    for (int i = 0; i < 8; i++) x[i] = (x[i] ^ (x[(i + 1) & 7] >> 3)) & 0x1FFFFFFFu;
+    for (int i = 0; i < 8; i++) x[i] = (x[i] ^ (x[(i + 1) & 7] >> 3)) & 0x3FFFFFFFu;
   }
-  const uint64_t s = (uint64_t)tot[0] + tot[1] + tot[2] + tot[3];
+  const uint64_t s = acc[0] + acc[1] + acc[2] + acc[3];
   if (s == never) atomicAdd(sink, 1ull);  // a runtime value no sum reaches: keeps the work observable
 }
 

@@ -56,7 +56,7 @@ struct TcStep {
   uint32_t fa, fb, k;            // M = 2^fa, N = 2^fb, K = 2^k
   uint32_t log_split;            // K split over 2^log_split CTAs per tile (partials summed after)
   uint64_t wm[32], wn[32];       // output address weight of row bit j / column bit j
-  uint32_t p, pinv;              // prime, -p^{-1} mod 2^32 (operands are in Montgomery form)
+  uint32_t p, red_pad;
   uint64_t mu;
   uint32_t w256[7];              // 256^s mod p (w256[5] = 2^40 mod p is used)
   uint32_t pad2;
@@ -352,11 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_step_kernel(const TcStep* __re
     const uint32_t w40 = g->w256[5];  // 2^40 mod p
 #pragma unroll
     for (int j = 0; j < 16; j++)
-      // sum of (a R)(b R): one REDC leaves (sum a b) R, the Montgomery form
-      res[j] = tnc_dev::redc(tnc_dev::mod_reduce(tnc_dev::mod_reduce(lo[j], p, mu) +
-                                                     (uint64_t)tnc_dev::mod_reduce(hi[j], p, mu) * w40,
-                                                 p, mu),
-                             p, g->pinv);
+      res[j] = tnc_dev::mod_reduce(tnc_dev::mod_reduce(lo[j], p, mu) +
+                                       (uint64_t)tnc_dev::mod_reduce(hi[j], p, mu) * w40,
+                                   p, mu);
   }
   if (ok) {
     // C[o(m, n)]: o = sum of the output weights of m's and n's bits
@@ -462,11 +460,6 @@ void tc_make_step(const StepDesc& d, uint32_t p, void* out) {
   }
   t.p = p;
   t.mu = ~0ull / p;
-  {
-    uint32_t inv = p;  // Newton: p^{-1} mod 2^32
-    for (int i = 0; i < 5; i++) inv *= 2u - p * inv;
-    t.pinv = 0u - inv;
-  }
   uint64_t w = 1;
   for (int s = 0; s < 7; s++) {
     t.w256[s] = (uint32_t)w;

@@ -71,7 +71,6 @@ struct P8Args {
   uint32_t n_items, tiles_m;      // work items (tiles x splits); row tiles
   uint32_t rg, pad;               // residues per entry (1, 2 or 4), computed together
   uint32_t p[4];
-  uint32_t rinv[4];         // 2^-32 mod p: operands are in Montgomery form, (a R)(b R) R^-1 = (a b) R
   float pf[4], invp[4];
   uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
   uint8_t ebit[16];         // the tile's row and column bits by output weight, lightest first
@@ -210,16 +209,6 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
   const float q = rintf(x * invp);
   return fmaf(-q, pf, x);
-}
-
-// (r s) mod p for r, s < p <= 251 (r s < 2^16, exact in fp32; the quotient
-// estimate is off by at most one).
-__device__ __forceinline__ uint32_t mulmod_small(uint32_t r, uint32_t s, uint32_t p, float invp) {
-  const int x = (int)(r * s);
-  int t = x - (int)__float2int_rz((float)x * invp) * (int)p;
-  if (t < 0) t += (int)p;
-  if (t >= (int)p) t -= (int)p;
-  return (uint32_t)t;
 }
 
 // The canonical residue in [0, p) of such a representative.
@@ -533,8 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                   for (uint32_t jj = 0; jj < 16; jj++)
                     stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * 4 + r] =
-                        (uint8_t)mulmod_small(canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]),
-                                              g.rinv[r], g.p[r], invp);
+                        (uint8_t)canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]);
               }
             }
             if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -724,9 +712,6 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
     g.p[i] = pp.p[i];
     g.pf[i] = (float)pp.p[i];
     g.invp[i] = 1.0f / (float)pp.p[i];
-    uint32_t ri = 1;  // 2^-32 mod p = (2^-1)^32 mod p, 2^-1 = (p + 1) / 2
-    for (int b = 0; b < 32; b++) ri = (uint32_t)((uint64_t)ri * ((pp.p[i] + 1) / 2) % pp.p[i]);
-    g.rinv[i] = ri;
   }
   // output address weights (the output bit j comes from one operand's free bit)
   int op[64] = {0}, dst[64] = {0};
