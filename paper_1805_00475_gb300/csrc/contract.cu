@@ -129,6 +129,12 @@ uint32_t result_flags(const tnc_plan_t* p, const Arith& a) {
   return p->net.log2_bound >= a.log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u;
 }
 
+// The word type of a residue in a pass (u32, or a byte on the 8-bit-prime path).
+template <typename T>
+struct WordTag {
+  using type = T;
+};
+
 template <typename F>
 int dispatch_rg(int rg, F&& f) {
   switch (rg) {
@@ -235,7 +241,7 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
     if (tc_eligible(d) && tc_split_log(d) > 0)
       part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
     if (path == TNC_PATH_TC_P8 && p8_eligible(d))
-      part_bytes = std::max<uint64_t>(part_bytes, p8_part_entries(d, rg_max) * sizeof(uint32_t));
+      part_bytes = std::max<uint64_t>(part_bytes, p8_part_bytes(d, rg_max));
   }
   uint64_t p8_bytes = 0;
   if (path == TNC_PATH_TC_P8)
@@ -250,7 +256,8 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
   s.off_p8 = o;
   o = align_up(o + p8_bytes);
   s.off_arena = o;
-  o = align_up(o + std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) * rg_max * sizeof(uint32_t));
+  const size_t word = path == TNC_PATH_TC_P8 ? 1 : sizeof(uint32_t);  // bytes per residue
+  o = align_up(o + std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) * rg_max * word);
   s.total = o;
   return s;
 }
@@ -427,7 +434,6 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   }
   const GridStep* d_steps = (const GridStep*)(ws + L.off_steps);
   const StepDesc* d_small = (const StepDesc*)(ws + L.off_small);
-  uint32_t* arena = (uint32_t*)(ws + L.off_arena);
   uint32_t* results = (uint32_t*)(ws + L.off_results);
   uint32_t* part = (uint32_t*)(ws + L.off_part);
   RootMap rm{};
@@ -439,17 +445,21 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     uint32_t gp[4];
     for (int r = 0; r < 4; r++) gp[r] = r < groups.rg[gi] ? a.primes[groups.col[gi] + r] : a.primes[groups.col[gi]];
     const ModGroup mg = tnc_dev::make_mod_group(gp);
-    rc = dispatch_rg(groups.rg[gi], [&](auto rgc) -> int {
+    // one pass over the residue group; the 8-bit-prime path stores a residue
+    // per byte
+    auto pass = [&](auto rgc, auto wtag) -> int {
       constexpr int RG = decltype(rgc)::value;
+      using W = typename decltype(wtag)::type;
+      W* arena = reinterpret_cast<W*>(ws + L.off_arena);
       const int nl = (int)leaves.size();
-      tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
+      tnc_dev::leaf_fill_kernel<RG, W><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
       for (size_t l = 0; l < small_lo.size(); l++) {
         const uint32_t n_small = small_hi[l] - small_lo[l];
         if (n_small) {
           const uint32_t w = small_work[l];
           const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, (uint64_t)sms * 8);
-          tnc_dev::level_kernel<RG><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
+          tnc_dev::level_kernel<RG, W><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
         }
         for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
           if (kind[i] == kSmall) continue;
@@ -463,11 +473,11 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
               CUDA_TRY(cudaEventRecord(ev[0], st));
             }
             if (p8) {
-              rc2 = p8_launch(lw.lvl_steps[i], a.primes.data() + groups.col[gi], RG, arena, ws + L.off_p8, part, d_err,
-                              sms, st);
+              rc2 = p8_launch(lw.lvl_steps[i], a.primes.data() + groups.col[gi], RG, reinterpret_cast<uint8_t*>(arena),
+                              ws + L.off_p8, reinterpret_cast<uint8_t*>(part), d_err, sms, st);
             } else {
               const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
-              rc2 = tc_launch(dstep, lw.lvl_steps[i], arena, part, d_err, st);
+              rc2 = tc_launch(dstep, lw.lvl_steps[i], reinterpret_cast<uint32_t*>(arena), part, d_err, st);
             }
             if (g_time_dense) {
               CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -478,20 +488,23 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
           } else if (kind[i] == kSplit) {
             const uint32_t ls = splitk_log(lw.lvl_steps[i]);
             const uint64_t nblk = 1ull << (lw.lvl_steps[i].c + ls);
-            tnc_dev::splitk_partial_kernel<RG><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls, mg);
-            tnc_dev::splitk_final_kernel<RG><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
+            tnc_dev::splitk_partial_kernel<RG, W><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls, mg);
+            tnc_dev::splitk_final_kernel<RG, W><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
                 d_steps + slot[i], arena, part, ls, mg);
           } else {
             int threads, blocks, sh;
             grid_shape(lw.lvl_steps[i].c, &threads, &blocks, &sh);
-            tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
+            tnc_dev::step_kernel<RG, W><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
           }
         }
       }
-      tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
+      tnc_dev::extract_kernel<RG, W><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
           arena, root_off, rm, results, a.R, groups.col[gi]);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
+    };
+    rc = dispatch_rg(groups.rg[gi], [&](auto rgc) -> int {
+      return p8 ? pass(rgc, WordTag<uint8_t>()) : pass(rgc, WordTag<uint32_t>());
     });
     if (rc) return rc;
   }

@@ -9,9 +9,22 @@
 
 namespace tnc_dev {
 
-template <int RG>
-__device__ __forceinline__ void load_entry(const uint32_t* src, uint32_t (&v)[RG]) {
-  if constexpr (RG == 4) {
+// An entry holds the RG residues of its group side by side, one word W per
+// residue: u32 words for primes below 2^31, bytes for the 8-bit primes of the
+// TNC_PATH_TC_P8 arithmetic (four residues in one 32-bit word).
+template <int RG, typename W = uint32_t>
+__device__ __forceinline__ void load_entry(const W* src, uint32_t (&v)[RG]) {
+  if constexpr (sizeof(W) == 1) {
+    if constexpr (RG == 4) {
+      const uint32_t t = *reinterpret_cast<const uint32_t*>(src);
+      v[0] = t & 0xFFu; v[1] = (t >> 8) & 0xFFu; v[2] = (t >> 16) & 0xFFu; v[3] = t >> 24;
+    } else if constexpr (RG == 2) {
+      const uint32_t t = *reinterpret_cast<const uint16_t*>(src);
+      v[0] = t & 0xFFu; v[1] = t >> 8;
+    } else {
+      v[0] = *src;
+    }
+  } else if constexpr (RG == 4) {
     const uint4 t = *reinterpret_cast<const uint4*>(src);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
   } else if constexpr (RG == 2) {
@@ -22,9 +35,18 @@ __device__ __forceinline__ void load_entry(const uint32_t* src, uint32_t (&v)[RG
   }
 }
 
-template <int RG>
-__device__ __forceinline__ void store_entry(uint32_t* dst, const uint32_t (&v)[RG]) {
-  if constexpr (RG == 4) {
+// (byte words: every residue is below 2^8)
+template <int RG, typename W = uint32_t>
+__device__ __forceinline__ void store_entry(W* dst, const uint32_t (&v)[RG]) {
+  if constexpr (sizeof(W) == 1) {
+    if constexpr (RG == 4) {
+      *reinterpret_cast<uint32_t*>(dst) = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+    } else if constexpr (RG == 2) {
+      *reinterpret_cast<uint16_t*>(dst) = (uint16_t)(v[0] | (v[1] << 8));
+    } else {
+      dst[0] = (W)v[0];
+    }
+  } else if constexpr (RG == 4) {
     *reinterpret_cast<uint4*>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
   } else if constexpr (RG == 2) {
     *reinterpret_cast<uint2*>(dst) = make_uint2(v[0], v[1]);
@@ -76,8 +98,8 @@ __device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uin
 // values are 2^ka and 2^kb entries apart).  A product of residues is below
 // (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64 bits:
 // reduce after every (red_mask+1)-th product and once at the end.
-template <int RG>
-__device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, const uint32_t* A, const uint32_t* B,
+template <int RG, typename W = uint32_t>
+__device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, const W* A, const W* B,
                                          const ModGroup& mg, uint32_t (&out)[RG]) {
   const uint64_t sa = (uint64_t)RG << ka, sb = (uint64_t)RG << kb;
   const uint32_t K = 1u << k;
@@ -89,8 +111,8 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       uint32_t va[RG], vb[RG];
-      load_entry<RG>(A + (uint64_t)(q + u) * sa, va);
-      load_entry<RG>(B + (uint64_t)(q + u) * sb, vb);
+      load_entry<RG, W>(A + (uint64_t)(q + u) * sa, va);
+      load_entry<RG, W>(B + (uint64_t)(q + u) * sb, vb);
 #pragma unroll
       for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     }
@@ -101,8 +123,8 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
   }
   for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
     uint32_t va[RG], vb[RG];
-    load_entry<RG>(A + (uint64_t)q * sa, va);
-    load_entry<RG>(B + (uint64_t)q * sb, vb);
+    load_entry<RG, W>(A + (uint64_t)q * sa, va);
+    load_entry<RG, W>(B + (uint64_t)q * sb, vb);
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
@@ -112,38 +134,37 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
 
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
 // multiplied as matrices): entry o of C from the operand entries ia, ib.
-template <int RG>
+template <int RG, typename W = uint32_t>
 __device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
-                                              uint64_t ib, const uint32_t* A0, const uint32_t* B0, uint32_t* C0,
-                                              const ModGroup& mg) {
+                                              uint64_t ib, const W* A0, const W* B0, W* C0, const ModGroup& mg) {
   uint32_t out[RG];
-  step_sum<RG>(k, ka, kb, A0 + ia * RG, B0 + ib * RG, mg, out);
-  store_entry<RG>(C0 + o * RG, out);
+  step_sum<RG, W>(k, ka, kb, A0 + ia * RG, B0 + ib * RG, mg, out);
+  store_entry<RG, W>(C0 + o * RG, out);
 }
 
-template <int RG>
-__device__ __forceinline__ void step_entry(const StepDesc& d, uint64_t o, const uint32_t* A0, const uint32_t* B0,
-                                           uint32_t* C0, const ModGroup& mg) {
+template <int RG, typename W = uint32_t>
+__device__ __forceinline__ void step_entry(const StepDesc& d, uint64_t o, const W* A0, const W* B0, W* C0,
+                                           const ModGroup& mg) {
   uint64_t ia, ib;
   map_addr(d, o, ia, ib);
-  step_entry_at<RG>(d.k, d.ka, d.kb, o, ia, ib, A0, B0, C0, mg);
+  step_entry_at<RG, W>(d.k, d.ka, d.kb, o, ia, ib, A0, B0, C0, mg);
 }
 
 // ------------------------------------------------------------------ kernels
 
-template <int RG>
+template <int RG, typename W = uint32_t>
 __global__ void __launch_bounds__(256) leaf_fill_kernel(const LeafDesc* __restrict__ leaves, int n_leaves,
                                                         const uint32_t* __restrict__ tables,
-                                                        uint32_t* __restrict__ arena, ModGroup mg) {
+                                                        W* __restrict__ arena, ModGroup mg) {
   for (int l = blockIdx.x; l < n_leaves; l += gridDim.x) {
     const LeafDesc ld = leaves[l];
     const uint64_t n = 1ull << ld.rank;
-    uint32_t* dst = arena + ld.off * RG;
+    W* dst = arena + ld.off * RG;
     for (uint64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
       uint32_t v[RG];
 #pragma unroll
       for (int r = 0; r < RG; r++) v[r] = leaf_value(ld.kind, ld.rank, (uint32_t)idx, tables, ld.table_off, mg.p[r]);
-      store_entry<RG>(dst + idx * RG, v);
+      store_entry<RG, W>(dst + idx * RG, v);
     }
   }
 }
@@ -162,14 +183,14 @@ struct GridStep {
   uint32_t pad[3];
 };
 
-template <int RG>
-__global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ g, uint32_t* __restrict__ arena,
+template <int RG, typename W = uint32_t>
+__global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ g, W* __restrict__ arena,
                                                    ModGroup mg) {
   const uint32_t c = g->d.c, k = g->d.k, ka = g->d.ka, kb = g->d.kb, s = g->s;
   const uint64_t n = 1ull << c;
-  const uint32_t* A0 = arena + g->d.a_off * RG;
-  const uint32_t* B0 = arena + g->d.b_off * RG;
-  uint32_t* C0 = arena + g->d.c_off * RG;
+  const W* A0 = arena + g->d.a_off * RG;
+  const W* B0 = arena + g->d.b_off * RG;
+  W* C0 = arena + g->d.c_off * RG;
   uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
   uint64_t ia = 0, ib = 0;
@@ -179,7 +200,7 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
       ib += g->wB[j];
     }
   for (;;) {
-    step_entry_at<RG>(k, ka, kb, o, ia, ib, A0, B0, C0, mg);
+    step_entry_at<RG, W>(k, ka, kb, o, ia, ib, A0, B0, C0, mg);
     const uint64_t u = o >> s;
     o += 1ull << s;
     if (o >= n) break;
@@ -194,8 +215,8 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
 // (o, part) sums A*B over its slice of the 2^k shared values, the block's
 // threads combine their residues with modular additions, and a second kernel
 // adds the parts of each output.  part[o * n_split + j] holds RG residues.
-template <int RG>
-__global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __restrict__ g, const uint32_t* arena,
+template <int RG, typename W = uint32_t>
+__global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __restrict__ g, const W* arena,
                                                              uint32_t* __restrict__ part, uint32_t log_split,
                                                              ModGroup mg) {
   __shared__ uint32_t red[256 * RG];
@@ -209,8 +230,8 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
       ia += g->wA[b];
       ib += g->wB[b];
     }
-  const uint32_t* A = arena + (g->d.a_off + ia) * RG;
-  const uint32_t* B = arena + (g->d.b_off + ib) * RG;
+  const W* A = arena + (g->d.a_off + ia) * RG;
+  const W* B = arena + (g->d.b_off + ib) * RG;
   const uint64_t per = (1ull << k) >> log_split;
   uint64_t acc[RG];
 #pragma unroll
@@ -218,8 +239,8 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
   uint32_t cnt = 0;
   for (uint64_t q = j * per + threadIdx.x; q < (j + 1) * per; q += blockDim.x) {
     uint32_t va[RG], vb[RG];
-    load_entry<RG>(A + (q << ka) * RG, va);
-    load_entry<RG>(B + (q << kb) * RG, vb);
+    load_entry<RG, W>(A + (q << ka) * RG, va);
+    load_entry<RG, W>(B + (q << kb) * RG, vb);
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     if ((++cnt & mg.red_mask) == 0) {
@@ -245,8 +266,8 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
 }
 
 // One block per output entry: its threads add the parts, then combine.
-template <int RG>
-__global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __restrict__ g, uint32_t* arena,
+template <int RG, typename W = uint32_t>
+__global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __restrict__ g, W* arena,
                                                            const uint32_t* __restrict__ part, uint32_t log_split,
                                                            ModGroup mg) {
   __shared__ uint32_t red[256 * RG];
@@ -272,15 +293,15 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
     }
     __syncthreads();
   }
-  if (threadIdx.x < RG) arena[(g->d.c_off + o) * RG + threadIdx.x] = red[threadIdx.x];
+  if (threadIdx.x < RG) arena[(g->d.c_off + o) * RG + threadIdx.x] = (W)red[threadIdx.x];
 }
 
 // All the small steps of one tree level in one launch: they are independent,
 // so their output entries form one index space (step i owns [work_lo,
 // work_lo + 2^c)); each thread finds its step by binary search.
-template <int RG>
+template <int RG, typename W = uint32_t>
 __global__ void __launch_bounds__(256) level_kernel(const StepDesc* __restrict__ steps, uint32_t n_steps,
-                                                    uint32_t total, uint32_t* arena, ModGroup mg) {
+                                                    uint32_t total, W* arena, ModGroup mg) {
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
     uint32_t lo = 0, hi = n_steps - 1;
     while (lo < hi) {
@@ -289,7 +310,7 @@ __global__ void __launch_bounds__(256) level_kernel(const StepDesc* __restrict__
       else hi = mid - 1;
     }
     const StepDesc& d = steps[lo];
-    step_entry<RG>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
+    step_entry<RG, W>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
   }
 }
 
@@ -299,8 +320,8 @@ struct RootMap {
 };
 
 // Root tensor -> result residues [entry][R], entry index bit i = open var i.
-template <int RG>
-__global__ void extract_kernel(const uint32_t* __restrict__ arena, uint64_t root_off, RootMap rm,
+template <int RG, typename W = uint32_t>
+__global__ void extract_kernel(const W* __restrict__ arena, uint64_t root_off, RootMap rm,
                                uint32_t* __restrict__ results, int R, int col) {
   const uint32_t n_out = 1u << rm.n_open;
   for (uint32_t J = blockIdx.x * blockDim.x + threadIdx.x; J < n_out; J += gridDim.x * blockDim.x) {

@@ -13,10 +13,11 @@
 // 8-bit limb: one fp16 MMA per residue instead of the 16 limb pairs of a
 // 30-bit residue (about 7.8 bits of the count per MMA against 1.9).
 //
-// Data path: a pack kernel turns each operand (u32 residues, the lowering's
-// column-major layout: row index low, shared index high; all residues of the
-// pass at once) into balanced fp16 matrices, one per residue, row-major with
-// the shared index contiguous.  TMA moves tiles of rows x 64 values (128-byte
+// Data path: tensors on this path hold one byte per residue (an entry is the
+// RG residues of its pass side by side: 4 bytes for RG = 4).  A pack kernel
+// turns each operand (the lowering's column-major layout: row index low,
+// shared index high; all residues of the pass at once) into balanced fp16
+// matrices, one per residue, row-major with the shared index contiguous.  TMA moves tiles of rows x 64 values (128-byte
 // lines) into shared memory with the 128-byte swizzle, the canonical K-major
 // SWIZZLE_128B layout of the MMA operand descriptors.
 // Persistent CTAs (one per SM) run three warp roles:
@@ -76,7 +77,7 @@ struct P8Args {
   uint8_t ebit[16];         // the tile's row and column bits by output weight, lightest first
                             // (column bit j: 0x80 | j; row bit j: j); bits 0..4 go to lanes
   uint32_t n_ebits, pad3;
-  uint32_t* out;            // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
+  uint8_t* out;             // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
 };
 
 // ---- PTX helpers -----------------------------------------------------------
@@ -222,7 +223,7 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 
 // ---- operand packing ------------------------------------------------------
 
-// X: the operand's u32 residues in [0, p_i), entry q * R + r at
+// X: the operand's residues in [0, p_i), one byte each, entry q * R + r at
 // X + (q * R + r) * RG (R = 2^f rows, K = 2^k shared values, RG residues per
 // entry); Y_i (i < RG, Y_i = Y + i * R * K): balanced fp16 residues mod p_i,
 // row-major, Y_i[r * Kp + q] with rows padded to Kp = max(K, 64) values by
@@ -234,7 +235,7 @@ struct PackPrimes {
 };
 
 template <int RG>
-__global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict__ X, __half* __restrict__ Y,
+__global__ void __launch_bounds__(256) p8_pack_kernel(const uint8_t* __restrict__ X, __half* __restrict__ Y,
                                                       uint32_t f, uint32_t k, uint32_t kp, PackPrimes pp) {
   // a row of the tile is 64 values + 2 of padding: 33 words, so the 32 lanes of
   // a warp (32 rows) hit 32 different banks in both phases
@@ -258,13 +259,13 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
             for (int i = 0; i < RG; i++) v[h][i] = 0;
             continue;
           }
-          const uint32_t* src = X + ((uint64_t)(q0 + 2 * qp + h) * R + r0 + rr) * RG;
+          const uint8_t* src = X + ((uint64_t)(q0 + 2 * qp + h) * R + r0 + rr) * RG;
           if constexpr (RG == 4) {
-            const uint4 w = *reinterpret_cast<const uint4*>(src);
-            v[h][0] = w.x; v[h][1] = w.y; v[h][2] = w.z; v[h][3] = w.w;
+            const uint32_t w = *reinterpret_cast<const uint32_t*>(src);
+            v[h][0] = w & 0xFFu; v[h][1] = (w >> 8) & 0xFFu; v[h][2] = (w >> 16) & 0xFFu; v[h][3] = w >> 24;
           } else if constexpr (RG == 2) {
-            const uint2 w = *reinterpret_cast<const uint2*>(src);
-            v[h][0] = w.x; v[h][1] = w.y;
+            const uint32_t w = *reinterpret_cast<const uint16_t*>(src);
+            v[h][0] = w & 0xFFu; v[h][1] = w >> 8;
           } else {
             v[h][0] = src[0];
           }
@@ -296,15 +297,15 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint32_t* __restrict
 }
 
 // Sum of the K-split partials: C[i] = sum_j part[j][i] mod p_(i mod rg) for
-// the n = 2^c * rg residues of the step's output.
-__global__ void p8_split_final_kernel(const uint32_t* __restrict__ part, uint32_t* __restrict__ C, uint32_t c,
+// the n = 2^c * rg residues (bytes) of the step's output.
+__global__ void p8_split_final_kernel(const uint8_t* __restrict__ part, uint8_t* __restrict__ C, uint32_t c,
                                       uint32_t log_split, uint32_t rg, uint4 primes) {
   const uint64_t n = (uint64_t)rg << c;
   const uint32_t pr[4] = {primes.x, primes.y, primes.z, primes.w};
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t s = 0;
     for (uint32_t j = 0; j < (1u << log_split); j++) s += part[(uint64_t)j * n + i];
-    C[i] = s % pr[i % rg];
+    C[i] = (uint8_t)(s % pr[i % rg]);
   }
 }
 
@@ -319,7 +320,7 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // chunk but the last; after the last it turns it into canonical residues,
 // staged in shared memory as one byte per residue of each entry, and frees the
 // accumulator at once, so the next item's MMAs start while the staged entries
-// are written out whole (RG u32 residues per entry, the pass's layout).
+// are written out whole (RG residue bytes per entry, the pass's layout).
 template <uint32_t TN, uint32_t RG>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -534,18 +535,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       epi_bar();  // every residue of the item is staged
       if (ok) {
-        uint32_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull);
+        uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull);
         for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
           const uint32_t hc = hi_tab[e >> 5];
           const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
           const uint32_t w = staging[cc * kStagePitch + rr];
-          uint32_t* dst = outp + (om_tab[rr] + on_tab[cc]) * RG;
+          uint8_t* dst = outp + (om_tab[rr] + on_tab[cc]) * RG;
           if constexpr (RG == 4) {
-            *reinterpret_cast<uint4*>(dst) = make_uint4(w & 0xFFu, (w >> 8) & 0xFFu, (w >> 16) & 0xFFu, w >> 24);
+            *reinterpret_cast<uint32_t*>(dst) = w;
           } else if constexpr (RG == 2) {
-            *reinterpret_cast<uint2*>(dst) = make_uint2(w & 0xFFu, (w >> 8) & 0xFFu);
+            *reinterpret_cast<uint16_t*>(dst) = (uint16_t)w;
           } else {
-            *dst = w & 0xFFu;
+            *dst = (uint8_t)w;
           }
         }
       }
@@ -665,12 +666,12 @@ uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
   return 2ull * (uint64_t)rg * ((1ull << (d.ka + kp)) + (1ull << (d.kb + kp)));
 }
 
-uint64_t p8_part_entries(const StepDesc& d, int rg) {
+uint64_t p8_part_bytes(const StepDesc& d, int rg) {
   const uint32_t ls = p8_split_log(d);
   return ls ? (uint64_t)rg << (d.c + ls) : 0;
 }
 
-int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, void* scratch, uint8_t* part,
               uint32_t* dev_err, int sms, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (rg != 1 && rg != 2 && rg != 4) return set_error(TNC_ERR_INVALID, "internal: residues per pass must be 1, 2 or 4");
@@ -687,7 +688,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* 
   auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
     const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.kp - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
-    const uint32_t* src = arena + off * rg;
+    const uint8_t* src = arena + off * rg;
     if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
     else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
     else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);

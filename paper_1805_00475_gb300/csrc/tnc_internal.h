@@ -131,11 +131,12 @@ bool tc_eligible(const StepDesc& d);
 bool p8_eligible(const StepDesc& d);
 uint32_t p8_split_log(const StepDesc& d);
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg);
-uint64_t p8_part_entries(const StepDesc& d, int rg);  // u32 words
+uint64_t p8_part_bytes(const StepDesc& d, int rg);
 // One dense step for all rg residues (primes[0..rg)) of a pass whose entries
-// hold rg residues: both operands packed once, then one GEMM launch that
-// computes every residue of each output tile and writes whole entries.
-int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint32_t* arena, void* scratch, uint32_t* part,
+// hold rg residues of one byte each: both operands packed once, then one GEMM
+// launch that computes every residue of each output tile and writes whole
+// entries.
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, void* scratch, uint8_t* part,
               uint32_t* dev_err, int sms, void* stream);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
