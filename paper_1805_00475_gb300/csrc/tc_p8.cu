@@ -224,72 +224,99 @@ __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
 // ---- operand packing ------------------------------------------------------
 
 // X: the operand's residues in [0, p_i), one byte each, entry q * R + r at
-// X + (q * R + r) * RG (R = 2^f rows, K = 2^k shared values, RG residues per
-// entry); Y_i (i < RG, Y_i = Y + i * R * K): balanced fp16 residues mod p_i,
-// row-major, Y_i[r * Kp + q] with rows padded to Kp = max(K, 64) values by
-// zeros.  A block transposes a tile of 32 rows x 64 shared
-// values through shared memory: reads of whole entries coalesced along r,
-// 16-byte writes coalesced along q.
+// X + (q * R + r) * RG (R = 2^f >= 16 rows, K = 2^k shared values, RG
+// residues per entry); Y_i (i < RG, Y_i = Y + i * R * Kp): balanced fp16
+// residues mod p_i, row-major, Y_i[r * Kp + q] with rows padded to
+// Kp = max(K, 64) values by zeros.  A block transposes tiles of 64 rows x 64
+// shared values through shared memory: a thread reads the entries of 4
+// consecutive rows at shared values q and q + 1 (4 RG bytes each, coalesced
+// along r) and builds, for each row and residue, the half2 (Y_i[r][q],
+// Y_i[r][q+1]); 16-byte writes are coalesced along q.
 struct PackPrimes {
   uint32_t p[4];
 };
 
+// half2 of the balanced residues (a, b) given as bytes ia of wa and ib of wb:
+// 0x64XX is the half 1024 + XX exactly, so one subtraction gives a, b as
+// halves, and v - p [v > (p-1)/2] is exact in fp16 (|v| <= 250).
+__device__ __forceinline__ uint32_t p8_half2(uint32_t wa, uint32_t ia, uint32_t wb, uint32_t ib, __half2 hp2,
+                                             __half2 np2) {
+  uint32_t t = __byte_perm(wa, wb, ia | ((4u + ib) << 8));
+  t = (t & 0x00FF00FFu) | 0x64006400u;  // byte 0 -> low half, byte 1 -> high half
+  __half2 h;
+  *reinterpret_cast<uint32_t*>(&h) = t;
+  h = __hsub2(h, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+  h = __hfma2(__hgt2(h, hp2), np2, h);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
 template <int RG>
 __global__ void __launch_bounds__(256) p8_pack_kernel(const uint8_t* __restrict__ X, __half* __restrict__ Y,
                                                       uint32_t f, uint32_t k, uint32_t kp, PackPrimes pp) {
-  // a row of the tile is 64 values + 2 of padding: 33 words, so the 32 lanes of
-  // a warp (32 rows) hit 32 different banks in both phases
-  __shared__ __align__(16) __half2 tile[RG][32][33];
-  // rows of Y hold Kp = 2^kp >= K values: shared values q >= K are zero
+  // [residue][row][pair of shared values] half2 words; a row is 32 words + 1
+  // of padding, so both phases are free of bank conflicts (phase 1: lanes =
+  // 8 row quads x 4 pairs; phase 2: lanes = 8 chunks x 4 rows)
+  __shared__ uint32_t tile[RG][64][33];
   const uint32_t R = 1u << f, K = 1u << k, Kp = 1u << kp;
-  const uint32_t tiles_r = (R + 31) / 32;
+  const uint32_t tiles_r = (R + 63) / 64;
   const uint64_t n_tiles = (uint64_t)tiles_r << (kp - 6);
-  const uint32_t t = threadIdx.x;
-  for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
-    const uint32_t r0 = (uint32_t)(b % tiles_r) * 32u, q0 = (uint32_t)(b / tiles_r) * 64u;
+  const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+  __half2 hp2[RG], np2[RG];
 #pragma unroll
-    for (int j = 0; j < 4; j++) {  // 1024 pairs (row, q..q+1) of the tile
-      const uint32_t pi = t + 256u * j, rr = pi & 31u, qp = pi >> 5;
-      if (r0 + rr < R) {
-        uint32_t v[2][RG];
+  for (int i = 0; i < RG; i++) {
+    hp2[i] = __float2half2_rn((float)((pp.p[i] - 1) / 2));
+    np2[i] = __float2half2_rn(-(float)pp.p[i]);
+  }
+  for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+    const uint32_t r0 = (uint32_t)(b % tiles_r) * 64u, q0 = (uint32_t)(b / tiles_r) * 64u;
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+      const uint32_t rq = (lane & 7u) + 8u * (warp & 1u);                // row quad 0..15
+      const uint32_t qp = (lane >> 3) + 4u * ((warp >> 1) + 4u * it);   // pair 0..31
+      const uint32_t r = r0 + 4u * rq, q = q0 + 2u * qp;
+      if (r < R) {  // R is a multiple of 16: a quad is wholly in or out
+        uint32_t w0[RG], w1[RG];  // 4 rows x RG bytes at q and at q + 1
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-          if (q0 + 2 * qp + h >= K) {
-#pragma unroll
-            for (int i = 0; i < RG; i++) v[h][i] = 0;
-            continue;
-          }
-          const uint8_t* src = X + ((uint64_t)(q0 + 2 * qp + h) * R + r0 + rr) * RG;
-          if constexpr (RG == 4) {
-            const uint32_t w = *reinterpret_cast<const uint32_t*>(src);
-            v[h][0] = w & 0xFFu; v[h][1] = (w >> 8) & 0xFFu; v[h][2] = (w >> 16) & 0xFFu; v[h][3] = w >> 24;
-          } else if constexpr (RG == 2) {
-            const uint32_t w = *reinterpret_cast<const uint16_t*>(src);
-            v[h][0] = w & 0xFFu; v[h][1] = w >> 8;
+          uint32_t* w = h ? w1 : w0;
+          if (q + h < K) {
+            const uint8_t* src = X + ((uint64_t)(q + h) * R + r) * RG;
+            if constexpr (RG == 4) {
+              const uint4 v = *reinterpret_cast<const uint4*>(src);
+              w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            } else if constexpr (RG == 2) {
+              const uint2 v = *reinterpret_cast<const uint2*>(src);
+              w[0] = v.x; w[1] = v.y;
+            } else {
+              w[0] = *reinterpret_cast<const uint32_t*>(src);
+            }
           } else {
-            v[h][0] = src[0];
+#pragma unroll
+            for (int i = 0; i < RG; i++) w[i] = 0;
           }
         }
 #pragma unroll
-        for (int i = 0; i < RG; i++) {
-          const int hp = (int)(pp.p[i] - 1) / 2, p = (int)pp.p[i];
-          const int x0 = (int)v[0][i], x1 = (int)v[1][i];
-          tile[i][rr][qp] = __halves2half2(__int2half_rn(x0 > hp ? x0 - p : x0), __int2half_rn(x1 > hp ? x1 - p : x1));
-        }
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+          for (int i = 0; i < RG; i++) {
+            const uint32_t idx = (uint32_t)(j * RG + i);  // byte of row j, residue i in the quad
+            tile[i][4u * rq + j][qp] = p8_half2(w0[idx >> 2], idx & 3u, w1[idx >> 2], idx & 3u, hp2[i], np2[i]);
+          }
       }
     }
     __syncthreads();
-    const uint32_t rr = t >> 3, c4 = (t & 7u) * 4u;  // 4 pairs = 8 values = 16 bytes of one row
-    if (r0 + rr < R) {
 #pragma unroll
-      for (int i = 0; i < RG; i++) {
-        const __half2* src = &tile[i][rr][c4];
+    for (int it = 0; it < 2 * RG; it++) {  // RG planes x 64 rows x 8 chunks of 16 bytes
+      const uint32_t id = t + 256u * it;
+      const uint32_t c = id & 7u, row = (id >> 3) & 63u, i = id >> 9;
+      if (r0 + row < R) {
+        const uint32_t* src = &tile[i][row][4u * c];
         uint4 w;
-        w.x = *reinterpret_cast<const uint32_t*>(src + 0);
-        w.y = *reinterpret_cast<const uint32_t*>(src + 1);
-        w.z = *reinterpret_cast<const uint32_t*>(src + 2);
-        w.w = *reinterpret_cast<const uint32_t*>(src + 3);
-        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * Kp + (uint64_t)(r0 + rr) * Kp + q0 + 2 * c4) = w;
+        w.x = src[0];
+        w.y = src[1];
+        w.z = src[2];
+        w.w = src[3];
+        *reinterpret_cast<uint4*>(Y + (uint64_t)i * R * Kp + (uint64_t)(r0 + row) * Kp + q0 + 8u * c) = w;
       }
     }
     __syncthreads();
@@ -686,7 +713,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
   const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
   auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
-    const uint64_t n = (uint64_t)((1u << f) + 31u) / 32u << (s.kp - 6);
+    const uint64_t n = (uint64_t)((1u << f) + 63u) / 64u << (s.kp - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
     const uint8_t* src = arena + off * rg;
     if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
