@@ -53,6 +53,8 @@ def parse():
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
+    ap.add_argument("--c4-compare", default="tc,int64",
+                    help="c4: arithmetic paths timed once beside the 8-bit-prime path ('' for none)")
     ap.add_argument("--train-formulas", type=int, default=20000, help="c5: generated training formulas")
     return ap.parse_args()
 
@@ -519,8 +521,11 @@ def run_c4(args):
         p8_primes.append(q)
         bits += math.log2(q)
     R8 = len(p8_primes)
-    ws = torch.empty(max(max(tnc.workspace_bytes(p, Rc) for p in plans),
-                         max(tnc.workspace_bytes(p, R8, "tc_p8") for p in plans)), dtype=torch.uint8, device=dev)
+    compare = [x for x in args.c4_compare.split(",") if x]
+    ws_bytes = max(tnc.workspace_bytes(p, R8, "tc_p8") for p in plans)
+    if compare:
+        ws_bytes = max(ws_bytes, max(tnc.workspace_bytes(p, Rc) for p in plans))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     macs = sum(p.stats.total_macs for p in plans)
     dense = sum(p.stats.dense_macs for p in plans)
@@ -558,9 +563,12 @@ def run_c4(args):
         dt, counts = one_pass("tc_p8", timed=True)
         times.append(dt)
     clk = clocks.stop()
-    ttc, counts_tc = one_pass("tc")
-    t64, counts64 = one_pass("int64")
-    assert counts == counts_tc == counts64, "the three arithmetic paths disagree"
+    others = {}
+    for path in compare:
+        others[path] = one_pass(path)
+        assert others[path][1] == counts, f"the {path} path disagrees with the 8-bit-prime path"
+    ttc = others["tc"][0] if "tc" in others else None
+    t64 = others["int64"][0] if "int64" in others else None
     s = sum(times) / len(times)
     dms = sum(dense_ms) / len(dense_ms)
     pk, pk_kind = peaks()
@@ -578,10 +586,12 @@ def run_c4(args):
                    "residues": R8, "primes": p8_primes, "log2_bound_max": round(bound, 2),
                    "l2": "inputs (up to 18 GB of tensors) far above L2"},
         "modular_macs_per_s": macs * R8 / s,
-        "tc_limb_path": {"residues": Rc, "ms_per_step": ttc * 1000.0, "speedup_tc_p8": ttc / s,
-                         "limb_tflops": dense * Rc * 16 * 2 / ttc / 1e12},
-        "int64_path": {"residues": Rc, "ms_per_step": t64 * 1000.0, "modular_macs_per_s": macs * Rc / t64,
-                       "speedup_tc_p8": t64 / s, "speedup_tc_limb": t64 / ttc},
+        "tc_limb_path": None if ttc is None else {
+            "residues": Rc, "ms_per_step": ttc * 1000.0, "speedup_tc_p8": ttc / s,
+            "limb_tflops": dense * Rc * 16 * 2 / ttc / 1e12},
+        "int64_path": None if t64 is None else {
+            "residues": Rc, "ms_per_step": t64 * 1000.0, "modular_macs_per_s": macs * Rc / t64,
+            "speedup_tc_p8": t64 / s, "speedup_tc_limb": t64 / ttc if ttc else None},
         "roofline": {"bound": "tensor", "achieved": p8_flops / dms / 1e9, "peak": pk["bf16_tflops"],
                      "unit": "TFLOP/s", "frac": p8_flops / dms / 1e9 / pk["bf16_tflops"], "traffic": None,
                      "peak_source": f"{pk_kind} bf16 burst (MEASURED_PEAKS.json); fp16 has the same dense rate",
@@ -594,6 +604,15 @@ def run_c4(args):
         "counts_log2": [round(math.log2(c), 2) for c in counts],
     }
     print(json.dumps(line), flush=True)
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# batch_kernel<4> launch on the default workload (8192 #Cubic-VC formulas on
+# 60 vertices, 4 residues, best plans, autotuned launch), the mean over the
+# five timed launches of one ncu capture: 194.8 MB read + 807.5 MB written.
+# The capture command is in profiles/batch_kernel_cubic_vc_n60_R4.md; set to
+# None when the kernel changes.
+C2_TRAFFIC_BYTES_PER_LAUNCH = 1.0023e9
 
 
 def run_tnc(args):
@@ -704,6 +723,7 @@ def run_tnc(args):
     # lanes issue a 32-bit IMAD per clock; a residue MAC (u32 x u32 + u64) is one
     # 64-bit-result IMAD, two issue slots; clock = max SM clock
     alu_peak = sms * 4 * 16 / 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    default_shape = args.batch == 8192 and args.planner == "best" and not args.launch
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -711,7 +731,10 @@ def run_tnc(args):
         "config": config(args, world),
         "modular_macs_per_s": macs * world / (ms / 1000.0),
         "roofline": {"bound": "alu", "achieved": achieved_macs / 1e12, "peak": alu_peak / 1e12,
-                     "unit": "Tmodmac/s", "frac": achieved_macs / alu_peak, "traffic": None,
+                     "unit": "Tmodmac/s", "frac": achieved_macs / alu_peak,
+                     "traffic": C2_TRAFFIC_BYTES_PER_LAUNCH if default_shape else None,
+                     "traffic_source": "ncu capture of this workload (profiles/batch_kernel_cubic_vc_n60_R4.md)"
+                     if default_shape else None,
                      "peak_source": "derived: SMs x 64 IMAD lanes / 2 slots per 64-bit MAC x max SM clock",
                      "measured_primitive_peak": probe / 1e12,
                      "kernel": "batch_kernel<4>", "algorithmic_macs_per_launch": macs,

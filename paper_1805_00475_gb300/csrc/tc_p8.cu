@@ -37,6 +37,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -49,22 +50,29 @@ constexpr uint32_t kStageK = 64;
 constexpr uint32_t kChunkK = 1024;
 constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
 constexpr uint32_t kEpiThreads = 256;
-constexpr uint32_t kMaxTN = 128;                    // columns per tile (TMEM: RG x TN <= 512)
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
-constexpr uint32_t kStagePitch = kTileM + 1;        // u32 words per staged column (+1: no bank conflicts)
+constexpr uint32_t kStagePitch = kTileM + 1;        // staged entries per column (+1: fewer bank conflicts)
 
-// Shared-memory plan of a tile width: stages of A (16 KiB) + B (TN x 64 fp16),
-// 1 KiB aligned for the 128-byte swizzle; as many stages (up to 8) as fit
-// next to the output staging in about 200 KiB (4 for TN = 128, 8 for narrow
-// tiles, whose steps stream a tall operand and need more bytes in flight).
-template <uint32_t TN>
+// Shared-memory plan of a tile width: NA = min(RG, 512 / TN) residues
+// accumulate together (NA TMEM accumulators of TN fp32 columns), in RG / NA
+// rounds per tile; stages of A (16 KiB) + B (TN x 64 fp16), 1 KiB aligned for
+// the 128-byte swizzle; the output staging holds NA bytes per entry of the
+// tile; as many stages (up to 8) as fit next to it in 220 KiB (3 for
+// TN = 256, 4 for TN = 128, more for narrow tiles, whose steps stream a tall
+// operand and need more bytes in flight).
+template <uint32_t TN, uint32_t RG>
 struct Cfg {
+  static constexpr uint32_t NA = RG * TN <= 512 ? RG : 512 / TN;
+  static constexpr uint32_t kRounds = RG / NA;
   static constexpr uint32_t kStageBytes = (kABytes + TN * kStageK * 2 + 1023u) / 1024u * 1024u;
-  static constexpr uint32_t kStagingBytes = TN * kStagePitch * 4;
-  static constexpr uint32_t kFit = (200u * 1024u - kStagingBytes) / kStageBytes;
+  static constexpr uint32_t kStagingBytes = (TN * kStagePitch * NA + 15u) / 16u * 16u;
+  static constexpr uint32_t kFit = (220u * 1024u - kStagingBytes) / kStageBytes;
   static constexpr uint32_t kStages = kFit > 8 ? 8 : kFit;
   static constexpr uint32_t kSmemBytes = kStages * kStageBytes + kStagingBytes + 1024;
 };
+// the NA-byte word of a staged entry
+template <uint32_t NA>
+using StageWord = std::conditional_t<NA == 4, uint32_t, std::conditional_t<NA == 2, uint16_t, uint8_t>>;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 struct P8Args {
@@ -341,36 +349,40 @@ __global__ void p8_split_final_kernel(const uint8_t* __restrict__ part, uint8_t*
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // One CTA per SM.  Work item = (output tile of 128 rows x TN columns, K
-// slice); for each item, each K chunk and each residue r < RG (in that order)
-// the MMA warp accumulates chunk c of C_r = A_r B_r^T into TMEM accumulator r
-// (columns r TN ..).  The epilogue reduces accumulator r in place after every
-// chunk but the last; after the last it turns it into canonical residues,
-// staged in shared memory as one byte per residue of each entry, and frees the
-// accumulator at once, so the next item's MMAs start while the staged entries
-// are written out whole (RG residue bytes per entry, the pass's layout).
+// slice); for each item, each round of NA residues, each K chunk and each
+// residue r of the round (in that order) the MMA warp accumulates chunk c of
+// C_r = A_r B_r^T into TMEM accumulator r mod NA (columns (r mod NA) TN ..).
+// The epilogue reduces an accumulator in place after every chunk but the
+// last; after the last it turns it into canonical residues, staged in shared
+// memory as one byte per residue of each entry, and frees the accumulator at
+// once, so the next MMAs start while the staged bytes are written out (NA
+// residue bytes of each entry per round, the pass's layout: RG bytes per
+// entry).
 template <uint32_t TN, uint32_t RG>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ P8Args g, uint32_t* err) {
-  constexpr uint32_t kStages = Cfg<TN>::kStages, kStageBytes = Cfg<TN>::kStageBytes;
+  using C = Cfg<TN, RG>;
+  constexpr uint32_t kStages = C::kStages, kStageBytes = C::kStageBytes, NA = C::NA, kRounds = C::kRounds;
+  using SW = StageWord<NA>;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * RG + 1];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * NA + 1];
   __shared__ uint32_t tmem_base_s;
   __shared__ uint64_t om_tab[kTileM], on_tab[TN];
   __shared__ uint16_t hi_tab[kTileM * TN / 32];  // row | col << 8 of the entry bits above the lane bits
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint32_t* staging = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes);  // [col][kStagePitch]
+  SW* staging = reinterpret_cast<SW*>(smem + kStages * kStageBytes);  // [col][kStagePitch] entries of NA bytes
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]);
-  const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + RG]);
-  const uint32_t drain = smem_u32(&bars[2 * kStages + 2 * RG]);
-  constexpr uint32_t kCols = RG * TN < 32 ? 32 : RG * TN;  // RG accumulators of TN columns
+  const uint32_t accf0 = smem_u32(&bars[2 * kStages]), acce0 = smem_u32(&bars[2 * kStages + NA]);
+  const uint32_t drain = smem_u32(&bars[2 * kStages + 2 * NA]);
+  constexpr uint32_t kCols = NA * TN < 32 ? 32 : NA * TN;  // NA accumulators of TN columns
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kStages; s++) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (uint32_t r = 0; r < RG; r++) {
+    for (uint32_t r = 0; r < NA; r++) {
       mbar_init(accf0 + 8 * r, 1);
       mbar_init(acce0 + 8 * r, kEpiThreads);
     }
@@ -404,8 +416,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t item = bid + t * G;
         const uint32_t split = item & split_mask, tile = item >> g.log_split;
         const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+        for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
-          for (uint32_t r = 0; r < RG && ok; r++) {
+          for (uint32_t ra = 0; ra < NA && ok; ra++) {
+            const uint32_t r = rd * NA + ra;
             const uint32_t q0 = split * Ks + c * chunk;
             for (uint32_t j = 0; j < spc; j++) {
               if (!mbar_try(empty0 + 8 * s, ph ^ 1u) && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
@@ -435,11 +449,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       constexpr uint32_t idesc = make_idesc(kTileM, TN);
-      uint32_t s = 0, ph = 0, na[RG];
-      for (uint32_t r = 0; r < RG; r++) na[r] = 0;
+      uint32_t s = 0, ph = 0, na[NA];
+      for (uint32_t r = 0; r < NA; r++) na[r] = 0;
       for (uint32_t t = 0; t < T && ok; t++)
+        for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
-          for (uint32_t r = 0; r < RG && ok; r++) {
+          for (uint32_t r = 0; r < NA && ok; r++) {
             if (!mbar_wait(acce0 + 8 * r, (na[r] & 1u) ^ 1u)) {  // the epilogue is done with accumulator r
               ok = false;
               break;
@@ -502,78 +517,75 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       hi_tab[h] = (uint16_t)(rw | cl << 8);
     }
-    uint32_t na[RG];
-    for (uint32_t r = 0; r < RG; r++) na[r] = 0;
+    uint32_t na[NA];
+    for (uint32_t r = 0; r < NA; r++) na[r] = 0;
     for (uint32_t t = 0; t < T; t++) {
       const uint32_t item = bid + t * G;
       const uint32_t split = item & split_mask, tile = item >> g.log_split;
       const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
-      for (uint32_t c = 0; c < n_chunks; c++) {
-        const bool last = c + 1 == n_chunks;
-        if (last) {
-          epi_bar();  // the previous item's entries are out: staging and tables are free
-          if (et < kTileM) {
-            uint64_t o = 0;
-            for (uint32_t j = 0; j < g.fa; j++)
-              if (((m0 + et) >> j) & 1u) o += g.wm[j];
-            om_tab[et] = o;
-          } else if (et - kTileM < TN) {
-            uint64_t o = 0;
-            for (uint32_t j = 0; j < g.fb; j++)
-              if (((n0 + et - kTileM) >> j) & 1u) o += g.wn[j];
-            on_tab[et - kTileM] = o;
-          }
-        }
-        for (uint32_t r = 0; r < RG; r++) {
-          if (ok && !mbar_wait(accf0 + 8 * r, na[r] & 1u)) ok = false;
-          tc_fence_after();
-          const uint32_t tb = tmem + ((quarter * 32u) << 16) + r * TN + cbeg;
-          if (ok && !idle) {
-            const float pf = g.pf[r], invp = g.invp[r];
-#pragma unroll 1
-            for (uint32_t col = 0; col < kHalf; col += kBatch) {
-              uint32_t v[kBatch / 16][16];
-#pragma unroll
-              for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-              if (!last) {  // reduce in place; the next chunk accumulates on top
-#pragma unroll
-                for (uint32_t b = 0; b < kBatch / 16; b++) {
-#pragma unroll
-                  for (int jj = 0; jj < 16; jj++)
-                    v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), pf, invp));
-                  tmem_st16(tb + col + 16 * b, v[b]);
+      for (uint32_t rd = 0; rd < kRounds; rd++) {
+        for (uint32_t c = 0; c < n_chunks; c++) {
+          const bool last = c + 1 == n_chunks;
+          if (last) {
+            epi_bar();  // the previous round's bytes are out: staging (and tables) are free
+            if (rd == 0)
+              for (uint32_t i = et; i < kTileM + TN; i += kEpiThreads) {
+                uint64_t o = 0;
+                if (i < kTileM) {
+                  for (uint32_t j = 0; j < g.fa; j++)
+                    if (((m0 + i) >> j) & 1u) o += g.wm[j];
+                  om_tab[i] = o;
+                } else {
+                  for (uint32_t j = 0; j < g.fb; j++)
+                    if (((n0 + i - kTileM) >> j) & 1u) o += g.wn[j];
+                  on_tab[i - kTileM] = o;
                 }
-              } else {  // canonical residue, one byte per residue of the staged entry
-#pragma unroll
-                for (uint32_t b = 0; b < kBatch / 16; b++)
-#pragma unroll
-                  for (uint32_t jj = 0; jj < 16; jj++)
-                    stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * 4 + r] =
-                        (uint8_t)canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]);
               }
-            }
-            if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           }
-          tc_fence_before();
-          mbar_arrive(acce0 + 8 * r);  // accumulator r is free (its values are in registers or staged)
-          na[r]++;
+          for (uint32_t ra = 0; ra < NA; ra++) {
+            const uint32_t r = rd * NA + ra;
+            if (ok && !mbar_wait(accf0 + 8 * ra, na[ra] & 1u)) ok = false;
+            tc_fence_after();
+            const uint32_t tb = tmem + ((quarter * 32u) << 16) + ra * TN + cbeg;
+            if (ok && !idle) {
+              const float pf = g.pf[r], invp = g.invp[r];
+#pragma unroll 1
+              for (uint32_t col = 0; col < kHalf; col += kBatch) {
+                uint32_t v[kBatch / 16][16];
+#pragma unroll
+                for (uint32_t b = 0; b < kBatch / 16; b++) tmem_ld16(tb + col + 16 * b, v[b]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!last) {  // reduce in place; the next chunk accumulates on top
+#pragma unroll
+                  for (uint32_t b = 0; b < kBatch / 16; b++) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; jj++)
+                      v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), pf, invp));
+                    tmem_st16(tb + col + 16 * b, v[b]);
+                  }
+                } else {  // canonical residue, one byte per residue of the round in the staged entry
+#pragma unroll
+                  for (uint32_t b = 0; b < kBatch / 16; b++)
+#pragma unroll
+                    for (uint32_t jj = 0; jj < 16; jj++)
+                      stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * NA + ra] =
+                          (uint8_t)canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]);
+                }
+              }
+              if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * ra);  // the accumulator is free (its values are in registers or staged)
+            na[ra]++;
+          }
         }
-      }
-      epi_bar();  // every residue of the item is staged
-      if (ok) {
-        uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull);
-        for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
-          const uint32_t hc = hi_tab[e >> 5];
-          const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
-          const uint32_t w = staging[cc * kStagePitch + rr];
-          uint8_t* dst = outp + (om_tab[rr] + on_tab[cc]) * RG;
-          if constexpr (RG == 4) {
-            *reinterpret_cast<uint32_t*>(dst) = w;
-          } else if constexpr (RG == 2) {
-            *reinterpret_cast<uint16_t*>(dst) = (uint16_t)w;
-          } else {
-            *dst = (uint8_t)w;
+        epi_bar();  // every residue of the round is staged
+        if (ok) {
+          uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA;
+          for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
+            const uint32_t hc = hi_tab[e >> 5];
+            const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
+            *reinterpret_cast<SW*>(outp + (om_tab[rr] + on_tab[cc]) * RG) = staging[cc * kStagePitch + rr];
           }
         }
       }
@@ -634,6 +646,8 @@ struct Shape {
   uint64_t tiles;
 };
 
+constexpr uint64_t kP8WideTiles = 456;
+
 Shape shape_of(const StepDesc& d) {
   Shape s;
   s.swap = !(d.ka >= 7 && d.kb >= 4);
@@ -641,8 +655,13 @@ Shape shape_of(const StepDesc& d) {
   s.fb = s.swap ? d.ka : d.kb;
   s.k = d.k;
   s.kp = std::max<uint32_t>(d.k, 6);
-  s.tn = std::min<uint32_t>(1u << s.fb, tnc_p8::kMaxTN);
-  s.tiles = ((1ull << s.fa) / tnc_p8::kTileM) * ((1ull << s.fb) / s.tn);
+  // 256 columns per tile (two residues at a time in TMEM, a quarter fewer
+  // operand bytes per product than 128) where that still leaves at least three
+  // tiles per SM; otherwise at most 128
+  const uint64_t tiles_m = (1ull << s.fa) / tnc_p8::kTileM;
+  s.tn = std::min<uint32_t>(1u << s.fb, 128);
+  if (s.fb >= 8 && tiles_m * ((1ull << s.fb) / 256) >= kP8WideTiles) s.tn = 256;
+  s.tiles = tiles_m * ((1ull << s.fb) / s.tn);
   return s;
 }
 
@@ -652,11 +671,11 @@ int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Ar
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tnc_p8::Cfg<TN>::kSmemBytes);
+                                         (int)tnc_p8::Cfg<TN, RG>::kSmemBytes);
     if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
     attr = true;
   }
-  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::Cfg<TN>::kSmemBytes, st>>>(ma, mb, g, err);
+  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::Cfg<TN, RG>::kSmemBytes, st>>>(ma, mb, g, err);
   return TNC_OK;
 }
 
@@ -667,7 +686,8 @@ int launch_gemm_rg(uint32_t tn, const CUtensorMap& ma, const CUtensorMap& mb, co
     case 16: return launch_gemm<16, RG>(ma, mb, g, grid, err, st);
     case 32: return launch_gemm<32, RG>(ma, mb, g, grid, err, st);
     case 64: return launch_gemm<64, RG>(ma, mb, g, grid, err, st);
-    default: return launch_gemm<128, RG>(ma, mb, g, grid, err, st);
+    case 128: return launch_gemm<128, RG>(ma, mb, g, grid, err, st);
+    default: return launch_gemm<256, RG>(ma, mb, g, grid, err, st);
   }
 }
 

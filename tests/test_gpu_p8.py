@@ -29,6 +29,8 @@ def _p8_shape(fa, fb, k):
     swap = not (fa >= 7 and fb >= 4)
     r, c = (fb, fa) if swap else (fa, fb)
     tn = min(1 << c, 128)
+    if c >= 8 and (1 << r) // 128 * ((1 << c) // 256) >= 456:  # 256-wide tiles, two residues per round
+        tn = 256
     tiles = (1 << r) // 128 * ((1 << c) // tn)
     ls = 0
     while (tiles << ls) < 160 and k - ls - 1 >= 10 and (1 << (fa + fb + ls + 1)) <= (1 << 26):
@@ -98,6 +100,21 @@ def test_p8_many_chunks_match_int64():
     b = tnc.contract(p, n_residues=26, path="tc_p8")
     assert a.flags == 0 and b.flags == 0
     assert a.counts == b.counts
+
+
+def test_p8_wide_tiles_match_int64():
+    """Steps with at least 456 tiles of 128 x 256 run 256-wide tiles: two
+    residues per round in TMEM, each round writing its two bytes of every
+    entry.  Counts equal the int64 path's (disjoint primes, both CRTs)."""
+    f = I.cubic_vertex_cover(180, 1)
+    p = tnc.plan_formula(f, heuristic="best", rank_cap=30)
+    wide = [sh for sh in (_p8_shape(*s) for s in _step_shapes(f, p)) if sh and sh[1] == 256]
+    assert wide
+    a = tnc.contract(p, n_residues=7, path="int64")
+    for R in (26, 21):  # 4-residue passes and a last pass of 2 residues; then of 1 residue
+        b = tnc.contract(p, n_residues=R, path="tc_p8")
+        assert a.flags == 0 and b.flags == 0
+        assert a.counts == b.counts
 
 
 def test_p8_one_in_three_with_open_bonds():
