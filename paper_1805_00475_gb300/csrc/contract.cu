@@ -1,5 +1,6 @@
 // C ABI, device half: single-formula contraction (one launch per step) and the
 // persistent, graph-captured batch.
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -165,14 +166,16 @@ void grid_shape(int c, int* threads, int* blocks, int* s) {
 }
 
 // Split-K for steps with at most 2^12 outputs and at least 2^9 shared values:
-// returns log2 of the number of K slices (0 = no split).  Each slice keeps at
-// least 256 shared values; outputs x slices stays at most 2^20.
+// returns log2 of the number of K slices (0 = no split).  A block sums one
+// slice of one output: slices keep at least 256 shared values (one per
+// thread), the grid aims at 2^10 blocks (about 7 per SM; a final dot product
+// of two rank-22 tensors then sums 16 values per thread instead of one) and
+// keeps at least two slices; outputs x slices stays at most 2^13.
 constexpr uint64_t kSplitPartEntries = 1ull << 20;
 uint32_t splitk_log(const StepDesc& d) {
   if (d.c > 12 || d.k < 9) return 0;
-  uint32_t ls = d.k - 8;
-  while (ls > 0 && (1ull << (d.c + ls)) > kSplitPartEntries) ls--;
-  return ls;
+  const uint32_t ls = d.c < 9 ? 10u - d.c : 1u;
+  return std::min<uint32_t>(ls, d.k - 8u);
 }
 
 GridStep make_grid_step(const StepDesc& d) {
@@ -447,9 +450,10 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     const ModGroup mg = tnc_dev::make_mod_group(gp);
     // one pass over the residue group; the 8-bit-prime path stores a residue
     // per byte
-    auto pass = [&](auto rgc, auto wtag) -> int {
+    auto pass = [&](auto rgc, auto wtag, auto n30tag) -> int {
       constexpr int RG = decltype(rgc)::value;
       using W = typename decltype(wtag)::type;
+      constexpr bool N30 = decltype(n30tag)::value;
       W* arena = reinterpret_cast<W*>(ws + L.off_arena);
       const int nl = (int)leaves.size();
       tnc_dev::leaf_fill_kernel<RG, W><<<std::min(nl, sms * 8), 64, 0, st>>>(
@@ -459,7 +463,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
         if (n_small) {
           const uint32_t w = small_work[l];
           const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, (uint64_t)sms * 8);
-          tnc_dev::level_kernel<RG, W><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
+          tnc_dev::level_kernel<RG, W, N30><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
         }
         for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
           if (kind[i] == kSmall) continue;
@@ -488,13 +492,14 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
           } else if (kind[i] == kSplit) {
             const uint32_t ls = splitk_log(lw.lvl_steps[i]);
             const uint64_t nblk = 1ull << (lw.lvl_steps[i].c + ls);
-            tnc_dev::splitk_partial_kernel<RG, W><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls, mg);
-            tnc_dev::splitk_final_kernel<RG, W><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
+            tnc_dev::splitk_partial_kernel<RG, W, N30><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls,
+                                                                                       mg);
+            tnc_dev::splitk_final_kernel<RG, W, N30><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
                 d_steps + slot[i], arena, part, ls, mg);
           } else {
             int threads, blocks, sh;
             grid_shape(lw.lvl_steps[i].c, &threads, &blocks, &sh);
-            tnc_dev::step_kernel<RG, W><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
+            tnc_dev::step_kernel<RG, W, N30><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
           }
         }
       }
@@ -504,7 +509,9 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
       return TNC_OK;
     };
     rc = dispatch_rg(groups.rg[gi], [&](auto rgc) -> int {
-      return p8 ? pass(rgc, WordTag<uint8_t>()) : pass(rgc, WordTag<uint32_t>());
+      if (p8) return pass(rgc, WordTag<uint8_t>(), std::false_type());
+      return mg.near30 ? pass(rgc, WordTag<uint32_t>(), std::true_type())
+                       : pass(rgc, WordTag<uint32_t>(), std::false_type());
     });
     if (rc) return rc;
   }
@@ -647,13 +654,13 @@ namespace {
 
 constexpr size_t kSmemMax = 227 * 1024;
 
-// CTAs of batch_kernel<RG> per SM for (threads, dynamic shared memory),
+// CTAs of batch_kernel<RG, N30> per SM for (threads, dynamic shared memory),
 // capped at `cap` (0: no cap).  The L1 / shared-memory split is then set to
 // the smallest shared-memory share that holds those CTAs, so that the rest of
 // the SM's 256 KiB serves as L1 for the formulas' global arenas.
-template <int RG>
+template <int RG, bool N30>
 int occupancy(int threads, size_t smem, int cap, int* blocks) {
-  auto k = tnc_dev::batch_kernel<RG>;
+  auto k = tnc_dev::batch_kernel<RG, N30>;
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int occ = 0;
@@ -680,8 +687,10 @@ int batch_configure(tnc_batch_t* b, int threads, size_t smem, int cap) {
   std::vector<int> grid;
   for (size_t gi = 0; gi < b->a.groups.rg.size(); gi++) {
     int occ = 0;
+    const bool n30 = b->a.group((int)gi).near30 != 0;
     int rc = dispatch_rg(b->a.groups.rg[gi], [&](auto rgc) -> int {
-      return occupancy<decltype(rgc)::value>(threads, b->max_blob + smem, cap, &occ);
+      return n30 ? occupancy<decltype(rgc)::value, true>(threads, b->max_blob + smem, cap, &occ)
+                 : occupancy<decltype(rgc)::value, false>(threads, b->max_blob + smem, cap, &occ);
     });
     if (rc) return rc;
     if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
@@ -928,7 +937,8 @@ int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
     const int threads = b->threads;
     int rc = dispatch_rg(rg, [&](auto rgc) -> int {
       constexpr int RG = decltype(rgc)::value;
-      tnc_dev::batch_kernel<RG><<<grid, threads, smem, st>>>(args, mg);
+      if (mg.near30) tnc_dev::batch_kernel<RG, true><<<grid, threads, smem, st>>>(args, mg);
+      else tnc_dev::batch_kernel<RG, false><<<grid, threads, smem, st>>>(args, mg);
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });

@@ -98,11 +98,43 @@ __device__ __forceinline__ uint32_t leaf_value(uint32_t kind, uint32_t rank, uin
 // values are 2^ka and 2^kb entries apart).  A product of residues is below
 // (p-1)^2, so red_mask+1 of them plus a reduced partial sum fit in 64 bits:
 // reduce after every (red_mask+1)-th product and once at the end.
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, const W* A, const W* B,
                                          const ModGroup& mg, uint32_t (&out)[RG]) {
   const uint64_t sa = (uint64_t)RG << ka, sb = (uint64_t)RG << kb;
   const uint32_t K = 1u << k;
+  if constexpr (sizeof(W) == 1) {
+    // byte residues (primes <= 251): a product is below 2^16, so red_mask + 1
+    // <= 16 of them plus a reduced sum stay below 2^32 -- 32-bit multiply-adds
+    uint32_t acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; r++) acc[r] = 0;
+    uint32_t q = 0;
+    for (; q + 4 <= K; q += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        uint32_t va[RG], vb[RG];
+        load_entry<RG, W>(A + (uint64_t)(q + u) * sa, va);
+        load_entry<RG, W>(B + (uint64_t)(q + u) * sb, vb);
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] += va[r] * vb[r];
+      }
+      if (((q + 4) & mg.red_mask) == 0) {
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] = mod_reduce32(acc[r], mg.p[r], (uint32_t)(mg.mu[r] >> 32));
+      }
+    }
+    for (; q < K; q++) {
+      uint32_t va[RG], vb[RG];
+      load_entry<RG, W>(A + (uint64_t)q * sa, va);
+      load_entry<RG, W>(B + (uint64_t)q * sb, vb);
+#pragma unroll
+      for (int r = 0; r < RG; r++) acc[r] += va[r] * vb[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RG; r++) out[r] = mod_reduce32(acc[r], mg.p[r], (uint32_t)(mg.mu[r] >> 32));
+    return;
+  }
   uint64_t acc[RG];
 #pragma unroll
   for (int r = 0; r < RG; r++) acc[r] = 0;
@@ -118,7 +150,7 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     }
     if (((q + 4) & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < RG; r++) acc[r] = reduce64<N30>(acc[r], mg, r);
     }
   }
   for (; q < K; q++) {  // K < 4 here: at most 3 products on a reduced sum
@@ -129,25 +161,25 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) out[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) out[r] = reduce64<N30>(acc[r], mg, r);
 }
 
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
 // multiplied as matrices): entry o of C from the operand entries ia, ib.
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __device__ __forceinline__ void step_entry_at(uint32_t k, uint32_t ka, uint32_t kb, uint64_t o, uint64_t ia,
                                               uint64_t ib, const W* A0, const W* B0, W* C0, const ModGroup& mg) {
   uint32_t out[RG];
-  step_sum<RG, W>(k, ka, kb, A0 + ia * RG, B0 + ib * RG, mg, out);
+  step_sum<RG, W, N30>(k, ka, kb, A0 + ia * RG, B0 + ib * RG, mg, out);
   store_entry<RG, W>(C0 + o * RG, out);
 }
 
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __device__ __forceinline__ void step_entry(const StepDesc& d, uint64_t o, const W* A0, const W* B0, W* C0,
                                            const ModGroup& mg) {
   uint64_t ia, ib;
   map_addr(d, o, ia, ib);
-  step_entry_at<RG, W>(d.k, d.ka, d.kb, o, ia, ib, A0, B0, C0, mg);
+  step_entry_at<RG, W, N30>(d.k, d.ka, d.kb, o, ia, ib, A0, B0, C0, mg);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -183,7 +215,7 @@ struct GridStep {
   uint32_t pad[3];
 };
 
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ g, W* __restrict__ arena,
                                                    ModGroup mg) {
   const uint32_t c = g->d.c, k = g->d.k, ka = g->d.ka, kb = g->d.kb, s = g->s;
@@ -200,7 +232,7 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
       ib += g->wB[j];
     }
   for (;;) {
-    step_entry_at<RG, W>(k, ka, kb, o, ia, ib, A0, B0, C0, mg);
+    step_entry_at<RG, W, N30>(k, ka, kb, o, ia, ib, A0, B0, C0, mg);
     const uint64_t u = o >> s;
     o += 1ull << s;
     if (o >= n) break;
@@ -215,7 +247,7 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
 // (o, part) sums A*B over its slice of the 2^k shared values, the block's
 // threads combine their residues with modular additions, and a second kernel
 // adds the parts of each output.  part[o * n_split + j] holds RG residues.
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __restrict__ g, const W* arena,
                                                              uint32_t* __restrict__ part, uint32_t log_split,
                                                              ModGroup mg) {
@@ -245,11 +277,11 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
     if ((++cnt & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < RG; r++) acc[r] = reduce64<N30>(acc[r], mg, r);
     }
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = reduce64<N30>(acc[r], mg, r);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -266,7 +298,7 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
 }
 
 // One block per output entry: its threads add the parts, then combine.
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __restrict__ g, W* arena,
                                                            const uint32_t* __restrict__ part, uint32_t log_split,
                                                            ModGroup mg) {
@@ -280,7 +312,7 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
     for (int r = 0; r < RG; r++) s[r] += part[((o << log_split) + j) * RG + r];  // < 2^31 each, < 2^20 of them
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = mod_reduce(s[r], mg.p[r], mg.mu[r]);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = reduce64<N30>(s[r], mg, r);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
@@ -299,7 +331,7 @@ __global__ void __launch_bounds__(256) splitk_final_kernel(const GridStep* __res
 // All the small steps of one tree level in one launch: they are independent,
 // so their output entries form one index space (step i owns [work_lo,
 // work_lo + 2^c)); each thread finds its step by binary search.
-template <int RG, typename W = uint32_t>
+template <int RG, typename W = uint32_t, bool N30 = false>
 __global__ void __launch_bounds__(256) level_kernel(const StepDesc* __restrict__ steps, uint32_t n_steps,
                                                     uint32_t total, W* arena, ModGroup mg) {
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
@@ -310,7 +342,7 @@ __global__ void __launch_bounds__(256) level_kernel(const StepDesc* __restrict__
       else hi = mid - 1;
     }
     const StepDesc& d = steps[lo];
-    step_entry<RG, W>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
+    step_entry<RG, W, N30>(d, w - d.work_lo, arena + d.a_off * RG, arena + d.b_off * RG, arena + d.c_off * RG, mg);
   }
 }
 
@@ -461,7 +493,7 @@ __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, i
 // barrier per level.  Descriptors are read from shared memory; the tensors
 // live in shared memory when the formula's arena fits, else in its own region
 // of global memory.
-template <int RG>
+template <int RG, bool N30 = false>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
@@ -517,7 +549,7 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
           const uint16_t* runs = runs_all + d.run0;
           const uint32_t ia = map_runs(o, runs, d.nra) + (slice << d.ka);
           const uint32_t ib = map_runs(o, runs + d.nra, d.nrb) + (slice << d.kb);
-          step_sum<RG>(d.k - sh, d.ka + sh, d.kb + sh, arena + ((uint64_t)d.a_off + ia) * RG,
+          step_sum<RG, uint32_t, N30>(d.k - sh, d.ka + sh, d.kb + sh, arena + ((uint64_t)d.a_off + ia) * RG,
                        arena + ((uint64_t)d.b_off + ib) * RG, mg, out);
         } else {
 #pragma unroll

@@ -1,6 +1,7 @@
 // Microbenchmark of the modular multiply-accumulate primitive used by every
 // step kernel: four residues per thread, u32 x u32 products accumulated in 64
-// bits, Barrett reduction after every 16th product (primes below 2^30).  Operands live in
+// bits, reduced after every 16th product as the step kernels do for the
+// default primes (just below 2^30: mod_reduce_near30).  Operands live in
 // registers and are scrambled every iteration (xor-shift) so that no product
 // is loop-invariant.  It gives a measured ceiling for steps bound by the
 // integer pipes, next to the ceiling derived from unit counts and clocks.
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) modmac_probe_kernel(uint32_t seed, uint32
     }
     if ((it & 3u) == 3u) {
 #pragma unroll
-      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::mod_reduce(acc[r], mg.p[r], mg.mu[r]);
+      for (int r = 0; r < 4; r++) acc[r] = tnc_dev::reduce64<true>(acc[r], mg, r);
     }
 #pragma unroll
     for (int i = 0; i < 8; i++) x[i] = (x[i] ^ (x[(i + 1) & 7] >> 3)) & 0x3FFFFFFFu;
