@@ -142,3 +142,40 @@ def test_gpu_training_lowers_loss_and_learned_plans_count_the_same():
         # the kept plan is never worse than the heuristic one (the fallback judges)
         assert (p.stats.max_rank, p.stats.total_macs) <= (h.stats.max_rank, h.stats.total_macs)
         assert tnc.contract(p, n_residues=2).counts == oracle.count(f)
+
+
+@pytest.mark.gpu
+def test_trained_scorer_gains_over_tensor_greedy():
+    """What the network adds to the method without it: the learned planner
+    is greedy merging ordered by the scorer instead of by tensor-greedy's
+    rule (smallest result rank, then fewest MACs).  After training on the
+    method's own cost labels for 600 generated monotone 1-in-3 formulas (n
+    40..100), the learned plans of 48 held-out formulas (n = 100, m = 62) need
+    fewer MACs than tensor-greedy's in geometric mean and on most formulas,
+    and count the same (residues of the learned plans = those of the
+    tensor-greedy plans)."""
+    import math
+    import torch
+    rng = np.random.default_rng(11)
+    train = []
+    for s in range(600):
+        n = int(rng.integers(40, 101))
+        train.append(I.one_in_three(n, int(round(n * rng.uniform(0.5, 0.8))), 50_000 + s))
+    X, T = tnc.learned_dataset(train, states=2, cands=tnc.LEARNED_CANDIDATES, seed=5)
+    perm = np.random.default_rng(0).permutation(len(T))
+    dp = torch.tensor(tnc.mlp_init(3), device="cuda")
+    tnc.mlp_train(dp, torch.tensor(X[perm], device="cuda"), torch.tensor(T[perm], device="cuda"),
+                  epochs=20, batch=1024, lr=2e-3)
+    pb = torch.empty(tnc.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    tnc.mlp_to_bf16(dp, pb)
+    evals = [I.one_in_three(100, 62, 90_000 + s) for s in range(48)]
+    plans, chose, lmacs = tnc.plan_learned_many(evals, pb, fallback="greedy")
+    greedy = [tnc.plan_formula(f, heuristic="greedy") for f in evals]
+    gl = [math.log2(g.stats.total_macs) for g in greedy]
+    ll = [math.log2(m) for m in lmacs]
+    assert sum(ll) < sum(gl)  # geometric mean
+    assert sum(l < g for l, g in zip(ll, gl)) > len(evals) // 2
+    for p, g in list(zip(plans, greedy))[:8]:
+        a = tnc.contract(p, n_residues=2)
+        b = tnc.contract(g, n_residues=2)
+        assert a.counts == b.counts and (a.residues == b.residues).all()
