@@ -169,13 +169,17 @@ void grid_shape(int c, int* threads, int* blocks, int* s) {
 // returns log2 of the number of K slices (0 = no split).  A block sums one
 // slice of one output: slices keep at least 256 shared values (one per
 // thread), the grid aims at 2^10 blocks (about 7 per SM; a final dot product
-// of two rank-22 tensors then sums 16 values per thread instead of one) and
-// keeps at least two slices; outputs x slices stays at most 2^13.
+// of two rank-22 tensors then sums 16 values per thread instead of one), a
+// thread sums at most 64 values when K allows, and there are at least two
+// slices; outputs x slices stays at most 2^20.
 constexpr uint64_t kSplitPartEntries = 1ull << 20;
 uint32_t splitk_log(const StepDesc& d) {
   if (d.c > 12 || d.k < 9) return 0;
-  const uint32_t ls = d.c < 9 ? 10u - d.c : 1u;
-  return std::min<uint32_t>(ls, d.k - 8u);
+  uint32_t ls = d.c < 9 ? 10u - d.c : 1u;
+  if (d.k > 14 && d.k - 14 > ls) ls = d.k - 14;
+  ls = std::min<uint32_t>(ls, d.k - 8u);
+  while (ls > 1 && d.c + ls > 20) ls--;
+  return ls;
 }
 
 GridStep make_grid_step(const StepDesc& d) {
@@ -661,7 +665,19 @@ constexpr size_t kSmemMax = 227 * 1024;
 template <int RG, bool N30>
 int occupancy(int threads, size_t smem, int cap, int* blocks) {
   auto k = tnc_dev::batch_kernel<RG, N30>;
-  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
+  // the limit is a property of the kernel, shared by every batch in the
+  // process: set it to the device's maximum, not to this batch's need (a batch
+  // configured later with smaller descriptors would otherwise make an earlier
+  // batch's launches fail)
+  int optin = 0, dev0 = 0;
+  cudaFuncAttributes fa{};
+  CUDA_TRY(cudaGetDevice(&dev0));
+  CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0));
+  CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // the opt-in limit covers static + dynamic
+  if (smem > (size_t)std::max(dyn_max, 0))
+    return set_error(TNC_ERR_TOO_LARGE, "batch kernel needs more shared memory than a CTA has");
+  CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   int occ = 0;
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem));

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "modarith.cuh"
 #include "step_desc.h"
@@ -164,6 +165,17 @@ __device__ __forceinline__ void step_sum(uint32_t k, uint32_t ka, uint32_t kb, c
   for (int r = 0; r < RG; r++) out[r] = reduce64<N30>(acc[r], mg, r);
 }
 
+// A partial sum reduced mod p_r: 64-bit sums by reduce64, 32-bit sums (byte
+// residues) by a 32-bit Barrett step.
+template <bool N30>
+__device__ __forceinline__ uint32_t reduce_acc(uint64_t x, const ModGroup& mg, int r) {
+  return reduce64<N30>(x, mg, r);
+}
+template <bool N30>
+__device__ __forceinline__ uint32_t reduce_acc(uint32_t x, const ModGroup& mg, int r) {
+  return mod_reduce32(x, mg.p[r], (uint32_t)(mg.mu[r] >> 32));
+}
+
 // One output entry of a pairwise step (Sec. 2.1: the permuted operands
 // multiplied as matrices): entry o of C from the operand entries ia, ib.
 template <int RG, typename W = uint32_t, bool N30 = false>
@@ -265,7 +277,9 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
   const W* A = arena + (g->d.a_off + ia) * RG;
   const W* B = arena + (g->d.b_off + ib) * RG;
   const uint64_t per = (1ull << k) >> log_split;
-  uint64_t acc[RG];
+  // byte residues: products below 2^16, sums of 16 of them in 32 bits
+  using Acc = std::conditional_t<sizeof(W) == 1, uint32_t, uint64_t>;
+  Acc acc[RG];
 #pragma unroll
   for (int r = 0; r < RG; r++) acc[r] = 0;
   uint32_t cnt = 0;
@@ -274,14 +288,14 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
     load_entry<RG, W>(A + (q << ka) * RG, va);
     load_entry<RG, W>(B + (q << kb) * RG, vb);
 #pragma unroll
-    for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+    for (int r = 0; r < RG; r++) acc[r] += (Acc)va[r] * vb[r];
     if ((++cnt & mg.red_mask) == 0) {
 #pragma unroll
-      for (int r = 0; r < RG; r++) acc[r] = reduce64<N30>(acc[r], mg, r);
+      for (int r = 0; r < RG; r++) acc[r] = reduce_acc<N30>(acc[r], mg, r);
     }
   }
 #pragma unroll
-  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = reduce64<N30>(acc[r], mg, r);
+  for (int r = 0; r < RG; r++) red[threadIdx.x * RG + r] = reduce_acc<N30>(acc[r], mg, r);
   __syncthreads();
   for (uint32_t h = blockDim.x >> 1; h > 0; h >>= 1) {
     if (threadIdx.x < h) {

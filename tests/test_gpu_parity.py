@@ -159,3 +159,21 @@ def test_prism_180_vertices_closed_form():
     f = I.independent_set_formula(2 * n, I.prism_graph(n))
     r = tnc.contract(tnc.plan_formula(f, heuristic="bisect"), n_residues=8)
     assert r.counts == [want] and r.flags == 0
+
+
+def test_batches_with_different_descriptor_sizes_coexist():
+    """The batch kernel's shared-memory limit is per kernel, not per batch: a
+    batch with large descriptors still launches after a batch with small
+    descriptors was created (and configured) after it."""
+    import torch
+    big_f = [I.cubic_vertex_cover(70, s) for s in range(6)]
+    small_f = [I.one_in_three(12, 6, s) for s in range(6)]
+    big = tnc.Batch([tnc.plan_formula(f, heuristic="best") for f in big_f], n_residues=4)
+    small = tnc.Batch([tnc.plan_formula(f, heuristic="best") for f in small_f], n_residues=4)
+    stream = torch.cuda.Stream()
+    for b, fs in ((big, big_f), (small, small_f), (big, big_f)):
+        ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device="cuda")
+        b.upload(ws, stream)
+        b.launch(ws, stream)
+        for r, f in zip(b.download(ws, stream), fs):
+            _check(r, oracle.count(f), 4)
