@@ -177,3 +177,35 @@ def test_batches_with_different_descriptor_sizes_coexist():
         b.launch(ws, stream)
         for r, f in zip(b.download(ws, stream), fs):
             _check(r, oracle.count(f), 4)
+
+
+# caller-supplied primes: near 2^31 (a reduction every 4 products), below
+# 2^30 - 2^10 (the Barrett reduction for every group), and groups mixing
+# them with primes just below 2^30 (whose groups otherwise take the two-fold
+# reduction)
+USER_PRIMES = {
+    "near_2_31": [2147483647, 2147483629, 2147483587, 2147483579],
+    "mid": [1073740793, 1073740783, 1073740781, 537919441],
+    "mixed_group": [1073741789, 2147483647, 1073741783, 1073740793, 2147483629],
+    "groups_of_both": [1073741789, 1073741783, 1073741741, 1073741723, 2147483647, 1073740793],
+}
+
+
+@pytest.mark.parametrize("which", sorted(USER_PRIMES))
+def test_user_primes_int64_and_batch(which):
+    import torch
+    primes = USER_PRIMES[which]
+    forms = [I.cubic_vertex_cover(70, s) for s in range(3)] + [I.one_in_three(30, 19, 7), I.worked_example()]
+    plans = [tnc.plan_formula(f, heuristic="best") for f in forms]
+    exact = [oracle.count(f) for f in forms]
+    for p, z in zip(plans, exact):
+        r = tnc.contract(p, n_residues=len(primes), primes=primes)
+        assert r.primes == primes
+        _check(r, z, len(primes))
+    b = tnc.Batch(plans, n_residues=len(primes), primes=primes)
+    ws = torch.empty(b.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    b.upload(ws, stream)
+    b.launch(ws, stream)
+    for r, z in zip(b.download(ws, stream), exact):
+        _check(r, z, len(primes))
