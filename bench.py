@@ -48,9 +48,9 @@ def parse():
     ap.add_argument("--planner", default="best")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=2,
-                    help="c2 e2e: formulas split into this many batches on their own streams, so that one "
-                         "batch's upload overlaps another's kernel")
+    ap.add_argument("--e2e-split", default="0.35,0.65",
+                    help="c2 e2e: shares of the formulas in consecutive batches on their own streams, so "
+                         "that one batch's upload overlaps the previous batch's kernel")
     ap.add_argument("--launch", default="", help="c2: fixed launch shape THREADS,SMEM_BYTES[,CTAS_PER_SM] instead of the autotuner")
     ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing", "fig4c"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
@@ -698,8 +698,13 @@ def run_tnc(args):
     e2e = None
     if not args.no_e2e:
         e2e_steps = max(3, min(args.steps, 10))
-        nch = max(1, min(args.e2e_chunks, len(plans)))
-        cuts = [len(plans) * c // nch for c in range(nch + 1)]
+        shares = [float(x) for x in args.e2e_split.split(",") if x]
+        acc, cuts = 0.0, [0]
+        for x in shares:
+            acc += x
+            cuts.append(min(len(plans), int(round(len(plans) * acc / sum(shares)))))
+        cuts = sorted(set(cuts))
+        nch = len(cuts) - 1
         chunks = []
         for c in range(nch):
             b = tnc.Batch(plans[cuts[c]:cuts[c + 1]], n_residues=R)
