@@ -56,6 +56,8 @@ def parse():
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
+    ap.add_argument("--c3-workers", type=int, default=4,
+                    help="c3: host threads contracting the heavy formulas, each with its own stream and workspace")
     ap.add_argument("--c4-compare", default="tc,int64",
                     help="c4: arithmetic paths timed once beside the 8-bit-prime path ('' for none)")
     ap.add_argument("--train-formulas", type=int, default=20000, help="c5: generated training formulas")
@@ -236,7 +238,7 @@ def run_c3(args):
     from paper_1805_00475_gb300 import tnc
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    Rc, R8, n_total, workers = 2, 8, args.formulas or 4096, 4
+    Rc, R8, n_total, workers = 2, 8, args.formulas or 4096, args.c3_workers
     light_macs, rank_max = 2.0 ** 24, 28
     forms = I.batch_one_in_three(n_total, 2026)
     t = time.perf_counter()
