@@ -614,10 +614,10 @@ def run_c4(args):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # batch_kernel<4> launch on the default workload (8192 #Cubic-VC formulas on
 # 60 vertices, 4 residues, best plans, autotuned launch), the mean over the
-# five timed launches of one ncu capture: 195.0 MB read + 806.8 MB written.
+# five timed launches of one ncu capture: 187.1 MB read + 457.0 MB written.
 # The capture command is in profiles/batch_kernel_cubic_vc_n60_R4.md; set to
 # None when the kernel changes.
-C2_TRAFFIC_BYTES_PER_LAUNCH = 1.0018e9
+C2_TRAFFIC_BYTES_PER_LAUNCH = 0.6441e9
 
 
 def run_tnc(args):

@@ -638,7 +638,8 @@ struct tnc_batch_s {
   std::vector<uint64_t> res_off;
   uint64_t max_arena = 0;    // entries
   uint64_t max_blob = 0;     // bytes of the largest descriptor blob
-  uint64_t garena_entries = 0;
+  uint64_t slot_entries = 0;  // global arena slot of one CTA (entries)
+  uint32_t slots = 0;         // CTAs any launch shape can have
   // launch configuration (autotuned)
   int threads = 128;
   int cta_cap = 0;           // CTAs per SM cap (0: as many as fit)
@@ -710,7 +711,7 @@ int batch_configure(tnc_batch_t* b, int threads, size_t smem, int cap) {
     });
     if (rc) return rc;
     if (occ <= 0) return set_error(TNC_ERR_TOO_LARGE, "batch kernel does not fit on an SM");
-    grid.push_back(std::max(1, std::min<int>(sms * occ, (int)b->n_forms)));
+    grid.push_back(std::max(1, std::min<int>(std::min<int>(sms * occ, (int)b->n_forms), (int)b->slots)));
   }
   b->threads = threads;
   b->smem_bytes = smem;
@@ -741,7 +742,7 @@ int batch_pack(tnc_batch_t* b) {
   std::vector<uint32_t> tables;
   std::vector<uint8_t> perms;
   b->res_off.assign(n, 0);
-  uint64_t out = 0, gbase = 0;
+  uint64_t out = 0;
   b->max_arena = 8;
   b->max_blob = 16;
   for (uint32_t i = 0; i < n; i++) {
@@ -863,8 +864,7 @@ int batch_pack(tnc_batch_t* b) {
     f.perm_off = (uint32_t)perms.size();
     f.root_off = (uint32_t)(lw.lvl_steps.empty() ? lw.lvl_leaf_off[p->tree.root] : lw.lvl_root_off);
     f.arena = (uint32_t)lw.lvl_arena_entries;
-    f.gbase = gbase;
-    gbase += (lw.lvl_arena_entries + 7) / 8 * 8;
+
     b->res_off[i] = out;
     out += f.n_out;
     const uint32_t toff = (uint32_t)tables.size();
@@ -883,7 +883,9 @@ int batch_pack(tnc_batch_t* b) {
   }
   if (blobs.size() / 16 >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "batch descriptors above 64 GiB");
   b->total_out = out;
-  b->garena_entries = gbase;
+  // one global arena slot per CTA: at most 32 CTAs per SM in any launch shape
+  b->slot_entries = (b->max_arena + 7) / 8 * 8;
+  b->slots = (uint32_t)std::min<uint64_t>(n, (uint64_t)sm_count() * 32u);
   // largest formulas first (longest-processing-time order)
   std::vector<uint32_t> order(n);
   for (uint32_t i = 0; i < n; i++) order[i] = i;
@@ -907,7 +909,7 @@ int batch_pack(tnc_batch_t* b) {
   b->desc_bytes = o - b->off_forms;
   sect(b->off_results, out * b->a.R * sizeof(uint32_t));
   sect(b->off_limbs, out * b->a.crt.n_limbs * sizeof(uint32_t));
-  sect(b->off_arena, (size_t)gbase * rg_max * sizeof(uint32_t));
+  sect(b->off_arena, (size_t)b->slots * b->slot_entries * rg_max * sizeof(uint32_t));
   b->total = o;
   CUDA_TRY(cudaMallocHost((void**)&b->staging, std::max<size_t>(b->desc_bytes, 1)));
   std::memset(b->staging, 0, b->desc_bytes);
@@ -943,6 +945,7 @@ int batch_enqueue(tnc_batch_t* b, void* dev_ws, cudaStream_t st) {
     args.queue = (uint32_t*)(ws + b->off_queue) + gi;
     args.results = (uint32_t*)(ws + b->off_results);
     args.garena = (uint32_t*)(ws + b->off_arena);
+    args.slot_entries = b->slot_entries;
     args.blob_cap = (uint32_t)b->max_blob;
     args.smem_cap = (uint32_t)(b->smem_bytes / (rg * sizeof(uint32_t)));
     args.R = b->a.R;

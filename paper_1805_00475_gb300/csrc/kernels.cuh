@@ -471,7 +471,6 @@ struct BForm {
   uint32_t segs_at, items_at, runs_at, lvl_at;  // byte offsets of the blob sections (steps at 0)
   uint32_t nlev, leaf0, nleaf, res_off, n_out, perm_off;
   uint32_t n_open, root_off, arena, pad;  // arena: entries this formula needs
-  uint64_t gbase;                          // first entry of its global arena
 };
 
 struct BatchArgs {
@@ -484,7 +483,8 @@ struct BatchArgs {
   uint32_t n_forms;
   uint32_t* queue;        // work counter, zeroed before the launch
   uint32_t* results;      // [entry][R]
-  uint32_t* garena;       // global arenas, one region per formula
+  uint32_t* garena;       // global arenas, one slot per CTA, reused by every formula the CTA takes
+  uint64_t slot_entries;  // entries of a slot (the largest formula's arena)
   uint32_t blob_cap;      // bytes of dynamic shared memory reserved for a blob
   uint32_t smem_cap;      // entries of dynamic shared memory available for an arena
   int R;
@@ -505,8 +505,10 @@ __device__ __forceinline__ uint32_t map_runs(uint32_t o, const uint16_t* runs, i
 // alone, tree level by tree level: all steps of a level are independent, so
 // the level is a list of segments shared out over the CTA's warps, with one
 // barrier per level.  Descriptors are read from shared memory; the tensors
-// live in shared memory when the formula's arena fits, else in its own region
-// of global memory.
+// live in shared memory when the formula's arena fits, else in the CTA's own
+// slot of global memory, reused by each formula the CTA takes, so that the
+// live arenas (CTAs x slot) stay in L2 instead of every formula's arena being
+// written back to DRAM.
 template <int RG, bool N30 = false>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
     if (t >= a.n_forms) break;
     const BForm f = a.forms[a.order[t]];
     for (uint32_t i = threadIdx.x; i < f.blob_n; i += blockDim.x) blob[i] = a.blobs[f.blob + i];
-    uint32_t* arena = f.arena <= a.smem_cap ? sarena : a.garena + f.gbase * RG;
+    uint32_t* arena = f.arena <= a.smem_cap ? sarena : a.garena + (uint64_t)blockIdx.x * a.slot_entries * RG;
     for (uint32_t l = threadIdx.x; l < f.nleaf; l += blockDim.x) {
       const BLeaf ld = a.leaves[f.leaf0 + l];
       uint32_t* dst = arena + (uint64_t)ld.off * RG;
