@@ -258,16 +258,25 @@ __device__ __forceinline__ uint32_t p8_half2(uint32_t wa, uint32_t ia, uint32_t 
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// One operand of a dense step to pack: X its byte entries, Y its RG planes,
+// 2^f rows.
+struct PackOperand {
+  const uint8_t* X;
+  __half* Y;
+  uint32_t f;
+};
+
+// Both operands of a step in one launch: the tiles of A, then those of B.
 template <int RG>
-__global__ void __launch_bounds__(256) p8_pack_kernel(const uint8_t* __restrict__ X, __half* __restrict__ Y,
-                                                      uint32_t f, uint32_t k, uint32_t kp, PackPrimes pp) {
+__global__ void __launch_bounds__(256) p8_pack_kernel(PackOperand opA, PackOperand opB, uint32_t k, uint32_t kp,
+                                                      PackPrimes pp) {
   // [residue][row][pair of shared values] half2 words; a row is 32 words + 1
   // of padding, so both phases are free of bank conflicts (phase 1: lanes =
   // 8 row quads x 4 pairs; phase 2: lanes = 8 chunks x 4 rows)
   __shared__ uint32_t tile[RG][64][33];
-  const uint32_t R = 1u << f, K = 1u << k, Kp = 1u << kp;
-  const uint32_t tiles_r = (R + 63) / 64;
-  const uint64_t n_tiles = (uint64_t)tiles_r << (kp - 6);
+  const uint32_t K = 1u << k, Kp = 1u << kp;
+  const uint64_t tiles_a = (uint64_t)(((1u << opA.f) + 63u) / 64u) << (kp - 6);
+  const uint64_t n_tiles = tiles_a + ((uint64_t)(((1u << opB.f) + 63u) / 64u) << (kp - 6));
   const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
   __half2 hp2[RG], np2[RG];
 #pragma unroll
@@ -275,7 +284,13 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(const uint8_t* __restrict_
     hp2[i] = __float2half2_rn((float)((pp.p[i] - 1) / 2));
     np2[i] = __float2half2_rn(-(float)pp.p[i]);
   }
-  for (uint64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
+  for (uint64_t bt = blockIdx.x; bt < n_tiles; bt += gridDim.x) {
+    const bool isA = bt < tiles_a;  // uniform over the block
+    const uint8_t* __restrict__ X = isA ? opA.X : opB.X;
+    __half* __restrict__ Y = isA ? opA.Y : opB.Y;
+    const uint32_t R = 1u << (isA ? opA.f : opB.f);
+    const uint32_t tiles_r = (R + 63) / 64;
+    const uint64_t b = isA ? bt : bt - tiles_a;
     const uint32_t r0 = (uint32_t)(b % tiles_r) * 64u, q0 = (uint32_t)(b / tiles_r) * 64u;
 #pragma unroll
     for (int it = 0; it < 2; it++) {
@@ -732,16 +747,14 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   __half* a16 = (__half*)scratch;    // rg planes of a_elems
   __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
   const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
-  auto pack = [&](uint64_t off, __half* dst, uint32_t f) {
-    const uint64_t n = (uint64_t)((1u << f) + 63u) / 64u << (s.kp - 6);
+  {  // both operands packed by one launch
+    const tnc_p8::PackOperand oa{arena + a_off * rg, a16, s.fa}, ob{arena + b_off * rg, b16, s.fb};
+    const uint64_t n = ((uint64_t)((1u << s.fa) + 63u) / 64u + (uint64_t)((1u << s.fb) + 63u) / 64u) << (s.kp - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
-    const uint8_t* src = arena + off * rg;
-    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
-    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
-    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(src, dst, f, s.k, s.kp, pp);
-  };
-  pack(a_off, a16, s.fa);
-  pack(b_off, b16, s.fb);
+    if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
+    else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
+    else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
+  }
   CUtensorMap ma, mb;
   int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
   if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
