@@ -15,20 +15,22 @@
 //
 // Data path: tensors on this path hold one byte per residue (an entry is the
 // RG residues of its pass side by side: 4 bytes for RG = 4).  A pack kernel
-// turns each operand (the lowering's column-major layout: row index low,
-// shared index high; all residues of the pass at once) into balanced fp16
-// matrices, one per residue, row-major with the shared index contiguous.  TMA moves tiles of rows x 64 values (128-byte
-// lines) into shared memory with the 128-byte swizzle, the canonical K-major
-// SWIZZLE_128B layout of the MMA operand descriptors.
-// Persistent CTAs (one per SM) run three warp roles:
-//   warp 0, lane 0: TMA producer over a 4-stage shared-memory ring;
+// turns both operands of a step (the lowering's column-major layout: row
+// index low, shared index high; all residues of the pass at once) into
+// balanced fp16 matrices, one per residue, row-major with the shared index
+// contiguous.  TMA moves tiles of rows x 64 values (128-byte lines) into
+// shared memory with the 128-byte swizzle, the canonical K-major SWIZZLE_128B
+// layout of the MMA operand descriptors.
+// Persistent CTAs (one per SM, 320 threads) run three warp roles:
+//   warp 0, lane 0: TMA producer over a ring of 3 to 8 shared-memory stages;
 //   warp 1, lane 0: MMA issuer (kind::f16, 128 x TN x 16, fp32 in TMEM);
-//   warps 2..5: epilogue (TMEM lane quarter = warp % 4).
-// A CTA takes its output tiles two at a time, with one TMEM accumulator each,
-// and alternates their K chunks, so one tile's reduction overlaps the other
-// tile's MMAs.  Every wait is bounded (about 2 s); on timeout the kernel
-// records an error word, drains its own copies and MMAs, frees its TMEM and
-// returns.
+//   warps 2..9: epilogue (TMEM lane quarter = warp % 4, column half =
+//   (warp - 2) / 4).
+// A work item is an output tile of 128 rows x TN columns (TN <= 256) and a K
+// slice; NA = min(RG, 512 / TN) residues accumulate at once, one TMEM
+// accumulator each, so one residue's reduction overlaps the next residue's
+// MMAs.  Every wait is bounded (about 2 s); on timeout the kernel records an
+// error word, drains its own copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
