@@ -70,18 +70,20 @@ extern "C" {
 #define TNC_PATH_INT64 0 /* CUDA cores: u32 residues, 64-bit multiply-accumulate */
 #define TNC_PATH_TC 1    /* dense steps (k >= 6 shared bonds, one side >= 2^7 and the
                             other >= 2^5 free entries) as exact 8-bit-limb GEMMs on the
-                            tcgen05 tensor cores (bf16 limbs, fp32 accumulation below
+                            tcgen05 tensor cores (fp16 limbs, fp32 accumulation below
                             2^24, K chunks of 64); other steps as TNC_PATH_INT64; one
                             pass per residue.  tnc_contract only. */
 #define TNC_PATH_TC_P8 2 /* residues modulo primes p <= 251 (Sec. 3.2's exact counts
                             from more, smaller residues): each residue is one 8-bit
                             limb, taken balanced (|r| <= 125) and exact in fp16.
-                            Dense steps (k >= 6, one side >= 2^7 and the other >= 2^4
-                            free entries) run as fp16 GEMMs on tcgen05, operand tiles
-                            by TMA, fp32 accumulation in TMEM reduced mod p in place
-                            every 1024 shared values (1024 * 125^2 + 125 < 2^24: exact);
-                            other steps as TNC_PATH_INT64; one pass per residue.
-                            Workspace: tnc_workspace_bytes_opts.  tnc_contract only. */
+                            Tensors hold one byte per residue, passes of up to 4
+                            residues.  Dense steps (k >= 4, one side >= 2^7 and the
+                            other >= 2^4 free entries) run as fp16 GEMMs on tcgen05,
+                            operand tiles by TMA, fp32 accumulation in TMEM reduced
+                            mod p in place every 1024 shared values (1024 * 125^2 +
+                            125 < 2^24: exact); other steps on CUDA cores with 32-bit
+                            multiply-accumulate.  Workspace: tnc_workspace_bytes_opts.
+                            tnc_contract only. */
 
 /* ---- result flags -------------------------------------------------------- */
 #define TNC_MAYBE_WRAPPED 1u /* the certified bound on the count is not below the
@@ -137,8 +139,9 @@ typedef struct {
   double total_macs;      /* sum of 2^(a+b-k)                                     */
   double total_entries;   /* sum of 2^a + 2^b + 2^(a+b-2k): entries moved          */
   double log2_bound;      /* log2 of the certified upper bound on every count      */
-  uint64_t arena_entries; /* peak live entries, one launch per step (x 4 bytes x
-                             residues per pass = tnc_contract's tensor arena)       */
+  uint64_t arena_entries; /* peak live entries, one launch per step (x residues per
+                             pass x 4 bytes, 1 byte on TNC_PATH_TC_P8 = the tensor
+                             arena of tnc_contract)                                */
   uint64_t batch_arena_entries; /* same for the level-by-level batch schedule     */
   int32_t n_dense_steps;  /* steps TNC_PATH_TC runs on the tensor cores            */
   double dense_macs;      /* their share of total_macs                             */
