@@ -10,9 +10,9 @@
 // 2^24: at most 4 limb pairs share an s, 4 * 255^2 * 64 < 2^24, so K is
 // processed in chunks of 64 and every chunk's C_s is folded into 64-bit
 // integer accumulators, C += sum_s 256^s C_s mod p.  No precision is lost.
-// The tensor cores run kind::f16 with fp16 inputs and fp32 accumulation: on
-// this GPU the 8-bit integer tensor rate is far below the 16-bit float rate,
-// and fp16 carries 8-bit limbs exactly (a limb v becomes the half 1024 + v by
+// The tensor cores run kind::f16 with fp16 inputs and fp32 accumulation: the
+// 8-bit integer form (kind::i8) does not exist for sm_103a, and fp16 carries
+// 8-bit limbs exactly (a limb v becomes the half 1024 + v by
 // bit operations, minus 1024 in one packed subtract).
 //
 // CTA tile: 128 rows of C (TMEM lanes) x 32 columns, 256 threads (8 warps);
