@@ -238,6 +238,29 @@ int tnc_last_dense_time(double* ms, int32_t* n_steps);
 /* Same mode: device time (ms) of the last tnc_contract's kernels, from its
  * first launch to its CRT (host work and the final copies excluded). */
 int tnc_last_contract_time(double* device_ms);
+/* The device kernels the calling thread's last tnc_contract,
+ * tnc_contract_sliced or tnc_contract_noalloc enqueued, by kind: a record of
+ * which branches of the pairwise step (Sec. 2.1) actually ran.  Always
+ * recorded (host counters, no device work); a sliced call sums its slices. */
+typedef struct {
+  int32_t leaf_fill;      /* leaf tensors (Eq. var, Eq. or, Eq. 1in3, ...)           */
+  int32_t level;          /* one launch for all small steps of a tree level           */
+  int32_t grid_step;      /* one large step over the whole GPU                       */
+  int32_t splitk;         /* split-K steps on CUDA cores (a partial + final pair)    */
+  int32_t tc_gemm;        /* TNC_PATH_TC dense steps (tcgen05 limb GEMM launches)     */
+  int32_t tc_split;       /*   of which split over K (partials summed after)          */
+  int32_t p8_pack;        /* TNC_PATH_TC_P8 operand packing launches                  */
+  int32_t p8_gemm;        /* TNC_PATH_TC_P8 dense steps (tcgen05 GEMM launches)       */
+  int32_t p8_split;       /*   of which split over K                                 */
+  int32_t p8_tile_n[5];   /*   by tile width: 16, 32, 64, 128, 256 columns            */
+  int32_t p8_max_chunks;  /* most 1024-value chunks one tile accumulates in TMEM per
+                             residue (each reduced mod p in place before the next)   */
+  int32_t p8_swapped;     /*   with the row operand taken from B (A too narrow)       */
+  int32_t p8_padded;      /*   with fewer than 64 shared values, zero-padded to 64     */
+  int32_t extract;        /* root tensor -> result residues                          */
+  int32_t crt;            /* Chinese remaindering                                     */
+} tnc_launch_counts;
+int tnc_last_launch_counts(tnc_launch_counts* out);
 /* Contracts the plan on the GPU and returns the count(s) in `out` (host).
  * dev_ws: device buffer of at least tnc_workspace_bytes_opts(plan, opts) bytes
  * (= tnc_workspace_bytes(plan, R) on TNC_PATH_INT64 and TNC_PATH_TC), 256-byte
@@ -367,15 +390,17 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
 
 /* ---- diagnostics --------------------------------------------------------- */
 /* Measured rate of the modular multiply-accumulate primitive of the step
- * kernels (4 residues per thread, 64-bit accumulation, Barrett reduction every
- * fourth product), operands in registers, all SMs busy: a ceiling for steps
- * bound by the integer pipes.  `iters` loop trips per thread (16 MACs each).
+ * kernels (4 residues per thread, 64-bit accumulation, reduced after every
+ * 16th product by the two-fold reduction the step kernels use for the default
+ * primes just below 2^30), operands in registers, all SMs busy: a ceiling for
+ * steps bound by the integer pipes.  `iters` loop trips per thread (16 MACs each).
  * Allocates an 8-byte device counter with cudaMallocAsync; synchronises. */
 int tnc_probe_modmac(void* cuda_stream, int32_t iters, double* macs_per_s);
 
 /* ---- allocation-free variant (the paper has no counterpart) --------------
- * Same counts as tnc_contract, for callers that cannot allocate device memory
- * themselves: a host application whose device memory is owned entirely by
+ * The counts of tnc_contract on TNC_PATH_INT64 (the only path it takes: other
+ * paths fail with TNC_ERR_INVALID), for callers that cannot allocate device
+ * memory themselves: a host application whose device memory is owned entirely by
  * another allocator (a framework's caching pool that forbids raw cudaMalloc),
  * or a latency-bound loop that cannot afford cudaMalloc/cudaFree, which may
  * synchronise the whole device.  It calls no cudaMalloc, cudaFree or other
@@ -385,7 +410,9 @@ int tnc_probe_modmac(void* cuda_stream, int32_t iters, double* macs_per_s);
  * and the host result buffers of `out` (output).
  *   - The first call on each device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept with the device's
+ *     context; if the context changes (after cudaDeviceReset) the next call
+ *     looks it up again.
  *   - Every call shares the one array: calls that overlap on the GPU (other
  *     streams, other host threads, same device) race and corrupt each other's
  *     results.  Serialise them.  Nothing in the array needs to start zeroed,

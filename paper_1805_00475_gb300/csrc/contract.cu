@@ -1,6 +1,7 @@
 // C ABI, device half: single-formula contraction (one launch per step) and the
 // persistent, graph-captured batch.
 #include <type_traits>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +37,7 @@ thread_local bool g_time_dense = false;
 thread_local double g_dense_ms = 0.0;
 thread_local int g_dense_launches = 0;
 thread_local double g_total_ms = 0.0;
+thread_local tnc_launch_counts g_launches{};
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int sm_count() {
@@ -173,7 +175,6 @@ void grid_shape(int c, int* threads, int* blocks, int* s) {
 // keeps at least two slices; outputs x slices stays at most 2^13.  (Capping
 // the values per thread at 64 with more slices measured 6 % slower on the
 // 1-in-3 batch's heavy formulas and no faster on C4-sized ones.)
-constexpr uint64_t kSplitPartEntries = 1ull << 20;
 uint32_t splitk_log(const StepDesc& d) {
   if (d.c > 12 || d.k < 9) return 0;
   const uint32_t ls = d.c < 9 ? 10u - d.c : 1u;
@@ -242,7 +243,8 @@ SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
   o = align_up(o + 64);
   uint64_t part_bytes = 0;
   for (const StepDesc& d : p->low.lvl_steps) {
-    if (splitk_log(d) > 0) part_bytes = std::max<uint64_t>(part_bytes, kSplitPartEntries * rg_max * sizeof(uint32_t));
+    if (splitk_log(d) > 0)
+      part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + splitk_log(d))) * rg_max * sizeof(uint32_t));
     if (tc_eligible(d) && tc_split_log(d) > 0)
       part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
     if (path == TNC_PATH_TC_P8 && p8_eligible(d))
@@ -301,6 +303,14 @@ extern "C" int tnc_last_dense_time(double* ms, int32_t* n_steps) {
 
 extern "C" int tnc_last_contract_time(double* device_ms) {
   if (device_ms) *device_ms = g_total_ms;
+  return TNC_OK;
+}
+
+tnc_launch_counts& tnc::launch_counts() { return g_launches; }
+
+extern "C" int tnc_last_launch_counts(tnc_launch_counts* out) {
+  if (!out) return set_error(TNC_ERR_INVALID, "NULL argument");
+  *out = g_launches;
   return TNC_OK;
 }
 
@@ -460,12 +470,14 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
       const int nl = (int)leaves.size();
       tnc_dev::leaf_fill_kernel<RG, W><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
+      g_launches.leaf_fill++;
       for (size_t l = 0; l < small_lo.size(); l++) {
         const uint32_t n_small = small_hi[l] - small_lo[l];
         if (n_small) {
           const uint32_t w = small_work[l];
           const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, (uint64_t)sms * 8);
           tnc_dev::level_kernel<RG, W, N30><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
+          g_launches.level++;
         }
         for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
           if (kind[i] == kSmall) continue;
@@ -498,15 +510,18 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
                                                                                        mg);
             tnc_dev::splitk_final_kernel<RG, W, N30><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
                 d_steps + slot[i], arena, part, ls, mg);
+            g_launches.splitk++;
           } else {
             int threads, blocks, sh;
             grid_shape(lw.lvl_steps[i].c, &threads, &blocks, &sh);
             tnc_dev::step_kernel<RG, W, N30><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
+            g_launches.grid_step++;
           }
         }
       }
       tnc_dev::extract_kernel<RG, W><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
           arena, root_off, rm, results, a.R, groups.col[gi]);
+      g_launches.extract++;
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     };
@@ -531,6 +546,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((L.n_out + 127) / 128, 1024), 128, 0, st>>>(results, L.n_out, a.crt,
                                                                                                   limbs);
+  g_launches.crt++;
   CUDA_TRY(cudaGetLastError());
   if (g_time_dense) CUDA_TRY(cudaEventRecord(whole[1], st));
   uint32_t h_err = 0;
@@ -556,6 +572,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
 extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
                             void* cuda_stream, tnc_count* out) {
   clear_error();
+  g_launches = tnc_launch_counts{};
   return contract_core(plan, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
 }
 
@@ -580,6 +597,7 @@ extern "C" size_t tnc_workspace_bytes_sliced(const tnc_plan_t* const* plans, int
 extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                                    void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* out) {
   clear_error();
+  g_launches = tnc_launch_counts{};
   if (!plans || n <= 0 || !out || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
   Arith a;
   int rc = make_arith(opts, a);
@@ -607,6 +625,7 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
     if (rc) return rc;
   }
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((n_out + 127) / 128, 1024), 128, 0, st>>>(acc, n_out, a.crt, limbs);
+  g_launches.crt++;
   CUDA_TRY(cudaGetLastError());
   std::vector<uint32_t> h_res(n_out * a.R), h_limbs(n_out * a.crt.n_limbs);
   CUDA_TRY(cudaMemcpyAsync(h_res.data(), acc, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
@@ -1203,20 +1222,44 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_base[kMaxDevices] = {nullptr};
+CUcontext g_noalloc_ctx[kMaxDevices] = {nullptr};
+
+// The driver's current context, fetched through the runtime (no link-time
+// dependency on the driver library); nullptr if unavailable.
+CUcontext current_context() {
+  using GetCtx = CUresult (*)(CUcontext*);
+  static GetCtx fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<GetCtx>(p);
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 // Device address of the scratch array on the current device.  In host code
 // `g_noalloc_scratch` names a host-side shadow, not device memory, so the
-// address is looked up once per device, with that device current.
+// address is looked up once per device, with that device current, and kept
+// with the context it belongs to: after a device reset the runtime makes a
+// new context (and loads the module again), and the address is looked up
+// anew.  (Before the runtime has made a context current the context reads as
+// nullptr; the next call then looks the address up once more.)
 int noalloc_base(void** out) {
   int dev = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return set_error(TNC_ERR_INVALID, "device ordinal out of range");
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_base[dev]) {
+  if (!g_noalloc_base[dev] || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     if (!p) return set_error(TNC_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
     g_noalloc_base[dev] = p;
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_base[dev];
   return TNC_OK;
@@ -1227,8 +1270,10 @@ int noalloc_base(void** out) {
 extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* cuda_stream,
                                     tnc_count* out) {
   clear_error();
+  g_launches = tnc_launch_counts{};
   if (!plan || !opts || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
-  if (opts->path != TNC_PATH_INT64) return set_error(TNC_ERR_INVALID, "unknown arithmetic path");
+  if (opts->path != TNC_PATH_INT64)
+    return set_error(TNC_ERR_INVALID, "tnc_contract_noalloc supports TNC_PATH_INT64 only");
   const int R = opts->n_residues;
   if (R < 1 || R > 16) return set_error(TNC_ERR_INVALID, "n_residues must be in [1, 16]");
   // primes and CRT constants, on the stack
@@ -1328,6 +1373,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
   uint32_t* arena = (uint32_t*)(ws + L.off_arena);
   uint32_t* results = (uint32_t*)(ws + L.off_results);
   uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
+  uint32_t* part = (uint32_t*)(ws + L.off_part);
   RootMap rm{};
   rm.n_open = (int)plan->net.open_vars.size();
   for (int j = 0; j < rm.n_open; j++) rm.perm[j] = plan->low.root_perm[j];
@@ -1343,13 +1389,25 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
       constexpr int RG = decltype(rgc)::value;
       tnc_dev::leaf_fill_kernel<RG><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
+      g_launches.leaf_fill++;
       for (size_t i = 0; i < plan->low.seq_steps.size(); i++) {
+        const StepDesc& d = plan->low.seq_steps[i];
+        const uint32_t ls = splitk_log(d);
+        if (ls > 0) {  // few outputs, long shared sum: K split over blocks, as in tnc_contract
+          tnc_dev::splitk_partial_kernel<RG><<<(unsigned)(1ull << (d.c + ls)), 256, 0, st>>>(d_steps + i, arena, part,
+                                                                                           ls, mg);
+          tnc_dev::splitk_final_kernel<RG><<<(unsigned)(1ull << d.c), 256, 0, st>>>(d_steps + i, arena, part, ls, mg);
+          g_launches.splitk++;
+          continue;
+        }
         int threads, blocks, sh;
-        grid_shape(plan->low.seq_steps[i].c, &threads, &blocks, &sh);
+        grid_shape(d.c, &threads, &blocks, &sh);
         tnc_dev::step_kernel<RG><<<blocks, threads, 0, st>>>(d_steps + i, arena, mg);
+        g_launches.grid_step++;
       }
       tnc_dev::extract_kernel<RG><<<(unsigned)std::min<uint64_t>((n_out + 255) / 256, 1024), 256, 0, st>>>(
           arena, root_off, rm, results, R, grp_col[gi]);
+      g_launches.extract++;
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     });
@@ -1357,6 +1415,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
   }
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((n_out + 127) / 128, 1024), 128, 0, st>>>(results, n_out, cc,
                                                                                                 limbs);
+  g_launches.crt++;
   CUDA_TRY(cudaGetLastError());
   if (out->residues)
     CUDA_TRY(cudaMemcpyAsync(out->residues, results, n_out * R * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

@@ -485,6 +485,8 @@ int tc_launch(const void* dev_step, const StepDesc& d, uint32_t* arena, uint32_t
   if (tiles >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
   tnc_tc::tc_step_kernel<<<(unsigned)tiles, tnc_tc::kThreads, tnc_tc::kSmemBytes, st>>>(
       (const tnc_tc::TcStep*)dev_step, arena, part, dev_err);
+  launch_counts().tc_gemm++;
+  if (ls) launch_counts().tc_split++;
   if (ls) {
     const uint64_t n = 1ull << (fa + fb);
     tnc_tc::tc_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 8192), 256, 0, st>>>(

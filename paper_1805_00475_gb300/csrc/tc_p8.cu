@@ -757,6 +757,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
     else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
   }
+  launch_counts().p8_pack++;
   CUtensorMap ma, mb;
   int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
   if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
@@ -815,6 +816,18 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, ma, mb, g, grid, dev_err, st);
   else rc = launch_gemm_rg<1>(s.tn, ma, mb, g, grid, dev_err, st);
   if (rc) return rc;
+  {
+    tnc_launch_counts& lc = launch_counts();
+    lc.p8_gemm++;
+    if (ls) lc.p8_split++;
+    int w = 0;
+    while ((16u << w) < s.tn) w++;
+    lc.p8_tile_n[w]++;
+    const int32_t chunks = (int32_t)std::max<uint64_t>(1, ((1ull << s.kp) >> ls) / tnc_p8::kChunkK);
+    lc.p8_max_chunks = std::max(lc.p8_max_chunks, chunks);
+    if (s.swap) lc.p8_swapped++;
+    if (s.kp > s.k) lc.p8_padded++;
+  }
   if (ls) {
     const uint64_t n = (uint64_t)rg << d.c;
     tnc_p8::p8_split_final_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(

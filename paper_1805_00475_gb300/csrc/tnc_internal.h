@@ -99,6 +99,10 @@ namespace tnc {
 int set_error(int code, const std::string& msg);
 void clear_error();
 
+// Kernel launches of the calling thread's current (or last) contraction
+// (tnc_last_launch_counts); contract.cu resets it per call.
+tnc_launch_counts& launch_counts();
+
 // network.cpp
 int build_network(const tnc_formula* f, Network& out);
 

@@ -31,7 +31,7 @@ TNC_MAYBE_WRAPPED = 1
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -72,6 +72,13 @@ class _PlanStats(ctypes.Structure):
                 ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64),
                 ("n_dense_steps", ctypes.c_int32), ("dense_macs", ctypes.c_double),
                 ("n_dense_steps_p8", ctypes.c_int32), ("dense_macs_p8", ctypes.c_double)]
+
+
+class _LaunchCounts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("leaf_fill", "level", "grid_step", "splitk", "tc_gemm", "tc_split",
+                                              "p8_pack", "p8_gemm", "p8_split")] + \
+               [("p8_tile_n", ctypes.c_int32 * 5)] + \
+               [(n, ctypes.c_int32) for n in ("p8_max_chunks", "p8_swapped", "p8_padded", "extract", "crt")]
 
 
 class _ContractOpts(ctypes.Structure):
@@ -123,6 +130,7 @@ def lib():
             "tnc_set_step_timing": ([i32], None),
             "tnc_last_dense_time": ([ctypes.POINTER(ctypes.c_double), i32p], ctypes.c_int),
             "tnc_last_contract_time": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "tnc_last_launch_counts": ([ctypes.POINTER(_LaunchCounts)], ctypes.c_int),
             "tnc_workspace_bytes_sliced": ([vp, i32, vp], sz),
             "tnc_contract_sliced": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
@@ -399,6 +407,19 @@ def last_contract_time() -> float:
     ms = ctypes.c_double()
     _check(lib().tnc_last_contract_time(ctypes.byref(ms)))
     return ms.value
+
+
+P8_TILE_WIDTHS = (16, 32, 64, 128, 256)
+
+
+def last_launch_counts() -> dict:
+    """tnc_last_launch_counts: kernels the calling thread's last contraction
+    enqueued, by kind; "p8_tile_n" maps tile width -> GEMM launches."""
+    c = _LaunchCounts()
+    _check(lib().tnc_last_launch_counts(ctypes.byref(c)))
+    d = {n: int(getattr(c, n)) for n, _ in _LaunchCounts._fields_ if n != "p8_tile_n"}
+    d["p8_tile_n"] = {w: int(c.p8_tile_n[i]) for i, w in enumerate(P8_TILE_WIDTHS)}
+    return d
 
 
 def contract_sliced(plans: Sequence[Plan], n_residues: int = 4, primes=None, workspace=None, stream=None,

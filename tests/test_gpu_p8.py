@@ -10,32 +10,12 @@ from paper_1805_00475_gb300 import build as tnc_build
 from paper_1805_00475_gb300 import instances as I
 from paper_1805_00475_gb300 import tnc
 
-from test_gpu_tc import _step_shapes
-
 pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
     tnc_build.build()
-
-
-def _p8_shape(fa, fb, k):
-    """(rows from B, columns per tile, K chunks, log2 K split, shared values
-    zero-padded) of a step the path runs on the tensor cores, else None (the
-    library's rule restated)."""
-    if not (k >= 4 and ((fa >= 7 and fb >= 4) or (fb >= 7 and fa >= 4))):
-        return None
-    swap = not (fa >= 7 and fb >= 4)
-    r, c = (fb, fa) if swap else (fa, fb)
-    tn = min(1 << c, 128)
-    if c >= 8 and (1 << r) // 128 * ((1 << c) // 256) >= 456:  # 256-wide tiles, two residues per round
-        tn = 256
-    tiles = (1 << r) // 128 * ((1 << c) // tn)
-    ls = 0
-    while (tiles << ls) < 160 and k - ls - 1 >= 10 and (1 << (fa + fb + ls + 1)) <= (1 << 26):
-        ls += 1
-    return swap, tn, max(1, (1 << (max(k, 6) - ls)) // 1024), ls, k < 6
 
 
 ORACLE_CASES = [(70, "greedy", 0), (70, "greedy", 1), (70, "greedy", 2), (70, "gn", 1), (70, "bisect", 0),
@@ -46,48 +26,49 @@ ORACLE_CASES = [(70, "greedy", 0), (70, "greedy", 1), (70, "greedy", 2), (70, "g
 def test_p8_matches_oracle(n, h, seed):
     f = I.cubic_vertex_cover(n, seed)
     p = tnc.plan_formula(f, heuristic=h, rank_cap=28)
-    assert any(_p8_shape(*s) for s in _step_shapes(f, p))
     exact = oracle.count(f, max_rank=28)
     r = tnc.contract(p, n_residues=12, path="tc_p8")
+    assert tnc.last_launch_counts()["p8_gemm"] >= 1
     assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
     assert r.flags == 0 and r.counts == exact
 
 
 def test_p8_oracle_cases_cover_every_tile_width_and_both_orientations():
-    seen = set()
+    """The oracle cases above, by the library's own launch record: every tile
+    width up to 128 (256: tests/test_gpu_dense_branches.py), rows from A and
+    from B, zero-padded and unpadded shared dimensions."""
+    widths, swapped, unswapped, padded, unpadded = set(), 0, 0, 0, 0
     for n, h, seed in ORACLE_CASES:
-        f = I.cubic_vertex_cover(n, seed)
-        p = tnc.plan_formula(f, heuristic=h, rank_cap=28)
-        for s in _step_shapes(f, p):
-            sh = _p8_shape(*s)
-            if sh:
-                seen.add(("tn", sh[1]))
-                seen.add(("swap", sh[0]))
-                seen.add(("padded", sh[4]))
-    assert {("tn", t) for t in (16, 32, 64, 128)} <= seen
-    assert {("swap", True), ("swap", False)} <= seen
-    assert ("padded", True) in seen and ("padded", False) in seen
+        p = tnc.plan_formula(I.cubic_vertex_cover(n, seed), heuristic=h, rank_cap=28)
+        tnc.contract(p, n_residues=4, path="tc_p8")
+        lc = tnc.last_launch_counts()
+        widths |= {w for w, c in lc["p8_tile_n"].items() if c}
+        swapped += lc["p8_swapped"]
+        unswapped += lc["p8_gemm"] - lc["p8_swapped"]
+        padded += lc["p8_padded"]
+        unpadded += lc["p8_gemm"] - lc["p8_padded"]
+    assert {16, 32, 64, 128} <= widths
+    assert swapped and unswapped and padded and unpadded
 
 
 @pytest.mark.parametrize("n,h,seed", [(100, "greedy", 0), (100, "greedy", 2), (120, "greedy", 2), (120, "bisect", 2)])
 def test_p8_matches_int64_with_k_split(n, h, seed):
     f = I.cubic_vertex_cover(n, seed)
     p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
-    shapes = [_p8_shape(*s) for s in _step_shapes(f, p)]
-    assert any(s for s in shapes)
     a = tnc.contract(p, n_residues=5, path="int64")
     b = tnc.contract(p, n_residues=20, path="tc_p8")
+    assert tnc.last_launch_counts()["p8_gemm"] >= 1
     assert a.flags == 0 and b.flags == 0
     assert a.counts == b.counts
 
 
 def test_p8_k_split_cases_really_split():
-    splits = []
+    splits = 0
     for n, h, seed in [(100, "greedy", 2), (120, "greedy", 2)]:
-        f = I.cubic_vertex_cover(n, seed)
-        p = tnc.plan_formula(f, heuristic=h, rank_cap=30)
-        splits += [s[3] for s in map(lambda x: _p8_shape(*x), _step_shapes(f, p)) if s]
-    assert max(splits) >= 2
+        p = tnc.plan_formula(I.cubic_vertex_cover(n, seed), heuristic=h, rank_cap=30)
+        tnc.contract(p, n_residues=4, path="tc_p8")
+        splits += tnc.last_launch_counts()["p8_split"]
+    assert splits >= 2
 
 
 def test_p8_many_chunks_match_int64():
@@ -95,9 +76,9 @@ def test_p8_many_chunks_match_int64():
     1024 per tile, each reduced in place in TMEM before the next."""
     f = I.cubic_vertex_cover(180, 1)
     p = tnc.plan_formula(f, heuristic="best", rank_cap=30)
-    assert max(sh[2] for sh in (_p8_shape(*s) for s in _step_shapes(f, p)) if sh) >= 8
     a = tnc.contract(p, n_residues=7, path="int64")
     b = tnc.contract(p, n_residues=26, path="tc_p8")
+    assert tnc.last_launch_counts()["p8_max_chunks"] >= 8
     assert a.flags == 0 and b.flags == 0
     assert a.counts == b.counts
 
@@ -108,11 +89,10 @@ def test_p8_wide_tiles_match_int64():
     entry.  Counts equal the int64 path's (disjoint primes, both CRTs)."""
     f = I.cubic_vertex_cover(180, 1)
     p = tnc.plan_formula(f, heuristic="best", rank_cap=30)
-    wide = [sh for sh in (_p8_shape(*s) for s in _step_shapes(f, p)) if sh and sh[1] == 256]
-    assert wide
     a = tnc.contract(p, n_residues=7, path="int64")
     for R in (26, 21):  # 4-residue passes and a last pass of 2 residues; then of 1 residue
         b = tnc.contract(p, n_residues=R, path="tc_p8")
+        assert tnc.last_launch_counts()["p8_tile_n"][256] >= 1
         assert a.flags == 0 and b.flags == 0
         assert a.counts == b.counts
 

@@ -91,6 +91,8 @@ def test_split_k_final_dot_product(path):
     else:
         pytest.skip("no split-K step among the seeds")
     assert tnc.contract(p, n_residues=4, path=path).counts == oracle.count(f, max_rank=28)
+    lc = tnc.last_launch_counts()
+    assert lc["splitk"] + lc["tc_split"] >= 1
 
 
 # ---------------------------------------------------------------- full C4 size
