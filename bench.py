@@ -10,6 +10,12 @@ cheapest per formula) in one persistent, graph-captured launch.
 Metric: exact model counts per second (formulas fully counted: all residues
 and the CRT) and modular MACs per second (sum over steps of 2^(a+b-k), times R).
 
+Beside it, in the same line (block "c4"): the comparison of the arithmetic
+paths on 16 #Cubic-Vertex-Cover formulas on 180 vertices (tensor-greedy-free
+best plans of rank <= 30): the 8-bit-prime tensor-core path timed over the
+steps, the int64 CUDA-core path and the limb tensor-core path timed once, the
+same counts asserted, and the dense steps' roofline from CUDA events.
+
   python bench.py [--gpus N --steps K --warmup W --batch B]
   python bench.py --impl reference ...   # the CPU oracle as the reference arm
 
@@ -48,6 +54,9 @@ def parse():
     ap.add_argument("--planner", default="best")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="default run: leave out the C4 comparison block")
+    ap.add_argument("--min-timed-s", type=float, default=1.0,
+                    help="c2: repeat the block of K timed steps until this much device time is covered")
     ap.add_argument("--e2e-split", default="0.35,0.65",
                     help="c2 e2e: shares of the formulas in consecutive batches on their own streams, so "
                          "that one batch's upload overlaps the previous batch's kernel")
@@ -113,7 +122,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -503,15 +512,14 @@ def run_slicing(args):
     print(json.dumps(line), flush=True)
 
 
-def run_c4(args):
+def c4_block(args, dev, steps, warmup, compare):
     """16 #Cubic-VC formulas on 180 vertices: exact counts through tnc_contract
-    on the 8-bit-prime tensor-core path (timed steps); the 30-bit-prime limb
-    tensor-core path (8 residues) and the CUDA-core int64 path (8 residues)
-    timed once beside it; all three must give the same counts."""
+    on the 8-bit-prime tensor-core path (timed over `steps`), and, timed once
+    beside it, the paths in `compare` (the 30-bit-prime limb tensor-core path
+    and the CUDA-core int64 path, 8 residues each); all must give the same
+    counts.  Returns the block of the bench line."""
     import torch
     from paper_1805_00475_gb300 import tnc
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     Rc = 8
     t = time.perf_counter()
     kept = c4_workload(args.formulas or 16)
@@ -526,7 +534,6 @@ def run_c4(args):
         p8_primes.append(q)
         bits += math.log2(q)
     R8 = len(p8_primes)
-    compare = [x for x in args.c4_compare.split(",") if x]
     ws_bytes = max(tnc.workspace_bytes(p, R8, "tc_p8") for p in plans)
     if compare:
         ws_bytes = max(ws_bytes, max(tnc.workspace_bytes(p, Rc) for p in plans))
@@ -535,12 +542,11 @@ def run_c4(args):
     macs = sum(p.stats.total_macs for p in plans)
     dense = sum(p.stats.dense_macs for p in plans)
     dense8 = sum(p.stats.dense_macs_p8 for p in plans)
-
-    dense_ms, device_ms = [], []
+    dense_ms, device_ms, launches, io = [], [], [], []
 
     def one_pass(path, timed=False):
         R = R8 if path == "tc_p8" else Rc
-        counts, dms, gms = [], 0.0, 0.0
+        counts, dms, gms, nl, h2d, d2h = [], 0.0, 0.0, 0, 0, 0
         tnc.set_step_timing(timed)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -550,21 +556,30 @@ def run_c4(args):
             counts.append(r.counts[0])
             dms += tnc.last_dense_time()[0]
             gms += tnc.last_contract_time()
+            lc = tnc.last_launch_counts()
+            nl += sum(v for k, v in lc.items() if k not in ("p8_tile_n", "p8_max_chunks", "p8_swapped",
+                                                            "p8_padded", "tc_split", "p8_split"))
+            nl += lc["splitk"] + lc["tc_split"] + lc["p8_split"]  # split steps launch a second kernel
+            a, b = tnc.last_io_bytes()
+            h2d += a
+            d2h += b
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         tnc.set_step_timing(False)
         if timed:
             dense_ms.append(dms)
             device_ms.append(gms)
+            launches.append(nl)
+            io.append((h2d, d2h))
         return dt, counts
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         one_pass("tc_p8")
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
     times, counts = [], None
-    for _ in range(args.steps):
+    for _ in range(steps):
         dt, counts = one_pass("tc_p8", timed=True)
         times.append(dt)
     clk = clocks.stop()
@@ -580,44 +595,134 @@ def run_c4(args):
     # p8 dense steps: one fp16 product (2 flops) per MAC and residue; limb
     # path: 16 limb products per MAC and residue
     p8_flops = dense8 * R8 * 2
-    line = {
-        "metric": "exact model counts/s", "value": len(plans) / s, "unit": "counts/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1000.0, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32 residues mod primes <= 251; dense steps fp16 (exact), fp32 accumulate reduced every 1024",
-        "data": "synthetic",
-        "config": {"workload": f"cubic_vertex_cover_n180_{len(kept)}formulas", "seeds": [k[0] for k in kept],
-                   "max_ranks": [p.stats.max_rank for p in plans], "planner": "best", "path": "tc_p8",
-                   "residues": R8, "primes": p8_primes, "log2_bound_max": round(bound, 2),
-                   "l2": "inputs (up to 18 GB of tensors) far above L2"},
+    dev_ms = sum(device_ms) / len(device_ms)
+    return {
+        "workload": f"cubic_vertex_cover_n180_{len(kept)}formulas", "seeds": [k[0] for k in kept],
+        "max_ranks": [p.stats.max_rank for p in plans], "planner": "best",
+        "value": len(plans) / s, "unit": "counts/s", "ms_per_step": s * 1000.0, "steps": steps, "warmup": warmup,
+        "step": "tnc_contract of every formula, one after another, host result buffers (e2e through the C ABI: "
+                "descriptor uploads and result reads inside)",
+        "path": "tc_p8", "residues": R8, "primes": p8_primes, "log2_bound_max": round(bound, 2),
+        "dtype": "u8 residues mod primes <= 251; dense steps fp16 (exact), fp32 accumulate reduced every 1024",
         "modular_macs_per_s": macs * R8 / s,
+        "device_ms_per_step": dev_ms, "gpu_launches_per_step": sum(launches) / len(launches),
+        "e2e": {"value": len(plans) / s, "unit": "counts/s", "h2d_bytes_per_step": io[-1][0],
+                "d2h_bytes_per_step": io[-1][1],
+                "note": "the timed step is already end to end: tnc_contract uploads each plan's descriptors "
+                        "and returns host counts"},
         "tc_limb_path": None if ttc is None else {
             "residues": Rc, "ms_per_step": ttc * 1000.0, "speedup_tc_p8": ttc / s,
             "limb_tflops": dense * Rc * 16 * 2 / ttc / 1e12},
         "int64_path": None if t64 is None else {
             "residues": Rc, "ms_per_step": t64 * 1000.0, "modular_macs_per_s": macs * Rc / t64,
             "speedup_tc_p8": t64 / s, "speedup_tc_limb": t64 / ttc if ttc else None},
+        "counts_identical_across_paths": ["tc_p8"] + list(others),
         "roofline": {"bound": "tensor", "achieved": p8_flops / dms / 1e9, "peak": pk["bf16_tflops"],
                      "unit": "TFLOP/s", "frac": p8_flops / dms / 1e9 / pk["bf16_tflops"], "traffic": None,
-                     "peak_source": f"{pk_kind} bf16 burst (MEASURED_PEAKS.json); fp16 has the same dense rate",
-                     "kernel": "dense steps: p8_pack x2 + p8_gemm_kernel (+ split sum)",
-                     "dense_ms_per_step": dms, "dense_share_of_step": dms / (s * 1000.0),
-                     "device_ms_per_step": sum(device_ms) / len(device_ms),
+                     "peak_source": f"{pk_kind} bf16 dense burst (MEASURED_PEAKS.json); fp16 has the same dense rate",
+                     "kernel": "dense steps: p8_pack + p8_gemm_kernel (+ split sum), CUDA events around each",
+                     "dense_ms_per_step": dms, "dense_share_of_device_time": dms / dev_ms,
                      "whole_contraction_tflops": p8_flops / s / 1e12,
-                     "algorithmic_flops_per_step": p8_flops},
+                     "algorithmic_flops_per_step": p8_flops,
+                     "flops": "sum over dense steps of 2^(a+b-k) x residues x 2"},
         "clocks": clk, "plan_s": plan_s,
         "counts_log2": [round(math.log2(c), 2) for c in counts],
     }
+
+
+def c4_cpu_baseline(dev, budget_s=30.0):
+    """The oracle cannot contract the rank-29 C4 networks (tensors of 2^29 big
+    integers); it is timed instead on the largest #Cubic-VC formula it finishes
+    in seconds (n = 100, seed 11, tensor-greedy, rank 24), next to the
+    8-bit-prime path on the same formula."""
+    import oracle
+    import torch
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import tnc
+    f = I.cubic_vertex_cover(100, 11)
+    oracle.build()
+    t = time.perf_counter()
+    exact = oracle.count(f, max_rank=26)
+    cpu_s = time.perf_counter() - t
+    p = tnc.plan_formula(f, heuristic="greedy", rank_cap=26)
+    R8 = 0
+    bits = 0.0
+    for q in tnc.default_primes(53, "tc_p8"):
+        if bits > p.stats.log2_bound + 1:
+            break
+        bits += math.log2(q)
+        R8 += 1
+    r = tnc.contract(p, n_residues=R8, path="tc_p8")
+    assert r.counts == exact
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for _ in range(5):
+        tnc.contract(p, n_residues=R8, path="tc_p8")
+    torch.cuda.synchronize(dev)
+    gpu_s = (time.perf_counter() - t) / 5
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / cpu_s, "unit": "counts/s", "cores": threads, "kind": "oracle",
+            "sample": f"#Cubic-VC n=100 seed 11 (tensor-greedy, rank 24; C4's rank-29 networks are beyond the "
+                      f"oracle): oracle {cpu_s:.1f} s, tc_p8 path {gpu_s * 1000:.1f} ms on the same formula, "
+                      f"same count"}
+
+
+def run_c4(args):
+    """The C4 comparison alone (bench.py --config c4)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    blk = c4_block(args, dev, args.steps, args.warmup, [x for x in args.c4_compare.split(",") if x])
+    line = {"metric": METRIC, "value": blk["value"], "unit": "counts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": blk["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": blk["dtype"], "data": "synthetic",
+            "config": {"workload": blk["workload"], "seeds": blk["seeds"], "max_ranks": blk["max_ranks"],
+                       "planner": "best", "path": "tc_p8", "residues": blk["residues"], "primes": blk["primes"],
+                       "l2": "inputs (up to 18 GB of tensors) far above L2"},
+            "modular_macs_per_s": blk["modular_macs_per_s"], "tc_limb_path": blk["tc_limb_path"],
+            "int64_path": blk["int64_path"], "roofline": blk["roofline"], "clocks": blk["clocks"],
+            "plan_s": blk["plan_s"], "counts_log2": blk["counts_log2"],
+            "gpu_launches": int(blk["gpu_launches_per_step"] * args.steps),
+            "e2e": blk["e2e"],
+            "cpu_baseline": c4_cpu_baseline(dev)}
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# batch_kernel<4> launch on the default workload (8192 #Cubic-VC formulas on
-# 60 vertices, 4 residues, best plans, autotuned launch), the mean over the
-# five timed launches of one ncu capture: 187.1 MB read + 457.0 MB written.
-# The capture command is in profiles/batch_kernel_cubic_vc_n60_R4.md; set to
-# None when the kernel changes.
-C2_TRAFFIC_BYTES_PER_LAUNCH = 0.6441e9
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the C2 batch kernel come from an ncu capture summarised in this profile; the
+# figure is used only while the kernel's device sources are the ones captured
+# (their SHA-256 is recorded beside it), else the line reports null.
+C2_PROFILE = os.path.join(ROOT, "profiles", "batch_kernel_cubic_vc_n60_R4.md")
+C2_KERNEL_SOURCES = ["paper_1805_00475_gb300/csrc/kernels.cuh", "paper_1805_00475_gb300/csrc/modarith.cuh",
+                     "paper_1805_00475_gb300/csrc/step_desc.h"]
+
+
+def kernel_source_sha(paths) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(profile: str, sources) -> tuple:
+    """(bytes per launch, note) from the profile's 'traffic_bytes_per_launch
+    = B, kernel_source_sha = H' line if H matches the current sources, else
+    (None, why)."""
+    import re
+    try:
+        with open(profile) as fh:
+            txt = fh.read()
+    except OSError:
+        return None, "no profile"
+    m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)\s*,\s*kernel_source_sha\s*=\s*([0-9a-f]+)", txt)
+    if not m:
+        return None, "no traffic line in the profile"
+    sha = kernel_source_sha(sources)
+    if m.group(2) != sha:
+        return None, f"kernel changed since the capture (sources {sha}, captured {m.group(2)})"
+    return float(m.group(1)), f"ncu capture of this workload and kernel ({os.path.relpath(profile, ROOT)})"
 
 
 def run_tnc(args):
@@ -663,31 +768,43 @@ def run_tnc(args):
     out = batch.download(ws, stream)
     assert all(o.flags == 0 for o in out), "uncertified CRT in the workload"
 
+    # Blocks of exactly K timed steps, each bracketed by a barrier and a
+    # synchronize, repeated until the timed steps cover --min-timed-s of
+    # device time (so that the clock record spans the measurement); every
+    # rank runs the same number of blocks (the count is agreed on first).
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def timed_block():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            for s in range(args.steps):
+                flush.fill_(s & 0xFF)
+                starts[s].record(stream)
+                batch.launch(ws, stream)
+                ends[s].record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+
+    probe_ms = timed_block()
+    n_blocks = max(1, min(400, int(math.ceil(args.min_timed_s * 1000.0 / max(probe_ms, 1e-3)))))
+    if world > 1:
+        n_blocks = int(max_over_ranks(float(n_blocks), dist, dev))
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for s in range(args.steps):
-            flush.fill_(s & 0xFF)
-            starts[s].record(stream)
-            batch.launch(ws, stream)
-            ends[s].record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    block_ms = [timed_block() for _ in range(n_blocks)]
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = sum(block_ms)
     if world > 1:
         total_ms = max_over_ranks(total_ms, dist, dev)
-    ms = total_ms / args.steps
+    ms = total_ms / (args.steps * n_blocks)
     value = args.batch * world / (ms / 1000.0)
 
     # end to end through the C ABI with host buffers: every step uploads the
@@ -752,25 +869,32 @@ def run_tnc(args):
     # 64-bit-result IMAD, two issue slots; clock = max SM clock
     alu_peak = sms * 4 * 16 / 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
     default_shape = args.batch == 8192 and args.planner == "best" and not args.launch
+    traffic, traffic_src = captured_traffic(C2_PROFILE, C2_KERNEL_SOURCES) if default_shape else \
+        (None, "captured for the default workload only")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 residues, int64 accumulate", "data": "synthetic",
         "config": config(args, world),
         "modular_macs_per_s": macs * world / (ms / 1000.0),
-        "roofline": {"bound": "alu", "achieved": achieved_macs / 1e12, "peak": alu_peak / 1e12,
-                     "unit": "Tmodmac/s", "frac": achieved_macs / alu_peak,
-                     "traffic": C2_TRAFFIC_BYTES_PER_LAUNCH if default_shape else None,
-                     "traffic_source": "ncu capture of this workload (profiles/batch_kernel_cubic_vc_n60_R4.md)"
-                     if default_shape else None,
-                     "peak_source": "derived: SMs x 64 IMAD lanes / 2 slots per 64-bit MAC x max SM clock",
-                     "measured_primitive_peak": probe / 1e12,
+        "roofline": {"bound": "alu", "achieved": achieved_macs / 1e12, "peak": probe / 1e12,
+                     "unit": "Tmodmac/s", "frac": achieved_macs / probe,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_source": "measured in this run: tnc_probe_modmac (4 residues per thread, u32 x u32 "
+                                    "products in 64-bit sums reduced every 16th product, operands in registers, "
+                                    "all SMs)",
+                     "derived_peak": alu_peak / 1e12, "frac_of_derived": achieved_macs / alu_peak,
+                     "derived_peak_source": "SMs x 64 IMAD lanes / 2 slots per 64-bit MAC x max SM clock",
                      "kernel": "batch_kernel<4>", "algorithmic_macs_per_launch": macs,
                      "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_s_vs_hbm": achieved_gbs / pk["hbm_gbs"]},
         "autotune": {"threads": tuned_threads, "smem_arena_bytes": tuned_smem, "ctas_per_sm_cap": tuned_ctas,
                      "seconds": tune_s},
         "clocks": clk,
-        "gpu_launches": kpl * args.steps,
+        "gpu_launches": kpl * args.steps * n_blocks,
+        "timing": {"blocks": n_blocks, "steps_per_block": args.steps, "timed_steps": n_blocks * args.steps,
+                   "device_ms_timed": sum(block_ms),
+                   "how": "blocks of K steps, each between barrier + synchronize, CUDA events per step on the "
+                          "launching stream, L2 flushed before every step; ms_per_step = all timed steps' mean"},
         "plan_s": plan_s,
         "wall_s_timed_region": wall,
     }
@@ -780,6 +904,12 @@ def run_tnc(args):
     done, el, threads = oracle_sample(forms, args.cpu_seconds)
     line["cpu_baseline"] = {"value": done / el, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": f"first {done} formulas of the workload ({el:.1f} s, C bigint oracle)"}
+    if not args.no_c4 and world == 1:
+        del ws, flush
+        torch.cuda.empty_cache()
+        blk = c4_block(args, dev, max(3, min(args.steps, 10)), 2, ["tc", "int64"])
+        blk["cpu_baseline"] = c4_cpu_baseline(dev)
+        line["c4"] = blk
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

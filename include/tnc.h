@@ -261,6 +261,10 @@ typedef struct {
   int32_t crt;            /* Chinese remaindering                                     */
 } tnc_launch_counts;
 int tnc_last_launch_counts(tnc_launch_counts* out);
+/* Bytes the calling thread's last tnc_contract or tnc_contract_sliced copied
+ * host -> device (descriptors, weight tables) and device -> host (residues,
+ * CRT limbs, status word). */
+int tnc_last_io_bytes(uint64_t* h2d_bytes, uint64_t* d2h_bytes);
 /* Contracts the plan on the GPU and returns the count(s) in `out` (host).
  * dev_ws: device buffer of at least tnc_workspace_bytes_opts(plan, opts) bytes
  * (= tnc_workspace_bytes(plan, R) on TNC_PATH_INT64 and TNC_PATH_TC), 256-byte

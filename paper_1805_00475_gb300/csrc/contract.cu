@@ -38,6 +38,7 @@ thread_local double g_dense_ms = 0.0;
 thread_local int g_dense_launches = 0;
 thread_local double g_total_ms = 0.0;
 thread_local tnc_launch_counts g_launches{};
+thread_local uint64_t g_h2d_bytes = 0, g_d2h_bytes = 0;  // host <-> device copies of the last contraction
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int sm_count() {
@@ -314,6 +315,12 @@ extern "C" int tnc_last_launch_counts(tnc_launch_counts* out) {
   return TNC_OK;
 }
 
+extern "C" int tnc_last_io_bytes(uint64_t* h2d_bytes, uint64_t* d2h_bytes) {
+  if (h2d_bytes) *h2d_bytes = g_h2d_bytes;
+  if (d2h_bytes) *d2h_bytes = g_d2h_bytes;
+  return TNC_OK;
+}
+
 extern "C" size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts* opts) {
   clear_error();
   Arith a;
@@ -368,6 +375,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   std::vector<LeafDesc> leaves = lw.leaves;
   for (size_t i = 0; i < leaves.size(); i++) leaves[i].off = lw.lvl_leaf_off[i];
   CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice, st));
+  g_h2d_bytes += leaves.size() * sizeof(LeafDesc) + lw.leaf_tables.size() * sizeof(uint32_t);
   if (!lw.leaf_tables.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, lw.leaf_tables.data(), lw.leaf_tables.size() * sizeof(uint32_t),
                              cudaMemcpyHostToDevice, st));
@@ -403,6 +411,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     small_hi.push_back((uint32_t)small.size());
     small_work.push_back(work);
   }
+  g_h2d_bytes += gsteps.size() * sizeof(GridStep) + small.size() * sizeof(StepDesc);
   if (!gsteps.empty())
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_steps, gsteps.data(), gsteps.size() * sizeof(GridStep), cudaMemcpyHostToDevice,
                              st));
@@ -415,6 +424,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
         for (int r = 0; r < a.R; r++)
           tc_make_step(lw.lvl_steps[i], a.primes[r], tcbuf.data() + ((size_t)slot[i] * a.R + r) * tc_step_bytes());
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
+    g_h2d_bytes += tcbuf.size();
   }
   // residue groups: limb tensor-core passes carry one residue per entry; the
   // 8-bit-prime path keeps groups of 4 and runs its dense steps per residue
@@ -539,6 +549,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     CUDA_TRY(cudaGetLastError());
     uint32_t h_err0 = 0;
     CUDA_TRY(cudaMemcpyAsync(&h_err0, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    g_d2h_bytes += sizeof(uint32_t);
     CUDA_TRY(cudaStreamSynchronize(st));
     if (h_err0) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
     return TNC_OK;
@@ -554,6 +565,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   std::vector<uint32_t> h_res(L.n_out * a.R), h_limbs(L.n_out * a.crt.n_limbs);
   CUDA_TRY(cudaMemcpyAsync(h_res.data(), results, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
+  g_d2h_bytes += sizeof(uint32_t) + (h_res.size() + h_limbs.size()) * 4;
   CUDA_TRY(cudaStreamSynchronize(st));
   if (h_err) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
   for (size_t e = 0; e + 1 < dense_events.size(); e += 2) {  // pair 0: the whole contraction
@@ -573,6 +585,7 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
                             void* cuda_stream, tnc_count* out) {
   clear_error();
   g_launches = tnc_launch_counts{};
+  g_h2d_bytes = g_d2h_bytes = 0;
   return contract_core(plan, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
 }
 
@@ -598,6 +611,7 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
                                    void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* out) {
   clear_error();
   g_launches = tnc_launch_counts{};
+  g_h2d_bytes = g_d2h_bytes = 0;
   if (!plans || n <= 0 || !out || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
   Arith a;
   int rc = make_arith(opts, a);
@@ -630,6 +644,7 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
   std::vector<uint32_t> h_res(n_out * a.R), h_limbs(n_out * a.crt.n_limbs);
   CUDA_TRY(cudaMemcpyAsync(h_res.data(), acc, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
+  g_d2h_bytes += (h_res.size() + h_limbs.size()) * 4;
   CUDA_TRY(cudaStreamSynchronize(st));
   return fill_count(out, n_out, a, h_res.data(), h_limbs.data(), bound >= a.log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u);
 }

@@ -31,7 +31,7 @@ TNC_MAYBE_WRAPPED = 1
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -131,6 +131,7 @@ def lib():
             "tnc_last_dense_time": ([ctypes.POINTER(ctypes.c_double), i32p], ctypes.c_int),
             "tnc_last_contract_time": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_last_launch_counts": ([ctypes.POINTER(_LaunchCounts)], ctypes.c_int),
+            "tnc_last_io_bytes": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "tnc_workspace_bytes_sliced": ([vp, i32, vp], sz),
             "tnc_contract_sliced": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
@@ -420,6 +421,13 @@ def last_launch_counts() -> dict:
     d = {n: int(getattr(c, n)) for n, _ in _LaunchCounts._fields_ if n != "p8_tile_n"}
     d["p8_tile_n"] = {w: int(c.p8_tile_n[i]) for i, w in enumerate(P8_TILE_WIDTHS)}
     return d
+
+
+def last_io_bytes() -> Tuple[int, int]:
+    """tnc_last_io_bytes: (host->device, device->host) bytes of the last contraction."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().tnc_last_io_bytes(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def contract_sliced(plans: Sequence[Plan], n_residues: int = 4, primes=None, workspace=None, stream=None,
