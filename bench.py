@@ -473,8 +473,8 @@ def run_slicing(args):
         whole = tnc.plan_formula(f, heuristic="best", rank_cap=30)
         cases = [("whole", [whole], [])]
         for s in range(1, 5):
-            vs = S.choose_slice_vars(f, s)
-            cases.append((f"s={s}", S.sliced_plans(f, vs)[0], vs))
+            plans_s, vs = S.sliced_plans(f, s)
+            cases.append((f"s={s}", plans_s, vs))
         ref = None
         for name, plans, vs in cases:
             if name == "whole":

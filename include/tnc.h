@@ -65,6 +65,7 @@ extern "C" {
 #define TNC_PLAN_GN 2       /* tensor-GN: Girvan-Newman community dendrogram      */
 #define TNC_PLAN_EXPLICIT 3 /* caller-given pairwise order                        */
 #define TNC_PLAN_BEST 4     /* run GREEDY, BISECT and GN; keep the cheapest       */
+#define TNC_PLAN_PORTFOLIO 5 /* GREEDY, GN and BISECT with 8 seeds; the cheapest   */
 
 /* ---- arithmetic paths ---------------------------------------------------- */
 #define TNC_PATH_INT64 0 /* CUDA cores: u32 residues, 64-bit multiply-accumulate */
@@ -205,6 +206,35 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
  * tnc_last_error(). */
 int tnc_plan_many(const tnc_network_t* const* nets, int32_t n, const tnc_plan_opts* opts,
                   tnc_plan_t** out, tnc_plan_stats* stats);
+/* Bond slicing (memory is the method's bottleneck, Sec. 4): chooses s
+ * variables of the network (not open ones) and plans the 2^s slices, the
+ * networks with those variables fixed (Eq. z's trace split by their values;
+ * the fixed COPY tensors leave, the clause tensors on their bonds become
+ * tables over their other bonds).  Variables are added one at a time: each
+ * round scores the variables on the tensors of largest rank of the current
+ * plan by the exact cost of their slices (max rank, then total MACs; the
+ * lazy evaluation of Sec. 4), each planned by `opts` and by the current plan
+ * restricted to the slice, the cheaper kept (so the max rank never grows with
+ * s).  Slice j fixes vars_out[i] = bit i of j; all slices share one tree.
+ *   out: host array of 2^s plan handles (freed with tnc_free_plan);
+ *   vars_out: s variables; stats: 2^s entries or NULL.
+ * All or nothing on failure.  The count is the sum of the slices' counts
+ * (tnc_contract_sliced). */
+int tnc_plan_sliced(const tnc_network_t* net, int32_t s, const tnc_plan_opts* opts, tnc_plan_t** out,
+                    int32_t* vars_out, tnc_plan_stats* stats);
+/* The network of one slice: variables vars[i] fixed to bit i of `bits` (the
+ * restriction tnc_plan_sliced applies; for inspection and for callers that
+ * plan slices themselves).  Fixed variables leave and the others are
+ * renumbered in order.  Open variables cannot be fixed (TNC_ERR_INVALID). */
+int tnc_slice_network(const tnc_network_t* net, int32_t s, const int32_t* vars, uint32_t bits,
+                      tnc_network_t** out);
+/* The formula a network encodes (clause kinds as built: a clause restricted
+ * by slicing is a TABLE).  Call once with the array pointers NULL for the
+ * sizes (clauses, occurrences = sum of arities, table entries, open
+ * variables), then with arrays of those sizes. */
+int tnc_network_formula(const tnc_network_t* net, int32_t* n_vars, int32_t* n_cons, int32_t* n_occ,
+                        int32_t* n_table, int32_t* n_open, int32_t* arity, int32_t* var_of, uint8_t* kind,
+                        uint32_t* table, int32_t* open_vars);
 /* Contraction tree as pairs: for step i, the tensor ids it merges (ids as in
  * tnc_plan_opts.order).  left/right: host arrays of n_steps entries. */
 int tnc_plan_steps(const tnc_plan_t* plan, int32_t* left, int32_t* right, int32_t cap);

@@ -629,6 +629,23 @@ int plan_tree(const Network& net, const tnc_plan_opts& o, Tree& t) {
       t = std::move(cand[best]);
       return TNC_OK;
     }
+    case TNC_PLAN_PORTFOLIO: {
+      // tensor-greedy, tensor-GN and 8 independently seeded tensor-METIS
+      // runs; the cheapest exact cost (max rank, then MACs) is kept
+      plan_greedy(net, t);
+      TreeCost bc = tree_cost(t);
+      for (int i = 0; i < 9; i++) {
+        Tree c;
+        if (i == 0) plan_gn(net, c);
+        else plan_bisect(net, o.tries > 0 ? o.tries : 2, o.seed + 0x9E3779B97F4A7C15ull * (uint64_t)i, c);
+        const TreeCost cc = tree_cost(c);
+        if (cc.max_rank < bc.max_rank || (cc.max_rank == bc.max_rank && cc.macs < bc.macs)) {
+          bc = cc;
+          t = std::move(c);
+        }
+      }
+      return TNC_OK;
+    }
   }
   return set_error(TNC_ERR_INVALID, "unknown heuristic");
 }

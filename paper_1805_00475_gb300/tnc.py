@@ -24,14 +24,14 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libtnc.so")
 TNC_OK = 0
 ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4: "TNC_ERR_BUFFER",
           -5: "TNC_ERR_TIMEOUT", -6: "TNC_ERR_NOMEM"}
-HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4}
+HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4, "portfolio": 5}
 PATHS = {"int64": 0, "tc": 1, "tc_p8": 2}
 TNC_MAYBE_WRAPPED = 1
 
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_sliced", "tnc_slice_network", "tnc_network_formula", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
     "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
@@ -124,6 +124,11 @@ def lib():
             "tnc_plan_many": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp),
                                ctypes.POINTER(_PlanStats)], ctypes.c_int),
             "tnc_plan_steps": ([vp, i32p, i32p, i32], ctypes.c_int),
+            "tnc_plan_sliced": ([vp, i32, ctypes.POINTER(_PlanOpts), ctypes.POINTER(vp), i32p,
+                                 ctypes.POINTER(_PlanStats)], ctypes.c_int),
+            "tnc_slice_network": ([vp, i32, i32p, ctypes.c_uint32, ctypes.POINTER(vp)], ctypes.c_int),
+            "tnc_network_formula": ([vp, i32p, i32p, i32p, i32p, i32p, i32p, i32p, ctypes.POINTER(ctypes.c_uint8),
+                                     u32p, i32p], ctypes.c_int),
             "tnc_free_plan": ([vp], None),
             "tnc_workspace_bytes": ([vp, i32], sz),
             "tnc_workspace_bytes_opts": ([vp, vp], sz),
@@ -311,6 +316,69 @@ def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: in
     o = _PlanOpts(HEURISTICS[heuristic], rank_cap, tries, seed, _p(ordr, ctypes.c_int32), 0)
     _check(lib().tnc_plan_many(arr, n, ctypes.byref(o), outs, sts))
     return [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), len(formulas[i].open_vars)) for i in range(n)]
+
+
+def plan_sliced(formula, s: int, heuristic: str = "best", rank_cap: int = 64, tries: int = 2, seed: int = 0
+                ) -> Tuple[List[Plan], List[int]]:
+    """tnc_plan_sliced: the s variables the library chooses and the plans of
+    the 2^s slices (slice j fixes vars[i] = bit i of j)."""
+    net = build_network(formula)
+    n = 1 << s
+    outs = (ctypes.c_void_p * n)()
+    sts = (_PlanStats * n)()
+    vs = np.zeros(max(s, 1), dtype=np.int32)
+    ordr = np.zeros(1, dtype=np.int32)
+    o = _PlanOpts(HEURISTICS[heuristic], rank_cap, tries, seed, _p(ordr, ctypes.c_int32), 0)
+    _check(lib().tnc_plan_sliced(net.h, s, ctypes.byref(o), outs, _p(vs, ctypes.c_int32), sts))
+    n_open = len(formula.open_vars)
+    return [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), n_open) for i in range(n)], [int(v) for v in vs[:s]]
+
+
+class FormulaView:
+    """A formula read back from a network (tnc_network_formula): the
+    attributes the oracle and the instance generators use."""
+
+    def __init__(self, n_vars, clauses, kinds, tables, open_vars):
+        self.n_vars, self.clauses, self.kinds, self.tables, self.open_vars = n_vars, clauses, kinds, tables, open_vars
+        self.n_cons = len(clauses)
+        self.name = "network"
+
+
+def network_formula(net: Network) -> FormulaView:
+    a = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().tnc_network_formula(net.h, *[ctypes.byref(x) for x in a], None, None, None, None, None))
+    nv, nc, nocc, ntab, nopen = [x.value for x in a]
+    arity = np.zeros(max(nc, 1), dtype=np.int32)
+    var_of = np.zeros(max(nocc, 1), dtype=np.int32)
+    kind = np.zeros(max(nc, 1), dtype=np.uint8)
+    table = np.zeros(max(ntab, 1), dtype=np.uint32)
+    opens = np.zeros(max(nopen, 1), dtype=np.int32)
+    _check(lib().tnc_network_formula(net.h, *[ctypes.byref(x) for x in a], _p(arity, ctypes.c_int32),
+                                     _p(var_of, ctypes.c_int32), _p(kind, ctypes.c_uint8), _p(table, ctypes.c_uint32),
+                                     _p(opens, ctypes.c_int32)))
+    clauses, kinds, tables, o, t = [], [], [], 0, 0
+    for c in range(nc):
+        clauses.append(tuple(int(v) for v in var_of[o:o + arity[c]]))
+        o += int(arity[c])
+        kinds.append(int(kind[c]))
+        if kind[c] == 3:
+            tables.append([int(x) for x in table[t:t + (1 << int(arity[c]))]])
+            t += 1 << int(arity[c])
+        else:
+            tables.append(None)
+    return FormulaView(nv, clauses, kinds, tables, [int(v) for v in opens[:nopen]])
+
+
+def slice_network(formula, fixed: dict) -> FormulaView:
+    """tnc_slice_network: the formula of the slice with the variables of
+    `fixed` set to their values (read back through tnc_network_formula)."""
+    net = build_network(formula)
+    vs = list(fixed)
+    bits = sum((int(fixed[v]) & 1) << i for i, v in enumerate(vs))
+    arr = np.array(vs or [0], dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().tnc_slice_network(net.h, len(vs), _p(arr, ctypes.c_int32), bits, ctypes.byref(h)))
+    return network_formula(Network(h))
 
 
 def plan_formula(formula, **kw) -> Plan:

@@ -52,11 +52,63 @@ def test_fixed_variables_leave_the_network():
 def test_slicing_lowers_the_rank_of_a_large_network():
     f = I.cubic_vertex_cover(180, 3)
     full = tnc.plan_formula(f, heuristic="best", rank_cap=40)
-    vs = S.choose_slice_vars(f, 3)
-    plans, forms = S.sliced_plans(f, vs)
+    plans, vs = S.sliced_plans(f, 3)
     assert len(plans) == 8 and len(set(vs)) == 3
     assert max(p.stats.max_rank for p in plans) <= full.stats.max_rank - 2
     assert max(p.stats.arena_entries for p in plans) * 4 <= full.stats.arena_entries
+
+
+@pytest.mark.parametrize("seed", [3, 15])
+def test_slicing_cost_never_grows_with_s(seed):
+    """Each added slice variable is chosen by the exact plan cost of its
+    slices (the current plan restricted to a slice is always a candidate):
+    the max rank and the total MACs of all slices do not grow with s."""
+    f = I.cubic_vertex_cover(180, seed)
+    prev = None
+    for s in range(5):
+        plans, vs = S.sliced_plans(f, s)
+        assert len(plans) == 2 ** s and len(set(vs)) == s
+        cost = (max(p.stats.max_rank for p in plans), sum(p.stats.total_macs for p in plans))
+        if prev is not None:
+            assert cost[0] <= prev[0] and cost[1] <= prev[1] * (1 + 1e-12), (s, cost, prev)
+        prev = cost
+
+
+def test_library_slices_match_the_definition():
+    """tnc_slice_network's restricted clause tables, read back, are the clause
+    tensors with the fixed bonds set (checked entry by entry against the
+    definitions of Eq. 1in3, Eq. or and NAND)."""
+    rng = random.Random(5)
+    f = random_formula(rng, 10, 8)
+    g = S.slice_formula(f, {2: 1, 5: 0})
+    keep = [v for v in range(f.n_vars) if v not in (2, 5)]
+    assert g.n_vars == 8 and len(g.clauses) == len(f.clauses)
+    fixed = {2: 1, 5: 0}
+    for c, k, t, gc, gk, gt in zip(f.clauses, f.kinds, f.tables, g.clauses, g.kinds, g.tables):
+        free = [v for v in c if v not in fixed]
+        assert list(gc) == [keep.index(v) for v in free]
+        if len(free) == len(c):
+            assert gk == k
+            continue
+        assert gk == I.KIND_TABLE
+        for j in range(1 << len(free)):
+            val = dict(fixed)
+            val.update({v: (j >> i) & 1 for i, v in enumerate(free)})
+            idx = sum(val[v] << i for i, v in enumerate(c))
+            ones = bin(idx).count("1")
+            want = {I.KIND_1IN3: int(ones == 1), I.KIND_OR: int(idx != 0),
+                    I.KIND_NAND: int(idx != (1 << len(c)) - 1)}.get(k, None)
+            assert gt[j] == (t[idx] if k == I.KIND_TABLE else want)
+
+
+def test_library_rejects_slicing_an_open_variable():
+    f = I.one_in_three(16, 10, 3)
+    f.open_vars = [4]
+    arr = tnc.np.array([4], dtype=tnc.np.int32)
+    h = tnc.ctypes.c_void_p()
+    net = tnc.build_network(f)
+    rc = tnc.lib().tnc_slice_network(net.h, 1, tnc._p(arr, tnc.ctypes.c_int32), 0, tnc.ctypes.byref(h))
+    assert rc == -1
 
 
 def test_random_planar_cubic_graphs():
