@@ -303,6 +303,25 @@ int tnc_last_io_bytes(uint64_t* h2d_bytes, uint64_t* d2h_bytes);
 int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws,
                  size_t ws_bytes, void* cuda_stream, tnc_count* out);
 
+/* ---- host combine of residues from several processes ---------------------
+ * A count can be shared out over processes (one GPU each) without any device
+ * collective: each process counts modulo its own subset of the primes (the
+ * residues are independent), or contracts its own subset of the slices of a
+ * sliced network; the small residue arrays are gathered to one host, which
+ * adds the slices' residues and rebuilds the exact count (Sec. 3.2: exact
+ * counts need more than machine words; the paper leaves distributed
+ * contraction as a prospect, Sec. 4).  Host memory only, no device work. */
+/* Garner's mixed-radix CRT: residues [n][R] (entry e's residue mod primes[r]
+ * at e R + r) -> little-endian u32 limbs [n][cap_limbs] of the value in
+ * [0, prod p).  *n_limbs (may be NULL) receives the limbs needed;
+ * TNC_ERR_BUFFER if cap_limbs is smaller.  Primes: distinct odd primes below
+ * 2^31, any order. */
+int tnc_crt_host(const uint32_t* primes, int32_t R, const uint32_t* residues, int64_t n, uint32_t* limbs,
+                 int32_t cap_limbs, int32_t* n_limbs);
+/* acc[e R + r] = (acc[e R + r] + src[e R + r]) mod primes[r] for n entries
+ * (the sum of slices' counts, residue by residue). */
+int tnc_residue_add_host(const uint32_t* primes, int32_t R, uint32_t* acc, const uint32_t* src, int64_t n);
+
 /* ---- batches: many formulas in one persistent launch -------------------- */
 /* Packs the plans into compact descriptors in pinned host memory and picks a
  * default launch shape for the current device.  The plans must outlive the
@@ -336,6 +355,10 @@ int tnc_batch_autotune(tnc_batch_t* b, void* dev_ws, void* cuda_stream, int32_t*
  * CTA size, TNC_ERR_TOO_LARGE if the CTA does not fit on an SM.  Host only: no
  * device work is queued. */
 int tnc_batch_set_launch(tnc_batch_t* b, int32_t threads, int32_t smem_bytes, int32_t ctas_per_sm);
+/* The current launch shape (after tnc_batch_autotune: the one it chose), to be
+ * kept by the caller and given back with tnc_batch_set_launch.  Any out pointer
+ * may be NULL. */
+int tnc_batch_get_launch(const tnc_batch_t* b, int32_t* threads, int32_t* smem_bytes, int32_t* ctas_per_sm);
 /* Device -> host copy of the results; synchronises the stream.  outs: n counts. */
 int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs);
 /* Bulk form of tnc_batch_download: residues [E][R] and CRT limbs
@@ -369,6 +392,12 @@ int tnc_contract_batch(const tnc_plan_t* const* plans, int32_t n, const tnc_cont
 
 /* He-initialised parameters (host, TNC_MLP_PARAMS floats). */
 int tnc_mlp_init(uint64_t seed, float* params);
+/* Trained parameters to and from a file (host fp32, TNC_MLP_PARAMS floats):
+ * magic, layout (features, hidden width, count) and a checksum are written
+ * and checked; a file of another layout or a damaged one is refused
+ * (TNC_ERR_INVALID) and params is left untouched. */
+int tnc_learned_save(const char* path, const float* params);
+int tnc_learned_load(const char* path, float* params);
 /* Training rows: at `states` random points of an exploring tensor-greedy
  * trajectory of every network, each of its (at most `cands`) cheapest
  * candidate merges gets 16 features (x, host [rows][16]) and its regret
@@ -430,6 +459,22 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
  * steps bound by the integer pipes.  `iters` loop trips per thread (16 MACs each).
  * Allocates an 8-byte device counter with cudaMallocAsync; synchronises. */
 int tnc_probe_modmac(void* cuda_stream, int32_t iters, double* macs_per_s);
+
+/* ---- fault injection (host side; the paper has no counterpart) ----------
+ * Arms one failure: the (after+1)-th later call site of the given kind, in
+ * any thread, fails as described, and the injection disarms itself.  No
+ * device fault is ever made: LAUNCH fails before the call's first device
+ * call, TIMEOUT after the call's device work has completed (the status word a
+ * bounded device wait would have set).  TNC_INJECT_NONE disarms. */
+#define TNC_INJECT_NONE 0
+#define TNC_INJECT_NOMEM 1   /* tnc_build_network / tnc_plan / tnc_batch_create:
+                                host allocation fails -> TNC_ERR_NOMEM            */
+#define TNC_INJECT_PLAN 2    /* tnc_plan (also inside tnc_plan_many) -> TNC_ERR_TOO_LARGE */
+#define TNC_INJECT_LAUNCH 3  /* tnc_contract / _sliced / _noalloc / tnc_batch_launch
+                                -> TNC_ERR_CUDA, nothing enqueued                  */
+#define TNC_INJECT_TIMEOUT 4 /* tnc_contract / _sliced: the device status reads as a
+                                timed-out wait -> TNC_ERR_TIMEOUT                  */
+int tnc_inject_failure(int32_t kind, int32_t after);
 
 /* ---- allocation-free variant (the paper has no counterpart) --------------
  * The counts of tnc_contract on TNC_PATH_INT64 (the only path it takes: other

@@ -23,7 +23,7 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libtnc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-HOST_SRC = ["network.cpp", "planner.cpp", "lower.cpp", "learned.cpp", "slicing.cpp", "abi_host.cpp"]
+HOST_SRC = ["network.cpp", "planner.cpp", "lower.cpp", "learned.cpp", "slicing.cpp", "combine.cpp", "inject.cpp", "abi_host.cpp"]
 CUDA_SRC = ["contract.cu", "probe.cu", "tc.cu", "tc_p8.cu", "mlp.cu"]
 HEADERS = ["tnc_internal.h", "step_desc.h", "kernels.cuh", "modarith.cuh"]
 

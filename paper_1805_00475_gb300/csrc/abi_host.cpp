@@ -1,6 +1,7 @@
 // C ABI, host-only half: library info, networks and plans.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 
@@ -94,6 +95,7 @@ int tnc_build_network(const tnc_formula* f, tnc_network_t** out) {
   if (!out) return set_error(TNC_ERR_INVALID, "out is NULL");
   *out = nullptr;
   try {
+    if (inject_hit(TNC_INJECT_NOMEM)) throw std::bad_alloc();
     auto* h = new tnc_network_t();
     int rc = build_network(f, h->net);
     if (rc != TNC_OK) {
@@ -125,9 +127,12 @@ int tnc_plan(const tnc_network_t* net, const tnc_plan_opts* opts, tnc_plan_t** o
   if (!net || !opts || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
   *out = nullptr;
   try {
+    if (inject_hit(TNC_INJECT_NOMEM)) throw std::bad_alloc();
     auto* p = new tnc_plan_t();
     p->net = net->net;
     int rc = plan_tree(p->net, *opts, p->tree);
+    if (rc == TNC_OK && inject_hit(TNC_INJECT_PLAN))
+      rc = set_error(TNC_ERR_TOO_LARGE, "injected failure (TNC_INJECT_PLAN)");
     if (rc == TNC_OK) rc = finish_plan(p, opts->rank_cap, stats);
     if (rc != TNC_OK) {
       delete p;
@@ -188,6 +193,54 @@ int tnc_plan_steps(const tnc_plan_t* plan, int32_t* left, int32_t* right, int32_
 }
 
 void tnc_free_plan(tnc_plan_t* plan) { delete plan; }
+
+// Scorer parameter files: "TNCMLP01", then u32 features, hidden width and
+// parameter count, the fp32 parameters, and a 64-bit FNV-1a checksum of all
+// the bytes before it (little-endian throughout).
+static uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h = 0xCBF29CE484222325ull) {
+  for (size_t i = 0; i < n; i++) {
+    h ^= p[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+
+int tnc_learned_save(const char* path, const float* params) {
+  clear_error();
+  if (!path || !params) return set_error(TNC_ERR_INVALID, "NULL argument");
+  std::vector<unsigned char> buf(8 + 12 + sizeof(float) * TNC_MLP_PARAMS);
+  std::memcpy(buf.data(), "TNCMLP01", 8);
+  const uint32_t hdr[3] = {TNC_MLP_FEATURES, TNC_MLP_HIDDEN, TNC_MLP_PARAMS};
+  std::memcpy(buf.data() + 8, hdr, 12);
+  std::memcpy(buf.data() + 20, params, sizeof(float) * TNC_MLP_PARAMS);
+  const uint64_t sum = fnv1a(buf.data(), buf.size());
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return set_error(TNC_ERR_INVALID, std::string("cannot open ") + path + " for writing");
+  const bool ok = std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size() && std::fwrite(&sum, 8, 1, fp) == 1;
+  if (std::fclose(fp) != 0 || !ok) return set_error(TNC_ERR_INVALID, std::string("write failed: ") + path);
+  return TNC_OK;
+}
+
+int tnc_learned_load(const char* path, float* params) {
+  clear_error();
+  if (!path || !params) return set_error(TNC_ERR_INVALID, "NULL argument");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return set_error(TNC_ERR_INVALID, std::string("cannot open ") + path);
+  std::vector<unsigned char> buf(8 + 12 + sizeof(float) * TNC_MLP_PARAMS);
+  uint64_t sum = 0;
+  const bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size() && std::fread(&sum, 8, 1, fp) == 1 &&
+                  std::fgetc(fp) == EOF;
+  std::fclose(fp);
+  if (!ok) return set_error(TNC_ERR_INVALID, std::string("truncated or oversized parameter file: ") + path);
+  uint32_t hdr[3];
+  std::memcpy(hdr, buf.data() + 8, 12);
+  if (std::memcmp(buf.data(), "TNCMLP01", 8) != 0 || hdr[0] != TNC_MLP_FEATURES || hdr[1] != TNC_MLP_HIDDEN ||
+      hdr[2] != TNC_MLP_PARAMS)
+    return set_error(TNC_ERR_INVALID, "not a scorer parameter file of this layout");
+  if (fnv1a(buf.data(), buf.size()) != sum) return set_error(TNC_ERR_INVALID, "parameter file checksum mismatch");
+  std::memcpy(params, buf.data() + 20, sizeof(float) * TNC_MLP_PARAMS);
+  return TNC_OK;
+}
 
 int tnc_mlp_init(uint64_t seed, float* params) {
   clear_error();

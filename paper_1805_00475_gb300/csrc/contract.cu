@@ -3,6 +3,7 @@
 #include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -31,6 +32,15 @@ namespace {
   } while (0)
 
 constexpr size_t kAlign = 256;
+
+// An NVTX range for profilers (nvtx is header-only and costs nothing when no
+// tool is attached): whole calls, tree levels, dense steps, batch launches.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Dense-step timing of tnc_contract (off unless tnc_set_step_timing(1)).
 thread_local bool g_time_dense = false;
@@ -365,6 +375,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   }
   if (!dev_ws || ws_bytes < L.total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_workspace_bytes");
   if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
+  if (inject_hit(TNC_INJECT_LAUNCH)) return set_error(TNC_ERR_CUDA, "injected failure (TNC_INJECT_LAUNCH)");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   char* ws = (char*)dev_ws;
   // The contraction runs level by level (the tree-level schedule of the
@@ -482,6 +493,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
       g_launches.leaf_fill++;
       for (size_t l = 0; l < small_lo.size(); l++) {
+        NvtxRange level_range("tnc level");
         const uint32_t n_small = small_hi[l] - small_lo[l];
         if (n_small) {
           const uint32_t w = small_work[l];
@@ -492,6 +504,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
         for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
           if (kind[i] == kSmall) continue;
           if (kind[i] == kTc) {
+            NvtxRange dense_range("tnc dense step");
             if (RG != 1 && !p8) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
             int rc2 = TNC_OK;
             cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -551,6 +564,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     CUDA_TRY(cudaMemcpyAsync(&h_err0, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     g_d2h_bytes += sizeof(uint32_t);
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (inject_hit(TNC_INJECT_TIMEOUT)) h_err0 = 1;
     if (h_err0) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
     return TNC_OK;
   }
@@ -567,6 +581,7 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   CUDA_TRY(cudaMemcpyAsync(h_limbs.data(), limbs, h_limbs.size() * 4, cudaMemcpyDeviceToHost, st));
   g_d2h_bytes += sizeof(uint32_t) + (h_res.size() + h_limbs.size()) * 4;
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (inject_hit(TNC_INJECT_TIMEOUT)) h_err = 1;
   if (h_err) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
   for (size_t e = 0; e + 1 < dense_events.size(); e += 2) {  // pair 0: the whole contraction
     float ms = 0.f;
@@ -586,6 +601,7 @@ extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opt
   clear_error();
   g_launches = tnc_launch_counts{};
   g_h2d_bytes = g_d2h_bytes = 0;
+  NvtxRange range("tnc_contract");
   return contract_core(plan, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
 }
 
@@ -612,6 +628,7 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
   clear_error();
   g_launches = tnc_launch_counts{};
   g_h2d_bytes = g_d2h_bytes = 0;
+  NvtxRange range("tnc_contract_sliced");
   if (!plans || n <= 0 || !out || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
   Arith a;
   int rc = make_arith(opts, a);
@@ -1010,6 +1027,7 @@ extern "C" int tnc_batch_create(const tnc_plan_t* const* plans, int32_t n, const
   if (!plans || n <= 0 || !out) return set_error(TNC_ERR_INVALID, "bad batch arguments");
   *out = nullptr;
   try {
+    if (inject_hit(TNC_INJECT_NOMEM)) throw std::bad_alloc();
     auto* b = new tnc_batch_t();
     int rc = make_arith(opts, b->a);
     if (!rc && opts->path == TNC_PATH_TC_P8)
@@ -1059,6 +1077,8 @@ extern "C" int tnc_batch_upload(tnc_batch_t* b, void* dev_ws, size_t ws_bytes, v
 extern "C" int tnc_batch_launch(tnc_batch_t* b, void* dev_ws, void* cuda_stream) {
   clear_error();
   if (!b || !dev_ws) return set_error(TNC_ERR_INVALID, "NULL argument");
+  if (inject_hit(TNC_INJECT_LAUNCH)) return set_error(TNC_ERR_CUDA, "injected failure (TNC_INJECT_LAUNCH)");
+  NvtxRange range("tnc_batch_launch");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (st == nullptr) return batch_enqueue(b, dev_ws, st);  // legacy stream: cannot capture
   if (b->gexec && (b->g_ws != dev_ws || b->g_stream != st)) {
@@ -1160,6 +1180,16 @@ extern "C" int tnc_batch_set_launch(tnc_batch_t* b, int32_t threads, int32_t sme
   if (smem_bytes < 0 || (size_t)smem_bytes + b->max_blob > kSmemMax)
     return set_error(TNC_ERR_TOO_LARGE, "shared-memory arena too large");
   return batch_configure(b, threads, (size_t)smem_bytes, ctas_per_sm);
+}
+
+extern "C" int tnc_batch_get_launch(const tnc_batch_t* b, int32_t* threads, int32_t* smem_bytes,
+                                    int32_t* ctas_per_sm) {
+  clear_error();
+  if (!b) return set_error(TNC_ERR_INVALID, "NULL argument");
+  if (threads) *threads = b->threads;
+  if (smem_bytes) *smem_bytes = (int32_t)b->smem_bytes;
+  if (ctas_per_sm) *ctas_per_sm = b->cta_cap;
+  return TNC_OK;
 }
 
 extern "C" int tnc_batch_download(tnc_batch_t* b, const void* dev_ws, void* cuda_stream, tnc_count* outs) {
@@ -1286,6 +1316,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
                                     tnc_count* out) {
   clear_error();
   g_launches = tnc_launch_counts{};
+  NvtxRange range("tnc_contract_noalloc");
   if (!plan || !opts || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
   if (opts->path != TNC_PATH_INT64)
     return set_error(TNC_ERR_INVALID, "tnc_contract_noalloc supports TNC_PATH_INT64 only");
@@ -1350,6 +1381,7 @@ extern "C" int tnc_contract_noalloc(const tnc_plan_t* plan, const tnc_contract_o
     return set_error(TNC_ERR_TOO_LARGE, "plan needs " + std::to_string(L.total) +
                                             " bytes of scratch; tnc_contract_noalloc holds " +
                                             std::to_string((size_t)TNC_NOALLOC_SCRATCH_BYTES));
+  if (inject_hit(TNC_INJECT_LAUNCH)) return set_error(TNC_ERR_CUDA, "injected failure (TNC_INJECT_LAUNCH)");
   void* base = nullptr;
   int rc = noalloc_base(&base);
   if (rc) return rc;

@@ -103,6 +103,10 @@ void clear_error();
 // (tnc_last_launch_counts); contract.cu resets it per call.
 tnc_launch_counts& launch_counts();
 
+// Fault injection (inject.cpp): true if an armed failure of this kind fires
+// at this call site (tnc_inject_failure).
+bool inject_hit(int kind);
+
 // network.cpp
 int build_network(const tnc_formula* f, Network& out);
 

@@ -27,14 +27,16 @@ ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4
 HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4, "portfolio": 5}
 PATHS = {"int64": 0, "tc": 1, "tc_p8": 2}
 TNC_MAYBE_WRAPPED = 1
+INJECT = {"none": 0, "nomem": 1, "plan": 2, "launch": 3, "timeout": 4}
 
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
     "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_sliced", "tnc_slice_network", "tnc_network_formula", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
-    "tnc_contract", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch",
+    "tnc_contract", "tnc_crt_host", "tnc_residue_add_host", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch", "tnc_batch_get_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
-    "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac",
+    "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac", "tnc_inject_failure", "tnc_learned_save",
+    "tnc_learned_load",
     "tnc_mlp_init", "tnc_learned_dataset", "tnc_learned_dataset_on_policy", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
     "tnc_mlp_backward", "tnc_mlp_adam", "tnc_mlp_train_workspace_bytes", "tnc_mlp_train", "tnc_mlp_to_bf16",
     "tnc_mlp_forward_bf16", "tnc_plan_learned_workspace_bytes", "tnc_plan_learned_many",
@@ -143,6 +145,8 @@ def lib():
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
                                  ctypes.c_int),
+            "tnc_crt_host": ([u32p, i32, u32p, ctypes.c_int64, u32p, i32, i32p], ctypes.c_int),
+            "tnc_residue_add_host": ([u32p, i32, u32p, u32p, ctypes.c_int64], ctypes.c_int),
             "tnc_batch_workspace_bytes": ([vp], sz),
             "tnc_batch_info": ([vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_uint64),
                                 i32p], ctypes.c_int),
@@ -150,6 +154,10 @@ def lib():
             "tnc_batch_launch": ([vp, vp, vp], ctypes.c_int),
             "tnc_batch_autotune": ([vp, vp, vp, i32p, i32p, i32p], ctypes.c_int),
             "tnc_batch_set_launch": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+            "tnc_batch_get_launch": ([vp, i32p, i32p, i32p], ctypes.c_int),
+            "tnc_inject_failure": ([i32, i32], ctypes.c_int),
+            "tnc_learned_save": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "tnc_learned_load": ([ctypes.c_char_p, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "tnc_batch_download": ([vp, vp, vp, ctypes.POINTER(_Count)], ctypes.c_int),
             "tnc_batch_download_flat": ([vp, vp, vp, u32p, u32p, u32p], ctypes.c_int),
             "tnc_batch_status": ([vp, vp, vp], ctypes.c_int),
@@ -514,6 +522,28 @@ def contract_sliced(plans: Sequence[Plan], n_residues: int = 4, primes=None, wor
     return _to_count(c, res, limbs, pr)
 
 
+def crt_host(primes: Sequence[int], residues) -> List[int]:
+    """tnc_crt_host: exact values in [0, prod p) from residues [n, R] (host)."""
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    res = np.ascontiguousarray(np.asarray(residues, dtype=np.uint32).reshape(-1, len(pr)))
+    need = ctypes.c_int32()
+    cap = int(sum(np.log2(pr.astype(np.float64))) // 32) + 1
+    limbs = np.zeros((max(res.shape[0], 1), cap), dtype=np.uint32)
+    _check(lib().tnc_crt_host(_p(pr, ctypes.c_uint32), len(pr), _p(res, ctypes.c_uint32), res.shape[0],
+                              _p(limbs, ctypes.c_uint32), cap, ctypes.byref(need)))
+    return Batch.counts_from_limbs(limbs[: res.shape[0]])
+
+
+def residue_add_host(primes: Sequence[int], acc: np.ndarray, src: np.ndarray) -> np.ndarray:
+    """tnc_residue_add_host: acc = (acc + src) mod primes, residue by residue (in place)."""
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    assert acc.dtype == np.uint32 and acc.flags.c_contiguous and acc.shape == src.shape
+    s = np.ascontiguousarray(src, dtype=np.uint32)
+    _check(lib().tnc_residue_add_host(_p(pr, ctypes.c_uint32), len(pr), _p(acc, ctypes.c_uint32),
+                                      _p(s, ctypes.c_uint32), acc.size // len(pr)))
+    return acc
+
+
 def probe_modmac(iters: int = 4096, stream=None) -> float:
     """Measured modular MAC/s of the step kernels' inner primitive (tnc_probe_modmac)."""
     v = ctypes.c_double()
@@ -577,6 +607,42 @@ class Batch:
         """tnc_batch_set_launch: fix the launch shape without timing."""
         _check(lib().tnc_batch_set_launch(self.h, int(threads), int(smem_bytes), int(ctas_per_sm)))
 
+    def get_launch(self) -> Tuple[int, int, int]:
+        """tnc_batch_get_launch: (threads, shared-memory arena bytes, CTAs-per-SM cap)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tnc_batch_get_launch(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def signature(self) -> str:
+        """What an autotuned launch shape depends on: the device and the
+        batch's sizes (descriptor bytes, result entries, formulas, residues)."""
+        import torch
+        h2d, _, n_entries, _ = self.info()
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        return f"{props.name}|{props.multi_processor_count}|{h2d}|{n_entries}|{len(self.plans)}|{self.R}"
+
+    def autotune_cached(self, ws, stream=None, cache: Optional[str] = None) -> Tuple[int, int, int]:
+        """The launch shape from the JSON file `cache` if it holds one for this
+        batch's signature (tnc_batch_set_launch, no timing); else
+        tnc_batch_autotune, whose choice is then added to the file."""
+        import json
+        key = self.signature()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        if key in table:
+            self.set_launch(*table[key])
+            return tuple(table[key])
+        shape = self.autotune(ws, stream)
+        if cache:
+            table[key] = list(shape)
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1)
+            os.replace(tmp, cache)
+        return shape
+
     def download(self, ws, stream=None) -> List[Count]:
         n = len(self.plans)
         bufs = [_count_buffers(1 << pp.n_open, self.R) for pp in self.plans]
@@ -634,6 +700,26 @@ def count(formula, n_residues: int = 4, heuristic: str = "bisect", **kw) -> Coun
 
 def _dp(x):
     return ctypes.c_void_p(x.data_ptr() if x is not None else 0)
+
+
+def inject_failure(kind: str, after: int = 0):
+    """tnc_inject_failure: arm one host-side failure ("nomem", "plan",
+    "launch", "timeout"; "none" disarms)."""
+    _check(lib().tnc_inject_failure(INJECT[kind], after))
+
+
+def learned_save(path: str, params: np.ndarray):
+    """tnc_learned_save: host fp32 scorer parameters to a checked file."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == MLP_PARAMS
+    _check(lib().tnc_learned_save(path.encode(), _p(p, ctypes.c_float)))
+
+
+def learned_load(path: str) -> np.ndarray:
+    """tnc_learned_load: the parameters of a file written by learned_save."""
+    out = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(lib().tnc_learned_load(path.encode(), _p(out, ctypes.c_float)))
+    return out
 
 
 def mlp_init(seed: int = 0) -> np.ndarray:
