@@ -802,10 +802,34 @@ int batch_pack(tnc_batch_t* b) {
     const Lowered& lw = p->low;
     if (lw.lvl_arena_entries >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "formula arena above 2^32 entries");
     if (lw.lvl_steps.size() >= 65535) return set_error(TNC_ERR_TOO_LARGE, "more than 65534 steps in one formula");
-    // steps and runs
+    // per level: the share of one lane of a 256-thread CTA (at least 16
+    // products), and per step the lane split sh of its long shared sums: an
+    // entry of a step is split over 2^sh lanes so that no lane sums much more
+    // than that share
+    const uint32_t nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
+    std::vector<uint32_t> lvl_log_t(nlev, 4), step_sh(lw.lvl_steps.size(), 0);
+    for (uint32_t l = 0; l < nlev; l++) {
+      uint64_t work = 0;
+      for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++)
+        work += 1ull << (lw.lvl_steps[si].c + lw.lvl_steps[si].k);
+      uint32_t log_t = 4;
+      while (log_t < 24 && (1ull << log_t) * 256 < work) log_t++;
+      lvl_log_t[l] = log_t;
+      for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
+        const StepDesc& d = lw.lvl_steps[si];
+        uint32_t sh = 0;
+        while (sh < 5 && sh < d.k && d.k - sh > log_t) sh++;
+        step_sh[si] = sh;
+      }
+    }
+    // steps, runs and address deltas.  A lane group of a whole-warp block
+    // advances its entry by 2^g (g = 5 - sh): delta[t - g] = w[t] -
+    // sum_{g <= j < t} w[j] for the operand weights w[j] of output bit j.
     std::vector<BStep> steps;
     std::vector<uint16_t> runs;
-    for (const StepDesc& d : lw.lvl_steps) {
+    std::vector<int32_t> dls;  // pairs (A, B)
+    for (size_t si = 0; si < lw.lvl_steps.size(); si++) {
+      const StepDesc& d = lw.lvl_steps[si];
       BStep bs;
       std::memset(&bs, 0, sizeof(bs));
       bs.a_off = (uint32_t)d.a_off;
@@ -815,12 +839,21 @@ int batch_pack(tnc_batch_t* b) {
       bs.k = d.k;
       bs.ka = d.ka;
       bs.kb = d.kb;
-      bs.run0 = (uint32_t)runs.size();
+      if (runs.size() >= 65535 || dls.size() / 2 >= 65535)
+        return set_error(TNC_ERR_TOO_LARGE, "formula descriptors beyond 2^16 runs or deltas");
+      bs.run0 = (uint16_t)runs.size();
+      int64_t wA[32] = {0}, wB[32] = {0};
       if (d.nra != TNC_BITMAP) {
-        for (int r = 0; r < d.nra; r++)
-          runs.push_back(pack_run(d.map.runs.ra[r].src, d.map.runs.ra[r].dst, d.map.runs.ra[r].len));
-        for (int r = 0; r < d.nrb; r++)
-          runs.push_back(pack_run(d.map.runs.rb[r].src, d.map.runs.rb[r].dst, d.map.runs.rb[r].len));
+        for (int r = 0; r < d.nra; r++) {
+          const TncRun& x = d.map.runs.ra[r];
+          runs.push_back(pack_run(x.src, x.dst, x.len));
+          for (int q = 0; q < x.len; q++) wA[x.src + q] = 1ll << (x.dst + q);
+        }
+        for (int r = 0; r < d.nrb; r++) {
+          const TncRun& x = d.map.runs.rb[r];
+          runs.push_back(pack_run(x.src, x.dst, x.len));
+          for (int q = 0; q < x.len; q++) wB[x.src + q] = 1ll << (x.dst + q);
+        }
         bs.nra = d.nra;
         bs.nrb = d.nrb;
       } else {
@@ -829,24 +862,31 @@ int batch_pack(tnc_batch_t* b) {
             if ((d.map.bit[j] >> 7) == side) {
               runs.push_back(pack_run(j, d.map.bit[j] & 63, 1));
               (side ? bs.nrb : bs.nra)++;
+              (side ? wB : wA)[j] = 1ll << (d.map.bit[j] & 63);
             }
+      }
+      const uint32_t g = 5 - step_sh[si];
+      bs.g = (uint8_t)g;
+      bs.dl0 = (uint16_t)(dls.size() / 2);
+      for (uint32_t t = g; t < d.c; t++) {
+        int64_t sa = 0, sb = 0;
+        for (uint32_t j = g; j < t; j++) {
+          sa += wA[j];
+          sb += wB[j];
+        }
+        dls.push_back((int32_t)(wA[t] - sa));
+        dls.push_back((int32_t)(wB[t] - sb));
       }
       steps.push_back(bs);
     }
-    // segments per level.  An entry of a step with a long shared sum is split
-    // over 2^sh lanes, so that no lane sums much more than the level's share
-    // per lane of a 256-thread CTA (at least 16 products); steps whose
-    // entries take 32+ lanes get whole-warp segments, the others share packed
-    // segments lane by lane.  Segments are ordered by cost, longest first.
+    // segments per level: steps whose entries take 32+ lanes get whole-warp
+    // blocks of V entries per lane group (V such that a lane's work is about
+    // half the level's share, at most 4); the others share packed segments
+    // lane by lane.  Segments are ordered by cost, longest first.
     std::vector<Seg> segs;
     std::vector<uint32_t> items, lvl{0};
-    const uint32_t nlev = lw.lvl_start.empty() ? 0 : (uint32_t)lw.lvl_start.size() - 1;
     for (uint32_t l = 0; l < nlev; l++) {
-      uint64_t work = 0;
-      for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++)
-        work += 1ull << (lw.lvl_steps[si].c + lw.lvl_steps[si].k);
-      uint32_t log_t = 4;
-      while (log_t < 24 && (1ull << log_t) * 256 < work) log_t++;
+      const uint32_t log_t = lvl_log_t[l];
       struct Group {
         uint32_t si, o, sh, cost;
       };
@@ -854,16 +894,18 @@ int batch_pack(tnc_batch_t* b) {
       std::vector<std::pair<uint32_t, Seg>> lsegs;  // (cost, segment)
       for (uint32_t si = lw.lvl_start[l]; si < lw.lvl_start[l + 1]; si++) {
         const StepDesc& d = lw.lvl_steps[si];
-        uint32_t sh = 0;
-        while (sh < 5 && sh < d.k && d.k - sh > log_t) sh++;
+        const uint32_t sh = step_sh[si];
         const uint32_t cost = 1u << (d.k - sh);
         const uint32_t nout = 1u << d.c;
         if ((nout << sh) < 32) {
           for (uint32_t o = 0; o < nout; o++) small.push_back(Group{si, o, sh, cost});
           continue;
         }
-        for (uint32_t o0 = 0; o0 < nout; o0 += 32u >> sh)
-          lsegs.push_back({cost, Seg{o0, (uint16_t)si, 32, (uint8_t)sh}});
+        const uint32_t G = 32u >> sh;
+        uint32_t V = 1;
+        while (V < 4 && 2 * V * G <= nout && (2 * V) * cost <= (1u << (log_t - 1))) V *= 2;
+        for (uint32_t o0 = 0; o0 < nout; o0 += G * V)
+          lsegs.push_back({cost * V, Seg{o0, (uint16_t)si, (uint8_t)V, (uint8_t)sh}});
       }
       // widest groups first: each group then starts at a multiple of its size
       // and never crosses a 32-lane boundary
@@ -898,6 +940,7 @@ int batch_pack(tnc_batch_t* b) {
     f.segs_at = (uint32_t)blob_put(blob, segs.data(), segs.size() * sizeof(Seg));
     f.items_at = (uint32_t)blob_put(blob, items.data(), items.size() * sizeof(uint32_t));
     f.runs_at = (uint32_t)blob_put(blob, runs.data(), runs.size() * sizeof(uint16_t));
+    f.dl_at = (uint32_t)blob_put(blob, dls.data(), dls.size() * sizeof(int32_t));
     f.lvl_at = (uint32_t)blob_put(blob, lvl.data(), lvl.size() * sizeof(uint32_t));
     blob.resize((blob.size() + 15) / 16 * 16);
     f.blob = (uint32_t)(blobs.size() / 16);

@@ -431,33 +431,101 @@ __global__ void crt_kernel(const uint32_t* __restrict__ residues, uint64_t n_ent
 
 // Packed batch descriptors.  Everything one formula's contraction looks up is
 // one contiguous, 16-byte aligned blob (steps, segments, packed items, bit-map
-// runs, level table), copied to shared memory in one coalesced pass when a
-// CTA starts the formula.  Offsets are relative to the formula's own arena;
-// a run is a u16: src | dst << 5 | len << 10.
+// runs, address deltas, level table), copied to shared memory in one coalesced
+// pass when a CTA starts the formula.  Offsets are relative to the formula's
+// own arena; a run is a u16: src | dst << 5 | len << 10.
 struct BStep {
   uint32_t a_off, b_off, c_off;
-  uint32_t run0;  // first run of A's map (blob-relative); B's map follows
+  uint16_t run0;  // first run of A's map (blob-relative); B's map follows
+  uint16_t dl0;   // first address delta (blob-relative, int2 units)
   uint8_t c, k, ka, kb;
-  uint8_t nra, nrb, pad0, pad1;
+  uint8_t nra, nrb, g, pad;  // g: log2 of the entry stride of a lane group (5 - sh)
 };
 
 // The unit of work of one warp.  An output entry whose sum runs over 2^k
 // shared values may be split over 2^sh lanes (sh <= min(k, 5)): lane slice j
 // sums the shared values j, j + 2^sh, ..., and the lanes of the entry add
-// their residues with butterfly shuffles.  A segment is either 32 lanes of one
-// step: step = step index, o0 = first entry, lane L takes entry o0 + (L >> sh),
-// slice L & (2^sh - 1); or, for steps whose entries need fewer than 32 lanes,
-// the lanes of several such entries packed side by side: step = kPacked, o0 =
-// first of n lane items, each item = step | entry << 16 | slice << 21 |
-// sh << 26, the entries' lane groups aligned to their size; sh is then the
-// largest split in the segment.
+// their residues with butterfly shuffles.  A segment is either a block of one
+// step: step = step index, o0 = first entry, n = V entries per lane group: the
+// 2^(5 - sh) lane groups take entries o0 + group + i 2^(5 - sh), i < V, the
+// operand addresses advancing from one to the next by the step's precomputed
+// deltas (the output counter o >> g gains one, clearing its trailing ones and
+// setting bit t: each address changes by delta[t - g]); or, for steps whose
+// entries need fewer than 32 lanes, the lanes of several such entries packed
+// side by side: step = kPacked, o0 = first of n lane items, each item =
+// step | entry << 16 | slice << 21 | sh << 26, the entries' lane groups
+// aligned to their size; sh is then the largest split in the segment.
 constexpr uint16_t kPacked = 0xFFFF;
 struct Seg {
   uint32_t o0;
   uint16_t step;
-  uint8_t n;   // active lanes, 1..32
+  uint8_t n;   // whole-warp block: entries per lane group V; packed: active lanes
   uint8_t sh;  // log2 lanes per entry (packed: the largest)
 };
+
+// Sum of A*B over 2^KK shared values (KK <= 4) for residues whose products
+// fit 16 to a 64-bit accumulator (the default primes below 2^30): fully
+// unrolled, one reduction per residue at the end.  Operand entries of the
+// batch arena are addressed by 32-bit entry indices.
+template <int RG, bool N30, int KK>
+__device__ __forceinline__ void step_sum_fixed(uint32_t ka, uint32_t kb, const uint32_t* A, const uint32_t* B,
+                                               const ModGroup& mg, uint32_t (&out)[RG]) {
+  uint64_t acc[RG];
+#pragma unroll
+  for (int r = 0; r < RG; r++) acc[r] = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < (1u << KK); q++) {
+    uint32_t va[RG], vb[RG];
+    load_entry<RG>(A + ((q << ka) * RG), va);
+    load_entry<RG>(B + ((q << kb) * RG), vb);
+#pragma unroll
+    for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+  }
+#pragma unroll
+  for (int r = 0; r < RG; r++) out[r] = reduce64<N30>(acc[r], mg, r);
+}
+
+// step_sum for the batch kernel.  For the default primes (16 products fit a
+// 64-bit accumulator between reductions): up to 4 products fully unrolled;
+// longer sums in unrolled groups of 4 (one group's loads in flight at a
+// time, which bounds the registers), reduced after every 16th product.
+// Other primes: the general loop.
+template <int RG, bool N30>
+__device__ __forceinline__ void batch_sum(uint32_t k, uint32_t ka, uint32_t kb, const uint32_t* A, const uint32_t* B,
+                                          const ModGroup& mg, uint32_t (&out)[RG]) {
+  if (N30) {
+    switch (k) {
+      case 0: step_sum_fixed<RG, N30, 0>(ka, kb, A, B, mg, out); return;
+      case 1: step_sum_fixed<RG, N30, 1>(ka, kb, A, B, mg, out); return;
+      case 2: step_sum_fixed<RG, N30, 2>(ka, kb, A, B, mg, out); return;
+      default: {
+        uint64_t acc[RG];
+#pragma unroll
+        for (int r = 0; r < RG; r++) acc[r] = 0;
+        const uint32_t K = 1u << k;
+#pragma unroll 1
+        for (uint32_t q = 0; q < K; q += 4) {
+#pragma unroll
+          for (uint32_t u = 0; u < 4; u++) {
+            uint32_t va[RG], vb[RG];
+            load_entry<RG>(A + (((q + u) << ka) * RG), va);
+            load_entry<RG>(B + (((q + u) << kb) * RG), vb);
+#pragma unroll
+            for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
+          }
+          if (((q + 4) & 15u) == 0 && q + 4 < K) {
+#pragma unroll
+            for (int r = 0; r < RG; r++) acc[r] = reduce64<N30>(acc[r], mg, r);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < RG; r++) out[r] = reduce64<N30>(acc[r], mg, r);
+        return;
+      }
+    }
+  }
+  step_sum<RG, uint32_t, N30>(k, ka, kb, A, B, mg, out);
+}
 
 struct BLeaf {
   uint32_t off;
@@ -470,7 +538,7 @@ struct BForm {
   uint32_t blob_n;                   // uint4 count
   uint32_t segs_at, items_at, runs_at, lvl_at;  // byte offsets of the blob sections (steps at 0)
   uint32_t nlev, leaf0, nleaf, res_off, n_out, perm_off;
-  uint32_t n_open, root_off, arena, pad;  // arena: entries this formula needs
+  uint32_t n_open, root_off, arena, dl_at;  // arena: entries this formula needs; dl_at: deltas
 };
 
 struct BatchArgs {
@@ -542,31 +610,56 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
     const uint32_t* items = reinterpret_cast<const uint32_t*>(bb + f.items_at);
     const uint16_t* runs_all = reinterpret_cast<const uint16_t*>(bb + f.runs_at);
     const uint32_t* lvl = reinterpret_cast<const uint32_t*>(bb + f.lvl_at);
+    const int2* deltas = reinterpret_cast<const int2*>(bb + f.dl_at);
     for (uint32_t l = 0; l < f.nlev; l++) {
       const uint32_t s1 = lvl[l + 1];
       for (uint32_t sg = lvl[l] + warp; sg < s1; sg += nwarps) {
         const Seg seg = segs[sg];
-        uint32_t st = seg.step, o, slice, sh = seg.sh;
-        bool active = true;
-        if (st != kPacked) {
-          o = seg.o0 + (lane >> sh);
-          slice = lane & ((1u << sh) - 1u);
-        } else {
-          active = lane < seg.n;
-          const uint32_t it = items[seg.o0 + (active ? lane : 0)];
-          st = it & 0xFFFFu;
-          o = (it >> 16) & 31u;
-          slice = (it >> 21) & 31u;
-          sh = it >> 26;
+        if (seg.step != kPacked) {
+          // a block of V entries per lane group of one step
+          const BStep d = steps[seg.step];
+          const uint32_t sh = seg.sh, g = d.g;
+          uint32_t o = seg.o0 + (lane >> sh);
+          const uint32_t slice = lane & ((1u << sh) - 1u);
+          const uint16_t* runs = runs_all + d.run0;
+          uint32_t ia = map_runs(o, runs, d.nra) + (slice << d.ka);
+          uint32_t ib = map_runs(o, runs + d.nra, d.nrb) + (slice << d.kb);
+          const uint32_t* A0 = arena + (uint64_t)d.a_off * RG;
+          const uint32_t* B0 = arena + (uint64_t)d.b_off * RG;
+          uint32_t* C0 = arena + (uint64_t)d.c_off * RG;
+          const int2* dl = deltas + d.dl0;
+          for (uint32_t v = 0; v < seg.n; v++) {
+            uint32_t out[RG];
+            batch_sum<RG, N30>(d.k - sh, d.ka + sh, d.kb + sh, A0 + ia * RG, B0 + ib * RG, mg, out);
+            for (uint32_t m = 1; m < (1u << sh); m <<= 1) {
+#pragma unroll
+              for (int r = 0; r < RG; r++) {
+                const uint32_t t = out[r] + __shfl_xor_sync(0xFFFFFFFFu, out[r], m);
+                out[r] = t >= mg.p[r] ? t - mg.p[r] : t;
+              }
+            }
+            if (slice == 0) store_entry<RG>(C0 + o * RG, out);
+            if (v + 1 < seg.n) {
+              const int2 dd = dl[__ffs(~(o >> g)) - 1];
+              o += 1u << g;
+              ia += (uint32_t)dd.x;
+              ib += (uint32_t)dd.y;
+            }
+          }
+          continue;
         }
+        // packed lanes of small steps, one entry per lane
+        const bool active = lane < seg.n;
+        const uint32_t it = items[seg.o0 + (active ? lane : 0)];
+        const uint32_t st = it & 0xFFFFu, o = (it >> 16) & 31u, slice = (it >> 21) & 31u, sh = it >> 26;
         const BStep d = steps[st];
         uint32_t out[RG];
         if (active) {
           const uint16_t* runs = runs_all + d.run0;
           const uint32_t ia = map_runs(o, runs, d.nra) + (slice << d.ka);
           const uint32_t ib = map_runs(o, runs + d.nra, d.nrb) + (slice << d.kb);
-          step_sum<RG, uint32_t, N30>(d.k - sh, d.ka + sh, d.kb + sh, arena + ((uint64_t)d.a_off + ia) * RG,
-                       arena + ((uint64_t)d.b_off + ib) * RG, mg, out);
+          batch_sum<RG, N30>(d.k - sh, d.ka + sh, d.kb + sh, arena + ((uint64_t)d.a_off + ia) * RG,
+                             arena + ((uint64_t)d.b_off + ib) * RG, mg, out);
         } else {
 #pragma unroll
           for (int r = 0; r < RG; r++) out[r] = 0;
