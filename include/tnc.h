@@ -253,12 +253,27 @@ size_t tnc_workspace_bytes_opts(const tnc_plan_t* plan, const tnc_contract_opts*
  * ranks; the paper leaves memory as the bottleneck of its method, Sec. 4).
  * plans[i] are the networks of the slices (same open variables); the result
  * is the sum of their counts, exact: each slice's residues are added on the
- * device modulo the primes, then one CRT.  `flags` certifies the sum (the sum
+ * device modulo the primes, then one CRT.  As many slices at a time as the
+ * workspace holds beyond tnc_workspace_bytes_sliced's minimum run with their
+ * tree levels merged (as tnc_contract_many).  `flags` certifies the sum (the sum
  * of the slices' bounds).  dev_ws: tnc_workspace_bytes_sliced bytes, 256-byte
  * aligned.  Synchronises `cuda_stream`. */
 size_t tnc_workspace_bytes_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts);
 int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts, void* dev_ws,
                         size_t ws_bytes, void* cuda_stream, tnc_count* out);
+/* Many formulas in one call: independent contractions (Sec. 2.1) whose tree
+ * levels are merged, so that one launch covers the small steps of level l of
+ * every formula of a group, and the group's big, split-K and dense steps
+ * follow one another on the stream.  A group is as many consecutive plans as
+ * the workspace holds (each plan alone must fit: TNC_ERR_BUFFER otherwise).
+ * Any path; outs: n counts, as tnc_contract would give them one by one.
+ * tnc_workspace_bytes_many gives the bytes that hold groups of `group`
+ * consecutive plans (group = 1: the least that works).  dev_ws 256-byte
+ * aligned; synchronises `cuda_stream`. */
+size_t tnc_workspace_bytes_many(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                                int32_t group);
+int tnc_contract_many(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts, void* dev_ws,
+                      size_t ws_bytes, void* cuda_stream, tnc_count* outs);
 /* Measurement aid (calling thread only; off by default): with on != 0, every
  * later tnc_contract brackets each dense (tensor-core) step with CUDA events
  * on its stream, and tnc_last_dense_time returns the summed device time (ms)

@@ -160,11 +160,17 @@ int dispatch_rg(int rg, F&& f) {
 
 // ---------------------------------------------------------------- single formula
 
+// Workspace of a group of plans contracted together (one plan: the
+// single-formula layout).  Descriptors of all plans side by side; every plan's
+// tensors in its own part of one arena (arena_base, in entries, a multiple of
+// 64 so that every plan's entries start 16-byte aligned); scratch shared by
+// the group's steps, which run one after another on one stream.
 struct SeqLayout {
   size_t off_leaves, off_tables, off_steps, off_small, off_tc, off_err, off_part, off_results, off_limbs, off_p8,
       off_arena, total;
-  uint64_t n_out;
+  uint64_t n_out;  // result entries of the whole group
   size_t n_dense;
+  std::vector<uint64_t> arena_base, res_base, leaf_base, table_base;
 };
 
 using tnc_dev::GridStep;
@@ -233,52 +239,121 @@ GridStep make_grid_step(const StepDesc& d) {
   return g;
 }
 
-SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) {
-  SeqLayout s{};
+// What one plan adds to a group's workspace: counts of descriptors, result
+// entries and arena entries (summed over the group), and scratch bytes (the
+// group's maximum).
+struct Foot {
+  size_t leaves = 0, tables = 0, nseq = 0, nlvl = 0, n_dense = 0;
+  uint64_t n_out = 0, arena = 0, part = 0, p8 = 0;
+  void add(const Foot& f) {
+    leaves += f.leaves;
+    tables += f.tables;
+    nseq += f.nseq;
+    nlvl += f.nlvl;
+    n_dense += f.n_dense;
+    n_out += f.n_out;
+    arena += f.arena;
+    part = std::max(part, f.part);
+    p8 = std::max(p8, f.p8);
+  }
+};
+
+Foot foot_of(const tnc_plan_t* p, int R, int path) {
   const int rg_max = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
-  s.n_out = 1ull << p->net.open_vars.size();
-  size_t o = 0;
-  s.off_leaves = o;
-  o = align_up(o + p->low.leaves.size() * sizeof(LeafDesc));
-  s.off_tables = o;
-  o = align_up(o + p->low.leaf_tables.size() * sizeof(uint32_t));
-  s.off_steps = o;
-  o = align_up(o + p->low.seq_steps.size() * sizeof(GridStep));
-  s.off_small = o;
-  o = align_up(o + p->low.lvl_steps.size() * sizeof(StepDesc));
-  s.n_dense = 0;
-  for (const StepDesc& d : p->low.seq_steps) s.n_dense += tc_eligible(d) ? 1 : 0;
-  s.off_tc = o;
-  o = align_up(o + s.n_dense * R * tc_step_bytes());
-  s.off_err = o;
-  o = align_up(o + 64);
-  uint64_t part_bytes = 0;
+  Foot f;
+  f.leaves = p->low.leaves.size();
+  f.tables = p->low.leaf_tables.size();
+  f.nseq = p->low.seq_steps.size();
+  f.nlvl = p->low.lvl_steps.size();
+  f.n_out = 1ull << p->net.open_vars.size();
+  for (const StepDesc& d : p->low.seq_steps) f.n_dense += tc_eligible(d) ? 1 : 0;
   for (const StepDesc& d : p->low.lvl_steps) {
     if (splitk_log(d) > 0)
-      part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + splitk_log(d))) * rg_max * sizeof(uint32_t));
+      f.part = std::max<uint64_t>(f.part, (1ull << (d.c + splitk_log(d))) * rg_max * sizeof(uint32_t));
     if (tc_eligible(d) && tc_split_log(d) > 0)
-      part_bytes = std::max<uint64_t>(part_bytes, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
-    if (path == TNC_PATH_TC_P8 && p8_eligible(d))
-      part_bytes = std::max<uint64_t>(part_bytes, p8_part_bytes(d, rg_max));
+      f.part = std::max<uint64_t>(f.part, (1ull << (d.c + tc_split_log(d))) * sizeof(uint32_t));
+    if (path == TNC_PATH_TC_P8 && p8_eligible(d)) {
+      f.part = std::max<uint64_t>(f.part, p8_part_bytes(d, rg_max));
+      f.p8 = std::max<uint64_t>(f.p8, p8_scratch_bytes(d, rg_max));
+    }
   }
-  uint64_t p8_bytes = 0;
-  if (path == TNC_PATH_TC_P8)
-    for (const StepDesc& d : p->low.lvl_steps)
-      if (p8_eligible(d)) p8_bytes = std::max<uint64_t>(p8_bytes, p8_scratch_bytes(d, rg_max));
-  s.off_part = o;
-  o = align_up(o + part_bytes);
-  s.off_results = o;
-  o = align_up(o + s.n_out * R * sizeof(uint32_t));
-  s.off_limbs = o;
-  o = align_up(o + s.n_out * ((31 * R + 31) / 32) * sizeof(uint32_t));
-  s.off_p8 = o;
-  o = align_up(o + p8_bytes);
-  s.off_arena = o;
+  f.arena = (std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) + 63) / 64 * 64;
+  return f;
+}
+
+// Offsets of the workspace sections for the group footprint f.
+SeqLayout layout_of(const Foot& f, int R, int path) {
+  SeqLayout s{};
+  const int rg_max = R >= 4 ? 4 : (R >= 2 ? 2 : 1);
+  size_t o = 0;
+  auto sect = [&](size_t& off, size_t bytes) {
+    off = o;
+    o = align_up(o + bytes);
+  };
+  sect(s.off_leaves, f.leaves * sizeof(LeafDesc));
+  sect(s.off_tables, f.tables * sizeof(uint32_t));
+  sect(s.off_steps, std::max(f.nseq, f.nlvl) * sizeof(GridStep));
+  sect(s.off_small, f.nlvl * sizeof(StepDesc));
+  sect(s.off_tc, f.n_dense * R * tc_step_bytes());
+  sect(s.off_err, 64);
+  sect(s.off_part, f.part);
+  sect(s.off_results, f.n_out * R * sizeof(uint32_t));
+  sect(s.off_limbs, f.n_out * ((31 * R + 31) / 32) * sizeof(uint32_t));
+  sect(s.off_p8, f.p8);
   const size_t word = path == TNC_PATH_TC_P8 ? 1 : sizeof(uint32_t);  // bytes per residue
-  o = align_up(o + std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) * rg_max * word);
+  sect(s.off_arena, f.arena * rg_max * word);
   s.total = o;
+  s.n_out = f.n_out;
+  s.n_dense = f.n_dense;
   return s;
 }
+
+SeqLayout group_layout(const tnc_plan_t* const* plans, int n, int R, int path = TNC_PATH_INT64) {
+  Foot sum;
+  std::vector<uint64_t> arena_base, res_base, leaf_base, table_base;
+  for (int i = 0; i < n; i++) {
+    const Foot f = foot_of(plans[i], R, path);
+    leaf_base.push_back(sum.leaves);
+    table_base.push_back(sum.tables);
+    res_base.push_back(sum.n_out);
+    arena_base.push_back(sum.arena);
+    sum.add(f);
+  }
+  SeqLayout s = layout_of(sum, R, path);
+  s.arena_base = std::move(arena_base);
+  s.res_base = std::move(res_base);
+  s.leaf_base = std::move(leaf_base);
+  s.table_base = std::move(table_base);
+  return s;
+}
+
+// Consecutive groups of the plans whose workspace each fits `budget` bytes
+// (every plan alone must fit): [begin, end) ranges.
+int plan_groups(const tnc_plan_t* const* plans, int n, int R, int path, size_t budget,
+                std::vector<std::pair<int, int>>& out) {
+  out.clear();
+  int b = 0;
+  Foot sum;
+  for (int i = 0; i < n; i++) {
+    Foot f = foot_of(plans[i], R, path);
+    Foot t = sum;
+    t.add(f);
+    if (i > b && layout_of(t, R, path).total > budget) {
+      out.push_back({b, i});
+      b = i;
+      sum = Foot();
+      t = f;
+    }
+    if (layout_of(t, R, path).total > budget)
+      return set_error(TNC_ERR_BUFFER, "plan " + std::to_string(i) + " alone needs " +
+                                           std::to_string(layout_of(t, R, path).total) + " bytes of workspace");
+    sum = t;
+  }
+  if (b < n) out.push_back({b, n});
+  return TNC_OK;
+}
+
+SeqLayout seq_layout(const tnc_plan_t* p, int R, int path = TNC_PATH_INT64) { return group_layout(&p, 1, R, path); }
 
 int fill_count(tnc_count* out, uint64_t n_out, const Arith& a, const uint32_t* res, const uint32_t* limbs,
                uint32_t flags) {
@@ -348,79 +423,115 @@ __global__ void residue_add_kernel(uint32_t* __restrict__ acc, const uint32_t* _
   }
 }
 
-// The contraction of one plan.  With sum_into == nullptr the count is
-// finished (CRT, copy to `out`); otherwise the residues [2^n_open][R] are
-// added into the device buffer sum_into and nothing else is returned.
-static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
-                         void* cuda_stream, tnc_count* out, uint32_t* sum_into) {
-  if (!plan || (!out && !sum_into)) return set_error(TNC_ERR_INVALID, "NULL argument");
+// The contraction of a group of plans, their tree levels merged: level l of
+// every plan of the group runs together (one launch for all their steps with
+// fewer than 2^16 outputs, one launch each for big, split-K and dense steps).
+// With sum_into == nullptr every plan's count is finished (CRT, copy to
+// outs[i]); otherwise the residues [2^n_open][R] of every plan are added into
+// the device buffer sum_into (the plans are the slices of one count) and
+// nothing else is returned.
+static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contract_opts* opts, void* dev_ws,
+                          size_t ws_bytes, void* cuda_stream, tnc_count* outs, uint32_t* sum_into) {
+  if (!plans || n <= 0 || (!outs && !sum_into)) return set_error(TNC_ERR_INVALID, "NULL argument");
+  for (int i = 0; i < n; i++)
+    if (!plans[i]) return set_error(TNC_ERR_INVALID, "NULL plan");
   Arith a;
   int rc = make_arith(opts, a);
   if (rc) return rc;
-  const SeqLayout L = seq_layout(plan, a.R, opts->path);
-  const uint32_t flags = result_flags(plan, a);
-  if (plan->tree.nodes.empty()) {  // empty network: the empty product, 1
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // empty networks (the empty product, 1) are answered on the host
+  std::vector<const tnc_plan_t*> work;
+  std::vector<int> work_idx;
+  for (int i = 0; i < n; i++) {
+    if (!plans[i]->tree.nodes.empty()) {
+      work.push_back(plans[i]);
+      work_idx.push_back(i);
+      continue;
+    }
     std::vector<uint32_t> res(a.R, 1u), limbs(a.crt.n_limbs, 0u);
     limbs[0] = 1;
     if (sum_into) {
       if (!dev_ws || ws_bytes < (size_t)a.R * 4) return set_error(TNC_ERR_BUFFER, "workspace too small");
-      cudaStream_t st0 = (cudaStream_t)cuda_stream;
-      CUDA_TRY(cudaMemcpyAsync(dev_ws, res.data(), a.R * sizeof(uint32_t), cudaMemcpyHostToDevice, st0));
-      residue_add_kernel<<<1, 64, 0, st0>>>(sum_into, (const uint32_t*)dev_ws, (uint64_t)a.R, a.R, a.crt);
+      CUDA_TRY(cudaMemcpyAsync(dev_ws, res.data(), a.R * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+      residue_add_kernel<<<1, 64, 0, st>>>(sum_into, (const uint32_t*)dev_ws, (uint64_t)a.R, a.R, a.crt);
       CUDA_TRY(cudaGetLastError());
-      CUDA_TRY(cudaStreamSynchronize(st0));
-      return TNC_OK;
+      CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      rc = fill_count(&outs[i], 1, a, res.data(), limbs.data(), 0);
+      if (rc) return rc;
     }
-    return fill_count(out, 1, a, res.data(), limbs.data(), 0);
   }
+  if (work.empty()) return TNC_OK;
+  const int nw = (int)work.size();
+  const SeqLayout L = group_layout(work.data(), nw, a.R, opts->path);
   if (!dev_ws || ws_bytes < L.total) return set_error(TNC_ERR_BUFFER, "workspace smaller than tnc_workspace_bytes");
   if (((uintptr_t)dev_ws) % kAlign) return set_error(TNC_ERR_INVALID, "workspace must be 256-byte aligned");
   if (inject_hit(TNC_INJECT_LAUNCH)) return set_error(TNC_ERR_CUDA, "injected failure (TNC_INJECT_LAUNCH)");
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   char* ws = (char*)dev_ws;
-  // The contraction runs level by level (the tree-level schedule of the
-  // lowering): per level, one launch for all its steps with fewer than 2^16
-  // outputs, and one launch each for its big steps, its split-K steps and, on
-  // the tensor-core path, its dense steps.
-  const Lowered& lw = plan->low;
-  std::vector<LeafDesc> leaves = lw.leaves;
-  for (size_t i = 0; i < leaves.size(); i++) leaves[i].off = lw.lvl_leaf_off[i];
-  CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice, st));
-  g_h2d_bytes += leaves.size() * sizeof(LeafDesc) + lw.leaf_tables.size() * sizeof(uint32_t);
-  if (!lw.leaf_tables.empty())
-    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, lw.leaf_tables.data(), lw.leaf_tables.size() * sizeof(uint32_t),
-                             cudaMemcpyHostToDevice, st));
+  // Every plan runs level by level (the tree-level schedule of the lowering);
+  // offsets are shifted to the plan's part of the group's arena, tables and
+  // results.
   const bool p8 = opts->path == TNC_PATH_TC_P8;
   const bool tc = opts->path == TNC_PATH_TC || p8;
-  const size_t ns = lw.lvl_steps.size();
-  enum Kind { kSmall, kGrid, kSplit, kTc };
-  std::vector<int> kind(ns, kSmall), slot(ns, -1);
+  std::vector<LeafDesc> leaves;
+  std::vector<uint32_t> tables;
+  size_t n_lev = 0;
+  for (int w = 0; w < nw; w++) {
+    const Lowered& lw = work[w]->low;
+    for (size_t i = 0; i < lw.leaves.size(); i++) {
+      LeafDesc ld = lw.leaves[i];
+      ld.off = lw.lvl_leaf_off[i] + L.arena_base[w];
+      ld.table_off += (uint32_t)L.table_base[w];
+      leaves.push_back(ld);
+    }
+    tables.insert(tables.end(), lw.leaf_tables.begin(), lw.leaf_tables.end());
+    n_lev = std::max(n_lev, lw.lvl_start.empty() ? (size_t)0 : lw.lvl_start.size() - 1);
+  }
+  CUDA_TRY(cudaMemcpyAsync(ws + L.off_leaves, leaves.data(), leaves.size() * sizeof(LeafDesc), cudaMemcpyHostToDevice, st));
+  if (!tables.empty())
+    CUDA_TRY(cudaMemcpyAsync(ws + L.off_tables, tables.data(), tables.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                             st));
+  g_h2d_bytes += leaves.size() * sizeof(LeafDesc) + tables.size() * sizeof(uint32_t);
+  // the group's steps by level: small ones (one index space per level across
+  // the plans), big, split-K and dense ones (one launch each)
+  enum Kind { kGrid, kSplit, kTc };
+  struct Big {
+    int kind, slot;
+    StepDesc d;  // offsets shifted to the group's arena
+  };
+  std::vector<std::vector<Big>> big(n_lev);
   std::vector<GridStep> gsteps;
   std::vector<StepDesc> small;
-  std::vector<uint32_t> small_lo, small_hi, small_work;  // per level
+  std::vector<uint32_t> small_lo(n_lev), small_hi(n_lev), small_work(n_lev);
   std::vector<char> tcbuf;
   size_t nd = 0;
-  for (size_t l = 0; l + 1 < lw.lvl_start.size(); l++) {
-    small_lo.push_back((uint32_t)small.size());
-    uint32_t work = 0;
-    for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
-      const StepDesc& d = lw.lvl_steps[i];
-      if (tc && (p8 ? p8_eligible(d) : tc_eligible(d))) {
-        kind[i] = kTc;
-        slot[i] = (int)nd++;
-      } else if (splitk_log(d) > 0 || d.c >= 16) {
-        kind[i] = splitk_log(d) > 0 ? kSplit : kGrid;
-        slot[i] = (int)gsteps.size();
-        gsteps.push_back(make_grid_step(d));
-      } else {
-        StepDesc e = d;
-        e.work_lo = work;
-        work += 1u << d.c;
-        small.push_back(e);
+  for (size_t l = 0; l < n_lev; l++) {
+    small_lo[l] = (uint32_t)small.size();
+    uint64_t wk = 0;
+    for (int w = 0; w < nw; w++) {
+      const Lowered& lw = work[w]->low;
+      if (l + 1 >= lw.lvl_start.size()) continue;
+      const uint64_t base = L.arena_base[w];
+      for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
+        StepDesc d = lw.lvl_steps[i];
+        d.a_off += base;
+        d.b_off += base;
+        d.c_off += base;
+        if (tc && (p8 ? p8_eligible(d) : tc_eligible(d))) {
+          big[l].push_back(Big{kTc, (int)nd++, d});
+        } else if (splitk_log(d) > 0 || d.c >= 16) {
+          big[l].push_back(Big{splitk_log(d) > 0 ? kSplit : kGrid, (int)gsteps.size(), d});
+          gsteps.push_back(make_grid_step(d));
+        } else {
+          d.work_lo = (uint32_t)wk;
+          wk += 1u << d.c;
+          small.push_back(d);
+        }
       }
     }
-    small_hi.push_back((uint32_t)small.size());
-    small_work.push_back(work);
+    if (wk >= (1ull << 32)) return set_error(TNC_ERR_TOO_LARGE, "a merged level has more than 2^32 small outputs");
+    small_hi[l] = (uint32_t)small.size();
+    small_work[l] = (uint32_t)wk;
   }
   g_h2d_bytes += gsteps.size() * sizeof(GridStep) + small.size() * sizeof(StepDesc);
   if (!gsteps.empty())
@@ -430,10 +541,11 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_small, small.data(), small.size() * sizeof(StepDesc), cudaMemcpyHostToDevice, st));
   if (nd && !p8) {
     tcbuf.assign(nd * a.R * tc_step_bytes(), 0);
-    for (size_t i = 0; i < ns; i++)
-      if (kind[i] == kTc)
-        for (int r = 0; r < a.R; r++)
-          tc_make_step(lw.lvl_steps[i], a.primes[r], tcbuf.data() + ((size_t)slot[i] * a.R + r) * tc_step_bytes());
+    for (size_t l = 0; l < n_lev; l++)
+      for (const Big& b : big[l])
+        if (b.kind == kTc)
+          for (int r = 0; r < a.R; r++)
+            tc_make_step(b.d, a.primes[r], tcbuf.data() + ((size_t)b.slot * a.R + r) * tc_step_bytes());
     CUDA_TRY(cudaMemcpyAsync(ws + L.off_tc, tcbuf.data(), tcbuf.size(), cudaMemcpyHostToDevice, st));
     g_h2d_bytes += tcbuf.size();
   }
@@ -457,9 +569,6 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
       for (cudaEvent_t e : v) cudaEventDestroy(e);
     }
   } event_guard{dense_events};
-  g_dense_ms = 0.0;
-  g_dense_launches = 0;
-  g_total_ms = 0.0;
   cudaEvent_t whole[2] = {nullptr, nullptr};  // the device work of the whole contraction (timing mode)
   if (g_time_dense) {
     CUDA_TRY(cudaEventCreate(&whole[0]));
@@ -472,10 +581,15 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   const StepDesc* d_small = (const StepDesc*)(ws + L.off_small);
   uint32_t* results = (uint32_t*)(ws + L.off_results);
   uint32_t* part = (uint32_t*)(ws + L.off_part);
-  RootMap rm{};
-  rm.n_open = (int)plan->net.open_vars.size();
-  for (int j = 0; j < rm.n_open; j++) rm.perm[j] = lw.root_perm[j];
-  const uint64_t root_off = lw.lvl_steps.empty() ? lw.lvl_leaf_off[plan->tree.root] : lw.lvl_root_off;
+  std::vector<RootMap> rms(nw);
+  std::vector<uint64_t> root_off(nw);
+  for (int w = 0; w < nw; w++) {
+    const Lowered& lw = work[w]->low;
+    rms[w] = RootMap{};
+    rms[w].n_open = (int)work[w]->net.open_vars.size();
+    for (int j = 0; j < rms[w].n_open; j++) rms[w].perm[j] = lw.root_perm[j];
+    root_off[w] = L.arena_base[w] + (lw.lvl_steps.empty() ? lw.lvl_leaf_off[work[w]->tree.root] : lw.lvl_root_off);
+  }
   const int sms = sm_count();
   for (size_t gi = 0; gi < groups.rg.size(); gi++) {
     uint32_t gp[4];
@@ -492,18 +606,17 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
       tnc_dev::leaf_fill_kernel<RG, W><<<std::min(nl, sms * 8), 64, 0, st>>>(
           (const LeafDesc*)(ws + L.off_leaves), nl, (const uint32_t*)(ws + L.off_tables), arena, mg);
       g_launches.leaf_fill++;
-      for (size_t l = 0; l < small_lo.size(); l++) {
+      for (size_t l = 0; l < n_lev; l++) {
         NvtxRange level_range("tnc level");
         const uint32_t n_small = small_hi[l] - small_lo[l];
         if (n_small) {
-          const uint32_t w = small_work[l];
-          const unsigned blocks = (unsigned)std::min<uint64_t>((w + 255) / 256, (uint64_t)sms * 8);
-          tnc_dev::level_kernel<RG, W, N30><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, w, arena, mg);
+          const uint32_t wk = small_work[l];
+          const unsigned blocks = (unsigned)std::min<uint64_t>((wk + 255) / 256, (uint64_t)sms * 8);
+          tnc_dev::level_kernel<RG, W, N30><<<blocks, 256, 0, st>>>(d_small + small_lo[l], n_small, wk, arena, mg);
           g_launches.level++;
         }
-        for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
-          if (kind[i] == kSmall) continue;
-          if (kind[i] == kTc) {
+        for (const Big& b : big[l]) {
+          if (b.kind == kTc) {
             NvtxRange dense_range("tnc dense step");
             if (RG != 1 && !p8) return set_error(TNC_ERR_INVALID, "internal: tensor-core step in a multi-residue pass");
             int rc2 = TNC_OK;
@@ -514,11 +627,11 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
               CUDA_TRY(cudaEventRecord(ev[0], st));
             }
             if (p8) {
-              rc2 = p8_launch(lw.lvl_steps[i], a.primes.data() + groups.col[gi], RG, reinterpret_cast<uint8_t*>(arena),
+              rc2 = p8_launch(b.d, a.primes.data() + groups.col[gi], RG, reinterpret_cast<uint8_t*>(arena),
                               ws + L.off_p8, reinterpret_cast<uint8_t*>(part), d_err, sms, st);
             } else {
-              const char* dstep = ws + L.off_tc + ((size_t)slot[i] * a.R + groups.col[gi]) * tc_step_bytes();
-              rc2 = tc_launch(dstep, lw.lvl_steps[i], reinterpret_cast<uint32_t*>(arena), part, d_err, st);
+              const char* dstep = ws + L.off_tc + ((size_t)b.slot * a.R + groups.col[gi]) * tc_step_bytes();
+              rc2 = tc_launch(dstep, b.d, reinterpret_cast<uint32_t*>(arena), part, d_err, st);
             }
             if (g_time_dense) {
               CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -526,25 +639,28 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
               dense_events.push_back(ev[1]);
             }
             if (rc2) return rc2;
-          } else if (kind[i] == kSplit) {
-            const uint32_t ls = splitk_log(lw.lvl_steps[i]);
-            const uint64_t nblk = 1ull << (lw.lvl_steps[i].c + ls);
-            tnc_dev::splitk_partial_kernel<RG, W, N30><<<(unsigned)nblk, 256, 0, st>>>(d_steps + slot[i], arena, part, ls,
+          } else if (b.kind == kSplit) {
+            const uint32_t ls = splitk_log(b.d);
+            const uint64_t nblk = 1ull << (b.d.c + ls);
+            tnc_dev::splitk_partial_kernel<RG, W, N30><<<(unsigned)nblk, 256, 0, st>>>(d_steps + b.slot, arena, part, ls,
                                                                                        mg);
-            tnc_dev::splitk_final_kernel<RG, W, N30><<<(unsigned)(1ull << lw.lvl_steps[i].c), 256, 0, st>>>(
-                d_steps + slot[i], arena, part, ls, mg);
+            tnc_dev::splitk_final_kernel<RG, W, N30><<<(unsigned)(1ull << b.d.c), 256, 0, st>>>(d_steps + b.slot, arena,
+                                                                                              part, ls, mg);
             g_launches.splitk++;
           } else {
             int threads, blocks, sh;
-            grid_shape(lw.lvl_steps[i].c, &threads, &blocks, &sh);
-            tnc_dev::step_kernel<RG, W, N30><<<blocks, threads, 0, st>>>(d_steps + slot[i], arena, mg);
+            grid_shape(b.d.c, &threads, &blocks, &sh);
+            tnc_dev::step_kernel<RG, W, N30><<<blocks, threads, 0, st>>>(d_steps + b.slot, arena, mg);
             g_launches.grid_step++;
           }
         }
       }
-      tnc_dev::extract_kernel<RG, W><<<(unsigned)std::min<uint64_t>((L.n_out + 255) / 256, 1024), 256, 0, st>>>(
-          arena, root_off, rm, results, a.R, groups.col[gi]);
-      g_launches.extract++;
+      for (int w = 0; w < nw; w++) {
+        const uint64_t no = 1ull << rms[w].n_open;
+        tnc_dev::extract_kernel<RG, W><<<(unsigned)std::min<uint64_t>((no + 255) / 256, 1024), 256, 0, st>>>(
+            arena, root_off[w], rms[w], results + L.res_base[w] * a.R, a.R, groups.col[gi]);
+        g_launches.extract++;
+      }
       CUDA_TRY(cudaGetLastError());
       return TNC_OK;
     };
@@ -555,17 +671,19 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     });
     if (rc) return rc;
   }
-  if (sum_into) {  // one term of a sum: add the residues, check the device status
-    const uint64_t n = L.n_out * (uint64_t)a.R;
-    residue_add_kernel<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 1024), 256, 0, st>>>(sum_into, results, n, a.R,
-                                                                                           a.crt);
+  uint32_t h_err = 0;
+  if (sum_into) {  // terms of a sum: add every plan's residues, check the device status
+    for (int w = 0; w < nw; w++) {
+      const uint64_t m = (1ull << rms[w].n_open) * (uint64_t)a.R;
+      residue_add_kernel<<<(unsigned)std::min<uint64_t>((m + 255) / 256, 1024), 256, 0, st>>>(
+          sum_into, results + L.res_base[w] * a.R, m, a.R, a.crt);
+    }
     CUDA_TRY(cudaGetLastError());
-    uint32_t h_err0 = 0;
-    CUDA_TRY(cudaMemcpyAsync(&h_err0, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     g_d2h_bytes += sizeof(uint32_t);
     CUDA_TRY(cudaStreamSynchronize(st));
-    if (inject_hit(TNC_INJECT_TIMEOUT)) h_err0 = 1;
-    if (h_err0) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
+    if (inject_hit(TNC_INJECT_TIMEOUT)) h_err = 1;
+    if (h_err) return set_error(TNC_ERR_TIMEOUT, "a tensor-core step timed out waiting for its MMAs");
     return TNC_OK;
   }
   uint32_t* limbs = (uint32_t*)(ws + L.off_limbs);
@@ -574,7 +692,6 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
   g_launches.crt++;
   CUDA_TRY(cudaGetLastError());
   if (g_time_dense) CUDA_TRY(cudaEventRecord(whole[1], st));
-  uint32_t h_err = 0;
   CUDA_TRY(cudaMemcpyAsync(&h_err, d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   std::vector<uint32_t> h_res(L.n_out * a.R), h_limbs(L.n_out * a.crt.n_limbs);
   CUDA_TRY(cudaMemcpyAsync(h_res.data(), results, h_res.size() * 4, cudaMemcpyDeviceToHost, st));
@@ -587,22 +704,37 @@ static int contract_core(const tnc_plan_t* plan, const tnc_contract_opts* opts, 
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, dense_events[e], dense_events[e + 1]));
     if (e == 0) {
-      g_total_ms = ms;
+      g_total_ms += ms;
       continue;
     }
     g_dense_ms += ms;
     g_dense_launches++;
   }
-  return fill_count(out, L.n_out, a, h_res.data(), h_limbs.data(), flags);
+  for (int w = 0; w < nw; w++) {
+    rc = fill_count(&outs[work_idx[w]], 1ull << rms[w].n_open, a, h_res.data() + L.res_base[w] * a.R,
+                    h_limbs.data() + L.res_base[w] * a.crt.n_limbs, result_flags(work[w], a));
+    if (rc) return rc;
+  }
+  return TNC_OK;
+}
+
+// Resets the per-call records (launch counts, copies, timing) of the calling
+// thread.
+static void reset_records() {
+  g_launches = tnc_launch_counts{};
+  g_h2d_bytes = g_d2h_bytes = 0;
+  g_dense_ms = 0.0;
+  g_dense_launches = 0;
+  g_total_ms = 0.0;
 }
 
 extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,
                             void* cuda_stream, tnc_count* out) {
   clear_error();
-  g_launches = tnc_launch_counts{};
-  g_h2d_bytes = g_d2h_bytes = 0;
+  reset_records();
   NvtxRange range("tnc_contract");
-  return contract_core(plan, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
+  if (!plan || !out) return set_error(TNC_ERR_INVALID, "NULL argument");
+  return contract_group(&plan, 1, opts, dev_ws, ws_bytes, cuda_stream, out, nullptr);
 }
 
 // Slices of one count: the sum of the plans' counts (each plan the network of
@@ -626,8 +758,7 @@ extern "C" size_t tnc_workspace_bytes_sliced(const tnc_plan_t* const* plans, int
 extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
                                    void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* out) {
   clear_error();
-  g_launches = tnc_launch_counts{};
-  g_h2d_bytes = g_d2h_bytes = 0;
+  reset_records();
   NvtxRange range("tnc_contract_sliced");
   if (!plans || n <= 0 || !out || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
   Arith a;
@@ -651,8 +782,13 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
   uint32_t* limbs = (uint32_t*)(ws + align_up(n_out * a.R * sizeof(uint32_t)));
   const size_t head = sliced_head_bytes(n_out, a);
   CUDA_TRY(cudaMemsetAsync(acc, 0, n_out * a.R * sizeof(uint32_t), st));
-  for (int i = 0; i < n; i++) {
-    rc = contract_core(plans[i], opts, ws + head, ws_bytes - head, cuda_stream, nullptr, acc);
+  // as many slices at a time as the workspace holds, their levels merged
+  std::vector<std::pair<int, int>> grp;
+  rc = plan_groups(plans, n, a.R, opts->path, ws_bytes - head, grp);
+  if (rc) return rc;
+  for (const auto& g : grp) {
+    rc = contract_group(plans + g.first, g.second - g.first, opts, ws + head, ws_bytes - head, cuda_stream, nullptr,
+                        acc);
     if (rc) return rc;
   }
   tnc_dev::crt_kernel<<<(unsigned)std::min<uint64_t>((n_out + 127) / 128, 1024), 128, 0, st>>>(acc, n_out, a.crt, limbs);
@@ -664,6 +800,43 @@ extern "C" int tnc_contract_sliced(const tnc_plan_t* const* plans, int32_t n, co
   g_d2h_bytes += (h_res.size() + h_limbs.size()) * 4;
   CUDA_TRY(cudaStreamSynchronize(st));
   return fill_count(out, n_out, a, h_res.data(), h_limbs.data(), bound >= a.log2_prod - 1e-9 ? TNC_MAYBE_WRAPPED : 0u);
+}
+
+extern "C" size_t tnc_workspace_bytes_many(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                                           int32_t group) {
+  clear_error();
+  Arith a;
+  if (!plans || n <= 0 || group <= 0 || make_arith(opts, a)) return 0;
+  size_t need = 256;
+  for (int i = 0; i < n; i += group) {
+    const int m = std::min<int>(group, n - i);
+    for (int j = i; j < i + m; j++)
+      if (!plans[j]) return 0;
+    need = std::max(need, group_layout(plans + i, m, a.R, opts->path).total);
+  }
+  return need;
+}
+
+extern "C" int tnc_contract_many(const tnc_plan_t* const* plans, int32_t n, const tnc_contract_opts* opts,
+                                 void* dev_ws, size_t ws_bytes, void* cuda_stream, tnc_count* outs) {
+  clear_error();
+  reset_records();
+  NvtxRange range("tnc_contract_many");
+  if (!plans || n <= 0 || !outs || !opts) return set_error(TNC_ERR_INVALID, "NULL argument");
+  Arith a;
+  int rc = make_arith(opts, a);
+  if (rc) return rc;
+  for (int i = 0; i < n; i++)
+    if (!plans[i]) return set_error(TNC_ERR_INVALID, "NULL plan");
+  std::vector<std::pair<int, int>> grp;
+  rc = plan_groups(plans, n, a.R, opts->path, ws_bytes, grp);
+  if (rc) return rc;
+  for (const auto& g : grp) {
+    rc = contract_group(plans + g.first, g.second - g.first, opts, dev_ws, ws_bytes, cuda_stream, outs + g.first,
+                        nullptr);
+    if (rc) return rc;
+  }
+  return TNC_OK;
 }
 
 // ======================================================================= batch

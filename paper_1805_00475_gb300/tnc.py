@@ -33,6 +33,7 @@ INJECT = {"none": 0, "nomem": 1, "plan": 2, "launch": 3, "timeout": 4}
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
     "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_sliced", "tnc_slice_network", "tnc_network_formula", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
+    "tnc_workspace_bytes_many", "tnc_contract_many",
     "tnc_contract", "tnc_crt_host", "tnc_residue_add_host", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch", "tnc_batch_get_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
     "tnc_contract_batch", "tnc_contract_noalloc", "tnc_probe_modmac", "tnc_inject_failure", "tnc_learned_save",
@@ -141,6 +142,8 @@ def lib():
             "tnc_last_io_bytes": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "tnc_workspace_bytes_sliced": ([vp, i32, vp], sz),
             "tnc_contract_sliced": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
+            "tnc_workspace_bytes_many": ([vp, i32, vp, i32], sz),
+            "tnc_contract_many": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
             "tnc_contract": ([vp, ctypes.POINTER(_ContractOpts), vp, sz, vp, ctypes.POINTER(_Count)],
                              ctypes.c_int),
             "tnc_batch_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_ContractOpts), ctypes.POINTER(vp)],
@@ -465,6 +468,33 @@ def contract(p: Plan, n_residues: int = 4, primes=None, workspace=None, stream=N
     _check(lib().tnc_contract(p.h, ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb, _stream_ptr(stream),
                               ctypes.byref(c)))
     return _to_count(c, res, limbs, pr)
+
+
+def workspace_bytes_many(plans: Sequence[Plan], n_residues: int, path: str = "int64", group: int = 1,
+                         primes=None) -> int:
+    """tnc_workspace_bytes_many: bytes for groups of `group` consecutive plans."""
+    o, _ = _opts(n_residues, primes, path)
+    arr = (ctypes.c_void_p * len(plans))(*[pp.h.value for pp in plans])
+    nb = int(lib().tnc_workspace_bytes_many(arr, len(plans), ctypes.byref(o), group))
+    if nb == 0:
+        raise TncError(-1, lib().tnc_last_error().decode() or "invalid arguments")
+    return nb
+
+
+def contract_many(plans: Sequence[Plan], n_residues: int = 4, primes=None, workspace=None, stream=None,
+                  path: str = "int64", group: int = 16) -> List[Count]:
+    """tnc_contract_many: many plans, tree levels merged within groups that
+    fit the workspace (default: a workspace for groups of `group` plans)."""
+    o, pr = _opts(n_residues, primes, path)
+    arr = (ctypes.c_void_p * len(plans))(*[pp.h.value for pp in plans])
+    nb = workspace_bytes_many(plans, n_residues, path, group, primes) if workspace is None else \
+        workspace.numel() * workspace.element_size()
+    ws = _workspace(nb, workspace)
+    bufs = [_count_buffers(1 << pp.n_open, n_residues) for pp in plans]
+    outs = (_Count * len(plans))(*[b[0] for b in bufs])
+    _check(lib().tnc_contract_many(arr, len(plans), ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb,
+                                   _stream_ptr(stream), outs))
+    return [_to_count(outs[i], bufs[i][1], bufs[i][2], pr) for i in range(len(plans))]
 
 
 def set_step_timing(on: bool):
