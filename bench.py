@@ -65,8 +65,6 @@ def parse():
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
-    ap.add_argument("--c3-workers", type=int, default=4,
-                    help="c3: host threads contracting the heavy formulas, each with its own stream and workspace")
     ap.add_argument("--c4-compare", default="tc,int64",
                     help="c4: arithmetic paths timed once beside the 8-bit-prime path ('' for none)")
     ap.add_argument("--train-formulas", type=int, default=20000, help="c5: generated training formulas")
@@ -233,75 +231,76 @@ def c4_workload(count=16, n=180):
 
 
 def run_c3(args):
-    """4096 monotone 1-in-3 formulas, n ~ U{50..150}, m = round(n U[0.5, 0.8)).
-    Counted modulo about 2^60 like 2 residues below 2^30: formulas whose best
-    plan needs few MACs (<= 2^24, rank <= 16: the descriptors of a formula fit
-    in shared memory) go through one persistent, graph-captured batch launch
-    (2 residues below 2^30); the others one by one through tnc_contract on the
-    8-bit-prime tensor-core path (8 primes <= 251, product 2^62.8), spread over
-    host threads with a stream and a workspace each; plans above rank 28 are
-    left out and reported."""
-    import threading
+    """4096 monotone 1-in-3 formulas, n ~ U{50..150}, m = round(n U[0.5, 0.8)),
+    every one counted on the device, from one host thread on one stream:
+      * light plans (<= 2^24 MACs, rank <= 16; the descriptors of a formula fit
+        in shared memory): one persistent, graph-captured, autotuned batch
+        launch, 2 residues below 2^30;
+      * heavy plans (re-planned by the portfolio of the paper's heuristics):
+        tnc_contract_many on the 8-bit-prime tensor-core path, 8 primes <= 251
+        (product 2^62.8), tree levels merged across the formulas of a group;
+      * plans still above rank 26: bond-sliced (tnc_plan_sliced) to rank <= 26
+        and counted by tnc_contract_sliced, same primes.
+    Counts whose certified bound exceeds the product of the primes carry
+    TNC_MAYBE_WRAPPED (residues exact, CRT value the count modulo that product)."""
     import torch
     from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import slicing as S
     from paper_1805_00475_gb300 import tnc
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    Rc, R8, n_total, workers = 2, 8, args.formulas or 4096, args.c3_workers
-    light_macs, rank_max = 2.0 ** 24, 28
+    Rc, R8, n_total = 2, 8, args.formulas or 4096
+    light_macs, rank_many, ws_gb = 2.0 ** 24, 26, 16
     forms = I.batch_one_in_three(n_total, 2026)
     t = time.perf_counter()
     plans = tnc.plan_many(forms, heuristic="best", rank_cap=64)
-    plan_s = time.perf_counter() - t
     is_light = [p.stats.total_macs <= light_macs and p.stats.max_rank <= 16 for p in plans]
+    heavy_idx = [i for i, l in enumerate(is_light) if not l]
+    heavy_plans = tnc.plan_many([forms[i] for i in heavy_idx], heuristic="portfolio", rank_cap=64)
+    many_idx = [i for i, p in zip(heavy_idx, heavy_plans) if p.stats.max_rank <= rank_many]
+    many = [p for p in heavy_plans if p.stats.max_rank <= rank_many]
+    big_idx = [i for i, p in zip(heavy_idx, heavy_plans) if p.stats.max_rank > rank_many]
+    sliced = []
+    for i, p in zip(big_idx, [p for p in heavy_plans if p.stats.max_rank > rank_many]):
+        s = 1
+        while True:
+            sp, vs = S.sliced_plans(forms[i], s, heuristic="best")
+            if max(q.stats.max_rank for q in sp) <= rank_many or s >= 10:
+                break
+            s += 1
+        sliced.append((i, sp, vs))
+    plan_s = time.perf_counter() - t
     light = [p for p, l in zip(plans, is_light) if l]
-    heavy = [p for p, l in zip(plans, is_light) if not l and p.stats.max_rank <= rank_max]
-    left = [p.stats.max_rank for p in plans if p.stats.max_rank > rank_max]
     batch = tnc.Batch(light, n_residues=Rc)
     ws_b = torch.empty(batch.workspace_bytes(), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     batch.upload(ws_b, stream)
     tuned = batch.autotune(ws_b, stream)
-    # heavy formulas in two phases (rank <= 26, then 27..28), each spread
-    # longest first onto the least loaded of the workers
-    phases = [[p for p in heavy if p.stats.max_rank <= 26], [p for p in heavy if p.stats.max_rank > 26]]
-    bins = []
-    for ph in phases:
-        b, load = [[] for _ in range(workers)], [0.0] * workers
-        for p in sorted(ph, key=lambda p: -p.stats.total_macs):
-            w = load.index(min(load))
-            b[w].append(p)
-            load[w] += p.stats.total_macs
-        bins.append(b)
-    wss = [torch.empty(max([tnc.workspace_bytes(p, R8, "tc_p8") for ph in bins for p in ph[w]] + [256]),
-                       dtype=torch.uint8, device=dev) for w in range(workers)]
-    streams = [torch.cuda.Stream(device=dev) for _ in range(workers)]
+    ws = torch.empty(ws_gb << 30, dtype=torch.uint8, device=dev)
     macs_light = sum(p.stats.total_macs for p in light) * Rc
-    macs_heavy = sum(p.stats.total_macs for p in heavy) * R8
-    phase_s = [[], [], []]
-
-    def work(ph, w):
-        for p in bins[ph][w]:
-            tnc.contract(p, n_residues=R8, path="tc_p8", workspace=wss[w], stream=streams[w])
+    macs_many = sum(p.stats.total_macs for p in many) * R8
+    macs_sliced = sum(q.stats.total_macs for _, sp, _ in sliced for q in sp) * R8
+    phase_ms = [[], [], []]
+    results = {}
 
     def one_step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        ev[0].record(stream)
         batch.launch(ws_b, stream)
-        stream.synchronize()
-        t1 = time.perf_counter()
-        marks = [t0, t1]
-        for ph in range(2):
-            th = [threading.Thread(target=work, args=(ph, w)) for w in range(workers)]
-            for x in th:
-                x.start()
-            for x in th:
-                x.join()
-            torch.cuda.synchronize(dev)
-            marks.append(time.perf_counter())
-        for i in range(3):
-            phase_s[i].append(marks[i + 1] - marks[i])
-        return marks[-1] - t0
+        ev[1].record(stream)
+        res_many = tnc.contract_many(many, n_residues=R8, path="tc_p8", workspace=ws, stream=stream)
+        ev[2].record(stream)
+        res_sliced = [tnc.contract_sliced(sp, n_residues=R8, path="tc_p8", workspace=ws, stream=stream)
+                      for _, sp, _ in sliced]
+        ev[3].record(stream)
+        res_light = batch.download_flat(ws_b, stream)
+        torch.cuda.synchronize(dev)
+        for k in range(3):
+            phase_ms[k].append(ev[k].elapsed_time(ev[k + 1]))
+        results["many"], results["sliced"], results["light"] = res_many, res_sliced, res_light
+        return time.perf_counter() - t0
 
     for _ in range(max(args.warmup, 1)):
         one_step()
@@ -310,32 +309,32 @@ def run_c3(args):
     time.sleep(0.3)
     times = [one_step() for _ in range(args.steps)]
     clk = clocks.stop()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        batch.launch(ws_b, stream)
-        ev1.record(stream)
-    torch.cuda.synchronize(dev)
     s = sum(times) / len(times)
-    done = len(light) + len(heavy)
+    _, _, flags_light = results["light"]
+    wrapped = int(sum(flags_light != 0)) + sum(r.flags != 0 for r in results["many"]) + \
+        sum(r.flags != 0 for r in results["sliced"])
+    counted = len(light) + len(results["many"]) + len(results["sliced"])
+    assert counted == n_total
     line = {
-        "metric": "exact model counts/s", "value": done / s, "unit": "counts/s", "n_gpus": 1, "steps": args.steps,
+        "metric": "exact model counts/s", "value": counted / s, "unit": "counts/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": s * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u32 residues: batch 2 primes < 2^30 (int64); heavy 8 primes <= 251 (fp16 tensor-core dense steps)",
+        "dtype": "batch: u32 residues mod 2 primes < 2^30 (int64); heavy and sliced: u8 residues mod 8 primes <= 251 "
+                 "(fp16 tensor-core dense steps)",
         "data": "synthetic",
-        "config": {"workload": f"one_in_three_batch{n_total}", "batched_macs_le_2^24_rank_le_16": len(light),
-                   "heavy_tc_p8_rank_le_28": len(heavy), "left_out_rank_gt_28": len(left),
-                   "left_out_ranks": sorted(left), "planner": "best", "autotune": tuned, "host_threads": workers,
+        "config": {"workload": f"one_in_three_batch{n_total}", "counted": counted, "left_out": n_total - counted,
+                   "batched_macs_le_2^24_rank_le_16": len(light), "heavy_contract_many_rank_le_26": len(many),
+                   "sliced_to_rank_le_26": len(sliced),
+                   "slices": sum(len(sp) for _, sp, _ in sliced),
+                   "planner": "best; heavy re-planned by portfolio", "autotune": tuned, "host_threads": 1,
                    "modulus_bits": {"batch": round(sum(math.log2(q) for q in tnc.default_primes(Rc)), 1),
-                                    "heavy": round(sum(math.log2(q) for q in tnc.default_primes(R8, "tc_p8")), 1)}},
-        "modular_macs_per_s": (macs_light + macs_heavy) / s,
-        "batch_launch_ms": ev0.elapsed_time(ev1), "clocks": clk, "plan_s": plan_s,
-        "phases_ms": {"batch": 1000 * statistics.mean(phase_s[0][-args.steps:]),
-                      "heavy_rank_le_26": 1000 * statistics.mean(phase_s[1][-args.steps:]),
-                      "heavy_rank_27_28": 1000 * statistics.mean(phase_s[2][-args.steps:])},
-        "counts_per_s_rank_le_26": (len(light) + len(phases[0])) /
-                                   (statistics.mean(phase_s[0][-args.steps:]) + statistics.mean(phase_s[1][-args.steps:])),
+                                    "heavy": round(sum(math.log2(q) for q in tnc.default_primes(R8, "tc_p8")), 1)},
+                   "maybe_wrapped": wrapped},
+        "modular_macs_per_s": (macs_light + macs_many + macs_sliced) / s,
+        "phases_ms": {"batch": statistics.mean(phase_ms[0][-args.steps:]),
+                      "contract_many": statistics.mean(phase_ms[1][-args.steps:]),
+                      "sliced": statistics.mean(phase_ms[2][-args.steps:])},
+        "clocks": clk, "plan_s": plan_s,
     }
     print(json.dumps(line), flush=True)
 

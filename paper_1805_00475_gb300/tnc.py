@@ -546,6 +546,7 @@ def contract_sliced(plans: Sequence[Plan], n_residues: int = 4, primes=None, wor
     if nb == 0:
         raise TncError(-1, lib().tnc_last_error().decode() or "invalid slices")
     ws = _workspace(nb, workspace)
+    nb = ws.numel() * ws.element_size()  # a larger workspace lets slices run merged
     c, res, limbs = _count_buffers(1 << plans[0].n_open, n_residues)
     _check(lib().tnc_contract_sliced(arr, len(plans), ctypes.byref(o), ctypes.c_void_p(ws.data_ptr()), nb,
                                      _stream_ptr(stream), ctypes.byref(c)))

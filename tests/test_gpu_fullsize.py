@@ -82,3 +82,58 @@ def test_c3_batched_part_sampled_against_oracle():
     sub = [forms[i] for i in light]
     idx = sorted(set(random.Random(4096).sample(range(len(light)), 48) + [0, len(light) - 1]))
     _check_sample(out, sub, idx, order_of=lambda j: plans[light[j]].steps())
+
+
+def _c3_heavy():
+    """The benchmark's heavy 1-in-3 formulas: plans above 2^24 MACs or rank
+    16, re-planned by the portfolio of the paper's heuristics."""
+    forms = I.batch_one_in_three(4096, 2026)
+    plans = tnc.plan_many(forms, heuristic="best", rank_cap=64)
+    heavy = [i for i, p in enumerate(plans) if not (p.stats.total_macs <= 2.0 ** 24 and p.stats.max_rank <= 16)]
+    hp = tnc.plan_many([forms[i] for i in heavy], heuristic="portfolio", rank_cap=64)
+    return forms, heavy, hp
+
+
+def test_c3_heavy_part_sampled_against_oracle():
+    """All heavy formulas of rank <= 26 in one tnc_contract_many call (8 primes
+    <= 251, as the benchmark): every CRT value consistent with its residues;
+    24 sampled formulas (those of at most 2^30 MACs) against the oracle."""
+    import torch
+    forms, heavy, hp = _c3_heavy()
+    sel = [j for j, p in enumerate(hp) if p.stats.max_rank <= 26]
+    assert len(sel) > 1500
+    plans = [hp[j] for j in sel]
+    ws = torch.empty(16 << 30, dtype=torch.uint8, device="cuda")
+    out = tnc.contract_many(plans, n_residues=8, path="tc_p8", workspace=ws)
+    _check_consistent(out)
+    small = [k for k, p in enumerate(plans) if p.stats.total_macs <= 2.0 ** 30]
+    idx = sorted(random.Random(26).sample(small, 24))
+    sub = [forms[heavy[sel[k]]] for k in range(len(sel))]
+    _check_sample(out, sub, idx, order_of=lambda k: plans[k].steps())
+
+
+def test_c3_sliced_part_equals_unsliced():
+    """Formulas whose portfolio plan is above rank 26 are sliced to rank <= 26
+    (tnc_plan_sliced); on two of them the sliced count equals the unsliced
+    count of the 8-bit-prime path, and a disjoint set of primes rebuilds the
+    same integer."""
+    from paper_1805_00475_gb300 import slicing as S
+    forms, heavy, hp = _c3_heavy()
+    big = sorted((p.stats.total_macs, heavy[j]) for j, p in enumerate(hp) if 26 < p.stats.max_rank <= 29)[:2]
+    assert len(big) == 2
+    primes_a = tnc.default_primes(16, "tc_p8")
+    primes_b = tnc.default_primes(32, "tc_p8")[16:]
+    for _, i in big:
+        s = 1
+        while True:
+            sp, vs = S.sliced_plans(forms[i], s, heuristic="best")
+            if max(q.stats.max_rank for q in sp) <= 26:
+                break
+            s += 1
+        whole = tnc.plan_formula(forms[i], heuristic="portfolio", rank_cap=30)
+        a = tnc.contract(whole, n_residues=16, primes=primes_a, path="tc_p8")
+        b = tnc.contract_sliced(sp, n_residues=16, primes=primes_a, path="tc_p8")
+        c = tnc.contract_sliced(sp, n_residues=16, primes=primes_b, path="tc_p8")
+        assert a.residues.tolist() == b.residues.tolist()
+        assert a.flags == 0 and b.flags == 0 and c.flags == 0
+        assert a.counts == b.counts == c.counts
