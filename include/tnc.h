@@ -466,6 +466,38 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
                           const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes, void* cuda_stream,
                           tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned, double* learned_macs);
 
+/* Learned coarsening with heuristic completion.  The learned merges (the
+ * scorer's lowest predicted regret among the TNC_LEARNED_CANDIDATES cheapest
+ * merges, as above) coarsen the network; after checkpoints[j] % of a
+ * formula's merges the partial contraction is finished by `completion`, one
+ * of the paper's heuristics, planned on the network of the live tensors, and
+ * the cheapest of these plans is the learned plan, kept only if it is not
+ * worse than `fallback` on the whole network (the paper's heuristic as judge).
+ * Training rows for this mode label a candidate merge by the cost of the plan
+ * that makes it and is then finished by `completion` (the lazy cost of
+ * Sec. 4), at states drawn among the first max_pct % of the merges. */
+typedef struct {
+  int32_t states;         /* dataset: states sampled per formula                     */
+  int32_t cands;          /* dataset: candidates labelled per state                  */
+  int32_t completion;     /* TNC_PLAN_*; TNC_PLAN_GREEDY with no checkpoints: the
+                             learned merges go to the end (tnc_plan_learned_many)    */
+  int32_t n_checkpoints;  /* 0..8                                                     */
+  int32_t checkpoints[8]; /* percent of a formula's merges                           */
+  int32_t max_pct;        /* dataset: states among the first max_pct % (<= 0: 100)   */
+  uint64_t seed;          /* dataset sampling; seed of the randomised completion      */
+} tnc_learned_opts;
+/* d_params_bf16 NULL: the merges follow tensor-greedy's choice (the same
+ * coarsening without the scorer, for comparison); no device work then. */
+int tnc_plan_learned_opts(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                          const tnc_learned_opts* o, const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes,
+                          void* cuda_stream, tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned,
+                          double* learned_macs);
+/* Rows for this mode; d_params_bf16 NULL: exploring tensor-greedy
+ * trajectories, else the learned planner's own. */
+int tnc_learned_dataset_opts(const tnc_network_t* const* nets, int32_t n, const tnc_learned_opts* o,
+                             const void* d_params_bf16, void* d_ws, size_t ws_bytes, void* cuda_stream, float* x,
+                             float* t, int64_t cap_rows, int64_t* n_rows);
+
 /* ---- diagnostics --------------------------------------------------------- */
 /* Measured rate of the modular multiply-accumulate primitive of the step
  * kernels (4 residues per thread, 64-bit accumulation, reduced after every

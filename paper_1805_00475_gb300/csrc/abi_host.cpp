@@ -62,9 +62,11 @@ int finish_plan(tnc_plan_t* p, int rank_cap, tnc_plan_stats* stats) {
 }
 
 int learned_dataset(const std::vector<const Network*>& nets, int states, int cands, uint64_t seed, std::vector<float>& X,
-                    std::vector<float>& T, const std::vector<std::vector<int>>* policy);
+                    std::vector<float>& T, const std::vector<std::vector<int>>* policy,
+                    const tnc_plan_opts* completion, int max_pct);
 int learned_trees(const std::vector<const Network*>& nets, const void* d_params_bf16, void* d_ws, size_t ws_bytes,
-                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen);
+                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen,
+                  const tnc_plan_opts* completion, const std::vector<int>* pcts);
 
 }  // namespace tnc
 
@@ -277,7 +279,7 @@ int tnc_learned_dataset(const tnc_network_t* const* nets, int32_t n, int32_t sta
       v.push_back(&nets[i]->net);
     }
     std::vector<float> X, T;
-    learned_dataset(v, states, cands, seed, X, T, nullptr);
+    learned_dataset(v, states, cands, seed, X, T, nullptr, nullptr, 100);
     *n_rows = (int64_t)T.size();
     if (!x || !t || cap_rows < (int64_t)T.size())
       return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
@@ -303,10 +305,11 @@ int tnc_learned_dataset_on_policy(const tnc_network_t* const* nets, int32_t n, c
     }
     std::vector<Tree> trees;
     std::vector<std::vector<int>> chosen;
-    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, &chosen);
+    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, &chosen,
+                           nullptr, nullptr);
     if (rc) return rc;
     std::vector<float> X, T;
-    learned_dataset(v, states, TNC_LEARNED_CANDIDATES, seed, X, T, &chosen);
+    learned_dataset(v, states, TNC_LEARNED_CANDIDATES, seed, X, T, &chosen, nullptr, 100);
     *n_rows = (int64_t)T.size();
     if (!x || !t || cap_rows < (int64_t)T.size())
       return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
@@ -322,11 +325,12 @@ size_t tnc_plan_learned_workspace_bytes(int32_t n) {
   return n <= 0 ? 0 : (size_t)n * TNC_LEARNED_CANDIDATES * (TNC_MLP_FEATURES + 1) * sizeof(float);
 }
 
-int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
-                          const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes, void* cuda_stream,
-                          tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned, double* learned_macs) {
-  clear_error();
-  if (!nets || n <= 0 || !d_params_bf16 || !d_ws || !out) return set_error(TNC_ERR_INVALID, "bad arguments");
+static int plan_learned_impl(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                             const tnc_learned_opts* lo, const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes,
+                             void* cuda_stream, tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned,
+                             double* learned_macs) {
+  if (!nets || n <= 0 || (!lo && !d_params_bf16) || (d_params_bf16 && !d_ws) || !out)
+    return set_error(TNC_ERR_INVALID, "bad arguments");
   for (int i = 0; i < n; i++) out[i] = nullptr;
   try {
     std::vector<const Network*> v;
@@ -335,7 +339,17 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
       v.push_back(&nets[i]->net);
     }
     std::vector<Tree> trees;
-    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, nullptr);
+    tnc_plan_opts comp{};
+    std::vector<int> pcts;
+    if (lo) {
+      comp.heuristic = lo->completion;
+      comp.tries = 2;
+      comp.seed = lo->seed;
+      for (int j = 0; j < std::min<int>(std::max(lo->n_checkpoints, 0), 8); j++) pcts.push_back(lo->checkpoints[j]);
+    }
+    const bool hybrid = lo && !pcts.empty();
+    int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, nullptr,
+                           hybrid ? &comp : nullptr, hybrid ? &pcts : nullptr);
     if (rc) return rc;
     tnc_plan_opts fb{};
     if (fallback) fb = *fallback;
@@ -382,6 +396,62 @@ int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const voi
       }
       return set_error(first_rc, first_msg);
     }
+    return TNC_OK;
+  } catch (const std::bad_alloc&) {
+    return set_error(TNC_ERR_NOMEM, "out of host memory");
+  }
+}
+
+int tnc_plan_learned_many(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                          const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                          tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned, double* learned_macs) {
+  clear_error();
+  if (!d_params_bf16) return set_error(TNC_ERR_INVALID, "scorer parameters NULL");
+  return plan_learned_impl(nets, n, d_params_bf16, nullptr, fallback, d_ws, ws_bytes, cuda_stream, out, stats,
+                           chose_learned, learned_macs);
+}
+
+int tnc_plan_learned_opts(const tnc_network_t* const* nets, int32_t n, const void* d_params_bf16,
+                          const tnc_learned_opts* o, const tnc_plan_opts* fallback, void* d_ws, size_t ws_bytes,
+                          void* cuda_stream, tnc_plan_t** out, tnc_plan_stats* stats, int32_t* chose_learned,
+                          double* learned_macs) {
+  clear_error();
+  if (!o) return set_error(TNC_ERR_INVALID, "learned options NULL");
+  return plan_learned_impl(nets, n, d_params_bf16, o, fallback, d_ws, ws_bytes, cuda_stream, out, stats,
+                           chose_learned, learned_macs);
+}
+
+int tnc_learned_dataset_opts(const tnc_network_t* const* nets, int32_t n, const tnc_learned_opts* o,
+                             const void* d_params_bf16, void* d_ws, size_t ws_bytes, void* cuda_stream, float* x,
+                             float* t, int64_t cap_rows, int64_t* n_rows) {
+  clear_error();
+  if (!nets || n <= 0 || !o || o->states <= 0 || o->cands <= 1 || !n_rows || (d_params_bf16 && !d_ws))
+    return set_error(TNC_ERR_INVALID, "bad dataset arguments");
+  try {
+    std::vector<const Network*> v;
+    for (int i = 0; i < n; i++) {
+      if (!nets[i]) return set_error(TNC_ERR_INVALID, "NULL network");
+      v.push_back(&nets[i]->net);
+    }
+    tnc_plan_opts comp{};
+    comp.heuristic = o->completion;
+    comp.tries = 2;
+    comp.seed = o->seed;
+    std::vector<std::vector<int>> chosen;
+    if (d_params_bf16) {  // follow the learned planner's own merges
+      std::vector<Tree> trees;
+      int rc = learned_trees(v, d_params_bf16, d_ws, ws_bytes, cuda_stream, TNC_LEARNED_CANDIDATES, trees, &chosen,
+                             nullptr, nullptr);
+      if (rc) return rc;
+    }
+    std::vector<float> X, T;
+    learned_dataset(v, o->states, o->cands, o->seed, X, T, d_params_bf16 ? &chosen : nullptr,
+                    o->completion == TNC_PLAN_GREEDY ? nullptr : &comp, o->max_pct > 0 ? o->max_pct : 100);
+    *n_rows = (int64_t)T.size();
+    if (!x || !t || cap_rows < (int64_t)T.size())
+      return set_error(TNC_ERR_BUFFER, "need " + std::to_string(T.size()) + " rows");
+    std::copy(X.begin(), X.end(), x);
+    std::copy(T.begin(), T.end(), t);
     return TNC_OK;
   } catch (const std::bad_alloc&) {
     return set_error(TNC_ERR_NOMEM, "out of host memory");

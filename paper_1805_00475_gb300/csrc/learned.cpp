@@ -146,6 +146,63 @@ void top_candidates(const GState& s, std::vector<Cand>& cs, int cap) {
   if ((int)cs.size() > cap) cs.resize(cap);
 }
 
+// The network of the live tensors of a partial contraction: one leaf per
+// live tensor (its bonds), every bond between the two live tensors holding it
+// (bonds already contracted belong to no live tensor).  Only the structure
+// the planners read is set.  ids[j] = tree node of coarse leaf j.
+void coarse_network(const GState& s, const Network& net, Network& out, std::vector<int>& ids) {
+  out = Network();
+  ids.clear();
+  for (size_t i = 0; i < s.t.nodes.size(); i++)
+    if (s.live[i]) ids.push_back((int)i);
+  out.leaves.resize(ids.size());
+  out.n_bonds = net.n_bonds;
+  out.bond_end0.assign(net.n_bonds, -1);
+  out.bond_end1.assign(net.n_bonds, -1);
+  out.n_vars = 0;
+  out.n_cons = (int)ids.size();
+  for (size_t j = 0; j < ids.size(); j++) {
+    out.leaves[j].bonds = s.t.nodes[ids[j]].bonds;
+    for (int b : out.leaves[j].bonds) {
+      if (out.bond_end0[b] < 0) out.bond_end0[b] = (int)j;
+      else out.bond_end1[b] = (int)j;
+    }
+  }
+}
+
+// Finishes a partial contraction by the heuristic `h` planned on the network
+// of its live tensors (the paper's planners on the coarsened network); h =
+// TNC_PLAN_GREEDY is tensor-greedy's own finish.
+void complete_with(GState& s, const Network& net, const tnc_plan_opts& h) {
+  if (h.heuristic == TNC_PLAN_GREEDY) {
+    s.finish_greedy();
+    return;
+  }
+  Network cn;
+  std::vector<int> ids;
+  coarse_network(s, net, cn, ids);
+  if (ids.size() <= 1) {
+    s.finish_greedy();
+    return;
+  }
+  Tree ct;
+  if (plan_tree(cn, h, ct) != TNC_OK) {
+    s.finish_greedy();
+    return;
+  }
+  std::vector<int> map(ct.nodes.size(), -1);
+  for (int j = 0; j < ct.n_leaves; j++) map[j] = ids[j];
+  for (size_t i = ct.n_leaves; i < ct.nodes.size(); i++) {
+    s.merge(map[ct.nodes[i].left], map[ct.nodes[i].right]);
+    map[i] = (int)s.t.nodes.size() - 1;
+  }
+  s.t.root = map[ct.root >= 0 ? ct.root : 0];
+}
+
+bool cheaper_cost(const TreeCost& a, const TreeCost& b) {
+  return a.max_rank != b.max_rank ? a.max_rank < b.max_rank : a.macs < b.macs;
+}
+
 int live_max_rank(const GState& s) {
   int m = 0;
   for (size_t i = 0; i < s.t.nodes.size(); i++)
@@ -203,7 +260,8 @@ struct Rng {
 // policy[i] (merge sequences of a previous learned plan, as candidate
 // positions), so that the scorer also learns on the states it visits itself.
 int learned_dataset(const std::vector<const Network*>& nets, int states, int cands, uint64_t seed, std::vector<float>& X,
-                    std::vector<float>& T, const std::vector<std::vector<int>>* policy = nullptr) {
+                    std::vector<float>& T, const std::vector<std::vector<int>>* policy = nullptr,
+                    const tnc_plan_opts* completion = nullptr, int max_pct = 100) {
   const int n = (int)nets.size();
   std::vector<std::vector<float>> xs(n), ts(n);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -211,7 +269,7 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
     Rng rng(seed ^ (0x5851F42D4C957F2Dull * (uint64_t)(i + 1)));
     GState s;
     s.init(*nets[i]);
-    const int steps = std::max(1, nets[i]->n_leaves() - 1);
+    const int steps = std::max(1, (nets[i]->n_leaves() - 1) * std::min(std::max(max_pct, 1), 100) / 100);
     std::vector<int> at;
     for (int j = 0; j < states; j++) at.push_back((int)(rng.next() % (uint64_t)steps));
     std::sort(at.begin(), at.end());
@@ -226,7 +284,8 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
         for (size_t c = 0; c < cs.size(); c++) {
           GState r = s;
           r.merge(cs[c].a, cs[c].b);
-          r.finish_greedy();
+          if (completion) complete_with(r, *nets[i], *completion);
+          else r.finish_greedy();
           cost[c] = r.cost();
         }
         const double lo = *std::min_element(cost.begin(), cost.end());
@@ -243,6 +302,7 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
       if (policy && step < (int)(*policy)[i].size()) pick = std::min<size_t>((size_t)(*policy)[i][step], cs.size() - 1);
       if (cs.size() > 1 && rng.next() % 4 == 0) pick = 1 + rng.next() % std::min<size_t>(3, cs.size() - 1);
       s.merge(cs[pick].a, cs[pick].b);
+      if (next >= at.size() && completion) break;  // the states past the last sampled one are not needed
     }
   }
   X.clear();
@@ -257,16 +317,39 @@ int learned_dataset(const std::vector<const Network*>& nets, int states, int can
 // Learned plans for many formulas in lockstep: every round gathers the
 // candidates of all unfinished formulas, scores them in one bf16 inference
 // launch, and merges each formula's lowest predicted regret.
+//
+// With `completion` set, the learned merges only coarsen the network: at each
+// checkpoint (pcts[j] % of the formula's merges) the partial contraction is
+// finished by the heuristic `completion` planned on the network of its live
+// tensors, and the cheapest (max rank, MACs) of these plans is kept.  Without
+// d_params_bf16 the merges follow tensor-greedy's choice (the same loop with
+// no scorer: the ablation of the learned part).
 int learned_trees(const std::vector<const Network*>& nets, const void* d_params_bf16, void* d_ws, size_t ws_bytes,
-                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen = nullptr) {
+                  void* stream, int cands, std::vector<Tree>& trees, std::vector<std::vector<int>>* chosen = nullptr,
+                  const tnc_plan_opts* completion = nullptr, const std::vector<int>* pcts = nullptr) {
   const int n = (int)nets.size();
   std::vector<GState> st(n);
   for (int i = 0; i < n; i++) st[i].init(*nets[i]);
+  // checkpoints (merge counts) per formula, and the snapshots taken there
+  std::vector<std::vector<int>> marks(n);
+  std::vector<std::vector<GState>> snaps(n);
+  std::vector<int> merged(n, 0);
+  if (completion && pcts)
+    for (int i = 0; i < n; i++) {
+      for (int pc : *pcts) marks[i].push_back(std::max(0, (nets[i]->n_leaves() - 1) * std::min(std::max(pc, 0), 100) / 100));
+      std::sort(marks[i].begin(), marks[i].end());
+      marks[i].erase(std::unique(marks[i].begin(), marks[i].end()), marks[i].end());
+    }
+  auto take_snaps = [&](int i) {  // snapshot at every checkpoint reached; true once past the last
+    while (!marks[i].empty() && snaps[i].size() < marks[i].size() && merged[i] >= marks[i][snaps[i].size()])
+      snaps[i].push_back(st[i]);
+    return !marks[i].empty() && snaps[i].size() == marks[i].size();
+  };
   if (chosen) chosen->assign(n, {});
   std::vector<std::vector<Cand>> cs(n);
   std::vector<float> X, Y;
   const size_t max_rows = (size_t)n * cands;
-  if (ws_bytes < max_rows * (TNC_MLP_FEATURES + 1) * sizeof(float))
+  if (d_params_bf16 && ws_bytes < max_rows * (TNC_MLP_FEATURES + 1) * sizeof(float))
     return set_error(TNC_ERR_BUFFER, "learned planning workspace too small");
   float* dX = (float*)d_ws;
   float* dY = dX + max_rows * TNC_MLP_FEATURES;
@@ -274,7 +357,11 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
     X.clear();
     std::vector<std::pair<int, int>> span(n, {0, 0});
     for (int i = 0; i < n; i++) {
-      top_candidates(st[i], cs[i], cands);
+      if (take_snaps(i)) {  // coarsening done for this formula
+        cs[i].clear();
+        continue;
+      }
+      top_candidates(st[i], cs[i], d_params_bf16 ? cands : 1);
       span[i] = {(int)(X.size() / TNC_MLP_FEATURES), (int)cs[i].size()};
       const int lm = cs[i].empty() ? 0 : live_max_rank(st[i]);
       for (size_t c = 0; c < cs[i].size(); c++) {
@@ -285,14 +372,16 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
     }
     const int64_t rows = (int64_t)(X.size() / TNC_MLP_FEATURES);
     if (rows == 0) break;
-    int rc = TNC_OK;
-    copy_device(dX, X.data(), X.size() * sizeof(float), 0, stream, &rc);
-    if (rc) return rc;
-    rc = mlp_forward_bf16_dev(d_params_bf16, dX, rows, dY, stream);
-    if (rc) return rc;
-    Y.resize(rows);
-    copy_device(Y.data(), dY, rows * sizeof(float), 1, stream, &rc);
-    if (rc) return rc;
+    Y.assign(rows, 0.f);
+    if (d_params_bf16) {
+      int rc = TNC_OK;
+      copy_device(dX, X.data(), X.size() * sizeof(float), 0, stream, &rc);
+      if (rc) return rc;
+      rc = mlp_forward_bf16_dev(d_params_bf16, dX, rows, dY, stream);
+      if (rc) return rc;
+      copy_device(Y.data(), dY, rows * sizeof(float), 1, stream, &rc);
+      if (rc) return rc;
+    }
     for (int i = 0; i < n; i++) {
       if (span[i].second == 0) continue;
       int best = 0;
@@ -300,10 +389,26 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
         if (Y[span[i].first + c] < Y[span[i].first + best]) best = c;
       if (chosen) (*chosen)[i].push_back(best);
       st[i].merge(cs[i][best].a, cs[i][best].b);
+      merged[i]++;
     }
   }
   trees.resize(n);
+#pragma omp parallel for schedule(dynamic, 1)
   for (int i = 0; i < n; i++) {
+    if (completion && !snaps[i].empty()) {  // finish every snapshot by the heuristic, keep the cheapest
+      int best = -1;
+      TreeCost bc;
+      for (size_t j = 0; j < snaps[i].size(); j++) {
+        complete_with(snaps[i][j], *nets[i], *completion);
+        const TreeCost c = tree_cost(snaps[i][j].t);
+        if (best < 0 || cheaper_cost(c, bc)) {
+          best = (int)j;
+          bc = c;
+        }
+      }
+      trees[i] = std::move(snaps[i][best].t);
+      continue;
+    }
     st[i].finish_greedy();  // joins disconnected leftovers
     trees[i] = std::move(st[i].t);
   }

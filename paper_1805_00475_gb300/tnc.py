@@ -40,7 +40,8 @@ EXPORTS = [
     "tnc_learned_load",
     "tnc_mlp_init", "tnc_learned_dataset", "tnc_learned_dataset_on_policy", "tnc_mlp_forward", "tnc_mlp_backward_scratch_floats",
     "tnc_mlp_backward", "tnc_mlp_adam", "tnc_mlp_train_workspace_bytes", "tnc_mlp_train", "tnc_mlp_to_bf16",
-    "tnc_mlp_forward_bf16", "tnc_plan_learned_workspace_bytes", "tnc_plan_learned_many",
+    "tnc_mlp_forward_bf16", "tnc_plan_learned_workspace_bytes", "tnc_plan_learned_many", "tnc_plan_learned_opts",
+    "tnc_learned_dataset_opts",
 ]
 MLP_FEATURES = 16
 MLP_HIDDEN = 128
@@ -82,6 +83,12 @@ class _LaunchCounts(ctypes.Structure):
                                               "p8_pack", "p8_gemm", "p8_split")] + \
                [("p8_tile_n", ctypes.c_int32 * 5)] + \
                [(n, ctypes.c_int32) for n in ("p8_max_chunks", "p8_swapped", "p8_padded", "extract", "crt")]
+
+
+class _LearnedOpts(ctypes.Structure):
+    _fields_ = [("states", ctypes.c_int32), ("cands", ctypes.c_int32), ("completion", ctypes.c_int32),
+                ("n_checkpoints", ctypes.c_int32), ("checkpoints", ctypes.c_int32 * 8), ("max_pct", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class _ContractOpts(ctypes.Structure):
@@ -189,6 +196,12 @@ def lib():
                                        ctypes.POINTER(vp), ctypes.POINTER(_PlanStats), i32p,
                                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_contract_noalloc": ([vp, ctypes.POINTER(_ContractOpts), vp, ctypes.POINTER(_Count)], ctypes.c_int),
+            "tnc_plan_learned_opts": ([ctypes.POINTER(vp), i32, vp, ctypes.POINTER(_LearnedOpts),
+                                       ctypes.POINTER(_PlanOpts), vp, sz, vp, ctypes.POINTER(vp),
+                                       ctypes.POINTER(_PlanStats), i32p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "tnc_learned_dataset_opts": ([ctypes.POINTER(vp), i32, ctypes.POINTER(_LearnedOpts), vp, vp, sz, vp,
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -849,3 +862,65 @@ def plan_learned_many(formulas, params_bf16, fallback: str = "best", rank_cap: i
                                        _p(lmacs, ctypes.c_double)))
     plans = [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), len(formulas[i].open_vars)) for i in range(n)]
     return plans, chose.tolist(), lmacs.tolist()
+
+
+def _learned_opts(states=2, cands=8, completion="best", checkpoints=(), max_pct=100, seed=0):
+    cp = list(checkpoints)[:8]
+    arr = (ctypes.c_int32 * 8)(*(cp + [0] * (8 - len(cp))))
+    return _LearnedOpts(states, cands, HEURISTICS[completion], len(cp), arr, max_pct, seed)
+
+
+def plan_learned_coarsen(formulas, params_bf16=None, completion: str = "best",
+                         checkpoints: Sequence[int] = (20, 35, 50, 65, 80), fallback: str = "best",
+                         rank_cap: int = 64, seed: int = 0, stream=None):
+    """tnc_plan_learned_opts: learned merges coarsen each network, the
+    heuristic `completion` finishes it at each checkpoint (% of the merges),
+    the cheapest is the learned plan, kept only if not worse than `fallback`.
+    params_bf16 None: tensor-greedy coarsening (no scorer, host only).
+    Returns (plans, chose_learned list, learned_macs list)."""
+    nets = [build_network(f) for f in formulas]
+    n = len(nets)
+    arr = (ctypes.c_void_p * n)(*[x.h.value for x in nets])
+    outs = (ctypes.c_void_p * n)()
+    sts = (_PlanStats * n)()
+    chose = np.zeros(n, dtype=np.int32)
+    lmacs = np.zeros(n, dtype=np.float64)
+    ordr = np.zeros(1, dtype=np.int32)
+    fb = _PlanOpts(HEURISTICS[fallback], rank_cap, 2, 0, _p(ordr, ctypes.c_int32), 0)
+    lo = _learned_opts(completion=completion, checkpoints=checkpoints, seed=seed)
+    ws, nb = None, 0
+    if params_bf16 is not None:
+        import torch
+        ws = torch.empty(int(lib().tnc_plan_learned_workspace_bytes(n)), dtype=torch.uint8, device=params_bf16.device)
+        nb = ws.numel()
+    _check(lib().tnc_plan_learned_opts(arr, n, _dp(params_bf16), ctypes.byref(lo), ctypes.byref(fb), _dp(ws), nb,
+                                       _stream_ptr(stream) if params_bf16 is not None else None, outs, sts,
+                                       _p(chose, ctypes.c_int32), _p(lmacs, ctypes.c_double)))
+    plans = [Plan(ctypes.c_void_p(outs[i]), _stats(sts[i]), len(formulas[i].open_vars)) for i in range(n)]
+    return plans, chose.tolist(), lmacs.tolist()
+
+
+def learned_dataset_coarsen(formulas, states: int = 2, cands: int = 8, completion: str = "best", max_pct: int = 80,
+                            seed: int = 0, params_bf16=None, stream=None):
+    """tnc_learned_dataset_opts: rows labelled by heuristic completion
+    ((X [rows, 16], T [rows]) float32)."""
+    nets = [build_network(f) for f in formulas]
+    n = len(nets)
+    arr = (ctypes.c_void_p * n)(*[x.h.value for x in nets])
+    lo = _learned_opts(states=states, cands=cands, completion=completion, max_pct=max_pct, seed=seed)
+    ws, nb = None, 0
+    if params_bf16 is not None:
+        import torch
+        ws = torch.empty(int(lib().tnc_plan_learned_workspace_bytes(n)), dtype=torch.uint8, device=params_bf16.device)
+        nb = ws.numel()
+    st = _stream_ptr(stream) if params_bf16 is not None else None
+    cnt = ctypes.c_int64()
+    rc = lib().tnc_learned_dataset_opts(arr, n, ctypes.byref(lo), _dp(params_bf16), _dp(ws), nb, st, None, None, 0,
+                                        ctypes.byref(cnt))
+    if rc not in (TNC_OK, -4):
+        _check(rc)
+    X = np.zeros((max(cnt.value, 1), MLP_FEATURES), dtype=np.float32)
+    T = np.zeros(max(cnt.value, 1), dtype=np.float32)
+    _check(lib().tnc_learned_dataset_opts(arr, n, ctypes.byref(lo), _dp(params_bf16), _dp(ws), nb, st,
+                                          _p(X, ctypes.c_float), _p(T, ctypes.c_float), cnt.value, ctypes.byref(cnt)))
+    return X[: cnt.value], T[: cnt.value]
