@@ -147,28 +147,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// The same load delivered to every CTA of the cluster in `mask`, at the same
-// shared-memory offset, completing on each one's mbarrier at offset mbar.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
-                                               uint32_t mbar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Every thread of every CTA of the cluster (release / acquire).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // 2-D tiled TMA load of the box at (x, y) into shared memory, completing on
 // mbar with its byte count.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
@@ -213,15 +191,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-// One arrival, once the MMAs issued so far are done, on the mbarrier at
-// offset mbar of every CTA of the cluster in `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                   mbar),
-               "h"(mask)
                : "memory");
 }
 
@@ -406,17 +375,10 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // once, so the next MMAs start while the staged bytes are written out (NA
 // residue bytes of each entry per round, the pass's layout: RG bytes per
 // entry).
-//
-// CL = 2: clusters of two CTAs on two row tiles of the same column tile (and
-// the same K slice): each CTA loads its own A tile and half of the common B
-// tile, which TMA delivers to both CTAs (multicast), so every B byte leaves
-// L2 once for two tiles; a stage is refilled once the MMAs of both CTAs have
-// consumed it (each MMA issuer's commit arrives on both CTAs' barrier).
-template <uint32_t TN, uint32_t RG, uint32_t CL>
+template <uint32_t TN, uint32_t RG>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ P8Args g, uint32_t* err) {
-  static_assert(CL == 1 || CL == 2, "clusters of one or two CTAs");
   using C = Cfg<TN, RG>;
   constexpr uint32_t kStages = C::kStages, kStageBytes = C::kStageBytes, NA = C::NA, kRounds = C::kRounds;
   using SW = StageWord<NA>;
@@ -435,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < kStages; s++) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL);
+      mbar_init(empty0 + 8 * s, 1);
     }
     for (uint32_t r = 0; r < NA; r++) {
       mbar_init(accf0 + 8 * r, 1);
@@ -452,37 +414,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL == 2) cluster_sync();  // the partner's barriers exist before any copy or commit reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
 
-  // work items: CL = 1, item = blockIdx + t gridDim; CL = 2, the cluster takes
-  // pair items (two row tiles of one column tile) and this CTA the row tile
-  // of its rank
-  const uint32_t crank = CL == 2 ? cluster_rank() : 0u;
-  const uint32_t G = gridDim.x / CL, bid = blockIdx.x / CL;
-  const uint32_t n_work = g.n_items / CL;
-  const uint32_t T = n_work > bid ? (n_work - bid + G - 1) / G : 0;
-  auto coords = [&](uint32_t t, uint32_t& split, uint32_t& m0, uint32_t& n0) {
-    const uint32_t item = bid + t * G;
-    split = item & ((1u << g.log_split) - 1u);
-    const uint32_t tile = item >> g.log_split;
-    const uint32_t tm = g.tiles_m / CL;
-    m0 = ((tile % tm) * CL + crank) * kTileM;
-    n0 = (tile / tm) * TN;
-  };
+  const uint32_t G = gridDim.x, bid = blockIdx.x;
+  const uint32_t T = g.n_items > bid ? (g.n_items - bid + G - 1) / G : 0;
   const uint32_t Ks = (1u << g.k) >> g.log_split;
   const uint32_t chunk = Ks < kChunkK ? Ks : kChunkK;
   const uint32_t n_chunks = Ks / chunk;
   const uint32_t spc = chunk / kStageK;  // stages per chunk
+  const uint32_t split_mask = (1u << g.log_split) - 1u;
   bool ok = true;
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
       uint32_t s = 0, ph = 0, issued = 0;
       for (uint32_t t = 0; t < T && ok; t++) {
-        uint32_t split, m0, n0;
-        coords(t, split, m0, n0);
+        const uint32_t item = bid + t * G;
+        const uint32_t split = item & split_mask, tile = item >> g.log_split;
+        const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
         for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
           for (uint32_t ra = 0; ra < NA && ok; ra++) {
@@ -497,11 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int32_t x = (int32_t)(q0 + j * kStageK);
               mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
               tma_load_3d(sa, &tmA, x, (int32_t)m0, (int32_t)r, full0 + 8 * s);
-              if (CL == 2)  // this CTA's half of the B tile, to both CTAs
-                tma_load_3d_mc(sa + kABytes + crank * (TN / 2) * 128u, &tmB, x, (int32_t)(n0 + crank * (TN / 2)),
-                               (int32_t)r, full0 + 8 * s, (uint16_t)3);
-              else
-                tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
+              tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
               issued++;
               if (++s == kStages) {
                 s = 0;
@@ -543,9 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values: 32 bytes into each row
                 mma_f16(d, ad + 2u * ks, bd + 2u * ks, idesc, (c | j | ks) ? 1u : 0u);
-              // the stage is free once these MMAs (and, CL = 2, the partner's) are done
-              if (CL == 2) mma_commit_mc(empty0 + 8 * s, (uint16_t)3);
-              else mma_commit(empty0 + 8 * s);
+              mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
               if (++s == kStages) {
                 s = 0;
                 ph ^= 1u;
@@ -593,8 +537,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t na[NA];
     for (uint32_t r = 0; r < NA; r++) na[r] = 0;
     for (uint32_t t = 0; t < T; t++) {
-      uint32_t split, m0, n0;
-      coords(t, split, m0, n0);
+      const uint32_t item = bid + t * G;
+      const uint32_t split = item & split_mask, tile = item >> g.log_split;
+      const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
       for (uint32_t rd = 0; rd < kRounds; rd++) {
         for (uint32_t c = 0; c < n_chunks; c++) {
           const bool last = c + 1 == n_chunks;
@@ -666,7 +611,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL == 2) cluster_sync();  // no copy or commit of the partner still targets this CTA
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
@@ -716,7 +660,6 @@ int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t rg,
 struct Shape {
   bool swap;                   // rows come from B
   uint32_t fa, fb, k, kp, tn;  // row bits, column bits, shared bits (padded to >= 6), columns per tile
-  uint32_t cl;                 // CTAs per cluster (2: B tiles multicast to two row tiles)
   uint64_t tiles;
 };
 
@@ -736,75 +679,32 @@ Shape shape_of(const StepDesc& d) {
   s.tn = std::min<uint32_t>(1u << s.fb, 128);
   if (s.fb >= 8 && tiles_m * ((1ull << s.fb) / 256) >= kP8WideTiles) s.tn = 256;
   s.tiles = tiles_m * ((1ull << s.fb) / s.tn);
-  // 256-wide tiles in pairs of row tiles sharing their B tile (an even count
-  // of row tiles)
-  s.cl = s.tn == 256 && tiles_m % 2 == 0 ? 2 : 1;
   return s;
 }
 
-// Launches the GEMM for `work` work units (items, or item pairs for CL = 2)
-// on at most one CTA (CL = 2: one cluster of two CTAs) per SM.
-template <uint32_t TN, uint32_t RG, uint32_t CL>
-int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, uint64_t work, int sms,
-                uint32_t* err, cudaStream_t st) {
-  auto kern = tnc_p8::p8_gemm_kernel<TN, RG, CL>;
-  constexpr uint32_t smem = tnc_p8::Cfg<TN, RG>::kSmemBytes;
-  static int max_clusters = -1;  // clusters of two that fit at once (CL = 2)
-  if (max_clusters < 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <uint32_t TN, uint32_t RG>
+int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid, uint32_t* err,
+                cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tnc_p8::Cfg<TN, RG>::kSmemBytes);
     if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
-    max_clusters = 0;
-    if (CL == 2) {
-      cudaLaunchConfig_t cfg{};
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 2;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.gridDim = dim3(2 * (unsigned)std::max(1, sms / 2));
-      cfg.blockDim = dim3(tnc_p8::kThreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
-      if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 cluster occupancy: ") + cudaGetErrorString(e));
-      max_clusters = n;
-    }
+    attr = true;
   }
-  if (CL == 1) {
-    kern<<<(unsigned)std::min<uint64_t>(work, (uint64_t)sms), tnc_p8::kThreads, smem, st>>>(ma, mb, g, err);
-    return TNC_OK;
-  }
-  if (max_clusters <= 0) return set_error(TNC_ERR_CUDA, "no cluster of two CTAs fits the p8 GEMM");
-  cudaLaunchConfig_t cfg{};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(2 * (unsigned)std::min<uint64_t>(work, (uint64_t)max_clusters));
-  cfg.blockDim = dim3(tnc_p8::kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ma, mb, g, err);
-  if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 cluster launch: ") + cudaGetErrorString(e));
+  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::Cfg<TN, RG>::kSmemBytes, st>>>(ma, mb, g, err);
   return TNC_OK;
 }
 
 template <uint32_t RG>
-int launch_gemm_rg(uint32_t tn, uint32_t cl, const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g,
-                   uint64_t work, int sms, uint32_t* err, cudaStream_t st) {
+int launch_gemm_rg(uint32_t tn, const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid,
+                   uint32_t* err, cudaStream_t st) {
   switch (tn) {
-    case 16: return launch_gemm<16, RG, 1>(ma, mb, g, work, sms, err, st);
-    case 32: return launch_gemm<32, RG, 1>(ma, mb, g, work, sms, err, st);
-    case 64: return launch_gemm<64, RG, 1>(ma, mb, g, work, sms, err, st);
-    case 128: return launch_gemm<128, RG, 1>(ma, mb, g, work, sms, err, st);
-    default:
-      return cl == 2 ? launch_gemm<256, RG, 2>(ma, mb, g, work, sms, err, st)
-                     : launch_gemm<256, RG, 1>(ma, mb, g, work, sms, err, st);
+    case 16: return launch_gemm<16, RG>(ma, mb, g, grid, err, st);
+    case 32: return launch_gemm<32, RG>(ma, mb, g, grid, err, st);
+    case 64: return launch_gemm<64, RG>(ma, mb, g, grid, err, st);
+    case 128: return launch_gemm<128, RG>(ma, mb, g, grid, err, st);
+    default: return launch_gemm<256, RG>(ma, mb, g, grid, err, st);
   }
 }
 
@@ -860,7 +760,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   launch_counts().p8_pack++;
   CUtensorMap ma, mb;
   int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
-  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn / s.cl);
+  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
   if (rc) return rc;
   tnc_p8::P8Args g;
   std::memset(&g, 0, sizeof(g));
@@ -911,10 +811,10 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     for (size_t i = 0; i < bits.size(); i++) g.ebit[i] = bits[i].second;
   }
   g.out = ls ? part : arena + d.c_off * rg;
-  const uint64_t work = g.n_items / s.cl;
-  if (rg == 4) rc = launch_gemm_rg<4>(s.tn, s.cl, ma, mb, g, work, sms, dev_err, st);
-  else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, s.cl, ma, mb, g, work, sms, dev_err, st);
-  else rc = launch_gemm_rg<1>(s.tn, s.cl, ma, mb, g, work, sms, dev_err, st);
+  const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
+  if (rg == 4) rc = launch_gemm_rg<4>(s.tn, ma, mb, g, grid, dev_err, st);
+  else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, ma, mb, g, grid, dev_err, st);
+  else rc = launch_gemm_rg<1>(s.tn, ma, mb, g, grid, dev_err, st);
   if (rc) return rc;
   {
     tnc_launch_counts& lc = launch_counts();
