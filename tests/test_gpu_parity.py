@@ -209,3 +209,27 @@ def test_user_primes_int64_and_batch(which):
     b.launch(ws, stream)
     for r, z in zip(b.download(ws, stream), exact):
         _check(r, z, len(primes))
+
+
+def test_autotune_choice_is_persisted_and_reused(tmp_path):
+    """The autotuned launch shape is written to a JSON file keyed by device
+    and batch sizes; a second batch of the same sizes reads it back (no
+    timing) and counts the same."""
+    import json
+    import torch
+    forms = [I.cubic_vertex_cover(40, s) for s in range(64)]
+    plans = tnc.plan_many(forms, heuristic="gn")
+    cache = str(tmp_path / "tune.json")
+    st = torch.cuda.Stream()
+    b1 = tnc.Batch(plans, n_residues=2)
+    ws = torch.empty(b1.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    b1.upload(ws, st)
+    shape1 = b1.autotune_cached(ws, st, cache=cache)
+    assert tuple(shape1) == b1.get_launch()
+    table = json.load(open(cache))
+    assert list(table.values()) == [list(shape1)]
+    b2 = tnc.Batch(plans, n_residues=2)
+    b2.upload(ws, st)
+    assert tuple(b2.autotune_cached(ws, st, cache=cache)) == tuple(shape1) == b2.get_launch()
+    b2.launch(ws, st)
+    assert [o.counts for o in b2.download(ws, st)] == [oracle.count(f) for f in forms]
