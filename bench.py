@@ -366,7 +366,7 @@ def run_c5(args):
     t0 = time.perf_counter()
     losses = []
     for rnd in range(2):
-        # round 1 adds states along the learned planner's own merges
+        # the second training round adds states along the learned planner's own merges
         if rnd == 1:
             t1 = time.perf_counter()
             X2, T2 = tnc.learned_dataset_coarsen(train[: len(train) // 2], states=2, cands=tnc.LEARNED_CANDIDATES,
