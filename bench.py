@@ -740,10 +740,10 @@ def run_tnc(args):
     from paper_1805_00475_gb300 import tnc
 
     rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group(backend="nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group(backend="nccl", init_method="env://", device_id=dev)
 
     forms = workload(rank, args.batch)
     t = time.perf_counter()

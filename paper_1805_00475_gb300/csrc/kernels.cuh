@@ -581,8 +581,7 @@ template <int RG, bool N30 = false>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
   extern __shared__ uint4 smem_raw[];
   __shared__ uint32_t task;
-  __shared__ uint32_t seg_ctr[2];  // next segment of the current level (alternating by level parity)
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint4* blob = smem_raw;
   uint32_t* sarena = reinterpret_cast<uint32_t*>(smem_raw + (a.blob_cap >> 4));
   for (;;) {
@@ -591,7 +590,6 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
     const uint32_t t = task;
     if (t >= a.n_forms) break;
     const BForm f = a.forms[a.order[t]];
-    if (threadIdx.x == 0) seg_ctr[0] = seg_ctr[1] = 0;  // visible after the barrier below
     for (uint32_t i = threadIdx.x; i < f.blob_n; i += blockDim.x) blob[i] = a.blobs[f.blob + i];
     uint32_t* arena = f.arena <= a.smem_cap ? sarena : a.garena + (uint64_t)blockIdx.x * a.slot_entries * RG;
     for (uint32_t l = threadIdx.x; l < f.nleaf; l += blockDim.x) {
@@ -614,17 +612,8 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs a, ModGroup mg) {
     const uint32_t* lvl = reinterpret_cast<const uint32_t*>(bb + f.lvl_at);
     const int2* deltas = reinterpret_cast<const int2*>(bb + f.dl_at);
     for (uint32_t l = 0; l < f.nlev; l++) {
-      const uint32_t s0 = lvl[l], s1 = lvl[l + 1];
-      // warps take the level's segments (longest first) one at a time from a
-      // shared counter, so that they finish the level together; the other
-      // parity's counter, last used by the previous level, is reset for the
-      // next one (every warp has passed the barrier that ended it)
-      if (threadIdx.x == 0) seg_ctr[(l + 1) & 1] = 0;
-      for (;;) {
-        uint32_t sg = 0;
-        if (lane == 0) sg = s0 + atomicAdd(&seg_ctr[l & 1], 1u);
-        sg = __shfl_sync(0xFFFFFFFFu, sg, 0);
-        if (sg >= s1) break;
+      const uint32_t s1 = lvl[l + 1];
+      for (uint32_t sg = lvl[l] + warp; sg < s1; sg += nwarps) {
         const Seg seg = segs[sg];
         if (seg.step != kPacked) {
           // a block of V entries per lane group of one step
