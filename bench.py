@@ -551,7 +551,7 @@ def c4_block(args, dev, steps, warmup, compare):
     macs = sum(p.stats.total_macs for p in plans)
     dense = sum(p.stats.dense_macs for p in plans)
     dense8 = sum(p.stats.dense_macs_p8 for p in plans)
-    dense_ms, device_ms, launches, io = [], [], [], []
+    dense_ms, device_ms, launches, io, steps_rec = [], [], [], [], []
 
     def one_pass(path, timed=False):
         R = R8 if path == "tc_p8" else Rc
@@ -564,6 +564,8 @@ def c4_block(args, dev, steps, warmup, compare):
             assert r.flags == 0
             counts.append(r.counts[0])
             dms += tnc.last_dense_time()[0]
+            if timed:
+                steps_rec.extend(tnc.last_dense_steps())
             gms += tnc.last_contract_time()
             lc = tnc.last_launch_counts()
             nl += sum(v for k, v in lc.items() if k not in ("p8_tile_n", "p8_max_chunks", "p8_swapped",
@@ -605,6 +607,23 @@ def c4_block(args, dev, steps, warmup, compare):
     # path: 16 limb products per MAC and residue
     p8_flops = dense8 * R8 * 2
     dev_ms = sum(device_ms) / len(device_ms)
+    # per dense step: attained fraction of the peak (flops = 2 macs residues);
+    # MAC-weighted by class (tile width, long or short shared dimension) and
+    # the largest steps
+    peak = pk["bf16_tflops"] * 1e12
+    by_class = {}
+    for r in steps_rec:
+        key = f"tile{r['tile_n']}_{'k>=10' if r['k_log2'] >= 10 else 'k<10'}"
+        c = by_class.setdefault(key, [0.0, 0.0, 0])
+        c[0] += 2 * r["macs"] * r["residues"]
+        c[1] += r["ms"]
+        c[2] += 1
+    classes = {k: {"launches": v[2] // max(1, len(dense_ms)), "share_of_dense_flops": v[0] / max(1e-30, sum(
+        x[0] for x in by_class.values())), "frac": v[0] / (v[1] / 1000.0) / peak} for k, v in sorted(by_class.items())}
+    top = sorted(steps_rec, key=lambda r: -r["macs"] * r["residues"])[:5]
+    largest = [{"rows_log2": r["rows_log2"], "cols_log2": r["cols_log2"], "k_log2": r["k_log2"],
+                "residues": r["residues"], "tile_n": r["tile_n"], "ms": r["ms"],
+                "frac": 2 * r["macs"] * r["residues"] / (r["ms"] / 1000.0) / peak} for r in top]
     return {
         "workload": f"cubic_vertex_cover_n180_{len(kept)}formulas", "seeds": [k[0] for k in kept],
         "max_ranks": [p.stats.max_rank for p in plans], "planner": "best",
@@ -633,7 +652,10 @@ def c4_block(args, dev, steps, warmup, compare):
                      "dense_ms_per_step": dms, "dense_share_of_device_time": dms / dev_ms,
                      "whole_contraction_tflops": p8_flops / s / 1e12,
                      "algorithmic_flops_per_step": p8_flops,
-                     "flops": "sum over dense steps of 2^(a+b-k) x residues x 2"},
+                     "flops": "sum over dense steps of 2^(a+b-k) x residues x 2",
+                     "per_step": {"by_class": classes, "largest_launches": largest,
+                                  "note": "fraction of the measured peak per dense launch (packing + GEMM), from "
+                                          "CUDA events around each launch"}},
         "clocks": clk, "plan_s": plan_s,
         "counts_log2": [round(math.log2(c), 2) for c in counts],
     }

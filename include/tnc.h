@@ -280,6 +280,20 @@ int tnc_contract_many(const tnc_plan_t* const* plans, int32_t n, const tnc_contr
  * and the number of dense step launches of the last tnc_contract. */
 void tnc_set_step_timing(int32_t on);
 int tnc_last_dense_time(double* ms, int32_t* n_steps);
+/* Same mode, step by step: the device time of every dense step launch of the
+ * last contraction (operand packing + GEMM + split sum, in launch order) and
+ * its shape, for per-step roofline fractions (flops = 2 * macs * residues). */
+typedef struct {
+  double ms;         /* CUDA-event time of the launch                           */
+  double macs;       /* 2^(a+b-k): multiply-accumulates per residue              */
+  int32_t rows_log2; /* free bits of the two operands (before any exchange)      */
+  int32_t cols_log2;
+  int32_t k_log2;    /* shared bonds                                              */
+  int32_t residues;  /* residues computed by the launch                           */
+  int32_t tile_n;    /* columns per tile                                          */
+  int32_t log_split; /* K split                                                   */
+} tnc_dense_step_time;
+int tnc_last_dense_steps(tnc_dense_step_time* out, int32_t cap, int32_t* n);
 /* Same mode: device time (ms) of the last tnc_contract's kernels, from its
  * first launch to its CRT (host work and the final copies excluded). */
 int tnc_last_contract_time(double* device_ms);

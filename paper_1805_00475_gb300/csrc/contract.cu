@@ -48,6 +48,7 @@ thread_local double g_dense_ms = 0.0;
 thread_local int g_dense_launches = 0;
 thread_local double g_total_ms = 0.0;
 thread_local tnc_launch_counts g_launches{};
+thread_local std::vector<tnc_dense_step_time> g_dense_steps;  // timing mode: per dense launch
 thread_local uint64_t g_h2d_bytes = 0, g_d2h_bytes = 0;  // host <-> device copies of the last contraction
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -387,6 +388,15 @@ extern "C" int tnc_last_dense_time(double* ms, int32_t* n_steps) {
   return TNC_OK;
 }
 
+extern "C" int tnc_last_dense_steps(tnc_dense_step_time* out, int32_t cap, int32_t* n) {
+  if (n) *n = (int32_t)g_dense_steps.size();
+  if (!out) return TNC_OK;
+  if (cap < (int32_t)g_dense_steps.size())
+    return set_error(TNC_ERR_BUFFER, "need " + std::to_string(g_dense_steps.size()) + " entries");
+  std::copy(g_dense_steps.begin(), g_dense_steps.end(), out);
+  return TNC_OK;
+}
+
 extern "C" int tnc_last_contract_time(double* device_ms) {
   if (device_ms) *device_ms = g_total_ms;
   return TNC_OK;
@@ -563,6 +573,7 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
   CUDA_TRY(cudaMemsetAsync(d_err, 0, 64, st));
   // dense-step events (tnc_set_step_timing), destroyed on every return
   std::vector<cudaEvent_t> dense_events;
+  std::vector<tnc_dense_step_time> dense_info;  // shapes of the timed dense launches
   struct EventGuard {
     std::vector<cudaEvent_t>& v;
     ~EventGuard() {
@@ -637,6 +648,15 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
               CUDA_TRY(cudaEventRecord(ev[1], st));
               dense_events.push_back(ev[0]);
               dense_events.push_back(ev[1]);
+              tnc_dense_step_time info{};
+              info.macs = std::ldexp(1.0, b.d.ka + b.d.kb + b.d.k);
+              info.rows_log2 = b.d.ka;
+              info.cols_log2 = b.d.kb;
+              info.k_log2 = b.d.k;
+              info.residues = RG;
+              info.tile_n = p8 ? (int32_t)p8_tile_width(b.d) : 32;
+              info.log_split = (int32_t)(p8 ? p8_split_log(b.d) : tc_split_log(b.d));
+              dense_info.push_back(info);
             }
             if (rc2) return rc2;
           } else if (b.kind == kSplit) {
@@ -709,6 +729,9 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
     }
     g_dense_ms += ms;
     g_dense_launches++;
+    tnc_dense_step_time info = dense_info[e / 2 - 1];
+    info.ms = ms;
+    g_dense_steps.push_back(info);
   }
   for (int w = 0; w < nw; w++) {
     rc = fill_count(&outs[work_idx[w]], 1ull << rms[w].n_open, a, h_res.data() + L.res_base[w] * a.R,
@@ -726,6 +749,7 @@ static void reset_records() {
   g_dense_ms = 0.0;
   g_dense_launches = 0;
   g_total_ms = 0.0;
+  g_dense_steps.clear();
 }
 
 extern "C" int tnc_contract(const tnc_plan_t* plan, const tnc_contract_opts* opts, void* dev_ws, size_t ws_bytes,

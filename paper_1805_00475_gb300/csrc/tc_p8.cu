@@ -725,6 +725,8 @@ uint32_t p8_split_log(const StepDesc& d) {
   return ls;
 }
 
+uint32_t p8_tile_width(const StepDesc& d) { return shape_of(d).tn; }
+
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
   const uint32_t kp = std::max<uint32_t>(d.k, 6);
   return 2ull * (uint64_t)rg * ((1ull << (d.ka + kp)) + (1ull << (d.kb + kp)));

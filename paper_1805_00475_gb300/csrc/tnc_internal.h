@@ -138,6 +138,7 @@ bool tc_eligible(const StepDesc& d);
 // TNC_PATH_TC_P8 dense steps (tc_p8.cu).
 bool p8_eligible(const StepDesc& d);
 uint32_t p8_split_log(const StepDesc& d);
+uint32_t p8_tile_width(const StepDesc& d);
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg);
 uint64_t p8_part_bytes(const StepDesc& d, int rg);
 // One dense step for all rg residues (primes[0..rg)) of a pass whose entries

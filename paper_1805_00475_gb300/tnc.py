@@ -32,7 +32,7 @@ INJECT = {"none": 0, "nomem": 1, "plan": 2, "launch": 3, "timeout": 4}
 # every symbol include/tnc.h declares
 EXPORTS = [
     "tnc_version", "tnc_last_error", "tnc_default_primes", "tnc_default_primes_p8", "tnc_build_network", "tnc_network_info",
-    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_sliced", "tnc_slice_network", "tnc_network_formula", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
+    "tnc_free_network", "tnc_plan", "tnc_plan_many", "tnc_plan_sliced", "tnc_slice_network", "tnc_network_formula", "tnc_plan_steps", "tnc_free_plan", "tnc_workspace_bytes", "tnc_workspace_bytes_opts", "tnc_set_step_timing", "tnc_last_dense_time", "tnc_last_contract_time", "tnc_last_launch_counts", "tnc_last_io_bytes", "tnc_last_dense_steps", "tnc_workspace_bytes_sliced", "tnc_contract_sliced",
     "tnc_workspace_bytes_many", "tnc_contract_many",
     "tnc_contract", "tnc_crt_host", "tnc_residue_add_host", "tnc_batch_create", "tnc_batch_workspace_bytes", "tnc_batch_info", "tnc_batch_upload", "tnc_batch_autotune", "tnc_batch_set_launch", "tnc_batch_get_launch",
     "tnc_batch_launch", "tnc_batch_download", "tnc_batch_download_flat", "tnc_batch_status", "tnc_free_batch",
@@ -91,6 +91,11 @@ class _LearnedOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class _DenseStepTime(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("macs", ctypes.c_double)] + \
+               [(n, ctypes.c_int32) for n in ("rows_log2", "cols_log2", "k_log2", "residues", "tile_n", "log_split")]
+
+
 class _ContractOpts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("n_residues", ctypes.c_int32),
                 ("primes", ctypes.POINTER(ctypes.c_uint32))]
@@ -147,6 +152,7 @@ def lib():
             "tnc_last_contract_time": ([ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "tnc_last_launch_counts": ([ctypes.POINTER(_LaunchCounts)], ctypes.c_int),
             "tnc_last_io_bytes": ([ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+            "tnc_last_dense_steps": ([ctypes.POINTER(_DenseStepTime), i32, i32p], ctypes.c_int),
             "tnc_workspace_bytes_sliced": ([vp, i32, vp], sz),
             "tnc_contract_sliced": ([vp, i32, vp, vp, sz, vp, vp], ctypes.c_int),
             "tnc_workspace_bytes_many": ([vp, i32, vp, i32], sz),
@@ -540,6 +546,17 @@ def last_launch_counts() -> dict:
     d = {n: int(getattr(c, n)) for n, _ in _LaunchCounts._fields_ if n != "p8_tile_n"}
     d["p8_tile_n"] = {w: int(c.p8_tile_n[i]) for i, w in enumerate(P8_TILE_WIDTHS)}
     return d
+
+
+def last_dense_steps() -> List[dict]:
+    """tnc_last_dense_steps: per dense launch of the last contraction (timing
+    mode): ms, macs per residue, operand free bits, shared bits, residues,
+    tile width, K split."""
+    n = ctypes.c_int32()
+    _check(lib().tnc_last_dense_steps(None, 0, ctypes.byref(n)))
+    arr = (_DenseStepTime * max(n.value, 1))()
+    _check(lib().tnc_last_dense_steps(arr, n.value, ctypes.byref(n)))
+    return [{f: getattr(arr[i], f) for f, _ in _DenseStepTime._fields_} for i in range(n.value)]
 
 
 def last_io_bytes() -> Tuple[int, int]:
