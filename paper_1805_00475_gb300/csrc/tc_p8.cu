@@ -53,7 +53,12 @@ constexpr uint32_t kChunkK = 1024;
 constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
 constexpr uint32_t kEpiThreads = 256;
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
-constexpr uint32_t kStagePitch = kTileM + 1;        // staged entries per column (+1: fewer bank conflicts)
+// Staged entries per column of the output tile: at least the tile's 128 rows,
+// padded so that a column's stride is an odd number of 32-bit words (entries
+// of NA bytes: 132, 130 and 129 for NA = 1, 2, 4), which keeps both the
+// staging writes (lanes along rows) and the reads (lanes along rows or
+// along columns) free of bank conflicts.
+__host__ __device__ constexpr uint32_t stage_pitch(uint32_t na) { return na == 4 ? 129u : (na == 2 ? 130u : 132u); }
 
 // Shared-memory plan of a tile width: NA = min(RG, 512 / TN) residues
 // accumulate together (NA TMEM accumulators of TN fp32 columns), in RG / NA
@@ -67,6 +72,7 @@ struct Cfg {
   static constexpr uint32_t NA = RG * TN <= 512 ? RG : 512 / TN;
   static constexpr uint32_t kRounds = RG / NA;
   static constexpr uint32_t kStageBytes = (kABytes + TN * kStageK * 2 + 1023u) / 1024u * 1024u;
+  static constexpr uint32_t kStagePitch = stage_pitch(NA);
   static constexpr uint32_t kStagingBytes = (TN * kStagePitch * NA + 15u) / 16u * 16u;
   static constexpr uint32_t kFit = (220u * 1024u - kStagingBytes) / kStageBytes;
   static constexpr uint32_t kStages = kFit > 8 ? 8 : kFit;
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   using C = Cfg<TN, RG>;
   constexpr uint32_t kStages = C::kStages, kStageBytes = C::kStageBytes, NA = C::NA, kRounds = C::kRounds;
   using SW = StageWord<NA>;
+  constexpr uint32_t kStagePitch = C::kStagePitch;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * NA + 1];
   __shared__ uint32_t tmem_base_s;
@@ -599,10 +606,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         epi_bar();  // every residue of the round is staged
         if (ok) {
           uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA;
-          for (uint32_t e = et; e < kTileM * TN; e += kEpiThreads) {
-            const uint32_t hc = hi_tab[e >> 5];
-            const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
-            *reinterpret_cast<SW*>(outp + (om_tab[rr] + on_tab[cc]) * RG) = staging[cc * kStagePitch + rr];
+          // four entries per trip, their loads issued before their stores
+          static_assert((kTileM * TN) % (4 * kEpiThreads) == 0, "whole trips of four");
+          for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
+            uint64_t adr[4];
+            SW val[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+              const uint32_t hc = hi_tab[(e0 + u * kEpiThreads) >> 5];
+              const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
+              adr[u] = (om_tab[rr] + on_tab[cc]) * RG;
+              val[u] = staging[cc * kStagePitch + rr];
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) *reinterpret_cast<SW*>(outp + adr[u]) = val[u];
           }
         }
       }
