@@ -50,8 +50,9 @@ namespace tnc_p8 {
 constexpr uint32_t kTileM = 128;
 constexpr uint32_t kStageK = 64;
 constexpr uint32_t kChunkK = 1024;
-constexpr uint32_t kThreads = 320;  // 2 role warps + 8 epilogue warps
-constexpr uint32_t kEpiThreads = 256;
+constexpr uint32_t kEpiWarps = 16;  // 4 per TMEM lane quarter, each a quarter of the columns
+constexpr uint32_t kThreads = 64 + 32 * kEpiWarps;  // 2 role warps + the epilogue warps
+constexpr uint32_t kEpiThreads = 32 * kEpiWarps;
 constexpr uint32_t kABytes = kTileM * kStageK * 2;  // 16 KiB
 // Staged entries per column of the output tile: at least the tile's 128 rows,
 // padded so that a column's stride is an odd number of 32-bit words (entries
@@ -518,10 +519,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t et = threadIdx.x - 64u;
     const uint32_t quarter = warp & 3u;
     const uint32_t row = quarter * 32u + lane;
-    constexpr uint32_t kHalf = TN >= 32 ? TN / 2 : TN;  // columns per epilogue warp
+    // columns per epilogue warp: the tile's columns shared by the warps of a
+    // lane quarter, at least 16 per warp (the rest of the warps idle)
+    constexpr uint32_t kGroups = kEpiWarps / 4 < TN / 16 ? kEpiWarps / 4 : TN / 16;
+    constexpr uint32_t kHalf = TN / kGroups;
     constexpr uint32_t kBatch = kHalf >= 32 ? 32 : 16;  // columns per TMEM load batch
     const uint32_t cbeg = ((warp - 2u) >> 2) * kHalf;
-    const bool idle = cbeg >= TN;                         // second half when TN = 16
+    const bool idle = cbeg >= TN;
     uint8_t* stage8 = reinterpret_cast<uint8_t*>(staging);
     // write order of a tile's entries: entry index e has the tile's row and
     // column bits ordered by output weight, so consecutive e are as close in C
