@@ -21,11 +21,11 @@
 // contiguous.  TMA moves tiles of rows x 64 values (128-byte lines) into
 // shared memory with the 128-byte swizzle, the canonical K-major SWIZZLE_128B
 // layout of the MMA operand descriptors.
-// Persistent CTAs (one per SM, 320 threads) run three warp roles:
+// Persistent CTAs (one per SM, 576 threads) run three warp roles:
 //   warp 0, lane 0: TMA producer over a ring of 3 to 8 shared-memory stages;
 //   warp 1, lane 0: MMA issuer (kind::f16, 128 x TN x 16, fp32 in TMEM);
-//   warps 2..9: epilogue (TMEM lane quarter = warp % 4, column half =
-//   (warp - 2) / 4).
+//   warps 2..17: epilogue (TMEM lane quarter = warp % 4, column group =
+//   (warp - 2) / 4, a quarter of the tile's columns, at least 16).
 // A work item is an output tile of 128 rows x TN columns (TN <= 256) and a K
 // slice; NA = min(RG, 512 / TN) residues accumulate at once, one TMEM
 // accumulator each, so one residue's reduction overlaps the next residue's
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) atomicExch(err, 1u);
     }
   } else {
-    // epilogue: warps 2..9; TMEM lanes 32 (warp % 4) .., column half (warp - 2) / 4.
+    // epilogue: warps 2..17; TMEM lanes 32 (warp % 4) .., column group (warp - 2) / 4.
     // Every epilogue thread runs the same loop trips and named barriers; a
     // failed wait only turns the thread's work off.
     const uint32_t et = threadIdx.x - 64u;
