@@ -473,11 +473,14 @@ __device__ __forceinline__ void step_sum_fixed(uint32_t ka, uint32_t kb, const u
   uint64_t acc[RG];
 #pragma unroll
   for (int r = 0; r < RG; r++) acc[r] = 0;
+  const size_t sa = (size_t)RG << ka, sb = (size_t)RG << kb;
 #pragma unroll
   for (uint32_t q = 0; q < (1u << KK); q++) {
     uint32_t va[RG], vb[RG];
-    load_entry<RG>(A + ((q << ka) * RG), va);
-    load_entry<RG>(B + ((q << kb) * RG), vb);
+    load_entry<RG>(A, va);
+    load_entry<RG>(B, vb);
+    A += sa;
+    B += sb;
 #pragma unroll
     for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
   }
@@ -503,13 +506,16 @@ __device__ __forceinline__ void batch_sum(uint32_t k, uint32_t ka, uint32_t kb, 
 #pragma unroll
         for (int r = 0; r < RG; r++) acc[r] = 0;
         const uint32_t K = 1u << k;
+        const size_t sa = (size_t)RG << ka, sb = (size_t)RG << kb;
 #pragma unroll 1
         for (uint32_t q = 0; q < K; q += 4) {
 #pragma unroll
           for (uint32_t u = 0; u < 4; u++) {
             uint32_t va[RG], vb[RG];
-            load_entry<RG>(A + (((q + u) << ka) * RG), va);
-            load_entry<RG>(B + (((q + u) << kb) * RG), vb);
+            load_entry<RG>(A, va);
+            load_entry<RG>(B, vb);
+            A += sa;
+            B += sb;
 #pragma unroll
             for (int r = 0; r < RG; r++) acc[r] += (uint64_t)va[r] * vb[r];
           }
