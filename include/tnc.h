@@ -148,6 +148,10 @@ typedef struct {
   double dense_macs;      /* their share of total_macs                             */
   int32_t n_dense_steps_p8; /* steps TNC_PATH_TC_P8 runs on the tensor cores       */
   double dense_macs_p8;     /* their share of total_macs                           */
+  int32_t n_direct_p8;      /* of those, steps whose output goes straight to the fp16
+                               operand planes of the next dense step (no packing)  */
+  uint64_t p8_arena_entries; /* arena of TNC_PATH_TC_P8 (such outputs take twice
+                               their entries)                                      */
 } tnc_plan_stats;
 
 typedef struct {
@@ -318,6 +322,10 @@ typedef struct {
   int32_t p8_padded;      /*   with fewer than 64 shared values, zero-padded to 64     */
   int32_t extract;        /* root tensor -> result residues                          */
   int32_t crt;            /* Chinese remaindering                                     */
+  int32_t p8_direct_out;  /* TNC_PATH_TC_P8 dense steps whose output went straight to
+                             the fp16 planes the consuming dense step reads           */
+  int32_t p8_direct_in;   /* dense-step operands read from such planes (not packed)   */
+  int32_t p8_mn;          /* dense-step operands read row-contiguous (MN-major)       */
 } tnc_launch_counts;
 int tnc_last_launch_counts(tnc_launch_counts* out);
 /* Bytes the calling thread's last tnc_contract or tnc_contract_sliced copied

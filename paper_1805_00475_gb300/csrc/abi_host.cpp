@@ -57,6 +57,9 @@ int finish_plan(tnc_plan_t* p, int rank_cap, tnc_plan_stats* stats) {
       s.dense_macs_p8 += std::ldexp(1.0, d.ka + d.kb + d.k);
     }
   }
+  s.n_direct_p8 = 0;
+  for (uint8_t x : p->low.p8_direct) s.n_direct_p8 += x;
+  s.p8_arena_entries = p->low.p8_arena_entries;
   if (stats) *stats = s;
   return TNC_OK;
 }

@@ -278,7 +278,9 @@ Foot foot_of(const tnc_plan_t* p, int R, int path) {
       f.p8 = std::max<uint64_t>(f.p8, p8_scratch_bytes(d, rg_max));
     }
   }
-  f.arena = (std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries) + 63) / 64 * 64;
+  uint64_t arena = std::max(p->low.seq_arena_entries, p->low.lvl_arena_entries);
+  if (path == TNC_PATH_TC_P8) arena = std::max(arena, p->low.p8_arena_entries);
+  f.arena = (arena + 63) / 64 * 64;
   return f;
 }
 
@@ -490,7 +492,7 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
     const Lowered& lw = work[w]->low;
     for (size_t i = 0; i < lw.leaves.size(); i++) {
       LeafDesc ld = lw.leaves[i];
-      ld.off = lw.lvl_leaf_off[i] + L.arena_base[w];
+      ld.off = (p8 ? lw.p8_leaf_off[i] : lw.lvl_leaf_off[i]) + L.arena_base[w];
       ld.table_off += (uint32_t)L.table_base[w];
       leaves.push_back(ld);
     }
@@ -507,7 +509,8 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
   enum Kind { kGrid, kSplit, kTc };
   struct Big {
     int kind, slot;
-    StepDesc d;  // offsets shifted to the group's arena
+    StepDesc d;      // offsets shifted to the group's arena
+    uint32_t flags;  // p8: direct fp16 planes (kP8Direct*)
   };
   std::vector<std::vector<Big>> big(n_lev);
   std::vector<GridStep> gsteps;
@@ -523,14 +526,23 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
       if (l + 1 >= lw.lvl_start.size()) continue;
       const uint64_t base = L.arena_base[w];
       for (uint32_t i = lw.lvl_start[l]; i < lw.lvl_start[l + 1]; i++) {
-        StepDesc d = lw.lvl_steps[i];
+        StepDesc d = p8 ? lw.p8_steps[i] : lw.lvl_steps[i];
         d.a_off += base;
         d.b_off += base;
         d.c_off += base;
+        uint32_t flags = 0;
+        if (p8) {
+          const int sa = lw.lvl_src_a[i], sb = lw.lvl_src_b[i];
+          if (lw.p8_direct[i]) flags |= kP8DirectOut;
+          if (sa >= 0 && lw.p8_direct[sa]) flags |= kP8DirectA;
+          if (sb >= 0 && lw.p8_direct[sb]) flags |= kP8DirectB;
+        }
         if (tc && (p8 ? p8_eligible(d) : tc_eligible(d))) {
-          big[l].push_back(Big{kTc, (int)nd++, d});
+          big[l].push_back(Big{kTc, (int)nd++, d, flags});
+        } else if (flags) {
+          return set_error(TNC_ERR_INVALID, "internal: direct fp16 planes on a CUDA-core step");
         } else if (splitk_log(d) > 0 || d.c >= 16) {
-          big[l].push_back(Big{splitk_log(d) > 0 ? kSplit : kGrid, (int)gsteps.size(), d});
+          big[l].push_back(Big{splitk_log(d) > 0 ? kSplit : kGrid, (int)gsteps.size(), d, 0});
           gsteps.push_back(make_grid_step(d));
         } else {
           d.work_lo = (uint32_t)wk;
@@ -599,7 +611,8 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
     rms[w] = RootMap{};
     rms[w].n_open = (int)work[w]->net.open_vars.size();
     for (int j = 0; j < rms[w].n_open; j++) rms[w].perm[j] = lw.root_perm[j];
-    root_off[w] = L.arena_base[w] + (lw.lvl_steps.empty() ? lw.lvl_leaf_off[work[w]->tree.root] : lw.lvl_root_off);
+    root_off[w] = L.arena_base[w] + (lw.lvl_steps.empty() ? (p8 ? lw.p8_leaf_off : lw.lvl_leaf_off)[work[w]->tree.root]
+                                                          : (p8 ? lw.p8_root_off : lw.lvl_root_off));
   }
   const int sms = sm_count();
   for (size_t gi = 0; gi < groups.rg.size(); gi++) {
@@ -639,7 +652,8 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
             }
             if (p8) {
               rc2 = p8_launch(b.d, a.primes.data() + groups.col[gi], RG, reinterpret_cast<uint8_t*>(arena),
-                              ws + L.off_p8, reinterpret_cast<uint8_t*>(part), d_err, sms, st);
+                              (uint64_t)(L.total - L.off_arena), b.flags, ws + L.off_p8,
+                              reinterpret_cast<uint8_t*>(part), d_err, sms, st);
             } else {
               const char* dstep = ws + L.off_tc + ((size_t)b.slot * a.R + groups.col[gi]) * tc_step_bytes();
               rc2 = tc_launch(dstep, b.d, reinterpret_cast<uint32_t*>(arena), part, d_err, st);

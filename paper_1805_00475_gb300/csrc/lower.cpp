@@ -18,9 +18,10 @@
 namespace tnc {
 
 // Interval allocation: tensors live over [t0, t1] (inclusive); two tensors
-// whose lifetimes overlap never share memory.  First fit in t0 order.
+// whose lifetimes overlap never share memory.  First fit in t0 order; offsets
+// are multiples of `align` entries.
 static uint64_t allocate(const std::vector<uint64_t>& size, const std::vector<int>& t0,
-                         const std::vector<int>& t1, std::vector<uint64_t>& off) {
+                         const std::vector<int>& t1, std::vector<uint64_t>& off, uint64_t align = 8) {
   const size_t n = size.size();
   std::vector<int> ord(n);
   for (size_t i = 0; i < n; i++) ord[i] = (int)i;
@@ -30,7 +31,6 @@ static uint64_t allocate(const std::vector<uint64_t>& size, const std::vector<in
   off.assign(n, 0);
   std::vector<int> active;
   uint64_t peak = 0;
-  const uint64_t align = 8;
   for (int i : ord) {
     active.erase(std::remove_if(active.begin(), active.end(), [&](int a) { return t1[a] < t0[i]; }),
                  active.end());
@@ -230,6 +230,7 @@ int lower_plan(const Network& net, const Tree& tree, Lowered& low) {
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return lvl[a] < lvl[b]; });
     int nlev = lvl[root];
     low.lvl_start.assign(nlev + 1, 0);
+    std::vector<int> idx_of(N, -1);  // node -> index in lvl_steps
     size_t p = 0;
     for (int l = 1; l <= nlev; l++) {
       low.lvl_start[l - 1] = (uint32_t)p;
@@ -242,12 +243,50 @@ int lower_plan(const Network& net, const Tree& tree, Lowered& low) {
         d.c_off = off[z];
         d.work_lo = (uint32_t)work;
         work += 1ull << d.c;
+        idx_of[z] = (int)low.lvl_steps.size();
         low.lvl_steps.push_back(d);
         p++;
       }
     }
     low.lvl_start[nlev] = (uint32_t)p;
     low.lvl_root_off = off[root];
+    // producers and consumers among the level schedule's steps
+    low.lvl_src_a.assign(low.lvl_steps.size(), -1);
+    low.lvl_src_b.assign(low.lvl_steps.size(), -1);
+    low.lvl_dst.assign(low.lvl_steps.size(), -1);
+    for (int z = L; z < N; z++) {
+      const int i = idx_of[z];
+      low.lvl_src_a[i] = idx_of[tree.nodes[z].left];
+      low.lvl_src_b[i] = idx_of[tree.nodes[z].right];
+      if (parent[z] >= 0) low.lvl_dst[i] = idx_of[parent[z]];
+    }
+    // TNC_PATH_TC_P8: a dense step (unsplit) whose consumer is a dense step
+    // reading that operand row-contiguous writes it as fp16 planes, twice the
+    // entries' bytes; the same level lifetimes, sizes doubled for those
+    const size_t ns = low.lvl_steps.size();
+    low.p8_direct.assign(ns, 0);
+    std::vector<uint64_t> size8 = size;
+    for (int z = L; z < N; z++) {
+      const int i = idx_of[z], j = low.lvl_dst[i];
+      if (j < 0) continue;
+      const StepDesc& d = low.lvl_steps[i];
+      const StepDesc& e = low.lvl_steps[j];
+      if (!p8_eligible(d) || p8_split_log(d) != 0 || !p8_eligible(e)) continue;
+      if (!p8_operand_mn(e, low.lvl_src_a[j] == i ? 0 : 1)) continue;
+      low.p8_direct[i] = 1;
+      size8[z] = 2 * size[z];
+    }
+    std::vector<uint64_t> off8;  // 16 entries: fp16 planes start 16-byte aligned (TMA) at 1 residue per entry
+    low.p8_arena_entries = allocate(size8, t0, t1, off8, 16);
+    low.p8_leaf_off.assign(off8.begin(), off8.begin() + L);
+    low.p8_steps = low.lvl_steps;
+    for (int z = L; z < N; z++) {
+      StepDesc& d = low.p8_steps[idx_of[z]];
+      d.a_off = off8[tree.nodes[z].left];
+      d.b_off = off8[tree.nodes[z].right];
+      d.c_off = off8[z];
+    }
+    low.p8_root_off = off8[root];
   }
   return TNC_OK;
 }
@@ -349,6 +388,43 @@ int validate_lowered(const Network& net, const Tree& tree, Lowered& low) {
           return set_error(TNC_ERR_INVALID, "internal: level outputs overlap");
       }
     }
+  }
+  {  // the TNC_PATH_TC_P8 layout: direct outputs take twice their entries
+    const size_t ns = low.lvl_steps.size();
+    if (low.p8_steps.size() != ns || low.p8_direct.size() != ns || low.p8_leaf_off.size() != (size_t)L)
+      return set_error(TNC_ERR_INVALID, "internal: p8 layout size");
+    const uint64_t arena = low.p8_arena_entries;
+    for (int l = 0; l < L; l++)
+      if (low.p8_leaf_off[l] + (1ull << low.leaves[l].rank) > arena)
+        return set_error(TNC_ERR_INVALID, "internal: leaf outside the p8 arena");
+    auto ext = [&](int i, int rank) -> uint64_t { return (1ull << rank) * (i >= 0 && low.p8_direct[i] ? 2 : 1); };
+    std::vector<uint64_t> nc(ns), na(ns), nb(ns);
+    for (size_t i = 0; i < ns; i++) {
+      const StepDesc& d = low.p8_steps[i];
+      int rc = check_step(d, arena);
+      if (rc) return rc;
+      nc[i] = ext((int)i, d.c);
+      na[i] = ext(low.lvl_src_a[i], d.a_rank);
+      nb[i] = ext(low.lvl_src_b[i], d.b_rank);
+      if (d.c_off + nc[i] > arena || d.a_off + na[i] > arena || d.b_off + nb[i] > arena)
+        return set_error(TNC_ERR_INVALID, "internal: fp16 planes outside the p8 arena");
+      if (overlap(d.c_off, nc[i], d.a_off, na[i]) || overlap(d.c_off, nc[i], d.b_off, nb[i]))
+        return set_error(TNC_ERR_INVALID, "internal: p8 output overlaps an input");
+      if (low.p8_direct[i] && (low.lvl_dst[i] < 0 || p8_split_log(d) != 0))
+        return set_error(TNC_ERR_INVALID, "internal: direct planes without a dense consumer");
+    }
+    for (size_t l = 0; l + 1 < low.lvl_start.size(); l++)
+      for (uint32_t i = low.lvl_start[l]; i < low.lvl_start[l + 1]; i++)
+        for (uint32_t j = low.lvl_start[l]; j < low.lvl_start[l + 1]; j++) {
+          if (i == j) continue;
+          const StepDesc& d = low.p8_steps[i];
+          const StepDesc& e = low.p8_steps[j];
+          if (overlap(d.c_off, nc[i], e.c_off, nc[j]) || overlap(d.c_off, nc[i], e.a_off, na[j]) ||
+              overlap(d.c_off, nc[i], e.b_off, nb[j]))
+            return set_error(TNC_ERR_INVALID, "internal: p8 level outputs overlap");
+        }
+    if (low.p8_root_off + (1ull << tree.nodes[tree.root].bonds.size()) > arena)
+      return set_error(TNC_ERR_INVALID, "internal: root outside the p8 arena");
   }
   if (!fits) return TNC_OK;  // lvl_fits stays false: the batch kernel refuses this plan
   low.lvl_fits = true;

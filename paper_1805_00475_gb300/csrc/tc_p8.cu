@@ -94,6 +94,8 @@ struct P8Args {
   uint8_t ebit[16];         // the tile's row and column bits by output weight, lightest first
                             // (column bit j: 0x80 | j; row bit j: j); bits 0..4 go to lanes
   uint32_t n_ebits, pad3;
+  uint32_t a_mn, b_mn;      // operand planes row-contiguous (MN-major) instead of K-contiguous
+  uint32_t direct, pad4;    // output as rg balanced fp16 planes, plane i at out + i 2^(fa+fb) halves
   uint8_t* out;             // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
 };
 
@@ -181,10 +183,27 @@ __device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = F16, both K-major,
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N) {
-  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// The same for an MN-major operand (rows contiguous): each 128-byte line
+// holds 64 consecutive rows at one shared value, 8 lines (shared values) form
+// a 1024-byte swizzle atom; the tile's atoms run along K at 1024 bytes (the
+// stride byte offset) and along the rows at 8192 bytes (the leading byte
+// offset: one TMA box of 64 rows x 64 shared values).  The ks-th group of 16
+// shared values starts 2048 ks bytes further.
+__device__ __forceinline__ uint64_t make_desc_mn_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(8192u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = F16, K-major unless
+// the transpose bit of A (15) or B (16) marks it MN-major, N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N, uint32_t a_mn = 0, uint32_t b_mn = 0) {
+  return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -268,11 +287,13 @@ __device__ __forceinline__ uint32_t p8_half2(uint32_t wa, uint32_t ia, uint32_t 
 }
 
 // One operand of a dense step to pack: X its byte entries, Y its RG planes,
-// 2^f rows.
+// 2^f rows; mode 0: nothing to do (the producing step wrote the planes),
+// 1: K-contiguous planes (the transpose above), 2: row-contiguous planes,
+// Y_i[q * R + r] (no transpose: the entries' own order, K >= 64).
 struct PackOperand {
   const uint8_t* X;
   __half* Y;
-  uint32_t f;
+  uint32_t f, mode;
 };
 
 // Both operands of a step in one launch: the tiles of A, then those of B.
@@ -284,8 +305,8 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(PackOperand opA, PackOpera
   // 8 row quads x 4 pairs; phase 2: lanes = 8 chunks x 4 rows)
   __shared__ uint32_t tile[RG][64][33];
   const uint32_t K = 1u << k, Kp = 1u << kp;
-  const uint64_t tiles_a = (uint64_t)(((1u << opA.f) + 63u) / 64u) << (kp - 6);
-  const uint64_t n_tiles = tiles_a + ((uint64_t)(((1u << opB.f) + 63u) / 64u) << (kp - 6));
+  const uint64_t tiles_a = opA.mode ? (uint64_t)(((1u << opA.f) + 63u) / 64u) << (kp - 6) : 0;
+  const uint64_t n_tiles = tiles_a + (opB.mode ? (uint64_t)(((1u << opB.f) + 63u) / 64u) << (kp - 6) : 0);
   const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
   __half2 hp2[RG], np2[RG];
 #pragma unroll
@@ -301,6 +322,36 @@ __global__ void __launch_bounds__(256) p8_pack_kernel(PackOperand opA, PackOpera
     const uint32_t tiles_r = (R + 63) / 64;
     const uint64_t b = isA ? bt : bt - tiles_a;
     const uint32_t r0 = (uint32_t)(b % tiles_r) * 64u, q0 = (uint32_t)(b / tiles_r) * 64u;
+    if ((isA ? opA.mode : opB.mode) == 2) {  // row-contiguous: 64 shared values x 16 quads of rows
+#pragma unroll
+      for (int it = 0; it < 4; it++) {
+        const uint32_t id = t + 256u * it;
+        const uint32_t r = r0 + 4u * (id & 15u), q = q0 + (id >> 4);
+        if (r < R) {
+          const uint8_t* src = X + ((uint64_t)q * R + r) * RG;
+          uint32_t w[RG];  // 4 rows x RG bytes
+          if constexpr (RG == 4) {
+            const uint4 v = *reinterpret_cast<const uint4*>(src);
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+          } else if constexpr (RG == 2) {
+            const uint2 v = *reinterpret_cast<const uint2*>(src);
+            w[0] = v.x; w[1] = v.y;
+          } else {
+            w[0] = *reinterpret_cast<const uint32_t*>(src);
+          }
+#pragma unroll
+          for (int i = 0; i < RG; i++) {
+            const uint32_t b0 = (uint32_t)i, b1 = (uint32_t)(RG + i), b2 = (uint32_t)(2 * RG + i),
+                           b3 = (uint32_t)(3 * RG + i);  // byte of row j, residue i
+            uint2 h;
+            h.x = p8_half2(w[b0 >> 2], b0 & 3u, w[b1 >> 2], b1 & 3u, hp2[i], np2[i]);
+            h.y = p8_half2(w[b2 >> 2], b2 & 3u, w[b3 >> 2], b3 & 3u, hp2[i], np2[i]);
+            *reinterpret_cast<uint2*>(Y + (uint64_t)i * R * Kp + (uint64_t)q * R + r) = h;
+          }
+        }
+      }
+      continue;
+    }
 #pragma unroll
     for (int it = 0; it < 2; it++) {
       const uint32_t rq = (lane & 7u) + 8u * (warp & 1u);                // row quad 0..15
@@ -432,6 +483,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t n_chunks = Ks / chunk;
   const uint32_t spc = chunk / kStageK;  // stages per chunk
   const uint32_t split_mask = (1u << g.log_split) - 1u;
+  // row-contiguous operands (a tile of TN < 64 columns always reads B K-contiguous)
+  const bool a_mn = g.a_mn != 0, b_mn = TN >= 64 && g.b_mn != 0;
   bool ok = true;
 
   if (warp == 0) {
@@ -454,8 +507,20 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t sa = smem_u32(smem + s * kStageBytes);
               const int32_t x = (int32_t)(q0 + j * kStageK);
               mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
-              tma_load_3d(sa, &tmA, x, (int32_t)m0, (int32_t)r, full0 + 8 * s);
-              tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
+              // K-contiguous planes: one box of rows x 64 shared values;
+              // row-contiguous: boxes of 64 rows x 64 shared values, 8 KiB apart
+              if (a_mn) {
+                tma_load_3d(sa, &tmA, (int32_t)m0, x, (int32_t)r, full0 + 8 * s);
+                tma_load_3d(sa + 8192u, &tmA, (int32_t)m0 + 64, x, (int32_t)r, full0 + 8 * s);
+              } else {
+                tma_load_3d(sa, &tmA, x, (int32_t)m0, (int32_t)r, full0 + 8 * s);
+              }
+              if (b_mn) {
+                for (uint32_t h = 0; h < TN / 64u; h++)
+                  tma_load_3d(sa + kABytes + 8192u * h, &tmB, (int32_t)(n0 + 64u * h), x, (int32_t)r, full0 + 8 * s);
+              } else {
+                tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
+              }
               issued++;
               if (++s == kStages) {
                 s = 0;
@@ -473,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      constexpr uint32_t idesc = make_idesc(kTileM, TN);
+      const uint32_t idesc = make_idesc(kTileM, TN, a_mn ? 1u : 0u, b_mn ? 1u : 0u);
+      const uint32_t a_ks = a_mn ? 2048u >> 4 : 32u >> 4, b_ks = b_mn ? 2048u >> 4 : 32u >> 4;
       uint32_t s = 0, ph = 0, na[NA];
       for (uint32_t r = 0; r < NA; r++) na[r] = 0;
       for (uint32_t t = 0; t < T && ok; t++)
@@ -493,10 +559,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               tc_fence_after();
               const uint32_t sa = smem_u32(smem + s * kStageBytes), sb = sa + kABytes;
-              const uint64_t ad = make_desc_sw128(sa), bd = make_desc_sw128(sb);
+              const uint64_t ad = a_mn ? make_desc_mn_sw128(sa) : make_desc_sw128(sa);
+              const uint64_t bd = b_mn ? make_desc_mn_sw128(sb) : make_desc_sw128(sb);
 #pragma unroll
-              for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values: 32 bytes into each row
-                mma_f16(d, ad + 2u * ks, bd + 2u * ks, idesc, (c | j | ks) ? 1u : 0u);
+              for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values
+                mma_f16(d, ad + a_ks * ks, bd + b_ks * ks, idesc, (c | j | ks) ? 1u : 0u);
               mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
               if (++s == kStages) {
                 s = 0;
@@ -608,7 +675,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         epi_bar();  // every residue of the round is staged
-        if (ok) {
+        if (ok && g.direct) {
+          // balanced fp16 planes of the next dense step's operand, the
+          // entries' own order: plane of residue rd NA + ra at
+          // out + (rd NA + ra) 2^(fa+fb) halves
+          __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb));
+          for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
+            uint64_t adr[4];
+            SW val[4];
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+              const uint32_t hc = hi_tab[(e0 + u * kEpiThreads) >> 5];
+              const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
+              adr[u] = om_tab[rr] + on_tab[cc];
+              val[u] = staging[cc * kStagePitch + rr];
+            }
+#pragma unroll
+            for (uint32_t ra = 0; ra < NA; ra++) {
+              const int p = (int)g.p[rd * NA + ra];
+#pragma unroll
+              for (uint32_t u = 0; u < 4; u++) {
+                int v = (int)((uint32_t)val[u] >> (8 * ra)) & 0xFF;
+                if (v > (p - 1) / 2) v -= p;
+                planes[((uint64_t)ra << (g.fa + g.fb)) + adr[u]] = __int2half_rn(v);
+              }
+            }
+          }
+        } else if (ok) {
           uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA;
           // four entries per trip, their loads issued before their stores
           static_assert((kTileM * TN) % (4 * kEpiThreads) == 0, "whole trips of four");
@@ -670,6 +763,22 @@ int make_map(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t rg,
   const cuuint64_t dims[3] = {K, rows, rg};
   const cuuint64_t strides[2] = {K * 2, rows * K * 2};
   const cuuint32_t box[3] = {64, box_rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return TNC_OK;
+}
+
+// Row-contiguous planes (rg planes of K x rows fp16, a shared value's rows
+// contiguous) with boxes of 64 rows x 64 shared values of one plane.
+int make_map_mn(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t rg) {
+  EncodeTiled fn = encoder();
+  if (!fn) return set_error(TNC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[3] = {rows, K, rg};
+  const cuuint64_t strides[2] = {rows * 2, rows * K * 2};
+  const cuuint32_t box[3] = {64, 64, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -748,6 +857,16 @@ uint32_t p8_split_log(const StepDesc& d) {
 
 uint32_t p8_tile_width(const StepDesc& d) { return shape_of(d).tn; }
 
+// Operand `side` (0: A, 1: B) of a dense step is read row-contiguous when it
+// has at least 64 shared values and its tile side has at least 64 rows (the
+// row tile always; the column tile when 64 or more wide).
+bool p8_operand_mn(const StepDesc& d, int side) {
+  const Shape s = shape_of(d);
+  if (s.k < 6) return false;
+  const bool row_side = (side == 1) == s.swap;
+  return row_side || s.tn >= 64;
+}
+
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg) {
   const uint32_t kp = std::max<uint32_t>(d.k, 6);
   return 2ull * (uint64_t)rg * ((1ull << (d.ka + kp)) + (1ull << (d.kb + kp)));
@@ -758,8 +877,8 @@ uint64_t p8_part_bytes(const StepDesc& d, int rg) {
   return ls ? (uint64_t)rg << (d.c + ls) : 0;
 }
 
-int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, void* scratch, uint8_t* part,
-              uint32_t* dev_err, int sms, void* stream) {
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, uint64_t arena_bytes,
+              uint32_t flags, void* scratch, uint8_t* part, uint32_t* dev_err, int sms, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (rg != 1 && rg != 2 && rg != 4) return set_error(TNC_ERR_INVALID, "internal: residues per pass must be 1, 2 or 4");
   tnc_p8::PackPrimes pp{};
@@ -772,18 +891,43 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   __half* a16 = (__half*)scratch;    // rg planes of a_elems
   __half* b16 = a16 + rg * a_elems;  // rg planes of b_elems
   const uint64_t a_off = s.swap ? d.b_off : d.a_off, b_off = s.swap ? d.a_off : d.b_off;
-  {  // both operands packed by one launch
-    const tnc_p8::PackOperand oa{arena + a_off * rg, a16, s.fa}, ob{arena + b_off * rg, b16, s.fb};
-    const uint64_t n = ((uint64_t)((1u << s.fa) + 63u) / 64u + (uint64_t)((1u << s.fb) + 63u) / 64u) << (s.kp - 6);
+  // operands by tile side (row side = A unless swapped): read row-contiguous
+  // (mn), and taken straight from the planes their producing dense step
+  // wrote (direct), which occupy twice the entries' bytes
+  const int side_a = s.swap ? 1 : 0, side_b = 1 - side_a;
+  const bool mn_a = p8_operand_mn(d, side_a), mn_b = p8_operand_mn(d, side_b);
+  const bool dir_a = (flags & (side_a ? kP8DirectB : kP8DirectA)) != 0;
+  const bool dir_b = (flags & (side_b ? kP8DirectB : kP8DirectA)) != 0;
+  const bool dir_out = (flags & kP8DirectOut) != 0;
+  if ((dir_a && !mn_a) || (dir_b && !mn_b) || (dir_out && ls))
+    return set_error(TNC_ERR_INVALID, "internal: direct fp16 planes for an operand read K-contiguous");
+  {  // every range the launch touches lies inside the arena
+    const uint64_t ea = (1ull << (s.fa + s.k)) * rg * (dir_a ? 2 : 1), eb = (1ull << (s.fb + s.k)) * rg * (dir_b ? 2 : 1);
+    const uint64_t ec = (1ull << d.c) * rg * (dir_out ? 2 : 1);
+    if (a_off * rg + ea > arena_bytes || b_off * rg + eb > arena_bytes || d.c_off * rg + ec > arena_bytes)
+      return set_error(TNC_ERR_INVALID, "internal: dense step range outside the arena");
+  }
+  __half* pa = dir_a ? reinterpret_cast<__half*>(arena + a_off * rg) : a16;
+  __half* pb = dir_b ? reinterpret_cast<__half*>(arena + b_off * rg) : b16;
+  if (((uintptr_t)pa | (uintptr_t)pb) & 15u)
+    return set_error(TNC_ERR_INVALID, "internal: fp16 operand planes not 16-byte aligned");
+  if (!dir_a || !dir_b) {  // the operands still in entry form, packed by one launch
+    const tnc_p8::PackOperand oa{arena + a_off * rg, a16, s.fa, dir_a ? 0u : (mn_a ? 2u : 1u)};
+    const tnc_p8::PackOperand ob{arena + b_off * rg, b16, s.fb, dir_b ? 0u : (mn_b ? 2u : 1u)};
+    const uint64_t n = ((dir_a ? 0 : (uint64_t)((1u << s.fa) + 63u) / 64u) +
+                        (dir_b ? 0 : (uint64_t)((1u << s.fb) + 63u) / 64u))
+                       << (s.kp - 6);
     const unsigned blocks = (unsigned)std::min<uint64_t>(n, (uint64_t)sms * 16);
     if (rg == 4) tnc_p8::p8_pack_kernel<4><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
     else if (rg == 2) tnc_p8::p8_pack_kernel<2><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
     else tnc_p8::p8_pack_kernel<1><<<blocks, 256, 0, st>>>(oa, ob, s.k, s.kp, pp);
+    launch_counts().p8_pack++;
   }
-  launch_counts().p8_pack++;
   CUtensorMap ma, mb;
-  int rc = make_map(&ma, a16, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
-  if (!rc) rc = make_map(&mb, b16, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
+  int rc = mn_a ? make_map_mn(&ma, pa, 1ull << s.fa, 1ull << s.k, rg)
+                : make_map(&ma, pa, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
+  if (!rc)
+    rc = mn_b ? make_map_mn(&mb, pb, 1ull << s.fb, 1ull << s.k, rg) : make_map(&mb, pb, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
   if (rc) return rc;
   tnc_p8::P8Args g;
   std::memset(&g, 0, sizeof(g));
@@ -795,6 +939,9 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
   g.n_items = (uint32_t)(s.tiles << ls);
   g.rg = rg;
+  g.a_mn = mn_a ? 1u : 0u;
+  g.b_mn = mn_b ? 1u : 0u;
+  g.direct = dir_out ? 1u : 0u;
   for (uint32_t i = 0; i < 4; i++) {
     g.p[i] = pp.p[i];
     g.pf[i] = (float)pp.p[i];
@@ -833,7 +980,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     g.n_ebits = (uint32_t)bits.size();
     for (size_t i = 0; i < bits.size(); i++) g.ebit[i] = bits[i].second;
   }
-  g.out = ls ? part : arena + d.c_off * rg;
+  g.out = ls ? part : arena + d.c_off * rg;  // direct: the planes, same place (twice the bytes)
   const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
   if (rg == 4) rc = launch_gemm_rg<4>(s.tn, ma, mb, g, grid, dev_err, st);
   else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, ma, mb, g, grid, dev_err, st);
@@ -850,6 +997,9 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     lc.p8_max_chunks = std::max(lc.p8_max_chunks, chunks);
     if (s.swap) lc.p8_swapped++;
     if (s.kp > s.k) lc.p8_padded++;
+    if (dir_out) lc.p8_direct_out++;
+    lc.p8_direct_in += (dir_a ? 1 : 0) + (dir_b ? 1 : 0);
+    lc.p8_mn += (mn_a ? 1 : 0) + (mn_b ? 1 : 0);
   }
   if (ls) {
     const uint64_t n = (uint64_t)rg << d.c;

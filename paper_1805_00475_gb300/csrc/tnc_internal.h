@@ -70,6 +70,16 @@ struct Lowered {
   std::vector<uint64_t> lvl_leaf_off;
   uint64_t lvl_arena_entries = 0;
   uint64_t lvl_root_off = 0;
+  std::vector<int32_t> lvl_src_a, lvl_src_b;  // producing step of each operand (-1: a leaf)
+  std::vector<int32_t> lvl_dst;               // consuming step of each output (-1: the root)
+  // the level schedule as TNC_PATH_TC_P8 runs it: a dense step's output that
+  // the consuming dense step reads row-contiguous is written as fp16 planes
+  // (p8_direct), twice the entries, so the arena is laid out again
+  std::vector<uint8_t> p8_direct;
+  std::vector<StepDesc> p8_steps;  // lvl_steps with the offsets of this layout
+  std::vector<uint64_t> p8_leaf_off;
+  uint64_t p8_arena_entries = 0;
+  uint64_t p8_root_off = 0;
   // leaves
   std::vector<LeafDesc> leaves;          // offsets filled per schedule at pack time
   std::vector<uint32_t> leaf_tables;     // TABLE entries permuted to leaf layouts
@@ -141,12 +151,20 @@ uint32_t p8_split_log(const StepDesc& d);
 uint32_t p8_tile_width(const StepDesc& d);
 uint64_t p8_scratch_bytes(const StepDesc& d, int rg);
 uint64_t p8_part_bytes(const StepDesc& d, int rg);
+// Operand `side` (0: A, 1: B) of a dense step read row-contiguous (MN-major).
+bool p8_operand_mn(const StepDesc& d, int side);
+// Direct fp16 planes: the step's output goes straight to the planes of the
+// consuming dense step's operand (kP8DirectOut), and operand A / B is read
+// from planes its producer wrote (kP8DirectA / kP8DirectB); such a tensor
+// takes twice its entries' bytes in the arena.
+constexpr uint32_t kP8DirectOut = 1, kP8DirectA = 2, kP8DirectB = 4;
 // One dense step for all rg residues (primes[0..rg)) of a pass whose entries
-// hold rg residues of one byte each: both operands packed once, then one GEMM
-// launch that computes every residue of each output tile and writes whole
-// entries.
-int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, void* scratch, uint8_t* part,
-              uint32_t* dev_err, int sms, void* stream);
+// hold rg residues of one byte each: the operands not already in fp16 planes
+// packed by one launch, then one GEMM launch that computes every residue of
+// each output tile and writes whole entries (or planes).  arena_bytes bounds
+// every range the step touches (checked before any launch).
+int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* arena, uint64_t arena_bytes,
+              uint32_t flags, void* scratch, uint8_t* part, uint32_t* dev_err, int sms, void* stream);
 size_t tc_step_bytes();
 void tc_make_step(const StepDesc& d, uint32_t p, void* out);
 uint32_t tc_split_log(const StepDesc& d);

@@ -75,14 +75,16 @@ class _PlanStats(ctypes.Structure):
                 ("total_entries", ctypes.c_double), ("log2_bound", ctypes.c_double),
                 ("arena_entries", ctypes.c_uint64), ("batch_arena_entries", ctypes.c_uint64),
                 ("n_dense_steps", ctypes.c_int32), ("dense_macs", ctypes.c_double),
-                ("n_dense_steps_p8", ctypes.c_int32), ("dense_macs_p8", ctypes.c_double)]
+                ("n_dense_steps_p8", ctypes.c_int32), ("dense_macs_p8", ctypes.c_double),
+                ("n_direct_p8", ctypes.c_int32), ("p8_arena_entries", ctypes.c_uint64)]
 
 
 class _LaunchCounts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("leaf_fill", "level", "grid_step", "splitk", "tc_gemm", "tc_split",
                                               "p8_pack", "p8_gemm", "p8_split")] + \
                [("p8_tile_n", ctypes.c_int32 * 5)] + \
-               [(n, ctypes.c_int32) for n in ("p8_max_chunks", "p8_swapped", "p8_padded", "extract", "crt")]
+               [(n, ctypes.c_int32) for n in ("p8_max_chunks", "p8_swapped", "p8_padded", "extract", "crt",
+                                              "p8_direct_out", "p8_direct_in", "p8_mn")]
 
 
 class _LearnedOpts(ctypes.Structure):
@@ -293,6 +295,8 @@ class PlanStats:
     dense_macs: float = 0.0
     n_dense_steps_p8: int = 0
     dense_macs_p8: float = 0.0
+    n_direct_p8: int = 0
+    p8_arena_entries: int = 0
 
 
 class Plan:
@@ -330,7 +334,8 @@ def plan(network: Network, heuristic: str = "bisect", rank_cap: int = 32, tries:
 def _stats(st: _PlanStats) -> PlanStats:
     return PlanStats(st.max_rank, st.n_steps, st.n_leaves, st.depth, st.total_macs, st.total_entries,
                      st.log2_bound, int(st.arena_entries), int(st.batch_arena_entries), int(st.n_dense_steps),
-                     float(st.dense_macs), int(st.n_dense_steps_p8), float(st.dense_macs_p8))
+                     float(st.dense_macs), int(st.n_dense_steps_p8), float(st.dense_macs_p8),
+                     int(st.n_direct_p8), int(st.p8_arena_entries))
 
 
 def plan_many(formulas, heuristic: str = "bisect", rank_cap: int = 32, tries: int = 2, seed: int = 0

@@ -82,6 +82,22 @@ def test_p8_primes_and_options():
         tnc.Batch([p], n_residues=4, path="tc_p8")
 
 
+def test_p8_direct_plane_layout():
+    """TNC_PATH_TC_P8 lays the arena out again: a dense step whose output
+    feeds a dense step directly (as its fp16 operand planes) takes twice its
+    entries, and the path's workspace covers that arena (4 residue bytes per
+    entry in a pass of 4).  The lowering's own validation (every range inside
+    the arena, no overlap within a level) runs at plan time."""
+    p = tnc.plan_formula(I.cubic_vertex_cover(110, 6), heuristic="greedy", rank_cap=26)
+    st = p.stats
+    assert 1 <= st.n_direct_p8 < st.n_dense_steps_p8
+    assert st.batch_arena_entries < st.p8_arena_entries <= 2 * st.batch_arena_entries
+    assert tnc.workspace_bytes(p, 12, "tc_p8") >= 4 * st.p8_arena_entries
+    q = tnc.plan_formula(I.cubic_vertex_cover(30, 0))  # no dense step: the same layout, 16-entry aligned
+    assert q.stats.n_direct_p8 == 0
+    assert q.stats.batch_arena_entries <= q.stats.p8_arena_entries <= 1.25 * q.stats.batch_arena_entries
+
+
 def test_network_info_and_components():
     f = I.cubic_vertex_cover(20, 0)
     n, bonds, comps = tnc.build_network(f).info()

@@ -4,7 +4,9 @@ The formulas (#Cubic-Vertex-Cover on 100..130 vertices) have tensor-greedy
 plans of rank <= 24 whose dense steps, between them, take every branch of
 the dense kernels: 256-wide tiles on the 8-bit-prime path (two residues per
 TMEM round), several 1024-value chunks reduced mod p in TMEM before the next
-accumulates on top, K splits on both tensor-core paths.  The exact counts come
+accumulates on top, K splits on both tensor-core paths, operands read
+K-contiguous and row-contiguous, and dense outputs written straight to the
+fp16 planes of the next dense step.  The exact counts come
 from tests/golden/dense_branch_counts.json, written by the oracle alone
 (tests/golden/make_dense_counts.py).  Which branches ran is read from the
 library's own launch record (tnc_last_launch_counts), not from a restatement
@@ -61,7 +63,10 @@ def test_dense_branches_match_oracle(runs, n, seed, path):
     if path == "tc":
         assert lc["tc_gemm"] >= 1 and lc["p8_gemm"] == 0
     elif path == "tc_p8":
-        assert lc["p8_gemm"] >= 1 and lc["p8_pack"] == lc["p8_gemm"] and lc["tc_gemm"] == 0
+        assert lc["p8_gemm"] >= 1 and lc["tc_gemm"] == 0
+        # a step packs unless both operands came as fp16 planes from dense steps
+        assert lc["p8_pack"] <= lc["p8_gemm"] and lc["p8_pack"] >= lc["p8_gemm"] - lc["p8_direct_in"]
+        assert lc["p8_direct_in"] == lc["p8_direct_out"] <= lc["p8_mn"] <= 2 * lc["p8_gemm"]
     else:
         assert lc["tc_gemm"] == 0 and lc["p8_gemm"] == 0
 
@@ -76,6 +81,9 @@ def test_dense_cases_take_every_branch(runs):
     assert sum(lc["tc_split"] for lc in tc) >= 1, "no limb-path K split"
     assert sum(lc["tc_gemm"] - lc["tc_split"] for lc in tc) >= 1, "no unsplit limb-path step"
     assert sum(lc["p8_gemm"] - lc["p8_split"] for lc in p8) >= 1, "no unsplit p8 step"
+    assert sum(lc["p8_direct_out"] for lc in p8) >= 1, "no dense step wrote its consumer's fp16 planes"
+    assert sum(lc["p8_mn"] - lc["p8_direct_in"] for lc in p8) >= 1, "no row-contiguous operand packed"
+    assert sum(2 * lc["p8_gemm"] - lc["p8_mn"] for lc in p8) >= 1, "no K-contiguous operand"
     # one formula alone reaches all four
     both = [(n, s) for (n, s, path), (_, lc, _) in runs.items() if path == "tc_p8" and lc["p8_tile_n"][256]
             and lc["p8_max_chunks"] >= 2 and lc["p8_split"] and runs[(n, s, "tc")][1]["tc_split"]]
