@@ -240,21 +240,22 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// x (an exact integer of magnitude below 2^24, as fp32) reduced modulo p to
-// a representative of magnitude below 1.2 p: q is x/p rounded to nearest up
-// to the rounding of x * (1/p) (off by at most one), and the fma is exact.
+// x (an exact integer, as fp32) reduced modulo p to a representative of
+// magnitude at most 0.51 p: q is x/p rounded to nearest up to the rounding
+// of x * (1/p), and the fma is exact.  An accumulator holds at most
+// 1024 ((p-1)/2)^2 + 0.51 p in magnitude (one chunk of balanced products on
+// top of a reduced remainder), below 2^24, and x / p < 2^16, so x * (1/p) is
+// within 2^-7 of x / p: q is off by one only next to a half.
 __device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
   const float q = rintf(x * invp);
   return fmaf(-q, pf, x);
 }
 
-// The canonical residue in [0, p) of such a representative.
+// The canonical residue in [0, p) of such a representative (magnitude
+// below p): one conditional add of p.
 __device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
-  int v = __float2int_rn(r);
-  if (v < 0) v += (int)p;
-  if (v < 0) v += (int)p;
-  if (v >= (int)p) v -= (int)p;
-  return (uint32_t)v;
+  const int v = __float2int_rn(r);
+  return (uint32_t)(v + ((v >> 31) & (int)p));
 }
 
 // ---- operand packing ------------------------------------------------------
@@ -444,8 +445,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * kStages + 2 * NA + 1];
   __shared__ uint32_t tmem_base_s;
-  __shared__ uint64_t om_tab[kTileM], on_tab[TN];
-  __shared__ uint16_t hi_tab[kTileM * TN / 32];  // row | col << 8 of the entry bits above the lane bits
+  // per index h of the entry bits above the lane bits: their part of the
+  // entry's output offset (x) and of its staging index (y)
+  __shared__ uint2 ho_tab[kTileM * TN / 32];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   SW* staging = reinterpret_cast<SW*>(smem + kStages * kStageBytes);  // [col][kStagePitch] entries of NA bytes
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -596,47 +598,54 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* stage8 = reinterpret_cast<uint8_t*>(staging);
     // write order of a tile's entries: entry index e has the tile's row and
     // column bits ordered by output weight, so consecutive e are as close in C
-    // as the step's bit map allows (lane bits: the five lightest)
-    uint32_t lane_row = 0, lane_col = 0;
+    // as the step's bit map allows (lane bits: the five lightest).  An
+    // entry's output offset is a sum of one weight per set row or column bit,
+    // so it splits into the tile's base (the bits of m0 and n0), the lane
+    // bits' part and the part of the bits above them (ho_tab, the same for
+    // every tile: below 2^c <= 2^32); its staging index splits the same way.
+    uint32_t lane_off = 0, lane_sid = 0;
     for (uint32_t i = 0; i < 5; i++) {
-      const uint32_t b = g.ebit[i], v = (lane >> i) & 1u;
-      if (b & 0x80u) lane_col |= v << (b & 31u);
-      else lane_row |= v << b;
+      if (!((lane >> i) & 1u)) continue;
+      const uint32_t b = g.ebit[i];
+      if (b & 0x80u) {
+        lane_off += (uint32_t)g.wn[b & 31u];
+        lane_sid += kStagePitch << (b & 31u);
+      } else {
+        lane_off += (uint32_t)g.wm[b];
+        lane_sid += 1u << b;
+      }
     }
     for (uint32_t h = et; h < kTileM * TN / 32; h += kEpiThreads) {
-      uint32_t rw = 0, cl = 0;
+      uint32_t off = 0, sid = 0;
       for (uint32_t i = 5; i < g.n_ebits; i++) {
-        const uint32_t b = g.ebit[i], v = (h >> (i - 5)) & 1u;
-        if (b & 0x80u) cl |= v << (b & 31u);
-        else rw |= v << b;
+        if (!((h >> (i - 5)) & 1u)) continue;
+        const uint32_t b = g.ebit[i];
+        if (b & 0x80u) {
+          off += (uint32_t)g.wn[b & 31u];
+          sid += kStagePitch << (b & 31u);
+        } else {
+          off += (uint32_t)g.wm[b];
+          sid += 1u << b;
+        }
       }
-      hi_tab[h] = (uint16_t)(rw | cl << 8);
+      ho_tab[h] = make_uint2(off, sid);
     }
+    constexpr uint32_t kLogTN = TN == 256 ? 8 : TN == 128 ? 7 : TN == 64 ? 6 : TN == 32 ? 5 : 4;
     uint32_t na[NA];
     for (uint32_t r = 0; r < NA; r++) na[r] = 0;
     for (uint32_t t = 0; t < T; t++) {
       const uint32_t item = bid + t * G;
       const uint32_t split = item & split_mask, tile = item >> g.log_split;
       const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+      uint64_t tile_base = lane_off;  // output offset of the tile's origin + the lane bits' part
+      for (uint32_t j = 7; j < g.fa; j++)
+        if ((m0 >> j) & 1u) tile_base += g.wm[j];
+      for (uint32_t j = kLogTN; j < g.fb; j++)
+        if ((n0 >> j) & 1u) tile_base += g.wn[j];
       for (uint32_t rd = 0; rd < kRounds; rd++) {
         for (uint32_t c = 0; c < n_chunks; c++) {
           const bool last = c + 1 == n_chunks;
-          if (last) {
-            epi_bar();  // the previous round's bytes are out: staging (and tables) are free
-            if (rd == 0)
-              for (uint32_t i = et; i < kTileM + TN; i += kEpiThreads) {
-                uint64_t o = 0;
-                if (i < kTileM) {
-                  for (uint32_t j = 0; j < g.fa; j++)
-                    if (((m0 + i) >> j) & 1u) o += g.wm[j];
-                  om_tab[i] = o;
-                } else {
-                  for (uint32_t j = 0; j < g.fb; j++)
-                    if (((n0 + i - kTileM) >> j) & 1u) o += g.wn[j];
-                  on_tab[i - kTileM] = o;
-                }
-              }
-          }
+          if (last) epi_bar();  // the previous round's bytes are out: the staging is free
           for (uint32_t ra = 0; ra < NA; ra++) {
             const uint32_t r = rd * NA + ra;
             if (ok && !mbar_wait(accf0 + 8 * ra, na[ra] & 1u)) ok = false;
@@ -675,48 +684,49 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         epi_bar();  // every residue of the round is staged
+        const SW* sp = staging + lane_sid;
         if (ok && g.direct) {
           // balanced fp16 planes of the next dense step's operand, the
           // entries' own order: plane of residue rd NA + ra at
           // out + (rd NA + ra) 2^(fa+fb) halves
-          __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb));
+          __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb)) + tile_base;
           for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
-            uint64_t adr[4];
+            uint32_t adr[4];
             SW val[4];
 #pragma unroll
             for (uint32_t u = 0; u < 4; u++) {
-              const uint32_t hc = hi_tab[(e0 + u * kEpiThreads) >> 5];
-              const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
-              adr[u] = om_tab[rr] + on_tab[cc];
-              val[u] = staging[cc * kStagePitch + rr];
+              const uint2 t = ho_tab[(e0 + u * kEpiThreads) >> 5];
+              adr[u] = t.x;
+              val[u] = sp[t.y];
             }
 #pragma unroll
             for (uint32_t ra = 0; ra < NA; ra++) {
               const int p = (int)g.p[rd * NA + ra];
+              __half* pl = planes + ((uint64_t)ra << (g.fa + g.fb));
 #pragma unroll
               for (uint32_t u = 0; u < 4; u++) {
                 int v = (int)((uint32_t)val[u] >> (8 * ra)) & 0xFF;
                 if (v > (p - 1) / 2) v -= p;
-                planes[((uint64_t)ra << (g.fa + g.fb)) + adr[u]] = __int2half_rn(v);
+                pl[adr[u]] = __int2half_rn(v);
               }
             }
           }
         } else if (ok) {
-          uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA;
+          uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA +
+                          tile_base * RG;
           // four entries per trip, their loads issued before their stores
           static_assert((kTileM * TN) % (4 * kEpiThreads) == 0, "whole trips of four");
           for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
-            uint64_t adr[4];
+            uint8_t* adr[4];
             SW val[4];
 #pragma unroll
             for (uint32_t u = 0; u < 4; u++) {
-              const uint32_t hc = hi_tab[(e0 + u * kEpiThreads) >> 5];
-              const uint32_t rr = lane_row | (hc & 0xFFu), cc = lane_col | (hc >> 8);
-              adr[u] = (om_tab[rr] + on_tab[cc]) * RG;
-              val[u] = staging[cc * kStagePitch + rr];
+              const uint2 t = ho_tab[(e0 + u * kEpiThreads) >> 5];
+              adr[u] = outp + (uint64_t)t.x * RG;
+              val[u] = sp[t.y];
             }
 #pragma unroll
-            for (uint32_t u = 0; u < 4; u++) *reinterpret_cast<SW*>(outp + adr[u]) = val[u];
+            for (uint32_t u = 0; u < 4; u++) *reinterpret_cast<SW*>(adr[u]) = val[u];
           }
         }
       }
