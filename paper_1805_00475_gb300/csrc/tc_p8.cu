@@ -87,7 +87,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 struct P8Args {
   uint32_t fa, fb, k, log_split;  // rows 2^fa, columns 2^fb, shared 2^k, K split 2^log_split
   uint32_t n_items, tiles_m;      // work items (tiles x splits); row tiles
-  uint32_t rg, pad;               // residues per entry (1, 2 or 4), computed together
+  uint32_t rg, gm_log;            // residues per entry (1, 2 or 4), computed together; row tiles per raster group (log2)
   uint32_t p[4];
   float pf[4], invp[4];
   uint64_t wm[32], wn[32];  // output address weight of row bit j / column bit j
@@ -422,6 +422,18 @@ __global__ void p8_split_final_kernel(const uint8_t* __restrict__ part, uint8_t*
 
 // ---- the GEMM -------------------------------------------------------------
 
+// Origin of output tile `tile`: the tiles are taken in groups of 2^gm_log
+// row tiles, column tiles outermost within a group, row tiles fastest, so
+// that the CTAs running at one time share the operand rows of a few row tiles
+// and of a few column tiles.
+template <uint32_t TN>
+__device__ __forceinline__ void tile_origin(uint32_t tile, const P8Args& g, uint32_t& m0, uint32_t& n0) {
+  const uint32_t gm = g.gm_log, per_group = (g.n_items >> g.log_split) >> (31 - __clz(g.tiles_m) - gm);
+  const uint32_t grp = tile / per_group, w = tile - grp * per_group;
+  m0 = ((grp << gm) + (w & ((1u << gm) - 1u))) * kTileM;
+  n0 = (w >> gm) * TN;
+}
+
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 // One CTA per SM.  Work item = (output tile of 128 rows x TN columns, K
@@ -495,7 +507,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (uint32_t t = 0; t < T && ok; t++) {
         const uint32_t item = bid + t * G;
         const uint32_t split = item & split_mask, tile = item >> g.log_split;
-        const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+        uint32_t m0, n0;
+        tile_origin<TN>(tile, g, m0, n0);
         for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
           for (uint32_t ra = 0; ra < NA && ok; ra++) {
@@ -636,7 +649,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (uint32_t t = 0; t < T; t++) {
       const uint32_t item = bid + t * G;
       const uint32_t split = item & split_mask, tile = item >> g.log_split;
-      const uint32_t m0 = (tile % g.tiles_m) * kTileM, n0 = (tile / g.tiles_m) * TN;
+      uint32_t m0, n0;
+      tile_origin<TN>(tile, g, m0, n0);
       uint64_t tile_base = lane_off;  // output offset of the tile's origin + the lane bits' part
       for (uint32_t j = 7; j < g.fa; j++)
         if ((m0 >> j) & 1u) tile_base += g.wm[j];
@@ -858,6 +872,12 @@ bool p8_eligible(const StepDesc& d) {
 // kP8SplitTarget, each split keeps a whole chunk of 1024, and the partials
 // (2^c entries per split, each of up to 4 residues) stay within 2^26 entries.
 constexpr uint64_t kP8SplitTarget = 160;
+// Raster groups of a dense step's tiles: as many row tiles as keep their
+// operand rows (all residues of the pass) within 32 MiB, so that the CTAs of
+// one wave re-read rows and columns that are still in L2 (32 and 64 MiB
+// measured 2 % faster on C4 than all row tiles in one group, 8 MiB and
+// 128 MiB no better).
+constexpr uint64_t kP8GroupBytes = 32ull << 20;
 uint32_t p8_split_log(const StepDesc& d) {
   const Shape s = shape_of(d);
   uint32_t ls = 0;
@@ -946,6 +966,11 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   g.k = s.kp;  // zero-padded shared values contribute nothing
   g.log_split = ls;
   g.tiles_m = (1u << s.fa) / tnc_p8::kTileM;
+  {  // raster groups of 2^gm_log row tiles
+    uint32_t gm = 0;
+    while ((2u << gm) <= g.tiles_m && (uint64_t)(2u << gm) * tnc_p8::kTileM * (2ull << s.kp) * rg <= kP8GroupBytes) gm++;
+    g.gm_log = gm;
+  }
   if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
   g.n_items = (uint32_t)(s.tiles << ls);
   g.rg = rg;
