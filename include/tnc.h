@@ -326,6 +326,8 @@ typedef struct {
                              the fp16 planes the consuming dense step reads           */
   int32_t p8_direct_in;   /* dense-step operands read from such planes (not packed)   */
   int32_t p8_mn;          /* dense-step operands read row-contiguous (MN-major)       */
+  int32_t p8_pairs;       /* dense steps whose epilogue writes two entries at a time
+                             (output bit 0 is row bit 0)                              */
 } tnc_launch_counts;
 int tnc_last_launch_counts(tnc_launch_counts* out);
 /* Bytes the calling thread's last tnc_contract or tnc_contract_sliced copied

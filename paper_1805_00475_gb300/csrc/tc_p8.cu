@@ -95,7 +95,8 @@ struct P8Args {
                             // (column bit j: 0x80 | j; row bit j: j); bits 0..4 go to lanes
   uint32_t n_ebits, pad3;
   uint32_t a_mn, b_mn;      // operand planes row-contiguous (MN-major) instead of K-contiguous
-  uint32_t direct, pad4;    // output as rg balanced fp16 planes, plane i at out + i 2^(fa+fb) halves
+  uint32_t direct;          // output as rg balanced fp16 planes, plane i at out + i 2^(fa+fb) halves
+  uint32_t pairs;           // row bit 0 has output weight 1: entries written two at a time (TN >= 32)
   uint8_t* out;             // C (entry o at out[o * rg]), or the split partials [split][2^(fa+fb) * rg]
 };
 
@@ -616,10 +617,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     // so it splits into the tile's base (the bits of m0 and n0), the lane
     // bits' part and the part of the bits above them (ho_tab, the same for
     // every tile: below 2^c <= 2^32); its staging index splits the same way.
+    // With pairs, entry bit 0 is row bit 0 (output weight 1): a thread takes
+    // the two entries o, o + 1, adjacent in the staging and in C, and the
+    // lane and table bits start one higher.
+    const uint32_t pv = (TN >= 32 && g.pairs) ? 1u : 0u;
     uint32_t lane_off = 0, lane_sid = 0;
     for (uint32_t i = 0; i < 5; i++) {
       if (!((lane >> i) & 1u)) continue;
-      const uint32_t b = g.ebit[i];
+      const uint32_t b = g.ebit[pv + i];
       if (b & 0x80u) {
         lane_off += (uint32_t)g.wn[b & 31u];
         lane_sid += kStagePitch << (b & 31u);
@@ -628,10 +633,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         lane_sid += 1u << b;
       }
     }
-    for (uint32_t h = et; h < kTileM * TN / 32; h += kEpiThreads) {
+    for (uint32_t h = et; h < (kTileM * TN / 32) >> pv; h += kEpiThreads) {
       uint32_t off = 0, sid = 0;
-      for (uint32_t i = 5; i < g.n_ebits; i++) {
-        if (!((h >> (i - 5)) & 1u)) continue;
+      for (uint32_t i = 5 + pv; i < g.n_ebits; i++) {
+        if (!((h >> (i - 5 - pv)) & 1u)) continue;
         const uint32_t b = g.ebit[i];
         if (b & 0x80u) {
           off += (uint32_t)g.wn[b & 31u];
@@ -699,7 +704,43 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         epi_bar();  // every residue of the round is staged
         const SW* sp = staging + lane_sid;
-        if (ok && g.direct) {
+        if (ok && pv && g.direct) {
+          // pairs of entries: one staging load, one half2 store per residue
+          __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb)) + tile_base;
+          __half2 hp2[NA], np2[NA];
+#pragma unroll
+          for (uint32_t ra = 0; ra < NA; ra++) {
+            hp2[ra] = __float2half2_rn((float)((g.p[rd * NA + ra] - 1) / 2));
+            np2[ra] = __float2half2_rn(-(float)g.p[rd * NA + ra]);
+          }
+          for (uint32_t e0 = et; e0 < (kTileM * TN) / 2; e0 += 4 * kEpiThreads) {
+            uint32_t adr[4], w0[4], w1[4];  // the pair's staged bytes: entry o in w0, o + 1 in w1 (NA = 4) or both in w0
+#pragma unroll
+            for (uint32_t u = 0; u < 4; u++) {
+              const uint2 t = ho_tab[(e0 + u * kEpiThreads) >> 5];
+              adr[u] = t.x;
+              if constexpr (NA == 4) {
+                w0[u] = reinterpret_cast<const uint32_t*>(sp)[t.y];
+                w1[u] = reinterpret_cast<const uint32_t*>(sp)[t.y + 1];
+              } else if constexpr (NA == 2) {
+                w0[u] = *reinterpret_cast<const uint32_t*>(sp + t.y);
+                w1[u] = w0[u];
+              } else {
+                w0[u] = *reinterpret_cast<const uint16_t*>(sp + t.y);
+                w1[u] = w0[u];
+              }
+            }
+#pragma unroll
+            for (uint32_t ra = 0; ra < NA; ra++) {
+              __half* pl = planes + ((uint64_t)ra << (g.fa + g.fb));
+#pragma unroll
+              for (uint32_t u = 0; u < 4; u++) {
+                const uint32_t h2 = tnc_p8::p8_half2(w0[u], ra, w1[u], (NA == 4 ? 0u : NA) + ra, hp2[ra], np2[ra]);
+                *reinterpret_cast<uint32_t*>(pl + adr[u]) = h2;
+              }
+            }
+          }
+        } else if (ok && g.direct) {
           // balanced fp16 planes of the next dense step's operand, the
           // entries' own order: plane of residue rd NA + ra at
           // out + (rd NA + ra) 2^(fa+fb) halves
@@ -728,8 +769,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         } else if (ok) {
           uint8_t* outp = g.out + (g.log_split ? ((uint64_t)split << (g.fa + g.fb)) * RG : 0ull) + rd * NA +
                           tile_base * RG;
-          // four entries per trip, their loads issued before their stores
+          // four entries (or pairs) per trip, their loads issued before their stores
           static_assert((kTileM * TN) % (4 * kEpiThreads) == 0, "whole trips of four");
+          static_assert(TN < 32 || (kTileM * TN / 2) % (4 * kEpiThreads) == 0, "whole trips of four pairs");
+          if (pv) {
+            for (uint32_t e0 = et; e0 < (kTileM * TN) / 2; e0 += 4 * kEpiThreads) {
+              uint8_t* adr[4];
+              SW v0[4], v1[4];
+#pragma unroll
+              for (uint32_t u = 0; u < 4; u++) {
+                const uint2 t = ho_tab[(e0 + u * kEpiThreads) >> 5];
+                adr[u] = outp + (uint64_t)t.x * RG;
+                v0[u] = sp[t.y];
+                v1[u] = sp[t.y + 1];
+              }
+#pragma unroll
+              for (uint32_t u = 0; u < 4; u++) {
+                if constexpr (NA == RG) {  // the pair's entries are contiguous in C
+                  if constexpr (NA == 4) {
+                    *reinterpret_cast<uint2*>(adr[u]) = make_uint2(v0[u], v1[u]);
+                  } else if constexpr (NA == 2) {
+                    *reinterpret_cast<uint32_t*>(adr[u]) = (uint32_t)v0[u] | ((uint32_t)v1[u] << 16);
+                  } else {
+                    *reinterpret_cast<uint16_t*>(adr[u]) = (uint16_t)((uint32_t)v0[u] | ((uint32_t)v1[u] << 8));
+                  }
+                } else {
+                  *reinterpret_cast<SW*>(adr[u]) = v0[u];
+                  *reinterpret_cast<SW*>(adr[u] + RG) = v1[u];
+                }
+              }
+            }
+          } else
           for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
             uint8_t* adr[4];
             SW val[4];
@@ -1015,6 +1085,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     g.n_ebits = (uint32_t)bits.size();
     for (size_t i = 0; i < bits.size(); i++) g.ebit[i] = bits[i].second;
   }
+  g.pairs = (s.tn >= 32 && g.wm[0] == 1) ? 1u : 0u;  // output bit 0 is row bit 0
   g.out = ls ? part : arena + d.c_off * rg;  // direct: the planes, same place (twice the bytes)
   const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
   if (rg == 4) rc = launch_gemm_rg<4>(s.tn, ma, mb, g, grid, dev_err, st);
@@ -1035,6 +1106,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     if (dir_out) lc.p8_direct_out++;
     lc.p8_direct_in += (dir_a ? 1 : 0) + (dir_b ? 1 : 0);
     lc.p8_mn += (mn_a ? 1 : 0) + (mn_b ? 1 : 0);
+    if (g.pairs) lc.p8_pairs++;
   }
   if (ls) {
     const uint64_t n = (uint64_t)rg << d.c;

@@ -84,6 +84,8 @@ def test_dense_cases_take_every_branch(runs):
     assert sum(lc["p8_direct_out"] for lc in p8) >= 1, "no dense step wrote its consumer's fp16 planes"
     assert sum(lc["p8_mn"] - lc["p8_direct_in"] for lc in p8) >= 1, "no row-contiguous operand packed"
     assert sum(2 * lc["p8_gemm"] - lc["p8_mn"] for lc in p8) >= 1, "no K-contiguous operand"
+    assert sum(lc["p8_pairs"] for lc in p8) >= 1, "no epilogue writing pairs of entries"
+    assert sum(lc["p8_gemm"] - lc["p8_pairs"] for lc in p8) >= 1, "no epilogue writing single entries"
     # one formula alone reaches all four
     both = [(n, s) for (n, s, path), (_, lc, _) in runs.items() if path == "tc_p8" and lc["p8_tile_n"][256]
             and lc["p8_max_chunks"] >= 2 and lc["p8_split"] and runs[(n, s, "tc")][1]["tc_split"]]
