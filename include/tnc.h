@@ -328,6 +328,8 @@ typedef struct {
   int32_t p8_mn;          /* dense-step operands read row-contiguous (MN-major)       */
   int32_t p8_pairs;       /* dense steps whose epilogue writes two entries at a time
                              (output bit 0 is row bit 0)                              */
+  int32_t outer;          /* big steps with one small operand (at most 16 free rows,
+                             8 shared values), staged in shared memory               */
 } tnc_launch_counts;
 int tnc_last_launch_counts(tnc_launch_counts* out);
 /* Bytes the calling thread's last tnc_contract or tnc_contract_sliced copied

@@ -240,6 +240,55 @@ GridStep make_grid_step(const StepDesc& d) {
   return g;
 }
 
+// A big step with one small operand (at most 2^4 free rows, at most 2^3
+// shared values) runs as outer_kernel: the small operand staged in shared
+// memory, one row of the large operand per thread.
+bool outer_eligible(const StepDesc& d) {
+  return splitk_log(d) == 0 && d.c >= 16 && std::min(d.ka, d.kb) <= 4 && std::max(d.ka, d.kb) <= 32 && d.k <= 3;
+}
+
+tnc_dev::OuterStep make_outer_step(const StepDesc& d) {
+  tnc_dev::OuterStep o;
+  std::memset(&o, 0, sizeof(o));
+  const int s_side = d.ka <= d.kb ? 0 : 1;  // the small operand: A, or B
+  o.fs = s_side ? d.kb : d.ka;
+  o.fl = s_side ? d.ka : d.kb;
+  o.k = d.k;
+  o.s_off = s_side ? d.b_off : d.a_off;
+  o.l_off = s_side ? d.a_off : d.b_off;
+  o.c_off = d.c_off;
+  int op[64] = {0}, dst[64] = {0};
+  if (d.nra != TNC_BITMAP) {
+    for (int i = 0; i < d.nra; i++)
+      for (int q = 0; q < d.map.runs.ra[i].len; q++) {
+        op[d.map.runs.ra[i].src + q] = 0;
+        dst[d.map.runs.ra[i].src + q] = d.map.runs.ra[i].dst + q;
+      }
+    for (int i = 0; i < d.nrb; i++)
+      for (int q = 0; q < d.map.runs.rb[i].len; q++) {
+        op[d.map.runs.rb[i].src + q] = 1;
+        dst[d.map.runs.rb[i].src + q] = d.map.runs.rb[i].dst + q;
+      }
+  } else {
+    for (int j = 0; j < d.c; j++) {
+      op[j] = d.map.bit[j] >> 7;
+      dst[j] = d.map.bit[j] & 63;
+    }
+  }
+  uint64_t wS[4] = {0, 0, 0, 0};
+  for (int j = 0; j < d.c; j++) {
+    if (op[j] == s_side) wS[dst[j]] = 1ull << j;
+    else o.oL[dst[j]] = 1ull << j;
+  }
+  for (uint32_t x = 0; x < (1u << o.fs); x++)
+    for (uint32_t i = 0; i < o.fs; i++)
+      if ((x >> i) & 1u) o.oS[x] += wS[i];
+  o.contig = 1;
+  for (uint32_t i = 0; i < o.fs; i++)
+    if (wS[i] != (1ull << i)) o.contig = 0;
+  return o;
+}
+
 // What one plan adds to a group's workspace: counts of descriptors, result
 // entries and arena entries (summed over the group), and scratch bytes (the
 // group's maximum).
@@ -506,7 +555,7 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
   g_h2d_bytes += leaves.size() * sizeof(LeafDesc) + tables.size() * sizeof(uint32_t);
   // the group's steps by level: small ones (one index space per level across
   // the plans), big, split-K and dense ones (one launch each)
-  enum Kind { kGrid, kSplit, kTc };
+  enum Kind { kGrid, kSplit, kTc, kOuter };
   struct Big {
     int kind, slot;
     StepDesc d;      // offsets shifted to the group's arena
@@ -514,6 +563,7 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
   };
   std::vector<std::vector<Big>> big(n_lev);
   std::vector<GridStep> gsteps;
+  std::vector<tnc_dev::OuterStep> outers;
   std::vector<StepDesc> small;
   std::vector<uint32_t> small_lo(n_lev), small_hi(n_lev), small_work(n_lev);
   std::vector<char> tcbuf;
@@ -541,6 +591,9 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
           big[l].push_back(Big{kTc, (int)nd++, d, flags});
         } else if (flags) {
           return set_error(TNC_ERR_INVALID, "internal: direct fp16 planes on a CUDA-core step");
+        } else if (outer_eligible(d)) {
+          big[l].push_back(Big{kOuter, (int)outers.size(), d, 0});
+          outers.push_back(make_outer_step(d));
         } else if (splitk_log(d) > 0 || d.c >= 16) {
           big[l].push_back(Big{splitk_log(d) > 0 ? kSplit : kGrid, (int)gsteps.size(), d, 0});
           gsteps.push_back(make_grid_step(d));
@@ -673,6 +726,11 @@ static int contract_group(const tnc_plan_t* const* plans, int n, const tnc_contr
               dense_info.push_back(info);
             }
             if (rc2) return rc2;
+          } else if (b.kind == kOuter) {
+            const tnc_dev::OuterStep& os = outers[b.slot];
+            const unsigned blocks = (unsigned)std::min<uint64_t>(((1ull << os.fl) + 255) / 256, (uint64_t)sms * 8);
+            tnc_dev::outer_kernel<RG, W, N30><<<blocks, 256, 0, st>>>(os, arena, mg);
+            g_launches.outer++;
           } else if (b.kind == kSplit) {
             const uint32_t ls = splitk_log(b.d);
             const uint64_t nblk = 1ull << (b.d.c + ls);

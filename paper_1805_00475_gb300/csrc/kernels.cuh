@@ -254,6 +254,93 @@ __global__ void __launch_bounds__(256) step_kernel(const GridStep* __restrict__ 
   }
 }
 
+// A big step with one small operand (Sec. 2.1 with a skinny matrix): S has
+// 2^fs <= 16 rows, the shared dimension 2^k <= 8, the large operand L 2^fl
+// rows.  S's 2^(fs+k) entries are staged in shared memory; a thread takes a
+// row l of L, loads its 2^k entries once (consecutive threads, consecutive
+// rows: coalesced) and writes the 2^fs outputs C[oS(s) + oL(l)].  When S's
+// free bits are C's lowest bits (contig) those outputs are contiguous and a
+// thread writes them with vector stores (byte residues, 4 per entry).
+struct OuterStep {
+  uint64_t s_off, l_off, c_off;  // entry offsets of S, L, C in the arena
+  uint64_t oS[16];               // output offset of S's row s
+  uint64_t oL[32];               // output weight of L's free bit i
+  uint32_t fs, fl, k, contig;
+};
+
+template <int RG, typename W = uint32_t, bool N30 = false>
+__global__ void __launch_bounds__(256) outer_kernel(const __grid_constant__ OuterStep os, W* __restrict__ arena,
+                                                    ModGroup mg) {
+  __shared__ uint32_t sm[256 * RG];  // S entry (s, q) at (s + (q << fs)) * RG + r
+  const uint32_t fs = os.fs, fl = os.fl, K = 1u << os.k, NS = 1u << fs;
+  for (uint32_t i = threadIdx.x; i < (NS << os.k); i += blockDim.x) {
+    uint32_t v[RG];
+    load_entry<RG, W>(arena + (os.s_off + i) * RG, v);
+#pragma unroll
+    for (int r = 0; r < RG; r++) sm[i * RG + r] = v[r];
+  }
+  __syncthreads();
+  using Acc = std::conditional_t<sizeof(W) == 1, uint32_t, uint64_t>;
+  const W* L0 = arena + os.l_off * RG;
+  W* C0 = arena + os.c_off * RG;
+  const uint64_t nl = 1ull << fl;
+  for (uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lv[8][RG];
+#pragma unroll
+    for (uint32_t q = 0; q < 8; q++)
+      if (q < K) load_entry<RG, W>(L0 + (l + ((uint64_t)q << fl)) * RG, lv[q]);
+    uint64_t ol = 0;
+    for (uint32_t i = 0; i < fl; i++)
+      if ((l >> i) & 1ull) ol += os.oL[i];
+    // output s of this row: sum over q of S(s, q) L(l, q), reduced
+    auto entry = [&](uint32_t s, uint32_t (&out)[RG]) {
+      Acc acc[RG];
+#pragma unroll
+      for (int r = 0; r < RG; r++) acc[r] = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < 8; q++) {
+        if (q < K) {
+          const uint32_t* sv = sm + (s + (q << fs)) * RG;
+#pragma unroll
+          for (int r = 0; r < RG; r++) acc[r] += (Acc)sv[r] * lv[q][r];
+          if (((q + 1) & mg.red_mask) == 0 && q + 1 < K) {
+#pragma unroll
+            for (int r = 0; r < RG; r++) acc[r] = reduce_acc<N30>(acc[r], mg, r);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RG; r++) out[r] = reduce_acc<N30>(acc[r], mg, r);
+    };
+    bool done = false;
+    if constexpr (sizeof(W) == 1 && RG == 4) {
+      if (os.contig) {  // C entries ol .. ol + NS - 1, 4 bytes each; ol is a multiple of NS
+        uint32_t* dst = reinterpret_cast<uint32_t*>(C0 + ol * RG);
+        for (uint32_t s0 = 0; s0 < NS; s0 += 4) {
+          uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+          for (uint32_t j = 0; j < 4; j++)
+            if (s0 + j < NS) {
+              uint32_t out[RG];
+              entry(s0 + j, out);
+              w[j] = out[0] | (out[1] << 8) | (out[2] << 16) | (out[3] << 24);
+            }
+          if (NS >= 4) *reinterpret_cast<uint4*>(dst + s0) = make_uint4(w[0], w[1], w[2], w[3]);
+          else if (NS == 2) *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+          else dst[0] = w[0];
+        }
+        done = true;
+      }
+    }
+    if (!done)
+      for (uint32_t s = 0; s < NS; s++) {
+        uint32_t out[RG];
+        entry(s, out);
+        store_entry<RG, W>(C0 + (os.oS[s] + ol) * RG, out);
+      }
+  }
+}
+
 // Split-K for steps with few output entries and a long shared dimension (a
 // final dot product, a rank-19 tensor against a rank-19 tensor, ...): block
 // (o, part) sums A*B over its slice of the 2^k shared values, the block's
