@@ -370,6 +370,33 @@ __global__ void __launch_bounds__(256) splitk_partial_kernel(const GridStep* __r
 #pragma unroll
   for (int r = 0; r < RG; r++) acc[r] = 0;
   uint32_t cnt = 0;
+  bool dot = false;
+  if constexpr (sizeof(W) == 1 && RG == 4) {
+    // a dot product of contiguous byte-residue operands (no free bits): a
+    // thread loads 4 entries of each operand (16 bytes), regroups the bytes
+    // by residue (two rounds of byte permutes) and adds 4 products per
+    // residue with one dp4a; 1024 products (below 2^26) between reductions
+    if (ka == 0 && kb == 0 && (per & 1023u) == 0) {
+      dot = true;
+      for (uint64_t q = j * per + 4u * threadIdx.x; q < (j + 1) * per; q += 4u * blockDim.x) {
+        const uint4 a4 = *reinterpret_cast<const uint4*>(A + q * 4);
+        const uint4 b4 = *reinterpret_cast<const uint4*>(B + q * 4);
+        const uint32_t ta0 = __byte_perm(a4.x, a4.y, 0x5140), ta1 = __byte_perm(a4.x, a4.y, 0x7362);
+        const uint32_t ta2 = __byte_perm(a4.z, a4.w, 0x5140), ta3 = __byte_perm(a4.z, a4.w, 0x7362);
+        const uint32_t tb0 = __byte_perm(b4.x, b4.y, 0x5140), tb1 = __byte_perm(b4.x, b4.y, 0x7362);
+        const uint32_t tb2 = __byte_perm(b4.z, b4.w, 0x5140), tb3 = __byte_perm(b4.z, b4.w, 0x7362);
+        acc[0] = __dp4a(__byte_perm(ta0, ta2, 0x5410), __byte_perm(tb0, tb2, 0x5410), acc[0]);
+        acc[1] = __dp4a(__byte_perm(ta0, ta2, 0x7632), __byte_perm(tb0, tb2, 0x7632), acc[1]);
+        acc[2] = __dp4a(__byte_perm(ta1, ta3, 0x5410), __byte_perm(tb1, tb3, 0x5410), acc[2]);
+        acc[3] = __dp4a(__byte_perm(ta1, ta3, 0x7632), __byte_perm(tb1, tb3, 0x7632), acc[3]);
+        if ((++cnt & 255u) == 0) {
+#pragma unroll
+          for (int r = 0; r < RG; r++) acc[r] = reduce_acc<N30>(acc[r], mg, r);
+        }
+      }
+    }
+  }
+  if (!dot)
   for (uint64_t q = j * per + threadIdx.x; q < (j + 1) * per; q += blockDim.x) {
     uint32_t va[RG], vb[RG];
     load_entry<RG, W>(A + (q << ka) * RG, va);

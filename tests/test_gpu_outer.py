@@ -1,5 +1,7 @@
-"""Big pairwise steps with one small operand (Sec. 2.1: a skinny matrix times a
-tall one) run as outer_kernel: the small operand (at most 16 free rows, at
+"""Two shapes of the pairwise step (Sec. 2.1) with kernels of their own.
+
+Big steps with one small operand (a skinny matrix times a tall one) run as
+outer_kernel: the small operand (at most 16 free rows, at
 most 8 shared values) staged in shared memory, one row of the large operand
 per thread.  The formula below (#Cubic-Vertex-Cover, 100 vertices, seed 21,
 bisection plan, rank 20) has such a step with 2^16 or more outputs; its count
@@ -31,3 +33,16 @@ def test_outer_steps_match_oracle(path, R):
     assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
     assert r.flags == 0 and r.counts == exact
 
+
+@pytest.mark.parametrize("path,R", [("tc_p8", 12), ("tc_p8", 13), ("int64", 3)])
+def test_long_dot_product_matches_oracle(path, R):
+    """A final step that is a dot product of two rank-20 tensors (no free
+    bits, 2^20 shared values) runs split over K; on byte residues its slices
+    load 4 entries at a time and add 4 products per residue per dp4a."""
+    f = I.cubic_vertex_cover(100, 2)
+    p = tnc.plan_formula(f, heuristic="bisect", rank_cap=24)
+    exact = oracle.count(f, max_rank=24)
+    r = tnc.contract(p, n_residues=R, path=path)
+    assert tnc.last_launch_counts()["splitk"] >= 1
+    assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
+    assert r.flags == 0 and r.counts == exact
