@@ -242,21 +242,26 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // x (an exact integer, as fp32) reduced modulo p to a representative of
-// magnitude at most 0.51 p: q is x/p rounded to nearest up to the rounding
-// of x * (1/p), and the fma is exact.  An accumulator holds at most
-// 1024 ((p-1)/2)^2 + 0.51 p in magnitude (one chunk of balanced products on
-// top of a reduced remainder), below 2^24, and x / p < 2^16, so x * (1/p) is
-// within 2^-7 of x / p: q is off by one only next to a half.
+// magnitude at most 0.51 p: q is x (1/p) rounded to nearest, and the fma is
+// exact.  An accumulator holds at most 1024 ((p-1)/2)^2 + 0.51 p in magnitude
+// (one chunk of balanced products on top of a reduced remainder), below
+// 2^24, and |x| / p < 2^16, so x (1/p) is within 2^-7 of x / p: q is off by
+// one only next to a half.  The rounding adds 1.5 2^23 inside the fma (the
+// spacing of floats there is 1) and takes it off again: no float-to-integer
+// conversion.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 __device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
-  const float q = rintf(x * invp);
+  const float q = fmaf(x, invp, kMagic) - kMagic;
   return fmaf(-q, pf, x);
 }
 
-// The canonical residue in [0, p) of such a representative (magnitude
-// below p): one conditional add of p.
-__device__ __forceinline__ uint32_t canonical(float r, uint32_t p) {
-  const int v = __float2int_rn(r);
-  return (uint32_t)(v + ((v >> 31) & (int)p));
+// The canonical residue v in [0, p) of such a representative r (magnitude
+// below p), as the low byte of a float's bits: r + 1.5 2^23 (plus p when r
+// is negative) is the float 1.5 2^23 + v, exact (the spacing there is 1),
+// whose bits are 0x4B400000 + v.  pm = 1.5 2^23 + p.  No float-to-integer
+// conversion.
+__device__ __forceinline__ uint32_t canonical_bits(float r, float pm) {
+  return __float_as_uint(r + (r < 0.0f ? pm : kMagic));
 }
 
 // ---- operand packing ------------------------------------------------------
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t tb = tmem + ((quarter * 32u) << 16) + ra * TN + cbeg;
             if (ok && !idle) {
-              const float pf = g.pf[r], invp = g.invp[r];
+              const float pf = g.pf[r], invp = g.invp[r], pm = kMagic + pf;
 #pragma unroll 1
               for (uint32_t col = 0; col < kHalf; col += kBatch) {
                 uint32_t v[kBatch / 16][16];
@@ -692,7 +697,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (uint32_t jj = 0; jj < 16; jj++)
                       stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * NA + ra] =
-                          (uint8_t)canonical(reduce_p(__uint_as_float(v[b][jj]), pf, invp), g.p[r]);
+                          (uint8_t)canonical_bits(reduce_p(__uint_as_float(v[b][jj]), pf, invp), pm);
                 }
               }
               if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
