@@ -29,7 +29,10 @@ def test_outer_steps_match_oracle(path, R):
     p = tnc.plan_formula(f, heuristic="bisect", rank_cap=24)
     exact = oracle.count(f, max_rank=24)
     r = tnc.contract(p, n_residues=R, path=path)
-    assert tnc.last_launch_counts()["outer"] >= 1
+    lc = tnc.last_launch_counts()
+    assert lc["outer"] >= 1 and lc["level"] >= 1 and lc["leaf_fill"] >= 1
+    if path == "int64":  # the plan's other big steps on the grid-wide step kernel
+        assert lc["grid_step"] >= 1
     assert [int(x) for x in r.residues[0]] == [exact[0] % q for q in r.primes]
     assert r.flags == 0 and r.counts == exact
 
