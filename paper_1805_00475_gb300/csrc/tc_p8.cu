@@ -269,12 +269,14 @@ __device__ __forceinline__ uint32_t canonical_bits(float r, float pm) {
 // X: the operand's residues in [0, p_i), one byte each, entry q * R + r at
 // X + (q * R + r) * RG (R = 2^f >= 16 rows, K = 2^k shared values, RG
 // residues per entry); Y_i (i < RG, Y_i = Y + i * R * Kp): balanced fp16
-// residues mod p_i, row-major, Y_i[r * Kp + q] with rows padded to
-// Kp = max(K, 64) values by zeros.  A block transposes tiles of 64 rows x 64
-// shared values through shared memory: a thread reads the entries of 4
-// consecutive rows at shared values q and q + 1 (4 RG bytes each, coalesced
-// along r) and builds, for each row and residue, the half2 (Y_i[r][q],
-// Y_i[r][q+1]); 16-byte writes are coalesced along q.
+// residues mod p_i.  K-contiguous planes (mode 1): Y_i[r * Kp + q] with rows
+// padded to Kp = max(K, 64) values by zeros; a block transposes tiles of 64
+// rows x 64 shared values through shared memory: a thread reads the entries
+// of 4 consecutive rows at shared values q and q + 1 (4 RG bytes each,
+// coalesced along r) and builds, for each row and residue, the half2
+// (Y_i[r][q], Y_i[r][q+1]); 16-byte writes are coalesced along q.
+// Row-contiguous planes (mode 2, K >= 64): Y_i[q * R + r], the entries' own
+// order, converted in place of the transpose (8-byte writes along r).
 struct PackPrimes {
   uint32_t p[4];
 };
