@@ -570,7 +570,8 @@ def c4_block(args, dev, steps, warmup, compare):
             lc = tnc.last_launch_counts()
             nl += sum(v for k, v in lc.items() if k not in ("p8_tile_n", "p8_max_chunks", "p8_swapped",
                                                             "p8_padded", "tc_split", "p8_split",
-                                                            "p8_direct_out", "p8_direct_in", "p8_mn", "p8_pairs"))
+                                                            "p8_direct_out", "p8_direct_in", "p8_mn", "p8_pairs",
+                                                            "p8_cta_pair"))
             nl += lc["splitk"] + lc["tc_split"] + lc["p8_split"]  # split steps launch a second kernel
             a, b = tnc.last_io_bytes()
             h2d += a

@@ -330,6 +330,8 @@ typedef struct {
                              (output bit 0 is row bit 0)                              */
   int32_t outer;          /* big steps with one small operand (at most 16 free rows,
                              8 shared values), staged in shared memory               */
+  int32_t p8_cta_pair;    /* TNC_PATH_TC_P8 dense steps on CTA pairs: 256 x 256 tiles,
+                             one cta_group::2 MMA over two SMs' shared memory         */
 } tnc_launch_counts;
 int tnc_last_launch_counts(tnc_launch_counts* out);
 /* Bytes the calling thread's last tnc_contract or tnc_contract_sliced copied

@@ -68,11 +68,15 @@ __host__ __device__ constexpr uint32_t stage_pitch(uint32_t na) { return na == 4
 // tile; as many stages (up to 8) as fit next to it in 220 KiB (3 for
 // TN = 256, 4 for TN = 128, more for narrow tiles, whose steps stream a tall
 // operand and need more bytes in flight).
-template <uint32_t TN, uint32_t RG>
+// PAIR (TN = 256 only): a CTA pair shares one M = 256 MMA and each CTA stages
+// half of the B tile, so a stage is 16 + 16 KiB instead of 16 + 32 KiB and
+// four stages fit instead of three.
+template <uint32_t TN, uint32_t RG, bool PAIR = false>
 struct Cfg {
   static constexpr uint32_t NA = RG * TN <= 512 ? RG : 512 / TN;
   static constexpr uint32_t kRounds = RG / NA;
-  static constexpr uint32_t kStageBytes = (kABytes + TN * kStageK * 2 + 1023u) / 1024u * 1024u;
+  static constexpr uint32_t kRowsB = PAIR ? TN / 2 : TN;  // B rows (tile columns) staged by this CTA
+  static constexpr uint32_t kStageBytes = (kABytes + kRowsB * kStageK * 2 + 1023u) / 1024u * 1024u;
   static constexpr uint32_t kStagePitch = stage_pitch(NA);
   static constexpr uint32_t kStagingBytes = (TN * kStagePitch * NA + 15u) / 16u * 16u;
   static constexpr uint32_t kFit = (220u * 1024u - kStagingBytes) / kStageBytes;
@@ -146,6 +150,58 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
+// ---- CTA pairs (clusters of two CTAs sharing one tcgen05 MMA) --------------
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of both CTAs of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of the same shared-memory offset in the CTA
+// of cluster rank `rank`.
+__device__ __forceinline__ uint32_t mapa_cluster(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+
+// try_wait with cluster-scope acquire: the phase was completed by arrivals
+// of both CTAs of the pair (their tcgen05 stores are then visible).
+__device__ __forceinline__ bool mbar_try_cl(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded cluster-scope wait, as mbar_wait.
+__device__ __noinline__ bool mbar_wait_cl(uint32_t mbar, uint32_t parity) {
+  if (mbar_try_cl(mbar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 0; i < (1u << 26); i++) {
+    if (mbar_try_cl(mbar, parity)) return true;
+    if ((i & 63u) == 63u && gtimer() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+// One arrival (release at cluster scope) on the mbarrier at the
+// shared::cluster address `cmbar` (this CTA's or the peer's).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cmbar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cmbar) : "memory");
+}
+
 // 3-D tiled TMA load of the box at (x, y, z) into shared memory, completing
 // on mbar with its byte count.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
@@ -154,6 +210,18 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
           "r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+// The same load into this CTA's shared memory, completing on the mbarrier at
+// the shared::cluster address `cmbar`, which may lie in the peer CTA of the
+// pair (the pair's leader counts both CTAs' bytes on one barrier).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, int32_t z,
+                                                 uint32_t cmbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(cmbar)
       : "memory");
 }
 
@@ -207,18 +275,64 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N, uint32
   return (1u << 4) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// PAIR: one MMA of the CTA pair (cta_group::2), M = 256 rows, A's rows and
+// B's rows (tile columns) split between the two CTAs' shared memory at the
+// same offsets, the accumulator in both CTAs' TMEM (128 lanes each).
+template <bool PAIR>
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  if constexpr (PAIR)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// One arrival on this CTA's mbarrier once the MMAs issued so far are done.
+template <bool PAIR>
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
+  if constexpr (PAIR)
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// PAIR: the same arrival on the mbarrier at offset mbar of both CTAs.
+__device__ __forceinline__ void mma_commit_both(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(mbar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t cols) {
+  if constexpr (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  if constexpr (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -434,11 +548,12 @@ __global__ void p8_split_final_kernel(const uint8_t* __restrict__ part, uint8_t*
 // row tiles, column tiles outermost within a group, row tiles fastest, so
 // that the CTAs running at one time share the operand rows of a few row tiles
 // and of a few column tiles.
-template <uint32_t TN>
+// Row tiles are 128 rows (PAIR: 256, the pair's two 128-row halves).
+template <uint32_t TN, bool PAIR>
 __device__ __forceinline__ void tile_origin(uint32_t tile, const P8Args& g, uint32_t& m0, uint32_t& n0) {
   const uint32_t gm = g.gm_log, per_group = (g.n_items >> g.log_split) >> (31 - __clz(g.tiles_m) - gm);
   const uint32_t grp = tile / per_group, w = tile - grp * per_group;
-  m0 = ((grp << gm) + (w & ((1u << gm) - 1u))) * kTileM;
+  m0 = ((grp << gm) + (w & ((1u << gm) - 1u))) * (PAIR ? 2u * kTileM : kTileM);
   n0 = (w >> gm) * TN;
 }
 
@@ -454,11 +569,21 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"
 // once, so the next MMAs start while the staged bytes are written out (NA
 // residue bytes of each entry per round, the pass's layout: RG bytes per
 // entry).
-template <uint32_t TN, uint32_t RG>
+//
+// PAIR: clusters of two CTAs take work items of 256 rows x TN columns; CTA
+// rank q holds rows 128 q .. 128 q + 127 of the item (its A rows, its TMEM
+// lanes, its epilogue) and tile columns (TN / 2) q .. of the B tile.  The
+// leader (rank 0) issues the pair's M = 256 MMAs (cta_group::2); both
+// producers' copies complete on the leader's stage barrier (expecting both
+// CTAs' bytes), the leader's commits arrive on both CTAs' stage-free and
+// accumulator-full barriers, and one lane of each epilogue warp of both CTAs
+// arrives on the leader's accumulator-free barrier.
+template <uint32_t TN, uint32_t RG, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     p8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ P8Args g, uint32_t* err) {
-  using C = Cfg<TN, RG>;
+  static_assert(!PAIR || TN == 256, "CTA pairs for 256-wide tiles");
+  using C = Cfg<TN, RG, PAIR>;
   constexpr uint32_t kStages = C::kStages, kStageBytes = C::kStageBytes, NA = C::NA, kRounds = C::kRounds;
   using SW = StageWord<NA>;
   constexpr uint32_t kStagePitch = C::kStagePitch;
@@ -482,23 +607,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (uint32_t r = 0; r < NA; r++) {
       mbar_init(accf0 + 8 * r, 1);
-      mbar_init(acce0 + 8 * r, kEpiThreads);
+      mbar_init(acce0 + 8 * r, PAIR ? 2 * kEpiWarps : kEpiThreads);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                 "r"(kCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc<PAIR>(smem_u32(&tmem_base_s), kCols);  // PAIR: both CTAs' warp 1 together
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before any copy, commit or arrival reaches them
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
+  const uint32_t crank = PAIR ? cluster_rank() : 0u;
+  const bool leader = crank == 0;
 
-  const uint32_t G = gridDim.x, bid = blockIdx.x;
+  const uint32_t G = gridDim.x / (PAIR ? 2u : 1u), bid = blockIdx.x / (PAIR ? 2u : 1u);
   const uint32_t T = g.n_items > bid ? (g.n_items - bid + G - 1) / G : 0;
   const uint32_t Ks = (1u << g.k) >> g.log_split;
   const uint32_t chunk = Ks < kChunkK ? Ks : kChunkK;
@@ -516,7 +639,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t item = bid + t * G;
         const uint32_t split = item & split_mask, tile = item >> g.log_split;
         uint32_t m0, n0;
-        tile_origin<TN>(tile, g, m0, n0);
+        tile_origin<TN, PAIR>(tile, g, m0, n0);
+        m0 += crank * kTileM;                  // this CTA's rows
+        n0 += crank * C::kRowsB;               // this CTA's part of the B tile
         for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
           for (uint32_t ra = 0; ra < NA && ok; ra++) {
@@ -529,20 +654,26 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               const uint32_t sa = smem_u32(smem + s * kStageBytes);
               const int32_t x = (int32_t)(q0 + j * kStageK);
-              mbar_expect_tx(full0 + 8 * s, (kTileM + TN) * kStageK * 2u);
+              // PAIR: the stage's copies of both CTAs complete on the leader's barrier
+              const uint32_t fb = PAIR ? mapa_cluster(full0 + 8 * s, 0) : full0 + 8 * s;
+              if (leader) mbar_expect_tx(full0 + 8 * s, (PAIR ? 2u : 1u) * (kTileM + C::kRowsB) * kStageK * 2u);
+              auto load = [&](uint32_t dst, const CUtensorMap* map, int32_t cx, int32_t cy) {
+                if constexpr (PAIR) tma_load_3d_pair(dst, map, cx, cy, (int32_t)r, fb);
+                else tma_load_3d(dst, map, cx, cy, (int32_t)r, fb);
+              };
               // K-contiguous planes: one box of rows x 64 shared values;
               // row-contiguous: boxes of 64 rows x 64 shared values, 8 KiB apart
               if (a_mn) {
-                tma_load_3d(sa, &tmA, (int32_t)m0, x, (int32_t)r, full0 + 8 * s);
-                tma_load_3d(sa + 8192u, &tmA, (int32_t)m0 + 64, x, (int32_t)r, full0 + 8 * s);
+                load(sa, &tmA, (int32_t)m0, x);
+                load(sa + 8192u, &tmA, (int32_t)m0 + 64, x);
               } else {
-                tma_load_3d(sa, &tmA, x, (int32_t)m0, (int32_t)r, full0 + 8 * s);
+                load(sa, &tmA, x, (int32_t)m0);
               }
               if (b_mn) {
-                for (uint32_t h = 0; h < TN / 64u; h++)
-                  tma_load_3d(sa + kABytes + 8192u * h, &tmB, (int32_t)(n0 + 64u * h), x, (int32_t)r, full0 + 8 * s);
+                for (uint32_t h = 0; h < C::kRowsB / 64u; h++)
+                  load(sa + kABytes + 8192u * h, &tmB, (int32_t)(n0 + 64u * h), x);
               } else {
-                tma_load_3d(sa + kABytes, &tmB, x, (int32_t)n0, (int32_t)r, full0 + 8 * s);
+                load(sa + kABytes, &tmB, x, (int32_t)n0);
               }
               issued++;
               if (++s == kStages) {
@@ -552,16 +683,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
       }
-      // every copy issued has landed before the CTA can exit
-      for (uint32_t s2 = 0; s2 < kStages && s2 < issued; s2++) {
+      // every copy issued has landed before the CTA can exit (PAIR: the
+      // leader's barriers count the peer's copies too; the peer stays until
+      // the leader reaches the final cluster barrier)
+      for (uint32_t s2 = 0; s2 < kStages && s2 < issued && leader; s2++) {
         const uint32_t uses = issued / kStages + (s2 < issued % kStages ? 1u : 0u);
         if (!mbar_wait(full0 + 8 * s2, (uses - 1u) & 1u)) ok = false;
       }
       if (!ok) atomicExch(err, 1u);
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = make_idesc(kTileM, TN, a_mn ? 1u : 0u, b_mn ? 1u : 0u);
+    if (lane == 0 && leader) {  // MMA issuer (PAIR: the leader's, for both CTAs)
+      const uint32_t idesc = make_idesc(PAIR ? 2u * kTileM : kTileM, TN, a_mn ? 1u : 0u, b_mn ? 1u : 0u);
       const uint32_t a_ks = a_mn ? 2048u >> 4 : 32u >> 4, b_ks = b_mn ? 2048u >> 4 : 32u >> 4;
       uint32_t s = 0, ph = 0, na[NA];
       for (uint32_t r = 0; r < NA; r++) na[r] = 0;
@@ -569,7 +702,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
           for (uint32_t r = 0; r < NA && ok; r++) {
-            if (!mbar_wait(acce0 + 8 * r, (na[r] & 1u) ^ 1u)) {  // the epilogue is done with accumulator r
+            // the epilogue (PAIR: both CTAs' epilogues) is done with accumulator r
+            if (!(PAIR ? mbar_wait_cl(acce0 + 8 * r, (na[r] & 1u) ^ 1u) : mbar_wait(acce0 + 8 * r, (na[r] & 1u) ^ 1u))) {
               ok = false;
               break;
             }
@@ -586,19 +720,22 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint64_t bd = b_mn ? make_desc_mn_sw128(sb) : make_desc_sw128(sb);
 #pragma unroll
               for (uint32_t ks = 0; ks < kStageK / 16; ks++)  // the ks-th 16 K values
-                mma_f16(d, ad + a_ks * ks, bd + b_ks * ks, idesc, (c | j | ks) ? 1u : 0u);
-              mma_commit(empty0 + 8 * s);  // the stage is free once these MMAs are done
+                mma_f16<PAIR>(d, ad + a_ks * ks, bd + b_ks * ks, idesc, (c | j | ks) ? 1u : 0u);
+              // the stage (PAIR: in both CTAs) is free once these MMAs are done
+              if constexpr (PAIR) mma_commit_both(empty0 + 8 * s);
+              else mma_commit<false>(empty0 + 8 * s);
               if (++s == kStages) {
                 s = 0;
                 ph ^= 1u;
               }
             }
             if (!ok) break;
-            mma_commit(accf0 + 8 * r);
+            if constexpr (PAIR) mma_commit_both(accf0 + 8 * r);
+            else mma_commit<false>(accf0 + 8 * r);
             na[r]++;
           }
       // every MMA issued has completed before the TMEM is freed
-      mma_commit(drain);
+      mma_commit<PAIR>(drain);
       if (!mbar_wait(drain, 0)) ok = false;
       if (!ok) atomicExch(err, 1u);
     }
@@ -662,7 +799,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t item = bid + t * G;
       const uint32_t split = item & split_mask, tile = item >> g.log_split;
       uint32_t m0, n0;
-      tile_origin<TN>(tile, g, m0, n0);
+      tile_origin<TN, PAIR>(tile, g, m0, n0);
+      m0 += crank * kTileM;  // PAIR: this CTA's 128 rows of the item (its TMEM lanes)
       uint64_t tile_base = lane_off;  // output offset of the tile's origin + the lane bits' part
       for (uint32_t j = 7; j < g.fa; j++)
         if ((m0 >> j) & 1u) tile_base += g.wm[j];
@@ -705,7 +843,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (!last) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
-            mbar_arrive(acce0 + 8 * ra);  // the accumulator is free (its values are in registers or staged)
+            // the accumulator is free (its values are in registers or staged);
+            // PAIR: one arrival per warp of either CTA, on the leader's barrier
+            if constexpr (PAIR) {
+              __syncwarp();
+              if (lane == 0) mbar_arrive_cluster(mapa_cluster(acce0 + 8 * ra, 0));
+            } else {
+              mbar_arrive(acce0 + 8 * ra);
+            }
             na[ra]++;
           }
         }
@@ -826,9 +971,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // no copy, commit or arrival of the peer still targets this CTA
   tc_fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  if (warp == 1) tmem_dealloc<PAIR>(tmem, kCols);
 }
 
 }  // namespace tnc_p8
@@ -890,8 +1035,9 @@ int make_map_mn(CUtensorMap* m, void* base, uint64_t rows, uint64_t K, uint32_t 
 
 struct Shape {
   bool swap;                   // rows come from B
+  bool pair;                   // 256-wide tiles on CTA pairs (an even number of row tiles)
   uint32_t fa, fb, k, kp, tn;  // row bits, column bits, shared bits (padded to >= 6), columns per tile
-  uint64_t tiles;
+  uint64_t tiles;              // tiles of 128 rows x tn columns
 };
 
 constexpr uint64_t kP8WideTiles = 456;
@@ -910,32 +1056,75 @@ Shape shape_of(const StepDesc& d) {
   s.tn = std::min<uint32_t>(1u << s.fb, 128);
   if (s.fb >= 8 && tiles_m * ((1ull << s.fb) / 256) >= kP8WideTiles) s.tn = 256;
   s.tiles = tiles_m * ((1ull << s.fb) / s.tn);
+  s.pair = s.tn == 256 && tiles_m % 2 == 0;
   return s;
 }
 
-template <uint32_t TN, uint32_t RG>
-int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid, uint32_t* err,
+// One CTA per SM for the g.n_items work items (at most `sms` CTAs); PAIR:
+// clusters of two CTAs, as many as fit at once (at most one item each).
+template <uint32_t TN, uint32_t RG, bool PAIR>
+int launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, int sms, uint32_t* err,
                 cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tnc_p8::p8_gemm_kernel<TN, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tnc_p8::Cfg<TN, RG>::kSmemBytes);
+  auto kern = tnc_p8::p8_gemm_kernel<TN, RG, PAIR>;
+  constexpr uint32_t smem = tnc_p8::Cfg<TN, RG, PAIR>::kSmemBytes;
+  static int max_units = -1;  // CTAs (PAIR: clusters) resident at once
+  if (max_units < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 attribute: ") + cudaGetErrorString(e));
-    attr = true;
+    int units = sms;
+    if (PAIR) {
+      cudaLaunchConfig_t cfg{};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2u * (unsigned)std::max(1, sms / 2));
+      cfg.blockDim = dim3(tnc_p8::kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      units = 0;
+      e = cudaOccupancyMaxActiveClusters(&units, kern, &cfg);
+      if (e != cudaSuccess)
+        return set_error(TNC_ERR_CUDA, std::string("p8 cluster occupancy: ") + cudaGetErrorString(e));
+      if (units <= 0) return set_error(TNC_ERR_CUDA, "no cluster of two CTAs fits the p8 GEMM");
+    }
+    max_units = units;
   }
-  tnc_p8::p8_gemm_kernel<TN, RG><<<grid, tnc_p8::kThreads, tnc_p8::Cfg<TN, RG>::kSmemBytes, st>>>(ma, mb, g, err);
+  const unsigned units = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)std::min(max_units, sms));
+  if (!PAIR) {
+    kern<<<units, tnc_p8::kThreads, smem, st>>>(ma, mb, g, err);
+    return TNC_OK;
+  }
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2u * units);
+  cfg.blockDim = dim3(tnc_p8::kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ma, mb, g, err);
+  if (e != cudaSuccess) return set_error(TNC_ERR_CUDA, std::string("p8 cluster launch: ") + cudaGetErrorString(e));
   return TNC_OK;
 }
 
 template <uint32_t RG>
-int launch_gemm_rg(uint32_t tn, const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g, unsigned grid,
-                   uint32_t* err, cudaStream_t st) {
+int launch_gemm_rg(uint32_t tn, bool pair, const CUtensorMap& ma, const CUtensorMap& mb, const tnc_p8::P8Args& g,
+                   int sms, uint32_t* err, cudaStream_t st) {
   switch (tn) {
-    case 16: return launch_gemm<16, RG>(ma, mb, g, grid, err, st);
-    case 32: return launch_gemm<32, RG>(ma, mb, g, grid, err, st);
-    case 64: return launch_gemm<64, RG>(ma, mb, g, grid, err, st);
-    case 128: return launch_gemm<128, RG>(ma, mb, g, grid, err, st);
-    default: return launch_gemm<256, RG>(ma, mb, g, grid, err, st);
+    case 16: return launch_gemm<16, RG, false>(ma, mb, g, sms, err, st);
+    case 32: return launch_gemm<32, RG, false>(ma, mb, g, sms, err, st);
+    case 64: return launch_gemm<64, RG, false>(ma, mb, g, sms, err, st);
+    case 128: return launch_gemm<128, RG, false>(ma, mb, g, sms, err, st);
+    default:
+      return pair ? launch_gemm<256, RG, true>(ma, mb, g, sms, err, st)
+                  : launch_gemm<256, RG, false>(ma, mb, g, sms, err, st);
   }
 }
 
@@ -1034,7 +1223,8 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   int rc = mn_a ? make_map_mn(&ma, pa, 1ull << s.fa, 1ull << s.k, rg)
                 : make_map(&ma, pa, 1ull << s.fa, 1ull << s.kp, rg, tnc_p8::kTileM);
   if (!rc)
-    rc = mn_b ? make_map_mn(&mb, pb, 1ull << s.fb, 1ull << s.k, rg) : make_map(&mb, pb, 1ull << s.fb, 1ull << s.kp, rg, s.tn);
+    rc = mn_b ? make_map_mn(&mb, pb, 1ull << s.fb, 1ull << s.k, rg)
+              : make_map(&mb, pb, 1ull << s.fb, 1ull << s.kp, rg, s.pair ? s.tn / 2 : s.tn);
   if (rc) return rc;
   tnc_p8::P8Args g;
   std::memset(&g, 0, sizeof(g));
@@ -1042,14 +1232,15 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   g.fb = s.fb;
   g.k = s.kp;  // zero-padded shared values contribute nothing
   g.log_split = ls;
-  g.tiles_m = (1u << s.fa) / tnc_p8::kTileM;
+  const uint32_t tile_rows = tnc_p8::kTileM * (s.pair ? 2u : 1u);  // rows per work item
+  g.tiles_m = (1u << s.fa) / tile_rows;
   {  // raster groups of 2^gm_log row tiles
     uint32_t gm = 0;
-    while ((2u << gm) <= g.tiles_m && (uint64_t)(2u << gm) * tnc_p8::kTileM * (2ull << s.kp) * rg <= kP8GroupBytes) gm++;
+    while ((2u << gm) <= g.tiles_m && (uint64_t)(2u << gm) * tile_rows * (2ull << s.kp) * rg <= kP8GroupBytes) gm++;
     g.gm_log = gm;
   }
   if ((s.tiles << ls) >= (1ull << 31)) return set_error(TNC_ERR_TOO_LARGE, "dense step has too many tiles");
-  g.n_items = (uint32_t)(s.tiles << ls);
+  g.n_items = (uint32_t)((s.pair ? s.tiles / 2 : s.tiles) << ls);
   g.rg = rg;
   g.a_mn = mn_a ? 1u : 0u;
   g.b_mn = mn_b ? 1u : 0u;
@@ -1094,10 +1285,9 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
   }
   g.pairs = (s.tn >= 32 && g.wm[0] == 1) ? 1u : 0u;  // output bit 0 is row bit 0
   g.out = ls ? part : arena + d.c_off * rg;  // direct: the planes, same place (twice the bytes)
-  const unsigned grid = (unsigned)std::min<uint64_t>(g.n_items, (uint64_t)sms);
-  if (rg == 4) rc = launch_gemm_rg<4>(s.tn, ma, mb, g, grid, dev_err, st);
-  else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, ma, mb, g, grid, dev_err, st);
-  else rc = launch_gemm_rg<1>(s.tn, ma, mb, g, grid, dev_err, st);
+  if (rg == 4) rc = launch_gemm_rg<4>(s.tn, s.pair, ma, mb, g, sms, dev_err, st);
+  else if (rg == 2) rc = launch_gemm_rg<2>(s.tn, s.pair, ma, mb, g, sms, dev_err, st);
+  else rc = launch_gemm_rg<1>(s.tn, s.pair, ma, mb, g, sms, dev_err, st);
   if (rc) return rc;
   {
     tnc_launch_counts& lc = launch_counts();
@@ -1114,6 +1304,7 @@ int p8_launch(const StepDesc& d, const uint32_t* primes, uint32_t rg, uint8_t* a
     lc.p8_direct_in += (dir_a ? 1 : 0) + (dir_b ? 1 : 0);
     lc.p8_mn += (mn_a ? 1 : 0) + (mn_b ? 1 : 0);
     if (g.pairs) lc.p8_pairs++;
+    if (s.pair) lc.p8_cta_pair++;
   }
   if (ls) {
     const uint64_t n = (uint64_t)rg << d.c;

@@ -84,7 +84,8 @@ class _LaunchCounts(ctypes.Structure):
                                               "p8_pack", "p8_gemm", "p8_split")] + \
                [("p8_tile_n", ctypes.c_int32 * 5)] + \
                [(n, ctypes.c_int32) for n in ("p8_max_chunks", "p8_swapped", "p8_padded", "extract", "crt",
-                                              "p8_direct_out", "p8_direct_in", "p8_mn", "p8_pairs", "outer")]
+                                              "p8_direct_out", "p8_direct_in", "p8_mn", "p8_pairs", "outer",
+                                              "p8_cta_pair")]
 
 
 class _LearnedOpts(ctypes.Structure):

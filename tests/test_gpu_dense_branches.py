@@ -3,7 +3,7 @@
 The formulas (#Cubic-Vertex-Cover on 100..130 vertices) have tensor-greedy
 plans of rank <= 24 whose dense steps, between them, take every branch of
 the dense kernels: 256-wide tiles on the 8-bit-prime path (two residues per
-TMEM round), several 1024-value chunks reduced mod p in TMEM before the next
+TMEM round; 256 x 256 tiles on CTA pairs sharing one MMA), several 1024-value chunks reduced mod p in TMEM before the next
 accumulates on top, K splits on both tensor-core paths, operands read
 K-contiguous and row-contiguous, and dense outputs written straight to the
 fp16 planes of the next dense step.  The exact counts come
@@ -76,6 +76,8 @@ def test_dense_cases_take_every_branch(runs):
     tc = [lc for (n, s, path), (_, lc, _) in runs.items() if path == "tc"]
     p8 = [lc for (n, s, path), (_, lc, _) in runs.items() if path == "tc_p8"]
     assert sum(lc["p8_tile_n"][256] for lc in p8) >= 1, "no 256-wide p8 tile"
+    assert sum(lc["p8_cta_pair"] for lc in p8) >= 1, "no 256 x 256 tile on a CTA pair"
+    assert all(lc["p8_cta_pair"] <= lc["p8_tile_n"][256] for lc in p8)
     assert max(lc["p8_max_chunks"] for lc in p8) >= 2, "no step reduced in TMEM between chunks"
     assert sum(lc["p8_split"] for lc in p8) >= 1, "no p8 K split"
     assert sum(lc["tc_split"] for lc in tc) >= 1, "no limb-path K split"
