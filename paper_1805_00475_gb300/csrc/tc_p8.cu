@@ -196,10 +196,13 @@ __device__ __noinline__ bool mbar_wait_cl(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// One arrival (release at cluster scope) on the mbarrier at the
-// shared::cluster address `cmbar` (this CTA's or the peer's).
+// One arrival on the mbarrier at the shared::cluster address `cmbar` (this
+// CTA's or the peer's).  Default semantics (release at CTA scope): the
+// arrival follows the thread's completed tcgen05 loads and stores (waited for
+// and fenced before it); a cluster-scope release would also wait for the
+// thread's global stores in flight, which the MMA never reads.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cmbar) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cmbar) : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cmbar) : "memory");
 }
 
 // 3-D tiled TMA load of the box at (x, y, z) into shared memory, completing
@@ -356,14 +359,17 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // x (an exact integer, as fp32) reduced modulo p to a representative of
-// magnitude at most 0.51 p: q is x (1/p) rounded to nearest, and the fma is
-// exact.  An accumulator holds at most 1024 ((p-1)/2)^2 + 0.51 p in magnitude
-// (one chunk of balanced products on top of a reduced remainder), below
-// 2^24, and |x| / p < 2^16, so x (1/p) is within 2^-7 of x / p: q is off by
-// one only next to a half.  The rounding adds 1.5 2^23 inside the fma (the
-// spacing of floats there is 1) and takes it off again: no float-to-integer
-// conversion.
-constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+// magnitude at most (p+1)/2: q is x (1/p) rounded to nearest, and the fma is
+// exact.  Operands are representatives of magnitude at most (p+1)/2 <= 126
+// (balanced residues, or this function's own outputs), so an accumulator
+// holds at most 1024 126^2 + 126 < 2^24 in magnitude (one chunk of products
+// on top of a reduced remainder), where fp32 sums are exact, and
+// |x| / p < 2^16, so x (1/p) is within 2^-8 of x / p: q is off by one only
+// next to a half, and then |r| <= p/2 + p 2^-8 < p/2 + 1.  The rounding adds
+// 1.5 2^23 inside the fma (the spacing of floats there is 1) and takes it off
+// again: no float-to-integer conversion.
+constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23
+constexpr float kMagic128 = 12583040.0f;  // 1.5 * 2^23 + 128
 __device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
   const float q = fmaf(x, invp, kMagic) - kMagic;
   return fmaf(-q, pf, x);
@@ -376,6 +382,38 @@ __device__ __forceinline__ float reduce_p(float x, float pf, float invp) {
 // conversion.
 __device__ __forceinline__ uint32_t canonical_bits(float r, float pm) {
   return __float_as_uint(r + (r < 0.0f ? pm : kMagic));
+}
+
+// The representative r itself (|r| <= (p+1)/2 <= 126), offset by 128, as the
+// low byte of a float's bits: r + 128 + 1.5 2^23 is exact, with bits
+// 0x4B400000 + r + 128 (2 <= r + 128 <= 254).  Outputs that a dense step reads
+// as fp16 planes are staged this way: any representative of magnitude at most
+// (p+1)/2 keeps that step's chunk sums exact (reduce_p).
+__device__ __forceinline__ uint32_t offset_bits(float r) { return __float_as_uint(r + kMagic128); }
+
+// fp16 values of such staged bytes b: the half with bits 0x6400 | b is
+// 1024 + b exactly, and one packed add of -1152 leaves r = b - 128 (exact).
+// staged_half2: byte ra of the entries o (in w0) and o + 1 (in w1 when the
+// staged word holds 4 residues, else in w0 above o's NA bytes) as a half2.
+__device__ __forceinline__ uint32_t add_m1152(uint32_t h2) {  // both halves minus 1152 (0xE480)
+  uint32_t r;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(h2), "r"(0xE480E480u));
+  return r;
+}
+template <uint32_t NA>
+__device__ __forceinline__ uint32_t staged_half2(uint32_t w0, uint32_t w1, uint32_t ra) {
+  uint32_t t;
+  if constexpr (NA == 4) {
+    t = (__byte_perm(w0, w1, ra | ((4u + ra) << 8)) & 0x00FF00FFu) | 0x64006400u;
+  } else {
+    t = __byte_perm(w0, 0x64646464u, ra | (4u << 4) | ((NA + ra) << 8) | (4u << 12));
+  }
+  return add_m1152(t);
+}
+// bytes ra and ra + 1 of one entry's staged word as a half2 (low: residue ra)
+__device__ __forceinline__ uint32_t staged_half2_res(uint32_t w, uint32_t ra) {
+  uint32_t t = __byte_perm(w, 0x64646464u, ra | (4u << 4) | ((ra + 1u) << 8) | (4u << 12));
+  return add_m1152(t);
 }
 
 // ---- operand packing ------------------------------------------------------
@@ -670,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 load(sa, &tmA, x, (int32_t)m0);
               }
               if (b_mn) {
-                for (uint32_t h = 0; h < C::kRowsB / 64u; h++)
+                for (uint32_t h = 0; 64u * h < C::kRowsB; h++)
                   load(sa + kABytes + 8192u * h, &tmB, (int32_t)(n0 + 64u * h), x);
               } else {
                 load(sa + kABytes, &tmB, x, (int32_t)n0);
@@ -696,14 +734,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0 && leader) {  // MMA issuer (PAIR: the leader's, for both CTAs)
       const uint32_t idesc = make_idesc(PAIR ? 2u * kTileM : kTileM, TN, a_mn ? 1u : 0u, b_mn ? 1u : 0u);
       const uint32_t a_ks = a_mn ? 2048u >> 4 : 32u >> 4, b_ks = b_mn ? 2048u >> 4 : 32u >> 4;
-      uint32_t s = 0, ph = 0, na[NA];
-      for (uint32_t r = 0; r < NA; r++) na[r] = 0;
+      uint32_t s = 0, ph = 0, par = 0;  // bit r: phase parity of accumulator r
       for (uint32_t t = 0; t < T && ok; t++)
         for (uint32_t rd = 0; rd < kRounds && ok; rd++)
         for (uint32_t c = 0; c < n_chunks && ok; c++)
           for (uint32_t r = 0; r < NA && ok; r++) {
             // the epilogue (PAIR: both CTAs' epilogues) is done with accumulator r
-            if (!(PAIR ? mbar_wait_cl(acce0 + 8 * r, (na[r] & 1u) ^ 1u) : mbar_wait(acce0 + 8 * r, (na[r] & 1u) ^ 1u))) {
+            const uint32_t pr = ((par >> r) & 1u) ^ 1u;
+            if (!(PAIR ? mbar_wait_cl(acce0 + 8 * r, pr) : mbar_wait(acce0 + 8 * r, pr))) {
               ok = false;
               break;
             }
@@ -732,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             if constexpr (PAIR) mma_commit_both(accf0 + 8 * r);
             else mma_commit<false>(accf0 + 8 * r);
-            na[r]++;
+            par ^= 1u << r;
           }
       // every MMA issued has completed before the TMEM is freed
       mma_commit<PAIR>(drain);
@@ -793,8 +831,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       ho_tab[h] = make_uint2(off, sid);
     }
     constexpr uint32_t kLogTN = TN == 256 ? 8 : TN == 128 ? 7 : TN == 64 ? 6 : TN == 32 ? 5 : 4;
-    uint32_t na[NA];
-    for (uint32_t r = 0; r < NA; r++) na[r] = 0;
+    uint32_t par = 0;  // bit ra: phase parity of accumulator ra
     for (uint32_t t = 0; t < T; t++) {
       const uint32_t item = bid + t * G;
       const uint32_t split = item & split_mask, tile = item >> g.log_split;
@@ -812,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (last) epi_bar();  // the previous round's bytes are out: the staging is free
           for (uint32_t ra = 0; ra < NA; ra++) {
             const uint32_t r = rd * NA + ra;
-            if (ok && !mbar_wait(accf0 + 8 * ra, na[ra] & 1u)) ok = false;
+            if (ok && !mbar_wait(accf0 + 8 * ra, (par >> ra) & 1u)) ok = false;
             tc_fence_after();
             const uint32_t tb = tmem + ((quarter * 32u) << 16) + ra * TN + cbeg;
             if (ok && !idle) {
@@ -831,6 +868,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                       v[b][jj] = __float_as_uint(reduce_p(__uint_as_float(v[b][jj]), pf, invp));
                     tmem_st16(tb + col + 16 * b, v[b]);
                   }
+                } else if (g.direct) {  // r + 128, one byte per residue of the round in the staged entry
+#pragma unroll
+                  for (uint32_t b = 0; b < kBatch / 16; b++)
+#pragma unroll
+                    for (uint32_t jj = 0; jj < 16; jj++)
+                      stage8[((cbeg + col + 16 * b + jj) * kStagePitch + row) * NA + ra] =
+                          (uint8_t)offset_bits(reduce_p(__uint_as_float(v[b][jj]), pf, invp));
                 } else {  // canonical residue, one byte per residue of the round in the staged entry
 #pragma unroll
                   for (uint32_t b = 0; b < kBatch / 16; b++)
@@ -851,7 +895,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else {
               mbar_arrive(acce0 + 8 * ra);
             }
-            na[ra]++;
+            par ^= 1u << ra;
           }
         }
         epi_bar();  // every residue of the round is staged
@@ -859,12 +903,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ok && pv && g.direct) {
           // pairs of entries: one staging load, one half2 store per residue
           __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb)) + tile_base;
-          __half2 hp2[NA], np2[NA];
-#pragma unroll
-          for (uint32_t ra = 0; ra < NA; ra++) {
-            hp2[ra] = __float2half2_rn((float)((g.p[rd * NA + ra] - 1) / 2));
-            np2[ra] = __float2half2_rn(-(float)g.p[rd * NA + ra]);
-          }
           for (uint32_t e0 = et; e0 < (kTileM * TN) / 2; e0 += 4 * kEpiThreads) {
             uint32_t adr[4], w0[4], w1[4];  // the pair's staged bytes: entry o in w0, o + 1 in w1 (NA = 4) or both in w0
 #pragma unroll
@@ -887,15 +925,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               __half* pl = planes + ((uint64_t)ra << (g.fa + g.fb));
 #pragma unroll
               for (uint32_t u = 0; u < 4; u++) {
-                const uint32_t h2 = tnc_p8::p8_half2(w0[u], ra, w1[u], (NA == 4 ? 0u : NA) + ra, hp2[ra], np2[ra]);
-                *reinterpret_cast<uint32_t*>(pl + adr[u]) = h2;
+                *reinterpret_cast<uint32_t*>(pl + adr[u]) = staged_half2<NA>(w0[u], w1[u], ra);
               }
             }
           }
         } else if (ok && g.direct) {
-          // balanced fp16 planes of the next dense step's operand, the
-          // entries' own order: plane of residue rd NA + ra at
-          // out + (rd NA + ra) 2^(fa+fb) halves
+          // fp16 planes of the next dense step's operand (representatives of
+          // magnitude at most (p+1)/2), the entries' own order: plane of
+          // residue rd NA + ra at out + (rd NA + ra) 2^(fa+fb) halves
           __half* planes = reinterpret_cast<__half*>(g.out) + ((uint64_t)(rd * NA) << (g.fa + g.fb)) + tile_base;
           for (uint32_t e0 = et; e0 < kTileM * TN; e0 += 4 * kEpiThreads) {
             uint32_t adr[4];
@@ -907,14 +944,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               val[u] = sp[t.y];
             }
 #pragma unroll
-            for (uint32_t ra = 0; ra < NA; ra++) {
-              const int p = (int)g.p[rd * NA + ra];
+            for (uint32_t ra = 0; ra < NA; ra += 2) {  // two residues per half2
               __half* pl = planes + ((uint64_t)ra << (g.fa + g.fb));
 #pragma unroll
               for (uint32_t u = 0; u < 4; u++) {
-                int v = (int)((uint32_t)val[u] >> (8 * ra)) & 0xFF;
-                if (v > (p - 1) / 2) v -= p;
-                pl[adr[u]] = __int2half_rn(v);
+                const uint32_t h2 = staged_half2_res((uint32_t)val[u], ra);
+                pl[adr[u]] = __ushort_as_half((unsigned short)(h2 & 0xFFFFu));
+                if (ra + 1 < NA) pl[((uint64_t)1 << (g.fa + g.fb)) + adr[u]] = __ushort_as_half((unsigned short)(h2 >> 16));
               }
             }
           }
