@@ -665,7 +665,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t chunk = Ks < kChunkK ? Ks : kChunkK;
   const uint32_t n_chunks = Ks / chunk;
   const uint32_t spc = chunk / kStageK;  // stages per chunk
-  const uint32_t split_mask = (1u << g.log_split) - 1u;
+  // items run K slice by K slice (split-major): the items of one wave share
+  // their slice's operand rows in L2
+  const uint32_t tile_bits = 31u - __clz(g.n_items >> g.log_split), tile_mask = (1u << tile_bits) - 1u;
   // row-contiguous operands (a tile of TN < 64 columns always reads B K-contiguous)
   const bool a_mn = g.a_mn != 0, b_mn = TN >= 64 && g.b_mn != 0;
   bool ok = true;
@@ -675,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t s = 0, ph = 0, issued = 0;
       for (uint32_t t = 0; t < T && ok; t++) {
         const uint32_t item = bid + t * G;
-        const uint32_t split = item & split_mask, tile = item >> g.log_split;
+        const uint32_t split = item >> tile_bits, tile = item & tile_mask;
         uint32_t m0, n0;
         tile_origin<TN, PAIR>(tile, g, m0, n0);
         m0 += crank * kTileM;                  // this CTA's rows
@@ -834,7 +836,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t par = 0;  // bit ra: phase parity of accumulator ra
     for (uint32_t t = 0; t < T; t++) {
       const uint32_t item = bid + t * G;
-      const uint32_t split = item & split_mask, tile = item >> g.log_split;
+      const uint32_t split = item >> tile_bits, tile = item & tile_mask;
       uint32_t m0, n0;
       tile_origin<TN, PAIR>(tile, g, m0, n0);
       m0 += crank * kTileM;  // PAIR: this CTA's 128 rows of the item (its TMEM lanes)
@@ -1077,6 +1079,7 @@ struct Shape {
 };
 
 constexpr uint64_t kP8WideTiles = 456;
+constexpr uint64_t kP8Sms = 152;  // SMs of the GPU this path is laid out for
 
 Shape shape_of(const StepDesc& d) {
   Shape s;
@@ -1091,6 +1094,12 @@ Shape shape_of(const StepDesc& d) {
   const uint64_t tiles_m = (1ull << s.fa) / tnc_p8::kTileM;
   s.tn = std::min<uint32_t>(1u << s.fb, 128);
   if (s.fb >= 8 && tiles_m * ((1ull << s.fb) / 256) >= kP8WideTiles) s.tn = 256;
+  // long-K steps with fewer 256-wide tiles take CTA pairs too: their K split
+  // (p8_split_log) supplies the work items
+  if (s.fb >= 8 && tiles_m % 2 == 0 && s.k >= 11) s.tn = 256;
+  // steps with less than a wave of tiles: narrower tiles (down to 32 columns)
+  // while they stay within one wave, so that more SMs share the epilogue
+  while (s.tn > 32 && s.tn < 256 && tiles_m * ((2ull << s.fb) / s.tn) <= kP8Sms) s.tn /= 2;
   s.tiles = tiles_m * ((1ull << s.fb) / s.tn);
   s.pair = s.tn == 256 && tiles_m % 2 == 0;
   return s;
@@ -1180,9 +1189,25 @@ constexpr uint64_t kP8SplitTarget = 160;
 // measured 2 % faster on C4 than all row tiles in one group, 8 MiB and
 // 128 MiB no better).
 constexpr uint64_t kP8GroupBytes = 32ull << 20;
+// CTA-pair steps with fewer than three work items (pairs of tiles) per pair
+// of SMs: the split whose waves of items take the least time (waves x K per
+// item), the smallest within 5 % of it (fewer partial sums).
 uint32_t p8_split_log(const StepDesc& d) {
   const Shape s = shape_of(d);
   uint32_t ls = 0;
+  if (s.pair) {
+    if (s.tiles >= kP8WideTiles) return 0;
+    uint32_t max_ls = 0;
+    while (s.k - max_ls - 1 >= 10 && (1ull << (d.c + max_ls + 1)) <= (1ull << 26)) max_ls++;
+    double t[32], best = 1e300;
+    for (uint32_t l = 0; l <= max_ls; l++) {
+      const uint64_t items = (s.tiles / 2) << l, units = kP8Sms / 2;
+      t[l] = (double)((items + units - 1) / units) / (double)(1u << l);
+      best = std::min(best, t[l]);
+    }
+    while (t[ls] > 1.05 * best) ls++;
+    return ls;
+  }
   while ((s.tiles << ls) < kP8SplitTarget && s.k - ls - 1 >= 10 && (1ull << (d.c + ls + 1)) <= (1ull << 26)) ls++;
   return ls;
 }

@@ -34,9 +34,10 @@ def test_p8_matches_oracle(n, h, seed):
 
 
 def test_p8_oracle_cases_cover_every_tile_width_and_both_orientations():
-    """The oracle cases above, by the library's own launch record: every tile
-    width up to 128 (256: tests/test_gpu_dense_branches.py), rows from A and
-    from B, zero-padded and unpadded shared dimensions."""
+    """The oracle cases above, by the library's own launch record: the narrow
+    tile widths that steps with less than a wave of tiles take (64, 128 and
+    256: tests/test_gpu_dense_branches.py), rows from A and from B,
+    zero-padded and unpadded shared dimensions."""
     widths, swapped, unswapped, padded, unpadded = set(), 0, 0, 0, 0
     for n, h, seed in ORACLE_CASES:
         p = tnc.plan_formula(I.cubic_vertex_cover(n, seed), heuristic=h, rank_cap=28)
@@ -47,7 +48,7 @@ def test_p8_oracle_cases_cover_every_tile_width_and_both_orientations():
         unswapped += lc["p8_gemm"] - lc["p8_swapped"]
         padded += lc["p8_padded"]
         unpadded += lc["p8_gemm"] - lc["p8_padded"]
-    assert {16, 32, 64, 128} <= widths
+    assert {16, 32} <= widths
     assert swapped and unswapped and padded and unpadded
 
 
@@ -72,13 +73,14 @@ def test_p8_k_split_cases_really_split():
 
 
 def test_p8_many_chunks_match_int64():
-    """A dense step with 2^16 shared values over 2^2 K slices: 16 chunks of
-    1024 per tile, each reduced in place in TMEM before the next."""
+    """A dense step with 2^16 shared values (256 x 256 tiles on CTA pairs)
+    over 2^4 K slices: 4 chunks of 1024 per tile, each reduced in place in
+    TMEM before the next."""
     f = I.cubic_vertex_cover(180, 1)
     p = tnc.plan_formula(f, heuristic="best", rank_cap=30)
     a = tnc.contract(p, n_residues=7, path="int64")
     b = tnc.contract(p, n_residues=26, path="tc_p8")
-    assert tnc.last_launch_counts()["p8_max_chunks"] >= 8
+    assert tnc.last_launch_counts()["p8_max_chunks"] >= 4
     assert a.flags == 0 and b.flags == 0
     assert a.counts == b.counts
 
