@@ -21,6 +21,9 @@
 // contiguous.  TMA moves tiles of rows x 64 values (128-byte lines) into
 // shared memory with the 128-byte swizzle, the canonical K-major SWIZZLE_128B
 // layout of the MMA operand descriptors.
+// An output that feeds another dense step is written straight as that
+// step's fp16 planes (representatives of magnitude at most (p+1)/2, which
+// keep its chunk sums exact).
 // Persistent CTAs (one per SM, 576 threads) run three warp roles:
 //   warp 0, lane 0: TMA producer over a ring of 3 to 8 shared-memory stages;
 //   warp 1, lane 0: MMA issuer (kind::f16, 128 x TN x 16, fp32 in TMEM);
@@ -29,8 +32,14 @@
 // A work item is an output tile of 128 rows x TN columns (TN <= 256) and a K
 // slice; NA = min(RG, 512 / TN) residues accumulate at once, one TMEM
 // accumulator each, so one residue's reduction overlaps the next residue's
-// MMAs.  Every wait is bounded (about 2 s); on timeout the kernel records an
-// error word, drains its own copies and MMAs, frees its TMEM and returns.
+// MMAs.  256-wide tiles run on CTA pairs (clusters of two, one per SM): an
+// item is then 256 rows x 256 columns, the leader CTA issues one
+// cta_group::2 MMA (M = 256) over both CTAs' shared memory, each CTA staging
+// its own 128 A rows and half of the B tile (32 KiB per stage instead of 48,
+// four stages in flight instead of three) and reducing its own 128 TMEM
+// lanes.  Items run K slice by K slice.  Every wait is bounded (about 2 s);
+// on timeout the kernel records an error word, drains its own copies and
+// MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
