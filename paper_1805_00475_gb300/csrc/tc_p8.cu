@@ -740,6 +740,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!mbar_wait(full0 + 8 * s2, (uses - 1u) & 1u)) ok = false;
       }
       if (!ok) atomicExch(err, 1u);
+      // PAIR, after a failed wait: copies this CTA issued may not have been
+      // consumed, and their barrier is the leader's, which this thread cannot
+      // wait on; about 1 ms for them to land before the CTAs can exit
+      if (PAIR && !ok)
+        for (int i = 0; i < 1000; i++) __nanosleep(1000);
     }
   } else if (warp == 1) {
     if (lane == 0 && leader) {  // MMA issuer (PAIR: the leader's, for both CTAs)
