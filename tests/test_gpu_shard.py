@@ -49,7 +49,7 @@ def _rank(rank, world, port, out):
 
 
 def test_two_processes_share_one_count():
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(2, _free_port(), out), nprocs=2, join=True)
         res = dict(out)

@@ -40,7 +40,7 @@ def test_two_ranks_shard_and_take_the_slowest_time():
     import oracle
     from paper_1805_00475_gb300 import instances as I
     world, batch = 2, 3
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank, args=(world, _free_port(), batch, out), nprocs=world, join=True)
         res = dict(out)

@@ -77,7 +77,7 @@ def _rank_residues(rank, world, port, out):
 
 
 def test_two_ranks_residue_shards_rebuild_the_count():
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_residues, args=(2, _free_port(), out), nprocs=2, join=True)
         res = dict(out)
@@ -115,7 +115,7 @@ def _rank_slices(rank, world, port, out):
 
 def test_three_ranks_slice_shards_sum_to_the_count():
     """8 slices over 3 ranks (uneven shares); the host sums and remainders."""
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_slices, args=(3, _free_port(), out), nprocs=3, join=True)
         res = dict(out)
@@ -141,7 +141,7 @@ def _rank_lost(rank, world, port, out):
 
 
 def test_a_lost_shard_is_an_error_not_a_hang():
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         ctx = mp.spawn(_rank_lost, args=(2, _free_port(), out), nprocs=2, join=False)
         assert ctx.join(timeout=60) or ctx.join(timeout=60)
