@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=8192, help="formulas per rank per step")
     ap.add_argument("--impl", default="tnc", choices=["tnc", "reference"])
-    ap.add_argument("--planner", default="best")
+    ap.add_argument("--planner", default="coarsen",
+                    help="c2 planner: coarsen (tensor-greedy coarsening finished by the best of the paper's "
+                         "heuristics, fewest MACs) or any single heuristic")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c4", action="store_true", help="default run: leave out the C4 comparison block")
@@ -739,22 +741,26 @@ def kernel_source_sha(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def captured_traffic(profile: str, sources) -> tuple:
+def captured_traffic(profile: str, sources, planner: str) -> tuple:
     """(bytes per launch, note) from the profile's 'traffic_bytes_per_launch
-    = B, kernel_source_sha = H' line if H matches the current sources, else
-    (None, why)."""
+    = B, kernel_source_sha = H, planner = P' line if H matches the current
+    sources and P the planner of this run (the plans fix the launch's work),
+    else (None, why)."""
     import re
     try:
         with open(profile) as fh:
             txt = fh.read()
     except OSError:
         return None, "no profile"
-    m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)\s*,\s*kernel_source_sha\s*=\s*([0-9a-f]+)", txt)
+    m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)\s*,\s*kernel_source_sha\s*=\s*([0-9a-f]+)"
+                  r"\s*,\s*planner\s*=\s*(\w+)", txt)
     if not m:
         return None, "no traffic line in the profile"
     sha = kernel_source_sha(sources)
     if m.group(2) != sha:
         return None, f"kernel changed since the capture (sources {sha}, captured {m.group(2)})"
+    if m.group(3) != planner:
+        return None, f"captured with planner {m.group(3)}, this run plans with {planner}"
     return float(m.group(1)), f"ncu capture of this workload and kernel ({os.path.relpath(profile, ROOT)})"
 
 
@@ -901,8 +907,8 @@ def run_tnc(args):
     # lanes issue a 32-bit IMAD per clock; a residue MAC (u32 x u32 + u64) is one
     # 64-bit-result IMAD, two issue slots; clock = max SM clock
     alu_peak = sms * 4 * 16 / 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
-    default_shape = args.batch == 8192 and args.planner == "best" and not args.launch
-    traffic, traffic_src = captured_traffic(C2_PROFILE, C2_KERNEL_SOURCES) if default_shape else \
+    default_shape = args.batch == 8192 and not args.launch
+    traffic, traffic_src = captured_traffic(C2_PROFILE, C2_KERNEL_SOURCES, args.planner) if default_shape else \
         (None, "captured for the default workload only")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

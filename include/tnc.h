@@ -66,6 +66,10 @@ extern "C" {
 #define TNC_PLAN_EXPLICIT 3 /* caller-given pairwise order                        */
 #define TNC_PLAN_BEST 4     /* run GREEDY, BISECT and GN; keep the cheapest       */
 #define TNC_PLAN_PORTFOLIO 5 /* GREEDY, GN and BISECT with 8 seeds; the cheapest   */
+#define TNC_PLAN_COARSEN 6  /* two levels: tensor-greedy merges coarsen the network,
+                               BEST finishes it at 10, 20, .., 80 % of the merges;
+                               with GREEDY, BISECT and GN on the whole network, the
+                               plan with the fewest MACs within rank_cap is kept   */
 
 /* ---- arithmetic paths ---------------------------------------------------- */
 #define TNC_PATH_INT64 0 /* CUDA cores: u32 residues, 64-bit multiply-accumulate */

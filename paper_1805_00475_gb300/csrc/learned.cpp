@@ -415,4 +415,61 @@ int learned_trees(const std::vector<const Network*>& nets, const void* d_params_
   return TNC_OK;
 }
 
+// TNC_PLAN_COARSEN: the paper's heuristics (Sec. 3.1.1) used at two levels.
+// Tensor-greedy merges coarsen the network; at 10, 20, ..., 80 % of its
+// merges the network of the live tensors is finished by TNC_PLAN_BEST (the
+// coarse leaves are the live tensors, Sec. 2.2).  These plans, and
+// tensor-greedy, tensor-METIS and tensor-GN on the whole network, are the
+// candidates; their exact costs are known before any contraction (the lazy
+// evaluation of Sec. 4).  Kept: the fewest MACs among the candidates within the
+// rank cap (ties: smaller max rank); if none fits, the smallest (max rank, MACs).
+int plan_coarsen(const Network& net, const tnc_plan_opts& o, Tree& out) {
+  if (net.n_leaves() < 2) return plan_greedy(net, out);
+  std::vector<Tree> cands(3);
+  int rc = plan_greedy(net, cands[0]);
+  if (rc == TNC_OK) rc = plan_bisect(net, o.tries > 0 ? o.tries : 2, o.seed, cands[1]);
+  if (rc == TNC_OK) rc = plan_gn(net, cands[2]);
+  if (rc != TNC_OK) return rc;
+  GState s;
+  s.init(net);
+  std::vector<int> marks;
+  for (int pc = 10; pc <= 80; pc += 10) marks.push_back((net.n_leaves() - 1) * pc / 100);
+  marks.erase(std::unique(marks.begin(), marks.end()), marks.end());
+  std::vector<GState> snaps;
+  std::vector<Cand> cs;
+  for (int merged = 0; snaps.size() < marks.size();) {
+    while (snaps.size() < marks.size() && merged >= marks[snaps.size()]) snaps.push_back(s);
+    if (snaps.size() == marks.size()) break;
+    top_candidates(s, cs, 1);
+    if (cs.empty()) break;  // no two live tensors share a bond: coarsening ends here
+    s.merge(cs[0].a, cs[0].b);
+    merged++;
+  }
+  tnc_plan_opts best{};
+  best.heuristic = TNC_PLAN_BEST;
+  best.tries = o.tries;
+  best.seed = o.seed;
+  for (GState& g : snaps) {
+    complete_with(g, net, best);
+    cands.push_back(std::move(g.t));
+  }
+  const int cap = o.rank_cap > 0 ? o.rank_cap : 32;
+  int pick = -1;
+  TreeCost pc{};
+  for (size_t i = 0; i < cands.size(); i++) {
+    const TreeCost c = tree_cost(cands[i]);
+    bool better;
+    if (pick < 0) better = true;
+    else if ((c.max_rank <= cap) != (pc.max_rank <= cap)) better = c.max_rank <= cap;
+    else if (c.max_rank <= cap) better = c.macs < pc.macs || (c.macs == pc.macs && c.max_rank < pc.max_rank);
+    else better = cheaper_cost(c, pc);
+    if (better) {
+      pick = (int)i;
+      pc = c;
+    }
+  }
+  out = std::move(cands[pick]);
+  return TNC_OK;
+}
+
 }  // namespace tnc

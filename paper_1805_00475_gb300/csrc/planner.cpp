@@ -646,6 +646,7 @@ int plan_tree(const Network& net, const tnc_plan_opts& o, Tree& t) {
       }
       return TNC_OK;
     }
+    case TNC_PLAN_COARSEN: return plan_coarsen(net, o, t);
   }
   return set_error(TNC_ERR_INVALID, "unknown heuristic");
 }

@@ -128,6 +128,10 @@ int plan_greedy(const Network& net, Tree& t);
 int plan_bisect(const Network& net, int tries, uint64_t seed, Tree& t);
 int plan_gn(const Network& net, Tree& t);
 
+// learned.cpp: TNC_PLAN_COARSEN (tensor-greedy coarsening finished by
+// TNC_PLAN_BEST; fewest MACs within the rank cap)
+int plan_coarsen(const Network& net, const tnc_plan_opts& opts, Tree& out);
+
 // lower.cpp
 int lower_plan(const Network& net, const Tree& tree, Lowered& low);
 int validate_lowered(const Network& net, const Tree& tree, Lowered& low);

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libtnc.so")
 TNC_OK = 0
 ERRORS = {-1: "TNC_ERR_INVALID", -2: "TNC_ERR_TOO_LARGE", -3: "TNC_ERR_CUDA", -4: "TNC_ERR_BUFFER",
           -5: "TNC_ERR_TIMEOUT", -6: "TNC_ERR_NOMEM"}
-HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4, "portfolio": 5}
+HEURISTICS = {"greedy": 0, "bisect": 1, "gn": 2, "explicit": 3, "best": 4, "portfolio": 5, "coarsen": 6}
 PATHS = {"int64": 0, "tc": 1, "tc_p8": 2}
 TNC_MAYBE_WRAPPED = 1
 INJECT = {"none": 0, "nomem": 1, "plan": 2, "launch": 3, "timeout": 4}

@@ -120,7 +120,7 @@ def test_invalid_formulas_are_rejected():
                                              open_vars=[0, 0]))())
 
 
-@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best"])
+@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best", "coarsen"])
 def test_planners_build_full_trees(h):
     f = I.cubic_vertex_cover(60, 3)
     p = tnc.plan(tnc.build_network(f), heuristic=h)
@@ -199,9 +199,39 @@ DEGENERATE = [
 ]
 
 
-@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best"])
+@pytest.mark.parametrize("h", ["greedy", "bisect", "gn", "best", "coarsen"])
 def test_degenerate_formulas_plan(h):
     for f in DEGENERATE:
         p = tnc.plan_formula(f, heuristic=h)
         assert p.stats.n_steps == max(f.n_vars + f.n_cons - 1, 0)
     tnc.plan_many(DEGENERATE, heuristic=h)
+
+
+def test_coarsen_plan_is_never_costlier_than_the_whole_network_heuristics():
+    """TNC_PLAN_COARSEN keeps the fewest MACs within the rank cap among
+    candidates that include tensor-greedy, tensor-METIS (same tries and seed)
+    and tensor-GN planned on the whole network (Sec. 3.1.1), so within the
+    cap it never needs more MACs than any of the three."""
+    forms = [I.cubic_vertex_cover(60, s) for s in range(6)] + \
+        [I.one_in_three(100, 62, s) for s in range(4)]
+    gains = []
+    for f in forms:
+        net = tnc.build_network(f)
+        c = tnc.plan(net, heuristic="coarsen", rank_cap=32)
+        assert c.stats.max_rank <= 32
+        others = [tnc.plan(net, heuristic=h, rank_cap=64) for h in ("greedy", "bisect", "gn")]
+        fit = [o.stats.total_macs for o in others if o.stats.max_rank <= 32]
+        assert fit and c.stats.total_macs <= min(fit)
+        gains.append(min(fit) / c.stats.total_macs)
+    # the coarsened candidates do win on these workloads, not only tie
+    assert sum(g > 1.0 for g in gains) >= len(forms) // 2
+
+
+def test_coarsen_order_gives_the_oracle_count():
+    """The oracle contracting along the coarsen plan's own order (an explicit
+    pairwise order) gets the count it gets along its default order: the plan
+    is a full, valid contraction tree."""
+    import oracle
+    for f in (I.cubic_vertex_cover(40, 1), I.one_in_three(40, 26, 2), I.worked_example()):
+        p = tnc.plan_formula(f, heuristic="coarsen")
+        assert oracle.count(f, order=p.steps(), max_rank=26) == oracle.count(f, max_rank=26)

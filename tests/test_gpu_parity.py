@@ -55,7 +55,7 @@ def test_one_in_three_n20_bruteforce(seed):
 def test_cubic_vc_n60_four_residues(seed):
     f = I.cubic_vertex_cover(60, seed)
     exact = oracle.count(f)
-    for h in ("bisect", "gn"):
+    for h in ("bisect", "gn", "coarsen"):
         r = tnc.contract(tnc.plan_formula(f, heuristic=h), n_residues=4)
         _check(r, exact, 4)
         assert r.flags == 0 and r.counts == exact
