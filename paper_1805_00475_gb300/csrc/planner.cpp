@@ -456,46 +456,75 @@ struct GNGraph {
   std::vector<char> alive;
 };
 
+// Buffers of the betweenness computation, reused across a whole GN run.
+struct GNScratch {
+  std::vector<int> loc;               // leaf -> index in the current vertex set
+  std::vector<int> off, adj_v, adj_e; // alive edges inside the set, per vertex (g.nb order)
+  std::vector<int> dist, order;
+  std::vector<double> sigma, delta;
+};
+
 // Edge betweenness (Brandes 2001, unweighted) restricted to vertex set `vs`.
+// The alive edges inside `vs` are first gathered into per-vertex lists that
+// keep g.nb's neighbour order, so the |vs| breadth-first searches touch only
+// them; sources, visits and sums run in the same order as a search over g.nb
+// itself, so every sum is formed in the same order.
 static void betweenness(const GNGraph& g, const std::vector<int>& vs, const std::vector<char>& inset,
-                        std::vector<double>& eb) {
+                        std::vector<double>& eb, GNScratch& w) {
   std::fill(eb.begin(), eb.end(), 0.0);
-  std::vector<int> dist(g.n, -1);
-  std::vector<double> sigma(g.n, 0.0), delta(g.n, 0.0);
-  std::vector<int> order;
-  order.reserve(vs.size());
-  for (int s : vs) {
-    order.clear();
-    for (int v : vs) {
+  const int n = (int)vs.size();
+  w.loc.resize(g.n);
+  for (int i = 0; i < n; i++) w.loc[vs[i]] = i;
+  w.off.assign(n + 1, 0);
+  w.adj_v.clear();
+  w.adj_e.clear();
+  for (int i = 0; i < n; i++) {
+    for (auto& pe : g.nb[vs[i]]) {
+      if (!g.alive[pe.second] || !inset[pe.first]) continue;
+      w.adj_v.push_back(w.loc[pe.first]);
+      w.adj_e.push_back(pe.second);
+    }
+    w.off[i + 1] = (int)w.adj_v.size();
+  }
+  w.dist.assign(n, -1);
+  w.sigma.assign(n, 0.0);
+  w.delta.assign(n, 0.0);
+  w.order.resize(n);
+  int* dist = w.dist.data();
+  double* sigma = w.sigma.data();
+  double* delta = w.delta.data();
+  int* order = w.order.data();
+  const int* off = w.off.data();
+  const int* av = w.adj_v.data();
+  const int* ae = w.adj_e.data();
+  for (int s = 0; s < n; s++) {
+    for (int v = 0; v < n; v++) {
       dist[v] = -1;
       sigma[v] = 0;
       delta[v] = 0;
     }
     dist[s] = 0;
     sigma[s] = 1;
-    std::vector<int> q{s};
-    size_t head = 0;
-    while (head < q.size()) {
-      int u = q[head++];
-      order.push_back(u);
-      for (auto& pe : g.nb[u]) {
-        int v = pe.first;
-        if (!g.alive[pe.second] || !inset[v]) continue;
+    order[0] = s;
+    int head = 0, tail = 1;  // order[] is the queue and the visit order
+    while (head < tail) {
+      const int u = order[head++];
+      for (int j = off[u]; j < off[u + 1]; j++) {
+        const int v = av[j];
         if (dist[v] < 0) {
           dist[v] = dist[u] + 1;
-          q.push_back(v);
+          order[tail++] = v;
         }
         if (dist[v] == dist[u] + 1) sigma[v] += sigma[u];
       }
     }
-    for (size_t i = order.size(); i-- > 0;) {
-      int w = order[i];
-      for (auto& pe : g.nb[w]) {
-        int v = pe.first;
-        if (!g.alive[pe.second] || !inset[v]) continue;
-        if (dist[v] == dist[w] - 1) {
-          double c = sigma[v] / sigma[w] * (1.0 + delta[w]);
-          eb[pe.second] += c;
+    for (int i = tail; i-- > 0;) {
+      const int x = order[i];
+      for (int j = off[x]; j < off[x + 1]; j++) {
+        const int v = av[j];
+        if (dist[v] == dist[x] - 1) {
+          const double c = sigma[v] / sigma[x] * (1.0 + delta[x]);
+          eb[ae[j]] += c;
           delta[v] += c;
         }
       }
@@ -526,7 +555,7 @@ static std::vector<std::vector<int>> components(const GNGraph& g, const std::vec
   return comps;
 }
 
-static int gn_rec(Tree& t, GNGraph& g, std::vector<int> vs) {
+static int gn_rec(Tree& t, GNGraph& g, std::vector<int> vs, GNScratch& w) {
   if (vs.size() == 1) return vs[0];
   std::vector<char> inset(g.n, 0);
   for (int v : vs) inset[v] = 1;
@@ -535,7 +564,7 @@ static int gn_rec(Tree& t, GNGraph& g, std::vector<int> vs) {
     auto comps = components(g, vs, inset);
     if (comps.size() > 1) {
       std::vector<int> roots;
-      for (auto& c : comps) roots.push_back(gn_rec(t, g, c));
+      for (auto& c : comps) roots.push_back(gn_rec(t, g, c, w));
       // combine the communities smallest rank first (a binary dendrogram)
       while (roots.size() > 1) {
         std::sort(roots.begin(), roots.end(), [&](int x, int y) {
@@ -548,7 +577,7 @@ static int gn_rec(Tree& t, GNGraph& g, std::vector<int> vs) {
       }
       return roots[0];
     }
-    betweenness(g, vs, inset, eb);
+    betweenness(g, vs, inset, eb, w);
     int best = -1;
     for (size_t e = 0; e < g.eu.size(); e++) {
       if (!g.alive[e] || !inset[g.eu[e]] || !inset[g.ev[e]]) continue;
@@ -584,7 +613,8 @@ int plan_gn(const Network& net, Tree& t) {
   g.alive.assign(g.eu.size(), 1);
   std::vector<int> all(g.n);
   std::iota(all.begin(), all.end(), 0);
-  t.root = gn_rec(t, g, all);
+  GNScratch w;
+  t.root = gn_rec(t, g, all, w);
   return TNC_OK;
 }
 
