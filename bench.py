@@ -741,11 +741,12 @@ def kernel_source_sha(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def captured_traffic(profile: str, sources, planner: str) -> tuple:
+def captured_traffic(profile: str, sources, planner: str, plan_macs: float = None) -> tuple:
     """(bytes per launch, note) from the profile's 'traffic_bytes_per_launch
-    = B, kernel_source_sha = H, planner = P' line if H matches the current
-    sources and P the planner of this run (the plans fix the launch's work),
-    else (None, why)."""
+    = B, kernel_source_sha = H, planner = P[, plan_macs = M]' line if H
+    matches the current sources, P the planner of this run and M (the
+    algorithmic MACs of the captured launch) this launch's (the plans fix the
+    launch's work), else (None, why)."""
     import re
     try:
         with open(profile) as fh:
@@ -753,7 +754,7 @@ def captured_traffic(profile: str, sources, planner: str) -> tuple:
     except OSError:
         return None, "no profile"
     m = re.search(r"traffic_bytes_per_launch\s*=\s*([0-9.eE+]+)\s*,\s*kernel_source_sha\s*=\s*([0-9a-f]+)"
-                  r"\s*,\s*planner\s*=\s*(\w+)", txt)
+                  r"\s*,\s*planner\s*=\s*(\w+)(?:\s*,\s*plan_macs\s*=\s*([0-9]+))?", txt)
     if not m:
         return None, "no traffic line in the profile"
     sha = kernel_source_sha(sources)
@@ -761,6 +762,8 @@ def captured_traffic(profile: str, sources, planner: str) -> tuple:
         return None, f"kernel changed since the capture (sources {sha}, captured {m.group(2)})"
     if m.group(3) != planner:
         return None, f"captured with planner {m.group(3)}, this run plans with {planner}"
+    if m.group(4) is not None and plan_macs is not None and int(m.group(4)) != int(round(plan_macs)):
+        return None, f"plans changed since the capture ({int(round(plan_macs))} MACs per launch, captured {m.group(4)})"
     return float(m.group(1)), f"ncu capture of this workload and kernel ({os.path.relpath(profile, ROOT)})"
 
 
@@ -908,7 +911,7 @@ def run_tnc(args):
     # 64-bit-result IMAD, two issue slots; clock = max SM clock
     alu_peak = sms * 4 * 16 / 2 * pk.get("sm_max_mhz", 2070.0) * 1e6
     default_shape = args.batch == 8192 and not args.launch
-    traffic, traffic_src = captured_traffic(C2_PROFILE, C2_KERNEL_SOURCES, args.planner) if default_shape else \
+    traffic, traffic_src = captured_traffic(C2_PROFILE, C2_KERNEL_SOURCES, args.planner, macs) if default_shape else \
         (None, "captured for the default workload only")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
