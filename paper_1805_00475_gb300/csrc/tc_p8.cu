@@ -15,12 +15,15 @@
 //
 // Data path: tensors on this path hold one byte per residue (an entry is the
 // RG residues of its pass side by side: 4 bytes for RG = 4).  A pack kernel
-// turns both operands of a step (the lowering's column-major layout: row
-// index low, shared index high; all residues of the pass at once) into
-// balanced fp16 matrices, one per residue, row-major with the shared index
-// contiguous.  TMA moves tiles of rows x 64 values (128-byte lines) into
-// shared memory with the 128-byte swizzle, the canonical K-major SWIZZLE_128B
-// layout of the MMA operand descriptors.
+// turns the operands of a step that are still in entry form (the lowering's
+// column-major layout: row index low, shared index high; all residues of the
+// pass at once) into balanced fp16 planes, one per residue: in the entries'
+// own order (rows contiguous) where the GEMM reads the operand MN-major
+// (at least 64 shared values), else transposed so that the shared index is
+// contiguous (K-major).  TMA moves boxes of 128-byte lines (64 shared values
+// of a tile's rows, K-major; or 64 rows of 64 shared values, MN-major) into
+// shared memory with the 128-byte swizzle, the canonical SWIZZLE_128B layouts
+// of the MMA operand descriptors.
 // An output that feeds another dense step is written straight as that
 // step's fp16 planes (representatives of magnitude at most (p+1)/2, which
 // keep its chunk sums exact).
