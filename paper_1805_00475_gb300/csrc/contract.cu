@@ -1,5 +1,12 @@
-// C ABI, device half: single-formula contraction (one launch per step) and the
-// persistent, graph-captured batch.
+// C ABI, device half.  Contraction of one formula or of a group of formulas
+// (tnc_contract, tnc_contract_many, tnc_contract_sliced) runs tree level by
+// tree level: one level_kernel launch for the level's small steps of every
+// plan of the group, one launch each for its big, one-small-operand and
+// split-K steps, and the dense steps on the tensor-core paths (tc.cu,
+// tc_p8.cu); then the component product and the CRT.  The allocation-free
+// variant (tnc_contract_noalloc) runs the steps in order in a fixed array.
+// The persistent batch (tnc_batch_*) contracts many small plans in one
+// graph-captured launch of batch_kernel.
 #include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
