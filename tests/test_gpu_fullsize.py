@@ -51,13 +51,15 @@ def _check_consistent(out):
             assert [c % p for p in r.primes] == [int(x) for x in r.residues[e]]
 
 
-def test_c2_full_batch_sampled_against_oracle():
-    """#Cubic-Vertex-Cover on 60 vertices, seeds 0..8191, best plans, 4
-    residues below 2^30: the default benchmark's 8192 formulas in one
-    autotuned persistent launch; 64 sampled formulas plus the first and the
-    last against the oracle."""
+@pytest.mark.parametrize("planner", ["coarsen", "best"])
+def test_c2_full_batch_sampled_against_oracle(planner):
+    """#Cubic-Vertex-Cover on 60 vertices, seeds 0..8191, 4 residues below
+    2^30: the default benchmark's 8192 formulas in one autotuned persistent
+    launch, planned as the benchmark plans them (two-level plans) and by the
+    best of the paper's heuristics; 64 sampled formulas plus the first and
+    the last against the oracle."""
     forms = [I.cubic_vertex_cover(60, s) for s in range(8192)]
-    plans = tnc.plan_many(forms, heuristic="best")
+    plans = tnc.plan_many(forms, heuristic=planner)
     out = _run_batch(plans, 4)
     assert len(out) == 8192
     assert all(r.flags == 0 for r in out)  # 4 residues certify every count (bound <= 2^60)
