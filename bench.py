@@ -63,7 +63,7 @@ def parse():
                     help="c2 e2e: shares of the formulas in consecutive batches on their own streams, so "
                          "that one batch's upload overlaps the previous batch's kernel")
     ap.add_argument("--launch", default="", help="c2: fixed launch shape THREADS,SMEM_BYTES[,CTAS_PER_SM] instead of the autotuner")
-    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing", "fig4c"],
+    ap.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5", "slicing", "fig4c", "planners"],
                     help="c2: batch of cubic VC n=60 (default); c3: 4096 uneven monotone 1-in-3 "
                          "formulas, 2 residues; c4: cubic VC n=180, 8 residues, tensor-core vs CUDA-core path")
     ap.add_argument("--formulas", type=int, default=0, help="c3/c4/c5: number of formulas (0 = the config's)")
@@ -462,6 +462,41 @@ def run_fig4c(args):
             "data": "synthetic", "config": {"workload": "cubic_vertex_cover, random vs random planar cubic graphs",
                                             "seeds_per_n": seeds, "planner": "best"},
             "plan_s": time.perf_counter() - t0, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_planners(args):
+    """Planner only (exact plan costs before any contraction, Sec. 4), on the
+    host: total MACs, output entries, max rank and planning time of the
+    paper's heuristics (TNC_PLAN_BEST: tensor-greedy, tensor-METIS and
+    tensor-GN, the cheapest by (max rank, MACs)) against the two-level
+    planner (TNC_PLAN_COARSEN) on the formulas of the default workload (the
+    first 1024), of the C4 block and of the C5 evaluation set.  The C2 and C4
+    plans are capped at the ranks their runs use (32 and 30), C5's at 64."""
+    from paper_1805_00475_gb300 import instances as I
+    from paper_1805_00475_gb300 import tnc
+    sets = [("cubic_vertex_cover_n60_seeds0_1023", workload(0, 1024), 32),
+            ("c4_cubic_vertex_cover_n180_rank_le_30", [f for _, f, _ in c4_workload()], 30),
+            ("c5_one_in_three_n300_m186", [I.one_in_three(300, 186, 900000 + s) for s in range(args.formulas or 256)],
+             64)]
+    rows = []
+    for name, forms, cap in sets:
+        row = {"workload": name, "formulas": len(forms), "rank_cap": cap}
+        for h in ("best", "coarsen"):
+            t = time.perf_counter()
+            plans = tnc.plan_many(forms, heuristic=h, rank_cap=cap)
+            row[h] = {"plan_s": time.perf_counter() - t,
+                      "total_macs": sum(p.stats.total_macs for p in plans),
+                      "total_entries": sum(p.stats.total_entries for p in plans),
+                      "mean_log2_macs": statistics.mean(math.log2(p.stats.total_macs) for p in plans),
+                      "mean_max_rank": statistics.mean(p.stats.max_rank for p in plans),
+                      "max_max_rank": max(p.stats.max_rank for p in plans)}
+        row["macs_ratio_best_over_coarsen"] = row["best"]["total_macs"] / row["coarsen"]["total_macs"]
+        rows.append(row)
+    line = {"metric": "plan MACs, best heuristic / two-level planner (planner only)",
+            "value": rows[0]["macs_ratio_best_over_coarsen"], "unit": "x fewer MACs (default workload)",
+            "higher_is_better": True, "data": "synthetic", "host_threads": os.cpu_count(),
+            "config": {"workload": "default, C4 and C5 formulas", "planners": ["best", "coarsen"]}, "rows": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -965,6 +1000,8 @@ def main():
         run_c4(args)
     elif args.config == "slicing":
         run_slicing(args)
+    elif args.config == "planners":
+        run_planners(args)
     elif args.config == "fig4c":
         run_fig4c(args)
     elif args.config == "c3":
